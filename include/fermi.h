@@ -1,0 +1,185 @@
+/*
+ * fermi.h -- C ABI of the GB300 dense Chebyshev Fermi-operator solver.
+ *
+ * Computes the density matrix P = f(H) = [I + exp((H - mu I)/kT)]^{-1} of a dense real
+ * symmetric Hamiltonian as a Chebyshev expansion sum_n c_n T_n(X) evaluated with Liang's
+ * baby-step / giant-step scheme (arXiv 2306.12616, Sec. "Chebyshev expansions with
+ * O(sqrt L) number of matrix multiplications", Eq. (fermi), Eq. (ansatz)), so that the
+ * number of matrix products grows with the square root of the number of terms. The
+ * chemical potential mu is either given or fixed by tr(P) = N_e.
+ *
+ * Conventions shared by every call:
+ *  - Matrices are dense, row-major, float64, with a leading dimension ld >= n (elements).
+ *    H must be symmetric; only then is P = f(H) well defined. Pointers prefixed "d" are
+ *    device pointers on the context's device, prefixed "h" host pointers.
+ *  - The caller owns H, P and every output buffer. The context owns its workspace
+ *    (device scratch grown on demand and reused), which is freed by fo_destroy.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream). All
+ *    device work is enqueued on it; a call only blocks when it must return host values
+ *    (documented per call).
+ *  - No call throws. Every call returns an fo_status; CUDA failures map to FO_ERR_CUDA
+ *    and the message is kept in the context (fo_last_error).
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef FERMI_GB300_H
+#define FERMI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fo_ctx fo_ctx;
+
+typedef enum {
+    FO_OK = 0,
+    FO_ERR_ARG = 1,              /* invalid argument (size, pointer, parameter) */
+    FO_ERR_CUDA = 2,             /* a CUDA runtime/driver call failed */
+    FO_ERR_NOMEM = 3,            /* device workspace allocation failed */
+    FO_ERR_NONFINITE = 4,        /* H holds NaN or Inf (found by the bounds pass) */
+    FO_ERR_NO_BRACKET = 5,       /* mu bisection could not bracket tr(P) = N_e */
+    FO_ERR_NOT_CONVERGED = 6,    /* mu bisection hit its iteration cap */
+    FO_ERR_DEVICE_TIMEOUT = 7,   /* a bounded device-side wait gave up */
+    FO_ERR_UNSUPPORTED = 8       /* feature not available for these arguments */
+} fo_status;
+
+/* Arithmetic of the matrix products. FP64 runs everything in float64. The split forms
+ * keep float32 master copies of every matrix and run each product on the tensor cores
+ * as a sum of products of 16-bit planes with float32 accumulation:
+ *   BF16X3: A = a0 + a1 + a2 (bf16 planes), AB ~ sum_{i+j<=2} a_i b_j  (6 products)
+ *   FP16X2: A = a0 + a1 (fp16 planes),      AB ~ a0 b0 + a0 b1 + a1 b0 (3 products)
+ *   BF16X1: A = a0,                          AB ~ a0 b0                 (1 product)
+ * Bounds, coefficients, traces, moments and the mu search stay float64 in all modes. */
+typedef enum {
+    FO_PREC_FP64 = 0,
+    FO_PREC_BF16X3 = 1,
+    FO_PREC_FP16X2 = 2,
+    FO_PREC_BF16X1 = 3
+} fo_precision;
+
+typedef enum {
+    FO_MU_FIXED = 0,    /* use params.mu */
+    FO_MU_BISECT = 1,   /* bisection on sum_n c_n(mu) tau_n = N_e with exact moments */
+    FO_MU_LEARNED = 2   /* MLP proposal, verified on the trace; bisection as fallback */
+} fo_mu_mode;
+
+/* Flags (fo_params.flags). */
+#define FO_FLAG_TRACE_ONLY_DIAG  0x1u  /* reserved */
+#define FO_FLAG_NO_RESULT_SYNC   0x2u  /* fo_density_matrix: never block, leave fo_result untouched */
+
+typedef struct {
+    int32_t n_terms;          /* number of coefficients c_0..c_{n_terms-1}, >= 1 */
+    int32_t k;                /* baby steps; 0 = ceil(sqrt(n_terms)); m = ceil(n_terms/k) */
+    double  kT;               /* electronic temperature, same energy unit as H, > 0 */
+    double  mu;               /* chemical potential for FO_MU_FIXED */
+    int32_t precision;        /* fo_precision */
+    int32_t mu_mode;          /* fo_mu_mode */
+    int32_t use_given_bounds; /* 1: use emin/emax below instead of Gershgorin bounds */
+    int32_t n_quad;           /* Chebyshev-Gauss nodes; 0 = max(2048, 4 n_terms) */
+    double  emin, emax;       /* spectral bounds when use_given_bounds (emax > emin) */
+    int32_t max_bisect;       /* bisection cap; 0 = 200 */
+    uint32_t flags;           /* FO_FLAG_* */
+} fo_params;
+
+typedef struct {
+    double  mu;               /* chemical potential used for P */
+    double  trace;            /* tr(P) of the returned P, float64 sum of its diagonal */
+    double  trace_poly;       /* sum_n c_n(mu) tau_n from the moments (FO_MU_BISECT), else 0 */
+    double  frob2;            /* ||P||_F^2 */
+    double  emin, emax;       /* spectral bounds used */
+    int32_t k, m;             /* baby / giant steps */
+    int32_t n_gemm;           /* matrix products issued */
+    int32_t bisect_iters;     /* bisection halvings (0 if not bisected) */
+    int32_t learned_accepted; /* 1 if the learned mu was kept */
+    int32_t status;           /* fo_status of the device-side stages */
+} fo_result;
+
+/* Create a context on CUDA device `device`. *out is set on success. */
+fo_status fo_create(fo_ctx **out, int device);
+/* Free the context and its workspace (synchronises the device). NULL is accepted. */
+fo_status fo_destroy(fo_ctx *ctx);
+/* Message of the last failure in this context ("" if none). Owned by the context. */
+const char *fo_last_error(const fo_ctx *ctx);
+/* Static name of a status code. */
+const char *fo_status_string(fo_status s);
+/* Library version string, e.g. "fermi-gb300 0.1". */
+const char *fo_version(void);
+
+/*
+ * Spectral bounds (Sec. "Chebyshev expansions": e_a, e_b enclose the spectrum).
+ * Gershgorin discs: emin = min_i (h_ii - sum_{j!=i} |h_ij|), emax = max_i (h_ii + sum ...),
+ * reduced in float64 with warp shuffles. A degenerate interval (width <= 1e-12 max(1,|e|))
+ * becomes centre -+ 1. Writes d_bounds[0] = emin, d_bounds[1] = emax (device, 2 doubles)
+ * and d_bounds[2] = 0.0 if H is finite, 1.0 otherwise (3 doubles). Asynchronous; n >= 1, ld >= n.
+ */
+fo_status fo_spectral_bounds(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld,
+                             double *d_bounds, void *stream);
+
+/*
+ * Chebyshev coefficients of the Fermi-Dirac function on [emin, emax] (Sec. "Chebyshev
+ * expansions", Eq. (fermifunc)): Chebyshev-Gauss interpolation on n_quad nodes
+ * (0 = max(2048, 4 n_terms)), c_0 = (1/M) sum_j f_j, c_n = (2/M) sum_j f_j cos(n theta_j),
+ * theta_j = pi (j + 1/2) / M. Computed in float64 on the device into d_c[0..n_terms-1].
+ * Asynchronous.
+ */
+fo_status fo_chebyshev_coeffs(fo_ctx *ctx, double kT, double mu, double emin, double emax,
+                              int32_t n_terms, int32_t n_quad, double *d_c, void *stream);
+
+/*
+ * Density matrix (Eq. (fermi) with Eq. (ansatz)): dP[n x n, ldp] = sum_n c_n(mu) T_n(X),
+ * X = (2H - (emin+emax) I)/(emax - emin). Baby steps T_1..T_k by the three-term
+ * recurrence with the update 2 A B - C fused into the product epilogue; the expansion
+ * is regrouped as sum_l T_l(T_k) R_l, R_l = sum_i g_{i,l} T_i (the bracket d_i^T a_l of
+ * Eq. (formula for d)), and the giant steps run as a Clenshaw recurrence in T_k whose
+ * product epilogue accumulates R_l. mu per params.mu_mode; n_e is the electron count
+ * (tr P = n_e, spinless occupations in [0,1]). If res != NULL the call synchronises the
+ * stream and fills *res; with res == NULL (or FO_FLAG_NO_RESULT_SYNC) it never blocks.
+ * Returns the host-side status; device-side failures (non-finite H, no bracket) are
+ * reported through res->status and the return value when res != NULL.
+ */
+fo_status fo_density_matrix(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld,
+                            double n_e, const fo_params *params, double *dP, int64_t ldp,
+                            fo_result *res, void *stream);
+
+/*
+ * Same as fo_density_matrix with host buffers: copies hH to the device, runs, and
+ * copies P back to hP (hP[n x n, ldp]). Pinned host memory makes the copies
+ * asynchronous; the call always synchronises the stream before returning.
+ */
+fo_status fo_density_matrix_host(fo_ctx *ctx, const double *hH, int64_t n, int64_t ld,
+                                 double n_e, const fo_params *params, double *hP,
+                                 int64_t ldp, fo_result *res, void *stream);
+
+/*
+ * Chebyshev moments tau_j = tr T_j(X), j < n_moments, of the scaled Hamiltonian on the
+ * given bounds (d_bounds as written by fo_spectral_bounds), float64 into d_tau. Used as
+ * features of the learned mu and exposed for spectral analysis. Moments up to 2k come
+ * from baby-step traces and Frobenius products (tau_{a+b} = 2<T_a,T_b> - tau_{|a-b|},
+ * Eq. (identity)); precision selects the arithmetic of the products. Asynchronous.
+ */
+fo_status fo_moments(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld,
+                     const double *d_bounds, int32_t n_moments, int32_t precision,
+                     double *d_tau, void *stream);
+
+/*
+ * One recurrence product on float32 matrices (the kernel behind every step of the
+ * expansion): dOut = alpha * A B^T + beta * C + D + shift * I_n, with A, B, C, D, dOut
+ * n x n row-major float32 with leading dimension ld (C, D may be NULL), run on the tensor
+ * cores in the split form `precision` (FO_PREC_BF16X3, FP16X2 or BF16X1; FP64 is
+ * rejected). With symmetric != 0 only the entries on or above the diagonal are computed
+ * and mirrored (the form the solver uses: the result is exactly symmetric, valid when the
+ * true result is symmetric, e.g. A and B commuting symmetric matrices; then A B^T = A B);
+ * with symmetric == 0 the full A B^T is computed. FP16X2 needs |entries| <= 1 in A and B.
+ * Asynchronous.
+ */
+fo_status fo_recurrence_product(fo_ctx *ctx, int32_t precision, int32_t symmetric, int64_t n,
+                                int64_t ld, const float *dA, const float *dB, const float *dC,
+                                const float *dD, float alpha, float beta, float shift,
+                                float *dOut, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FERMI_GB300_H */

@@ -1,0 +1,276 @@
+"""Python binding of the GB300 dense Chebyshev Fermi-operator solver (include/fermi.h).
+
+The functions named ``fo_*`` mirror the C ABI one to one: they only marshal arguments
+(integers for device pointers and streams, ctypes structures for parameters) and call the
+shared library built from csrc/. Every step of the method runs in the library's CUDA
+kernels. There is no fallback: if the library has not been built, or no CUDA device is
+present, the calls raise.
+
+``Solver`` is a convenience wrapper over the same calls for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+__all__ = [
+    "FO_OK", "FO_PREC_FP64", "FO_PREC_BF16X3", "FO_PREC_FP16X2", "FO_PREC_BF16X1",
+    "FO_MU_FIXED", "FO_MU_BISECT", "FO_MU_LEARNED", "FO_FLAG_NO_RESULT_SYNC",
+    "FoParams", "FoResult", "FermiError", "lib", "library_path", "EXPORTED_SYMBOLS",
+    "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
+    "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
+    "fo_moments", "fo_recurrence_product", "Solver", "PRECISIONS", "MU_MODES",
+]
+
+FO_OK = 0
+FO_ERR_ARG, FO_ERR_CUDA, FO_ERR_NOMEM, FO_ERR_NONFINITE = 1, 2, 3, 4
+FO_ERR_NO_BRACKET, FO_ERR_NOT_CONVERGED, FO_ERR_DEVICE_TIMEOUT, FO_ERR_UNSUPPORTED = 5, 6, 7, 8
+FO_PREC_FP64, FO_PREC_BF16X3, FO_PREC_FP16X2, FO_PREC_BF16X1 = 0, 1, 2, 3
+FO_MU_FIXED, FO_MU_BISECT, FO_MU_LEARNED = 0, 1, 2
+FO_FLAG_NO_RESULT_SYNC = 0x2
+
+PRECISIONS = {"fp64": FO_PREC_FP64, "bf16x3": FO_PREC_BF16X3, "fp16x2": FO_PREC_FP16X2,
+              "bf16x1": FO_PREC_BF16X1}
+MU_MODES = {"fixed": FO_MU_FIXED, "bisect": FO_MU_BISECT, "learned": FO_MU_LEARNED}
+
+# Every symbol the header declares (checked by the CPU test suite against the .so).
+EXPORTED_SYMBOLS = (
+    "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
+    "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
+    "fo_moments", "fo_recurrence_product",
+)
+
+
+class FoParams(ctypes.Structure):
+    _fields_ = [
+        ("n_terms", ctypes.c_int32), ("k", ctypes.c_int32), ("kT", ctypes.c_double),
+        ("mu", ctypes.c_double), ("precision", ctypes.c_int32), ("mu_mode", ctypes.c_int32),
+        ("use_given_bounds", ctypes.c_int32), ("n_quad", ctypes.c_int32),
+        ("emin", ctypes.c_double), ("emax", ctypes.c_double), ("max_bisect", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class FoResult(ctypes.Structure):
+    _fields_ = [
+        ("mu", ctypes.c_double), ("trace", ctypes.c_double), ("trace_poly", ctypes.c_double),
+        ("frob2", ctypes.c_double), ("emin", ctypes.c_double), ("emax", ctypes.c_double),
+        ("k", ctypes.c_int32), ("m", ctypes.c_int32), ("n_gemm", ctypes.c_int32),
+        ("bisect_iters", ctypes.c_int32), ("learned_accepted", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class FermiError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libfermi_gb300.so")
+
+
+_LIB = None
+_c_ptr, _c_i64, _c_i32, _c_d, _c_f = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_double, ctypes.c_float)
+
+
+def lib() -> ctypes.CDLL:
+    """Load the shared library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run paper_2306_12616_gb300/build.py)")
+        L = ctypes.CDLL(path)
+        sig = {
+            "fo_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+            "fo_destroy": (ctypes.c_int, [_c_ptr]),
+            "fo_last_error": (ctypes.c_char_p, [_c_ptr]),
+            "fo_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "fo_version": (ctypes.c_char_p, []),
+            "fo_spectral_bounds": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_ptr, _c_ptr]),
+            "fo_chebyshev_coeffs": (ctypes.c_int, [_c_ptr, _c_d, _c_d, _c_d, _c_d, _c_i32, _c_i32,
+                                                   _c_ptr, _c_ptr]),
+            "fo_density_matrix": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_d,
+                                                 ctypes.POINTER(FoParams), _c_ptr, _c_i64,
+                                                 ctypes.POINTER(FoResult), _c_ptr]),
+            "fo_density_matrix_host": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_d,
+                                                      ctypes.POINTER(FoParams), _c_ptr, _c_i64,
+                                                      ctypes.POINTER(FoResult), _c_ptr]),
+            "fo_moments": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_ptr, _c_i32, _c_i32,
+                                          _c_ptr, _c_ptr]),
+            "fo_recurrence_product": (ctypes.c_int, [_c_ptr, _c_i32, _c_i32, _c_i64, _c_i64, _c_ptr, _c_ptr,
+                                                     _c_ptr, _c_ptr, _c_f, _c_f, _c_f, _c_ptr,
+                                                     _c_ptr]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+# ----------------------------------------------------------------- C ABI, one to one
+
+def fo_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    st = lib().fo_create(ctypes.byref(h), device)
+    if st != FO_OK:
+        raise FermiError(st, f"fo_create failed: {fo_status_string(st)}")
+    return h.value
+
+
+def fo_destroy(ctx: int) -> int:
+    return lib().fo_destroy(ctx)
+
+
+def fo_last_error(ctx: int) -> str:
+    return lib().fo_last_error(ctx).decode()
+
+
+def fo_status_string(status: int) -> str:
+    return lib().fo_status_string(status).decode()
+
+
+def fo_version() -> str:
+    return lib().fo_version().decode()
+
+
+def fo_spectral_bounds(ctx, d_h, n, ld, d_bounds, stream=0) -> int:
+    return lib().fo_spectral_bounds(ctx, d_h, n, ld, d_bounds, stream)
+
+
+def fo_chebyshev_coeffs(ctx, kT, mu, emin, emax, n_terms, n_quad, d_c, stream=0) -> int:
+    return lib().fo_chebyshev_coeffs(ctx, kT, mu, emin, emax, n_terms, n_quad, d_c, stream)
+
+
+def fo_density_matrix(ctx, d_h, n, ld, n_e, params: FoParams, d_p, ldp, result: FoResult | None,
+                      stream=0) -> int:
+    return lib().fo_density_matrix(ctx, d_h, n, ld, n_e, ctypes.byref(params), d_p, ldp,
+                                   ctypes.byref(result) if result is not None else None, stream)
+
+
+def fo_density_matrix_host(ctx, h_h, n, ld, n_e, params: FoParams, h_p, ldp,
+                           result: FoResult | None, stream=0) -> int:
+    return lib().fo_density_matrix_host(ctx, h_h, n, ld, n_e, ctypes.byref(params), h_p, ldp,
+                                        ctypes.byref(result) if result is not None else None,
+                                        stream)
+
+
+def fo_moments(ctx, d_h, n, ld, d_bounds, n_moments, precision, d_tau, stream=0) -> int:
+    return lib().fo_moments(ctx, d_h, n, ld, d_bounds, n_moments, precision, d_tau, stream)
+
+
+def fo_recurrence_product(ctx, precision, symmetric, n, ld, d_a, d_b, d_c, d_d, alpha, beta,
+                          shift, d_out, stream=0) -> int:
+    return lib().fo_recurrence_product(ctx, precision, symmetric, n, ld, d_a, d_b, d_c, d_d, alpha,
+                                       beta, shift, d_out, stream)
+
+
+# ------------------------------------------------------------ torch convenience layer
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+@dataclass
+class Solver:
+    """Owns one library context on a CUDA device; methods take torch tensors."""
+    device: int = 0
+
+    def __post_init__(self):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.ctx = fo_create(self.device)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            fo_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != FO_OK:
+            raise FermiError(st, fo_last_error(self.ctx) or fo_status_string(st))
+
+    @staticmethod
+    def params(n_terms: int, kT: float, *, mu: float = 0.0, precision: str | int = "fp64",
+               mu_mode: str | int = "bisect", k: int = 0, bounds=None, n_quad: int = 0,
+               max_bisect: int = 0, flags: int = 0) -> FoParams:
+        p = FoParams()
+        p.n_terms, p.k, p.kT, p.mu = n_terms, k, kT, mu
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        p.mu_mode = MU_MODES[mu_mode] if isinstance(mu_mode, str) else mu_mode
+        if bounds is not None:
+            p.use_given_bounds, p.emin, p.emax = 1, float(bounds[0]), float(bounds[1])
+        p.n_quad, p.max_bisect, p.flags = n_quad, max_bisect, flags
+        return p
+
+    def spectral_bounds(self, h, stream=None):
+        import torch
+        out = torch.empty(3, dtype=torch.float64, device=h.device)
+        self._check(fo_spectral_bounds(self.ctx, h.data_ptr(), h.shape[0], h.stride(0),
+                                       out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    def chebyshev_coeffs(self, kT, mu, emin, emax, n_terms, n_quad=0, stream=None):
+        import torch
+        out = torch.empty(n_terms, dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(fo_chebyshev_coeffs(self.ctx, kT, mu, emin, emax, n_terms, n_quad,
+                                        out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    def density_matrix(self, h, n_e: float, params: FoParams, out=None, stream=None,
+                       sync: bool = True):
+        import torch
+        assert h.dtype == torch.float64 and h.is_cuda and h.stride(1) == 1
+        n = h.shape[0]
+        p = out if out is not None else torch.empty((n, n), dtype=torch.float64, device=h.device)
+        res = FoResult() if sync else None
+        self._check(fo_density_matrix(self.ctx, h.data_ptr(), n, h.stride(0), float(n_e), params,
+                                      p.data_ptr(), p.stride(0), res, _stream_handle(stream)))
+        return p, (res.as_dict() if res is not None else None)
+
+    def density_matrix_host(self, h, n_e: float, params: FoParams, out, stream=None):
+        """h, out: CPU float64 tensors (pinned for asynchronous copies)."""
+        res = FoResult()
+        n = h.shape[0]
+        self._check(fo_density_matrix_host(self.ctx, h.data_ptr(), n, h.stride(0), float(n_e),
+                                           params, out.data_ptr(), out.stride(0), res,
+                                           _stream_handle(stream)))
+        return res.as_dict()
+
+    def moments(self, h, bounds, n_moments: int, precision="fp64", stream=None):
+        import torch
+        tau = torch.empty(n_moments, dtype=torch.float64, device=h.device)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        self._check(fo_moments(self.ctx, h.data_ptr(), h.shape[0], h.stride(0), bounds.data_ptr(),
+                               n_moments, prec, tau.data_ptr(), _stream_handle(stream)))
+        return tau
+
+    def recurrence_product(self, a, b, c=None, d=None, alpha=1.0, beta=0.0, shift=0.0,
+                           precision="bf16x3", symmetric=False, out=None, stream=None):
+        import torch
+        n = a.shape[0]
+        o = out if out is not None else torch.empty_like(a)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        self._check(fo_recurrence_product(
+            self.ctx, prec, 1 if symmetric else 0, n, a.stride(0), a.data_ptr(), b.data_ptr(),
+            c.data_ptr() if c is not None else None, d.data_ptr() if d is not None else None,
+            alpha, beta, shift, o.data_ptr(), _stream_handle(stream)))
+        return o

@@ -1,0 +1,377 @@
+// Coefficient pipeline of the expansion, all float64 on the device:
+//   cosine table -> DOS weights from the moments -> bisection for mu -> Fermi values at
+//   the Chebyshev-Gauss nodes -> coefficients c_n -> giant-step coefficients g_{i,l} ->
+//   contraction R_l = sum_i g_{i,l} T_i.
+//
+// Chebyshev-Gauss nodes: theta_j = pi (2j+1) / (2M), x_j = cos theta_j. Every cosine the
+// pipeline needs is cos(n theta_j) = cos(pi r / (2M)) with r = n (2j+1) mod 4M, so one
+// table ct[r] = cospi(r / (2M)), r < 4M, serves the nodes, the DCT and the DOS weights.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.cuh"
+
+namespace fo {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fermi-Dirac function f(e) = 1 / (1 + exp((e - mu)/kT)) (Eq. fermifunc) written as
+// (1 - tanh((e - mu)/(2 kT)))/2, which never overflows.
+__device__ __forceinline__ double fermi(double e, double mu, double inv2kT) {
+    return 0.5 - 0.5 * tanh((e - mu) * inv2kT);
+}
+
+__global__ void k_cos_table(int M, double* ct) {
+    const int64_t total = 4LL * M;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total;
+         r += (int64_t)gridDim.x * blockDim.x)
+        ct[r] = cospi((double)r / (2.0 * (double)M));
+}
+
+// w_j = (1/M) (tau_0 + 2 sum_{n=1}^{n_terms-1} tau_n cos(n theta_j)), so that
+// sum_n c_n(mu) tau_n = sum_j f(e_j; mu) w_j for the interpolation coefficients c_n.
+__global__ void k_dos_weights(const double* __restrict__ tau, int n_terms, int M,
+                              const double* __restrict__ ct, double* __restrict__ w) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int64_t q = 2LL * j + 1, fourM = 4LL * M;
+    int64_t r = 0;
+    double s = 0.0;
+    for (int n = 1; n < n_terms; ++n) {
+        r += q;
+        if (r >= fourM) r -= fourM;
+        s = fma(tau[n], ct[r], s);
+    }
+    w[j] = (tau[0] + 2.0 * s) / (double)M;
+}
+
+// Sum over the M nodes of w_j f(e_j; mu), fixed order, result broadcast to the block.
+__device__ double trace_at(double mu, const double* __restrict__ w, const double* __restrict__ ct,
+                           int M, double mid, double half, double inv2kT, double* sh) {
+    double s = 0.0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x)
+        s = fma(w[j], fermi(mid + half * ct[2 * j + 1], mu, inv2kT), s);
+    s = warp_sum(s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < nw; ++i) t += sh[i];
+        sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// Bisection for F(mu) = sum_n c_n(mu) tau_n - N_e = 0 on one block: bracket [emin, emax]
+// widened by 10 kT (at most 8 times per side), stop when |F| <= 1e-12 max(1, N_e) or the
+// bracket is below 1e-15 (emax - emin), at most max_iter halvings; mu = last midpoint.
+__global__ void __launch_bounds__(512) k_bisect(const double* __restrict__ w,
+                                                const double* __restrict__ ct, int M,
+                                                DevResult* res, double kT, double n_e,
+                                                int max_iter) {
+    __shared__ double sh[33];
+    const double ea = res->bounds[0], eb = res->bounds[1];
+    const double mid = 0.5 * (eb + ea), half = 0.5 * (eb - ea), inv2kT = 0.5 / kT;
+    double lo = ea, hi = eb;
+    for (int t = 0; t < 8; ++t) {
+        if (trace_at(lo, w, ct, M, mid, half, inv2kT, sh) - n_e <= 0.0) break;
+        lo -= 10.0 * kT;
+    }
+    for (int t = 0; t < 8; ++t) {
+        if (trace_at(hi, w, ct, M, mid, half, inv2kT, sh) - n_e >= 0.0) break;
+        hi += 10.0 * kT;
+    }
+    const double flo = trace_at(lo, w, ct, M, mid, half, inv2kT, sh) - n_e;
+    const double fhi = trace_at(hi, w, ct, M, mid, half, inv2kT, sh) - n_e;
+    int status = FO_OK, iters = 0;
+    double mu = 0.5 * (lo + hi);
+    if (flo > 0.0 || fhi < 0.0) {
+        status = FO_ERR_NO_BRACKET;
+    } else {
+        const double tol_f = 1e-12 * fmax(1.0, fabs(n_e));
+        const double tol_w = 1e-15 * (eb - ea);
+        bool done = false;
+        for (int it = 1; it <= max_iter; ++it) {
+            const double m = 0.5 * (lo + hi);
+            const double f = trace_at(m, w, ct, M, mid, half, inv2kT, sh) - n_e;
+            iters = it;
+            if (fabs(f) <= tol_f) { mu = m; done = true; break; }
+            if (f < 0.0) lo = m; else hi = m;
+            if (hi - lo <= tol_w) { mu = 0.5 * (lo + hi); done = true; break; }
+        }
+        if (!done) {
+            mu = 0.5 * (lo + hi);
+            status = FO_ERR_NOT_CONVERGED;
+        }
+    }
+    if (threadIdx.x == 0) {
+        res->mu = mu;
+        res->iters = iters;
+        res->mu_lo = lo;
+        res->mu_hi = hi;
+        if (res->status == FO_OK) res->status = status;
+    }
+}
+
+// f_j = f(e_j; mu) at the nodes e_j = mid + half x_j, mu read from the device record.
+__global__ void k_fermi_nodes(int M, const double* __restrict__ ct, const DevResult* res,
+                              double kT, double* __restrict__ f) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const double ea = res->bounds[0], eb = res->bounds[1];
+    f[j] = fermi(0.5 * (eb + ea) + 0.5 * (eb - ea) * ct[2 * j + 1], res->mu, 0.5 / kT);
+}
+
+// c_n = (2 - delta_{n0}) / M sum_j f_j cos(n theta_j) for n < n_terms, 0 for n_terms <= n < km.
+// One warp per n.
+__global__ void k_coeffs(const double* __restrict__ f, const double* __restrict__ ct, int M,
+                         int n_terms, int km, double* __restrict__ c) {
+    const int lane = threadIdx.x & 31;
+    const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (n >= km) return;
+    if (n >= n_terms) {
+        if (lane == 0) c[n] = 0.0;
+        return;
+    }
+    const int64_t fourM = 4LL * M;
+    double s = 0.0;
+    for (int j = lane; j < M; j += 32) {
+        const int64_t r = ((int64_t)n * (2LL * j + 1)) % fourM;
+        s = fma(f[j], ct[r], s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) c[n] = (n == 0 ? 1.0 : 2.0) * s / (double)M;
+}
+
+// Giant-step coefficients from c (zero-padded to km), g stored l-major: g[l*k + i].
+// c_{lk} = g_{0,l}; c_i = g_{i,0} + g_{k-i,1}/2; c_{lk+i} = (g_{i,l} + g_{k-i,l+1})/2 for
+// 1 <= l <= m-2; c_{(m-1)k+i} = g_{i,m-1}/2; c_i = g_{i,0} if m = 1. Solved downwards in l.
+__global__ void k_g_convert(const double* __restrict__ c, int k, int m, double* __restrict__ g) {
+    for (int l = m - 1; l >= 0; --l) {
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            const double ci = c[l * k + i];
+            double v;
+            if (i == 0 || m == 1) v = ci;
+            else if (l == m - 1) v = 2.0 * ci;
+            else if (l == 0) v = ci - 0.5 * g[1 * k + (k - i)];
+            else v = 2.0 * ci - g[(l + 1) * k + (k - i)];
+            g[l * k + i] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_poly_trace(const double* __restrict__ c, const double* __restrict__ tau,
+                             int n_terms, DevResult* res) {
+    double s = 0.0;
+    for (int n = threadIdx.x; n < n_terms; n += 32) s = fma(c[n], tau[n], s);
+    s = warp_sum(s);
+    if (threadIdx.x == 0) res->trace_poly = s;
+}
+
+// R_l = g_{0,l} I_n + sum_{i=1}^{k-1} g_{i,l} T_i for all l < m, float64. T_i is slot i-1.
+// Outputs are produced in groups of kGroup l's per pass over the T_i.
+constexpr int kGroup = 16;
+
+__global__ void __launch_bounds__(256) k_contract_f64(const double* __restrict__ gsrc, int k,
+                                                      int m, const double* __restrict__ tbase,
+                                                      int64_t tstride, double* __restrict__ rbase,
+                                                      int64_t rstride, int64_t n, int64_t np) {
+    extern __shared__ double gsh[];
+    for (int q = threadIdx.x; q < k * m; q += blockDim.x) gsh[q] = gsrc[q];
+    __syncthreads();
+    const int64_t total = np * np;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / np, col = idx - r * np;
+        const bool diag = (r == col) && (r < n);
+        for (int l0 = 0; l0 < m; l0 += kGroup) {
+            double acc[kGroup];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) acc[q] = 0.0;
+            for (int i = 1; i < k; ++i) {
+                const double t = tbase[(int64_t)(i - 1) * tstride + idx];
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q)
+                    if (l0 + q < m) acc[q] = fma(gsh[(l0 + q) * k + i], t, acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) {
+                if (l0 + q < m) {
+                    double v = acc[q];
+                    if (diag) v += gsh[(l0 + q) * k];
+                    rbase[(int64_t)(l0 + q) * rstride + idx] = v;
+                }
+            }
+        }
+    }
+}
+
+// float32 version: slots hold a float32 master at element offset 0 and 16-bit planes at
+// element offset plane_off_f (in floats) with plane stride np*np; planes are written for
+// R_{m-1} only (it is the first Clenshaw operand). Four entries per thread.
+__device__ __forceinline__ uint16_t bf16_bits_c(float v) {
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    return *reinterpret_cast<uint16_t*>(&h);
+}
+
+__global__ void __launch_bounds__(256) k_contract_f32(const double* __restrict__ gsrc, int k,
+                                                      int m, const float* __restrict__ tbase,
+                                                      int64_t tstride, float* __restrict__ rbase,
+                                                      int64_t rstride, int64_t n, int64_t np,
+                                                      int planes_last, int fp16, float pscale,
+                                                      int64_t plane_off, int* dbg) {
+    extern __shared__ float fsh[];
+    for (int q = threadIdx.x; q < k * m; q += blockDim.x) fsh[q] = (float)gsrc[q];
+    __syncthreads();
+    const int64_t total4 = np * np / 4;
+    for (int64_t i4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i4 < total4;
+         i4 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = i4 * 4;
+        const int64_t r = idx / np, col0 = idx - r * np;
+        for (int l0 = 0; l0 < m; l0 += kGroup) {
+            float4 acc[kGroup];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 1; i < k; ++i) {
+                const float* tp = tbase + (int64_t)(i - 1) * tstride + idx;
+                if (!FO_CHK(dbg, (reinterpret_cast<uintptr_t>(tp) & 15) == 0 && idx + 4 <= np * np, 301, i, idx)) continue;
+                const float4 t = *reinterpret_cast<const float4*>(tp);
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) {
+                    if (l0 + q < m) {
+                        const float gv = fsh[(l0 + q) * k + i];
+                        acc[q].x = fmaf(gv, t.x, acc[q].x);
+                        acc[q].y = fmaf(gv, t.y, acc[q].y);
+                        acc[q].z = fmaf(gv, t.z, acc[q].z);
+                        acc[q].w = fmaf(gv, t.w, acc[q].w);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) {
+                const int l = l0 + q;
+                if (l >= m) continue;
+                float v[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
+                if (r < n && r >= col0 && r < col0 + 4) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (col0 + e == r) v[e] += fsh[l * k];
+                }
+                float* dst = rbase + (int64_t)l * rstride + idx;
+                if (!FO_CHK(dbg, (reinterpret_cast<uintptr_t>(dst) & 15) == 0, 302, l, idx)) continue;
+                *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+                if (l == m - 1 && planes_last > 0) {
+                    uint16_t* p = reinterpret_cast<uint16_t*>(rbase + (int64_t)l * rstride + plane_off) + idx;
+                    const int64_t ps = np * np;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (!fp16) {
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[e]);
+                            p[e] = *reinterpret_cast<const uint16_t*>(&h0);
+                            if (planes_last > 1) {
+                                const float r1 = v[e] - __bfloat162float(h0);
+                                const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                                p[ps + e] = *reinterpret_cast<const uint16_t*>(&h1);
+                                if (planes_last > 2)
+                                    p[2 * ps + e] = bf16_bits_c(r1 - __bfloat162float(h1));
+                            }
+                        } else {
+                            const float vs = v[e] * pscale;
+                            const __half h0 = __float2half_rn(vs);
+                            p[e] = *reinterpret_cast<const uint16_t*>(&h0);
+                            if (planes_last > 1) {
+                                const __half h1 = __float2half_rn(vs - __half2float(h0));
+                                p[ps + e] = *reinterpret_cast<const uint16_t*>(&h1);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+int grid_for(int64_t total, int threads) {
+    int64_t b = (total + threads - 1) / threads;
+    if (b > 152 * 8) b = 152 * 8;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_cos_table(int M, double* ct, cudaStream_t s) {
+    k_cos_table<<<grid_for(4LL * M, 256), 256, 0, s>>>(M, ct);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dos_weights(const double* tau, int n_terms, int M, const double* ct, double* w,
+                               cudaStream_t s) {
+    k_dos_weights<<<(M + 127) / 128, 128, 0, s>>>(tau, n_terms, M, ct, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bisect(const double* w, const double* ct, int M, DevResult* res, double kT,
+                          double n_e, int max_iter, cudaStream_t s) {
+    k_bisect<<<1, 512, 0, s>>>(w, ct, M, res, kT, n_e, max_iter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fermi_nodes(int M, const double* ct, const DevResult* res, double kT,
+                               double* f, cudaStream_t s) {
+    k_fermi_nodes<<<(M + 255) / 256, 256, 0, s>>>(M, ct, res, kT, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coeffs(const double* f, const double* ct, int M, int n_terms, int km,
+                          double* c, cudaStream_t s) {
+    const int warps_per_block = 8;
+    k_coeffs<<<(km + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
+        f, ct, M, n_terms, km, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g_convert(const double* c, int k, int m, double* g, cudaStream_t s) {
+    k_g_convert<<<1, k < 1024 ? ((k + 31) / 32) * 32 : 1024, 0, s>>>(c, k, m, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poly_trace(const double* c, const double* tau, int n_terms, DevResult* res,
+                              cudaStream_t s) {
+    k_poly_trace<<<1, 32, 0, s>>>(c, tau, n_terms, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_f64(const double* g, int k, int m, const double* tbase,
+                                int64_t tstride, double* rbase, int64_t rstride, int64_t n,
+                                int64_t np, cudaStream_t s) {
+    const size_t smem = (size_t)k * m * sizeof(double);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_contract_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_contract_f64<<<grid_for(np * np, 256), 256, smem, s>>>(g, k, m, tbase, tstride, rbase,
+                                                              rstride, n, np);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_f32(const double* g, int k, int m, const float* tbase,
+                                int64_t tstride_f, float* rbase, int64_t rstride_f, int64_t n,
+                                int64_t np, int planes_last, int fp16, float pscale,
+                                int64_t plane_off_f, cudaStream_t s, int* dbg) {
+    const size_t smem = (size_t)k * m * sizeof(float);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_contract_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_contract_f32<<<grid_for(np * np / 4, 256), 256, smem, s>>>(
+        g, k, m, tbase, tstride_f, rbase, rstride_f, n, np, planes_last, fp16, pscale,
+        plane_off_f, dbg);
+    return cudaGetLastError();
+}
+
+}  // namespace fo

@@ -1,0 +1,627 @@
+// Split-precision recurrence product on the 5th-generation tensor cores (sm_103a).
+//
+//   out = alpha * sum_{(p,q) in products} A_p B_q^T + beta * C + D + shift * I_n
+//
+// A_p, B_q are the 16-bit planes of float32 working matrices (A = sum_p A_p), staged by
+// TMA (cp.async.bulk.tensor, 64-byte swizzle) into a multi-stage shared-memory ring and
+// multiplied by tcgen05.mma (kind::f16, M = N = 128, K = 16) into float32 accumulators in
+// tensor memory. The epilogue applies the recurrence update (2 T_1 T_i - T_{i-1}, or
+// 2 Y b_{l+1} - b_{l+2} + R_l for the Clenshaw giant steps) and writes the float32 master,
+// the split planes of the result (the next product's operand) or the final float64 P.
+//
+// Symmetric mode. Every matrix of the method is a polynomial in the symmetric X, so every
+// product of two of them is symmetric. Only the 128 x 128 tiles on or above the diagonal
+// are computed and each is written twice, at (r, c) and (c, r); the stored matrices are
+// then exactly symmetric, so reading B^T is exact, and half of the tensor work is saved.
+// (Reading B^T of a matrix that is only symmetric up to rounding makes the recurrence
+// unstable: in the eigenbasis of X the pair (T_ab, T_ba) is multiplied by a matrix with
+// eigenvalues +-2 sqrt(l_a l_b), which grows geometrically whenever l_a l_b < 0.)
+//
+// Accumulation. The tensor core rounds its float32 accumulator once per instruction, so a
+// long chain of MMAs into one accumulator loses accuracy linearly in K. The leading
+// product a_0 b_0 is therefore accumulated in segments of kSeg k-blocks, alternating
+// between two TMEM accumulators; the epilogue warps drain each finished segment into
+// float32 registers while the next one accumulates. The correction products (a_0 b_1,
+// a_1 b_0, ...), 2^-8 smaller, share a third accumulator for the whole K range.
+//
+// Roles (192 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs (warp 1 owns
+// the TMEM allocation), warps 2-5 drain TMEM lane quadrants (warp & 3) = tile rows. Every
+// mbarrier wait is bounded by a %globaltimer deadline: on expiry the CTA raises a device
+// error flag, drains what it has in flight (again bounded), frees its TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace fo {
+namespace {
+
+constexpr int kBM = 128;            // tile rows (UMMA M)
+constexpr int kBK = 32;             // k elements per stage: 64 bytes of 16-bit data per row
+constexpr int kRowBytes = kBK * 2;  // = swizzle span of CU_TENSOR_MAP_SWIZZLE_64B
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: a legitimate wait is microseconds
+constexpr uint64_t kDrainNs = 200000000ull;   // 0.2 s for draining after an abort
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait. Returns false when the deadline passes or another role aborted.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                          volatile int* abort_flag) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (abort_flag && *abort_flag) return false;
+            const uint64_t t = gtimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > limit_ns) return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+// TMEM -> registers, 32 lanes x 32 columns; the wait is in the same asm block so that no
+// use of the destination registers can be scheduled before the load has completed.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile with 64-byte swizzle: rows of
+// 64 bytes, 8-row core groups 512 bytes apart (stride byte offset), descriptor version 1,
+// layout type 4 = SWIZZLE_64B. The k16 slices inside the 64-byte row are addressed by
+// advancing the start address (the swizzle is a function of the absolute address, and
+// every stage buffer is 1024-byte aligned).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;        // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)4 << 61;                 // SWIZZLE_64B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: float32 accumulator, A/B bf16 (1) or fp16 (0), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int tile_n, bool fp16) {
+    return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) |
+           ((uint32_t)(tile_n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ uint16_t bits_bf16(float v) {
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    return *reinterpret_cast<uint16_t*>(&h);
+}
+
+constexpr int kBN = 128;          // tile columns (UMMA N)
+constexpr int kTmemCols = 512;    // main accumulators at columns 0 and 128, corrections at 256
+
+template <int PA, int PB, int NPROD, bool F16>
+struct TcCfg {
+    static constexpr int kStageBytes = (PA + PB) * kBM * kRowBytes;
+    static constexpr int kStagesRaw = (200 * 1024) / kStageBytes;
+    static constexpr int kStages = kStagesRaw > 8 ? 8 : (kStagesRaw < 2 ? 2 : kStagesRaw);
+    static constexpr int kSeg = NPROD >= 3 ? 2 : 8;   // k-blocks per drained segment
+    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr uint32_t kIdesc = idesc_f16(kBN, F16);
+    static_assert(kSmem <= 232448 - 64, "shared memory budget of one CTA exceeded");
+    static_assert(kStages * kStageBytes >= kBM * (kBN + 1) * 4, "result tile must fit the stage ring");
+};
+
+// (a-plane, b-plane) of each product, largest first:
+// (0,0) (0,1) (1,0) (0,2) (1,1) (2,0).
+__host__ __device__ constexpr int prod_a(int p) { return p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0); }
+__host__ __device__ constexpr int prod_b(int p) { return p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-uniform bounded wait: every lane observes the phase; the exit decision is shared.
+__device__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                               volatile int* abort_flag) {
+    const int lane = threadIdx.x & 31;
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        const bool done = mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        if ((it & 255u) == 255u) {
+            int stop = 0;
+            if (lane == 0) {
+                if (abort_flag && *abort_flag) stop = 1;
+                const uint64_t t = gtimer();
+                if (t0 == 0) t0 = t;
+                else if (t - t0 > limit_ns) stop = 1;
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void split3(float x, bool f16, float pscale, uint16_t& p0, uint16_t& p1,
+                                       uint16_t& p2) {
+    if (!f16) {
+        const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(b0);
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(b1);
+        p0 = *reinterpret_cast<const uint16_t*>(&b0);
+        p1 = *reinterpret_cast<const uint16_t*>(&b1);
+        p2 = bits_bf16(r2);
+    } else {
+        const float xs = x * pscale;
+        const __half f0 = __float2half_rn(xs);
+        const __half f1 = __float2half_rn(xs - __half2float(f0));
+        p0 = *reinterpret_cast<const uint16_t*>(&f0);
+        p1 = *reinterpret_cast<const uint16_t*>(&f1);
+        p2 = 0;
+    }
+}
+
+template <int PA, int PB, int NPROD, bool F16, bool SYM>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const Epilogue ep, int np, int* err_flag) {
+    using Cfg = TcCfg<PA, PB, NPROD, F16>;
+    constexpr int S = Cfg::kStages, G = Cfg::kSeg;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * Cfg::kStageBytes);
+    uint64_t* empty = full + S;
+    uint64_t* seg_full = empty + S;
+    uint64_t* seg_empty = seg_full + 2;
+    uint64_t* acc_full = seg_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = np / kBM;
+    int I, J;
+    if (SYM) {
+        int b = blockIdx.x;
+        I = 0;
+        while (b >= t - I) { b -= t - I; ++I; }
+        J = I + b;
+    } else {
+        I = blockIdx.x / t;
+        J = blockIdx.x - I * t;
+    }
+    const int m0 = I * kBM, n0 = J * kBN;
+    const int nk = np / kBK;
+    const int nseg = (nk + G - 1) / G;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&seg_full[b], 1);
+            mbar_init(&seg_empty[b], 128);
+        }
+        mbar_init(acc_full, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    volatile int* vabort = &abort_flag;
+
+    auto stage_a = [&](int s, int p) { return smem + s * Cfg::kStageBytes + p * kBM * kRowBytes; };
+    auto stage_b = [&](int s, int p) {
+        return smem + s * Cfg::kStageBytes + (PA + p) * kBM * kRowBytes;
+    };
+
+    float sum[kBN];  // accumulated tile row of an epilogue thread
+#pragma unroll
+    for (int j = 0; j < kBN; ++j) sum[j] = 0.0f;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % S;
+                if (kb >= S) {
+                    if (!mbar_wait(&empty[s], ((kb / S) - 1) & 1, kWaitNs, vabort)) {
+                        atomicExch(&abort_flag, 1);
+                        atomicExch(err_flag, 1);
+                        break;
+                    }
+                }
+                if (!FO_CHK(ep.dbg, kb * kBK < np && m0 + kBM <= np && n0 + kBN <= np, 108, m0, n0)) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                mbar_expect_tx(&full[s], Cfg::kStageBytes);
+#pragma unroll
+                for (int p = 0; p < PA; ++p) tma_load_3d(stage_a(s, p), &mapA, &full[s], kb * kBK, m0, p);
+#pragma unroll
+                for (int p = 0; p < PB; ++p) tma_load_3d(stage_b(s, p), &mapB, &full[s], kb * kBK, n0, p);
+                issued = kb + 1;
+            }
+            if (*vabort) {
+                for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
+                    mbar_wait(&full[kb % S], (kb / S) & 1, kDrainNs, nullptr);
+            } else {
+                // Producer tail: wait until the MMA warp has released every stage, i.e. until
+                // the tcgen05.commit arrivals of the last S k-blocks have landed. Otherwise the
+                // CTA could exit with mbarrier arrivals in flight, which would then land in the
+                // shared memory of the next CTA scheduled on this SM.
+                for (int kb = (nk > S ? nk - S : 0); kb < nk; ++kb)
+                    if (!mbar_wait(&empty[kb % S], (kb / S) & 1, kWaitNs, vabort)) {
+                        atomicExch(err_flag, 1);
+                        break;
+                    }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % S, seg = kb / G, buf = seg & 1;
+                const bool seg_first = (kb % G) == 0;
+                if (seg_first && seg >= 2) {
+                    if (!mbar_wait(&seg_empty[buf], ((seg >> 1) - 1) & 1, kWaitNs, vabort)) {
+                        atomicExch(&abort_flag, 1);
+                        atomicExch(err_flag, 1);
+                        break;
+                    }
+                }
+                if (!mbar_wait(&full[s], (kb / S) & 1, kWaitNs, vabort)) {
+                    atomicExch(&abort_flag, 1);
+                    atomicExch(err_flag, 1);
+                    break;
+                }
+                fence_after();
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    umma_f16(tmem + buf * kBN, sdesc_sw64(smem_u32(stage_a(s, 0)) + kk * 32),
+                             sdesc_sw64(smem_u32(stage_b(s, 0)) + kk * 32), Cfg::kIdesc,
+                             !(seg_first && kk == 0));
+#pragma unroll
+                    for (int pr = 1; pr < NPROD; ++pr) {
+                        umma_f16(tmem + 2 * kBN,
+                                 sdesc_sw64(smem_u32(stage_a(s, prod_a(pr))) + kk * 32),
+                                 sdesc_sw64(smem_u32(stage_b(s, prod_b(pr))) + kk * 32), Cfg::kIdesc,
+                                 !(kb == 0 && kk == 0 && pr == 1));
+                    }
+                }
+                umma_commit(&empty[s]);
+                if ((kb % G) == G - 1 || kb == nk - 1) umma_commit(&seg_full[buf]);
+            }
+            // arrives once every issued MMA has completed (also after an abort)
+            umma_commit(acc_full);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps, main loop: drain finished segments into registers
+        const int q = warp & 3;
+        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
+        for (int seg = 0; seg < nseg && ok; ++seg) {
+            const int buf = seg & 1;
+            if (!mbar_wait_warp(&seg_full[buf], (seg >> 1) & 1, kWaitNs, vabort)) {
+                ok = false;
+                break;
+            }
+            __syncwarp();
+            fence_after();
+#pragma unroll
+            for (int cb = 0; cb < kBN / 32; ++cb) {
+                uint32_t r[32];
+                tmem_ld32(t_row + buf * kBN + cb * 32, r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
+            }
+            fence_before();
+            mbar_arrive(&seg_empty[buf]);
+        }
+        // every MMA has completed (corrections final) before TMEM is read for the last time
+        if (!mbar_wait_warp(acc_full, 0, kWaitNs, nullptr)) ok = false;
+        __syncwarp();
+        fence_after();
+        if (ok && NPROD > 1) {
+#pragma unroll
+            for (int cb = 0; cb < kBN / 32; ++cb) {
+                uint32_t r[32];
+                tmem_ld32(t_row + 2 * kBN + cb * 32, r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
+            }
+        }
+        if (!ok && lane == 0) {
+            atomicExch(&abort_flag, 1);
+            atomicExch(err_flag, 1);
+        }
+    }
+    // ---------------- TMEM is no longer needed: free it before any global store
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+    if (warp < 2 || *vabort) return;  // uniform across the four epilogue warps
+
+    // ---------------- epilogue warps: update and store through shared memory. The stage ring
+    // is idle (every TMA load was consumed, every MMA completed), so it holds the 128 x 128
+    // float32 result tile; all global traffic below is coalesced across the warp.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    constexpr int LD = kBN + 1;
+    float* tile = reinterpret_cast<float*>(smem);
+    const int q = warp & 3;
+    const int rl = q * 32 + lane;
+#pragma unroll
+    for (int c = 0; c < kBN; ++c) tile[rl * LD + c] = ep.alpha * sum[c];
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+
+    const bool diag = SYM && (I == J);
+    const int64_t ld = ep.ld;
+    // store of the element pair (grow, gcol), (grow, gcol + 1); gcol even
+    auto store_pair = [&](int64_t grow, int64_t gcol, float v0, float v1) {
+        if (ep.out64) {
+            if (grow < ep.n_real) {
+                double* dst = ep.out64 + grow * ep.ldo + gcol;
+                if (gcol < ep.n_real) dst[0] = (double)v0;
+                if (gcol + 1 < ep.n_real) dst[1] = (double)v1;
+            }
+            return;
+        }
+        const int64_t o = grow * ld + gcol;
+        if (!FO_CHK(ep.dbg, o >= 0 && o + 2 <= ld * ld, 111, grow, gcol)) return;
+        if (ep.out.x) *reinterpret_cast<float2*>(ep.out.x + o) = make_float2(v0, v1);
+        if (ep.planes > 0) {
+            uint16_t a0, a1, a2, b0, b1, b2;
+            split3(v0, F16, ep.plane_scale, a0, a1, a2);
+            split3(v1, F16, ep.plane_scale, b0, b1, b2);
+            uint16_t* pl = ep.out.planes + o;
+            *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0 << 16);
+            if (ep.planes > 1)
+                *reinterpret_cast<uint32_t*>(pl + ep.out.plane_stride) = (uint32_t)a1 | ((uint32_t)b1 << 16);
+            if (ep.planes > 2)
+                *reinterpret_cast<uint32_t*>(pl + 2 * ep.out.plane_stride) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+        }
+    };
+
+    // row pass: this warp's 32 tile rows, lanes on column pairs; applies beta C + D + shift
+    const int r0 = q * 32;
+    for (int rr = 0; rr < 32; ++rr) {
+        const int r = r0 + rr;
+        const int64_t grow = (int64_t)m0 + r;
+#pragma unroll
+        for (int h = 0; h < kBN / 64; ++h) {
+            const int c = h * 64 + 2 * lane;
+            const int64_t gcol = (int64_t)n0 + c;
+            const int64_t o = grow * ld + gcol;
+            float v0 = tile[r * LD + c], v1 = tile[r * LD + c + 1];
+            if (ep.C) {
+                const float2 cc = *reinterpret_cast<const float2*>(ep.C + o);
+                v0 = fmaf(ep.beta, cc.x, v0);
+                v1 = fmaf(ep.beta, cc.y, v1);
+            }
+            if (ep.D) {
+                const float2 dd = *reinterpret_cast<const float2*>(ep.D + o);
+                v0 += dd.x;
+                v1 += dd.y;
+            }
+            if (grow < ep.n_real) {
+                if (gcol == grow) v0 += ep.shift;
+                if (gcol + 1 == grow) v1 += ep.shift;
+            }
+            tile[r * LD + c] = v0;
+            tile[r * LD + c + 1] = v1;
+            if (!diag) store_pair(grow, gcol, v0, v1);
+        }
+    }
+    if (!SYM) return;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (diag) {
+        // diagonal tile: the lower triangle takes the values of the upper one
+        for (int rr = 0; rr < 32; ++rr) {
+            const int r = r0 + rr;
+#pragma unroll
+            for (int h = 0; h < kBN / 64; ++h) {
+                const int c = h * 64 + 2 * lane;
+                if (c < r) tile[r * LD + c] = tile[c * LD + r];
+                if (c + 1 < r) tile[r * LD + c + 1] = tile[(c + 1) * LD + r];
+            }
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        for (int rr = 0; rr < 32; ++rr) {
+            const int r = r0 + rr;
+#pragma unroll
+            for (int h = 0; h < kBN / 64; ++h) {
+                const int c = h * 64 + 2 * lane;
+                store_pair((int64_t)m0 + r, (int64_t)n0 + c, tile[r * LD + c], tile[r * LD + c + 1]);
+            }
+        }
+    } else {
+        // mirror of an off-diagonal tile: output row n0 + c holds tile column c
+        for (int cc = 0; cc < 32; ++cc) {
+            const int c = r0 + cc;
+#pragma unroll
+            for (int h = 0; h < kBN / 64; ++h) {
+                const int r = h * 64 + 2 * lane;
+                store_pair((int64_t)n0 + c, (int64_t)m0 + r, tile[r * LD + c], tile[(r + 1) * LD + c]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeFn get_encode(std::string* err) {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    if (!fn && err) *err = "cuTensorMapEncodeTiled entry point not available";
+    return fn;
+}
+
+// 3-D tensor map over a slot's planes: (column k, row, plane), 16-bit elements, 32 x 128 box.
+bool make_map(CUtensorMap* map, const uint16_t* planes, int64_t np, int64_t plane_stride,
+              int nplanes, bool fp16, std::string* err) {
+    EncodeFn enc = get_encode(err);
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)np, (cuuint64_t)np, (cuuint64_t)nplanes};
+    cuuint64_t strides[2] = {(cuuint64_t)np * 2, (cuuint64_t)plane_stride * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)kBM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                     const_cast<uint16_t*>(planes), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        if (err) *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
+template <int PA, int PB, int NPROD, bool F16, bool SYM>
+cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Epilogue& ep, int64_t np,
+                      int* err_flag, cudaStream_t s) {
+    using Cfg = TcCfg<PA, PB, NPROD, F16>;
+    auto kern = k_tc_gemm<PA, PB, NPROD, F16, SYM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t t = np / kBM;
+    const int64_t tiles = SYM ? t * (t + 1) / 2 : t * t;
+    kern<<<(unsigned)tiles, 192, Cfg::kSmem, s>>>(ma, mb, ep, (int)np, err_flag);
+    return cudaGetLastError();
+}
+
+template <int PA, int PB, int NPROD, bool F16>
+cudaError_t dispatch_sym(int sym, const CUtensorMap& ma, const CUtensorMap& mb, const Epilogue& ep,
+                         int64_t np, int* err_flag, cudaStream_t s) {
+    return sym ? launch_tc<PA, PB, NPROD, F16, true>(ma, mb, ep, np, err_flag, s)
+               : launch_tc<PA, PB, NPROD, F16, false>(ma, mb, ep, np, err_flag, s);
+}
+
+}  // namespace
+
+int tc_planes(int prec) {
+    switch (prec) {
+        case FO_PREC_BF16X3: return 3;
+        case FO_PREC_FP16X2: return 2;
+        case FO_PREC_BF16X1: return 1;
+        default: return 0;
+    }
+}
+
+int64_t tc_tiles(int64_t np, int sym) {
+    const int64_t t = np / kBM;
+    return sym ? t * (t + 1) / 2 : t * t;
+}
+
+cudaError_t tc_gemm(int prec, int64_t np, const MatF32& A, const MatF32& B, const Epilogue& ep,
+                    int sym, int* flag, cudaStream_t s, std::string* err) {
+    const int planes = tc_planes(prec);
+    if (planes == 0 || np % kBM != 0 || np % kBN != 0) {
+        if (err) *err = "tc_gemm: unsupported precision or size";
+        return cudaErrorInvalidValue;
+    }
+    if (!flag) return cudaErrorInvalidValue;
+    const bool f16 = prec == FO_PREC_FP16X2;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A.planes, np, A.plane_stride, planes, f16, err)) return cudaErrorInvalidValue;
+    if (!make_map(&mb, B.planes, np, B.plane_stride, planes, f16, err)) return cudaErrorInvalidValue;
+    switch (prec) {
+        case FO_PREC_BF16X3: return dispatch_sym<3, 3, 6, false>(sym, ma, mb, ep, np, flag, s);
+        case FO_PREC_FP16X2: return dispatch_sym<2, 2, 3, true>(sym, ma, mb, ep, np, flag, s);
+        case FO_PREC_BF16X1: return dispatch_sym<1, 1, 1, false>(sym, ma, mb, ep, np, flag, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fo

@@ -19,3 +19,32 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 def load_golden(name):
     import numpy as np
     return np.loadtxt(os.path.join(GOLDEN, name), comments="#", ndmin=2)
+
+
+def header_symbols():
+    """Function names declared in include/fermi.h."""
+    import re
+    path = os.path.join(ROOT, "include", "fermi.h")
+    text = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(fo_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="session")
+def built_library():
+    """Path of the shared library, building it in-tree if it is missing."""
+    from paper_2306_12616_gb300 import build as B
+    path = B.lib_path()
+    if not os.path.exists(path):
+        B.build()
+    return path
+
+
+@pytest.fixture(scope="session")
+def solver(built_library):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_12616_gb300 import Solver
+    s = Solver(0)
+    yield s
+    s.close()
