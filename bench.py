@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Density matrices per second of the GB300 Chebyshev Fermi-operator solver.
+
+One step = one density matrix for each tight-binding Hamiltonian N in {1000, 2000, 5000}
+(4 orbitals per atom, 0.1 atoms / A^3, 400 Chebyshev terms, kT = 0.1 eV, N_e = N/2, mu by
+float64 bisection on exact moments), with the matrix products in BF16x3 split precision on
+the tensor cores. Inputs are resident in HBM; the L2 is flushed (256 MiB write) before every
+timed step. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle on the host cores on a bounded sample of the same
+workload (rank 0 only). Under torchrun every rank runs the same workload on its own GPU
+(independent replicas, weak scaling); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NS = (1000, 2000, 5000)
+N_TERMS = 400
+KT = 0.1
+METRIC = "density matrices/s & % tensor peak, N=1k-5k, mixed vs FP64 at ||dP||/sqrt(N)<=1e-6"
+WORKLOAD = ("tight-binding H (N/4 atoms, 0.1/A^3, 4 orbitals, hopping -2exp(-r/1.5A) cut at 6A), "
+            "one DM per N in {1000,2000,5000} per step, 400 terms, kT=0.1 eV, N_e=N/2, "
+            "mu by FP64 bisection on exact moments")
+SPLIT = {"bf16x3": 6, "fp16x2": 3, "bf16x1": 1, "fp64": 1}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", default="bf16x3", choices=("bf16x3", "fp16x2", "bf16x1", "fp64"))
+    ap.add_argument("--ns", default=",".join(str(n) for n in NS))
+    ap.add_argument("--no-fp64-check", action="store_true", help="skip the FP64 comparison run")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[3:7]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------- CPU baseline
+def cpu_baseline(ns, seconds_hint: float = 20.0) -> dict:
+    """The oracle (plain three-term recursion, mu by bisection on eigenvalue moments) on one
+    N=1000 instance, converted to density matrices per second of the step's N mix by the
+    N^3 cost ratio of the recursion."""
+    import numpy as np
+    import oracle
+    import synth
+    n0 = 1000
+    h = synth.tight_binding(n0, 2000 + n0)
+    t0 = time.perf_counter()
+    oracle.density_matrix(h, n0 / 2, KT, N_TERMS, route="naive")
+    t = time.perf_counter() - t0
+    scale = sum((n / n0) ** 3 for n in ns)
+    return {"value": len(ns) / (t * scale), "unit": "density matrices/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"oracle naive recursion + eigvalsh bisection, one N={n0} DM in {t:.2f} s; "
+                      f"N in {list(ns)} scaled by N^3 (factor {scale:.0f})",
+            "seconds": t}
+
+
+def traffic_record(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(kernel)
+    if not rec:
+        return None
+    with open(os.path.join(ROOT, source), "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != digest:
+        return None
+    return rec
+
+
+# --------------------------------------------------------------------------- main
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ns = [int(x) for x in args.ns.split(",")]
+    vals = []
+    sample = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(ns)
+        vals.append(cb["value"])
+        sample = cb
+    value = statistics.median(vals)
+    out = {"metric": METRIC, "value": value, "unit": "density matrices/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": len(ns) / value * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "n": ns, "n_terms": N_TERMS, "kT_eV": KT,
+                      "precision": "fp64 (numpy/LAPACK oracle)"},
+           "cpu_baseline": {"value": value, "unit": "density matrices/s", "cores": sample["cores"],
+                            "kind": "oracle", "sample": sample["sample"]},
+           "e2e": {"value": value, "unit": "density matrices/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import synth
+    from paper_2306_12616_gb300 import Solver
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ns = [int(x) for x in args.ns.split(",")]
+    solver = Solver(local)
+    stream = torch.cuda.current_stream()
+    prm = solver.params(N_TERMS, KT, precision=args.precision, mu_mode="bisect")
+
+    # inputs resident in HBM (a different replica per rank)
+    hs, ps, hcpu = {}, {}, {}
+    for n in ns:
+        h = synth.tight_binding(n, 2000 + n + 100003 * rank)
+        hcpu[n] = torch.from_numpy(h).pin_memory()
+        hs[n] = hcpu[n].to(dev)
+        ps[n] = torch.empty((n, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # validation pass: status, trace, and the mixed result against the FP64 GPU path
+    accuracy, fp64_ms, results = {}, {}, {}
+    for n in ns:
+        _, res = solver.density_matrix(hs[n], n / 2, prm, out=ps[n])
+        results[n] = res
+        if not args.no_fp64_check and args.precision != "fp64":
+            p64 = torch.empty_like(ps[n])
+            prm64 = solver.params(N_TERMS, KT, precision="fp64", mu_mode="bisect")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, r64 = solver.density_matrix(hs[n], n / 2, prm64, out=p64)
+            fp64_ms[n] = (time.perf_counter() - t0) * 1e3
+            accuracy[n] = {"dP_frob_over_sqrtN": float(torch.linalg.norm(ps[n] - p64) / math.sqrt(n)),
+                           "dmu": res["mu"] - r64["mu"], "trace_minus_Ne": res["trace"] - n / 2,
+                           "fp64_trace_minus_Ne": r64["trace"] - n / 2}
+            del p64
+
+    def step():
+        for n in ns:
+            solver.density_matrix(hs[n], n / 2, prm, out=ps[n], sync=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, events on the launching stream, L2 flushed before each step
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    solver.profile_enable(True)
+    per_step = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        per_step.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    prof = solver.profile_read(reset=True)
+    solver.profile_enable(False)
+    clk = clocks.stop()
+    total_ms = sum(per_step)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * len(ns) / (ms_per_step * 1e-3)
+
+    # end to end through the host-buffer C ABI call (H2D + solve + D2H inside the region)
+    hout = {n: torch.empty((n, n), dtype=torch.float64).pin_memory() for n in ns}
+    for n in ns:
+        solver.density_matrix_host(hcpu[n], n / 2, prm, hout[n])
+    e2e_steps = max(2, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for n in ns:
+            solver.density_matrix_host(hcpu[n], n / 2, prm, hout[n])
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e_bytes = sum(8 * n * n for n in ns)
+
+    pk, pk_kind = peaks()
+    prod = prof["products"]
+    achieved = prod["flops"] / (prod["ms"] * 1e-3) / 1e12 if prod["ms"] > 0 else None
+    if args.precision == "fp64":
+        peak = None
+        unit_peak = "TFLOP/s (fp64; no measured fp64 peak)"
+    else:
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        if args.precision == "fp16x2":
+            peak = peak  # fp16 and bf16 share the dense tensor rate
+        unit_peak = "TFLOP/s"
+    kernel_name = "k_tc_gemm" if args.precision != "fp64" else "k_gemm_f64"
+    trec = traffic_record(kernel_name, "paper_2306_12616_gb300/csrc/gemm_tc.cu"
+                          if args.precision != "fp64" else "paper_2306_12616_gb300/csrc/gemm_f64.cu")
+    launches_per_step = prof["call"]["launches"] / max(1, args.steps)
+    roof = {"bound": "tensor", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+            "unit": unit_peak, "frac": (achieved / peak) if (achieved and peak) else None,
+            "peak_kind": f"{pk_kind} bf16 sustained" if peak else None,
+            "avg_launch_ms": prod["ms"] / max(1, prod["launches"]),
+            "launches_timed": prod["launches"],
+            "share_of_step": prod["ms"] / max(1e-9, prof["call"]["ms"]),
+            "traffic": (trec["bytes_per_launch"] if trec else None),
+            "traffic_note": (trec["note"] if trec else "no ncu capture of the current kernel source")}
+    cb = cpu_baseline(ns) if (rank == 0 and world == 1) else None
+    per_n = {}
+    for n in ns:
+        per_n[str(n)] = {"n_gemm": results[n]["n_gemm"], "k": results[n]["k"], "m": results[n]["m"],
+                         "bisect_iters": results[n]["bisect_iters"], "mu_eV": results[n]["mu"],
+                         "status": results[n]["status"]}
+        if n in accuracy:
+            per_n[str(n)].update(accuracy[n])
+            per_n[str(n)]["fp64_gpu_ms"] = fp64_ms[n]
+    stages = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+              for k, v in prof.items() if isinstance(v, dict)}
+    out = {
+        "metric": METRIC, "value": value, "unit": "density matrices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if args.precision != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": ns, "n_terms": N_TERMS, "kT_eV": KT,
+                   "precision": f"{args.precision} split products, fp32 accumulation; fp64 bounds, "
+                                f"coefficients, moments, traces and mu" if args.precision != "fp64"
+                   else "fp64 throughout",
+                   "parallelism": f"replicas x{world}", "l2": "flushed before every timed step "
+                   "(256 MiB write); per-step working set several GB > L2"},
+        "e2e": {"value": world * len(ns) / (e2e_ms * 1e-3), "unit": "density matrices/s",
+                "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
+        "gpu_launches": int(round(launches_per_step)) * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cb,
+        "clocks": clk,
+        "per_n": per_n,
+        "stages": stages,
+        "fp64_gpu_dm_per_s": (len(fp64_ms) / (sum(fp64_ms.values()) * 1e-3)) if fp64_ms else None,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -93,7 +93,35 @@ typedef struct {
     int32_t bisect_iters;     /* bisection halvings (0 if not bisected) */
     int32_t learned_accepted; /* 1 if the learned mu was kept */
     int32_t status;           /* fo_status of the device-side stages */
+    int32_t n_launches;       /* kernels of this library launched by the call */
+    int32_t reserved;
 } fo_result;
+
+/* Stages of a density-matrix call, as recorded by the profiler. */
+enum {
+    FO_STAGE_BOUNDS = 0,      /* spectral bounds, scaling and plane split of X */
+    FO_STAGE_PRODUCTS = 1,    /* matrix products (baby, giant and Clenshaw steps) */
+    FO_STAGE_MOMENTS = 2,     /* traces and Frobenius products -> tau_n */
+    FO_STAGE_MU = 3,          /* DOS weights and bisection */
+    FO_STAGE_COEFFS = 4,      /* Chebyshev coefficients and giant-step coefficients */
+    FO_STAGE_CONTRACT = 5,    /* R_l = sum_i g_{i,l} T_i */
+    FO_STAGE_TRACE = 6,       /* tr P, ||P||_F^2 */
+    FO_STAGE_CALL = 7,        /* the whole call */
+    FO_PROFILE_STAGES = 8
+};
+
+/* Device-time profile accumulated over calls while profiling is enabled. Times come from
+ * CUDA events recorded on the caller's stream around each stage (products: around each
+ * launch). flops[FO_STAGE_PRODUCTS] is the algorithmic work of the products: a symmetric
+ * product of n x n matrices needs n^2 (n+1) flops per split product (only the upper
+ * triangle of the result is formed), times 6 / 3 / 1 split products for BF16X3 / FP16X2 /
+ * BF16X1 and 1 for FP64. */
+typedef struct {
+    double  ms[FO_PROFILE_STAGES];
+    double  flops[FO_PROFILE_STAGES];
+    int64_t launches[FO_PROFILE_STAGES];
+    int64_t calls;
+} fo_profile;
 
 /* Create a context on CUDA device `device`. *out is set on success. */
 fo_status fo_create(fo_ctx **out, int device);
@@ -173,6 +201,17 @@ fo_status fo_moments(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld,
  * with symmetric == 0 the full A B^T is computed. FP16X2 needs |entries| <= 1 in A and B.
  * Asynchronous.
  */
+/*
+ * Enable (1) or disable (0) the stage profiler of this context; enabling clears it. While
+ * enabled every density-matrix call records CUDA events around its stages.
+ */
+fo_status fo_profile_enable(fo_ctx *ctx, int32_t enable);
+/*
+ * Copy the accumulated profile to *out (synchronises on the recorded events); reset != 0
+ * clears it afterwards.
+ */
+fo_status fo_profile_read(fo_ctx *ctx, fo_profile *out, int32_t reset);
+
 fo_status fo_recurrence_product(fo_ctx *ctx, int32_t precision, int32_t symmetric, int64_t n,
                                 int64_t ld, const float *dA, const float *dB, const float *dC,
                                 const float *dD, float alpha, float beta, float shift,

@@ -20,7 +20,8 @@ __all__ = [
     "FoParams", "FoResult", "FermiError", "lib", "library_path", "EXPORTED_SYMBOLS",
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
-    "fo_moments", "fo_recurrence_product", "Solver", "PRECISIONS", "MU_MODES",
+    "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
+    "STAGE_NAMES", "Solver", "PRECISIONS", "MU_MODES",
 ]
 
 FO_OK = 0
@@ -38,7 +39,7 @@ MU_MODES = {"fixed": FO_MU_FIXED, "bisect": FO_MU_BISECT, "learned": FO_MU_LEARN
 EXPORTED_SYMBOLS = (
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
-    "fo_moments", "fo_recurrence_product",
+    "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read",
 )
 
 
@@ -58,11 +59,28 @@ class FoResult(ctypes.Structure):
         ("frob2", ctypes.c_double), ("emin", ctypes.c_double), ("emax", ctypes.c_double),
         ("k", ctypes.c_int32), ("m", ctypes.c_int32), ("n_gemm", ctypes.c_int32),
         ("bisect_iters", ctypes.c_int32), ("learned_accepted", ctypes.c_int32),
-        ("status", ctypes.c_int32),
+        ("status", ctypes.c_int32), ("n_launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+FO_PROFILE_STAGES = 8
+STAGE_NAMES = ("bounds", "products", "moments", "mu", "coeffs", "contract", "trace", "call")
+
+
+class FoProfile(ctypes.Structure):
+    _fields_ = [
+        ("ms", ctypes.c_double * FO_PROFILE_STAGES),
+        ("flops", ctypes.c_double * FO_PROFILE_STAGES),
+        ("launches", ctypes.c_int64 * FO_PROFILE_STAGES),
+        ("calls", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: {"ms": self.ms[i], "flops": self.flops[i], "launches": self.launches[i]}
+                for i, name in enumerate(STAGE_NAMES)} | {"calls": self.calls}
 
 
 class FermiError(RuntimeError):
@@ -105,6 +123,8 @@ def lib() -> ctypes.CDLL:
                                                       ctypes.POINTER(FoResult), _c_ptr]),
             "fo_moments": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_ptr, _c_i32, _c_i32,
                                           _c_ptr, _c_ptr]),
+            "fo_profile_enable": (ctypes.c_int, [_c_ptr, _c_i32]),
+            "fo_profile_read": (ctypes.c_int, [_c_ptr, ctypes.POINTER(FoProfile), _c_i32]),
             "fo_recurrence_product": (ctypes.c_int, [_c_ptr, _c_i32, _c_i32, _c_i64, _c_i64, _c_ptr, _c_ptr,
                                                      _c_ptr, _c_ptr, _c_f, _c_f, _c_f, _c_ptr,
                                                      _c_ptr]),
@@ -166,6 +186,14 @@ def fo_density_matrix_host(ctx, h_h, n, ld, n_e, params: FoParams, h_p, ldp,
 
 def fo_moments(ctx, d_h, n, ld, d_bounds, n_moments, precision, d_tau, stream=0) -> int:
     return lib().fo_moments(ctx, d_h, n, ld, d_bounds, n_moments, precision, d_tau, stream)
+
+
+def fo_profile_enable(ctx, enable: int) -> int:
+    return lib().fo_profile_enable(ctx, enable)
+
+
+def fo_profile_read(ctx, profile: FoProfile, reset: int = 0) -> int:
+    return lib().fo_profile_read(ctx, ctypes.byref(profile), reset)
 
 
 def fo_recurrence_product(ctx, precision, symmetric, n, ld, d_a, d_b, d_c, d_d, alpha, beta,
@@ -254,6 +282,14 @@ class Solver:
                                            params, out.data_ptr(), out.stride(0), res,
                                            _stream_handle(stream)))
         return res.as_dict()
+
+    def profile_enable(self, enable: bool = True):
+        self._check(fo_profile_enable(self.ctx, 1 if enable else 0))
+
+    def profile_read(self, reset: bool = False) -> dict:
+        prof = FoProfile()
+        self._check(fo_profile_read(self.ctx, prof, 1 if reset else 0))
+        return prof.as_dict()
 
     def moments(self, h, bounds, n_moments: int, precision="fp64", stream=None):
         import torch

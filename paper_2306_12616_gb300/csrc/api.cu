@@ -18,8 +18,22 @@
 
 using namespace fo;
 
+struct ProfEntry {
+    cudaEvent_t a, b;
+    int stage;
+    double flops;
+    int launches;
+};
+
 struct fo_ctx {
     int device = 0;
+    bool prof = false;
+    std::vector<ProfEntry> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[FO_PROFILE_STAGES] = {0};
+    double prof_flops[FO_PROFILE_STAGES] = {0};
+    int64_t prof_launches[FO_PROFILE_STAGES] = {0};
+    int64_t prof_calls = 0;
     int num_sms = 0;
     std::string err;
     void* ws = nullptr;        // device workspace
@@ -72,6 +86,49 @@ bool debug_sync() {
         if (e_ == cudaSuccess && debug_sync()) e_ = cudaDeviceSynchronize(); \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);      \
     } while (0)
+
+// ---------------------------------------------------------------- stage profiler
+cudaEvent_t ev_get(fo_ctx* ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Starts a timed stage when profiling is on; returns a handle for prof_end (or -1).
+int prof_begin(fo_ctx* ctx, cudaStream_t st, int stage) {
+    if (!ctx->prof) return -1;
+    ProfEntry e{ev_get(ctx), ev_get(ctx), stage, 0.0, 0};
+    cudaEventRecord(e.a, st);
+    ctx->prof_pending.push_back(e);
+    return (int)ctx->prof_pending.size() - 1;
+}
+
+void prof_end(fo_ctx* ctx, cudaStream_t st, int h, double flops, int launches) {
+    if (h < 0) return;
+    ProfEntry& e = ctx->prof_pending[h];
+    e.flops = flops;
+    e.launches = launches;
+    cudaEventRecord(e.b, st);
+}
+
+void prof_collect(fo_ctx* ctx) {
+    for (ProfEntry& e : ctx->prof_pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+            ctx->prof_ms[e.stage] += ms;
+            ctx->prof_flops[e.stage] += e.flops;
+            ctx->prof_launches[e.stage] += e.launches;
+        }
+        ctx->ev_pool.push_back(e.a);
+        ctx->ev_pool.push_back(e.b);
+    }
+    ctx->prof_pending.clear();
+}
 
 fo_status ensure_ws(fo_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->ws_bytes) return FO_OK;
@@ -204,8 +261,26 @@ struct Product {
     int index = 0;
 };
 
+fo_status run_product_impl(fo_ctx* ctx, const Plan& p, const Slots& S, const Product& q,
+                           cudaStream_t st, int sym);
+
+// Algorithmic flops of one symmetric product: n^2 (n+1) per split product.
+double product_flops(const Plan& p) {
+    const double n = (double)p.n;
+    const int s = p.prec == FO_PREC_BF16X3 ? 6 : (p.prec == FO_PREC_FP16X2 ? 3 : 1);
+    return s * n * n * (n + 1.0);
+}
+
 fo_status run_product(fo_ctx* ctx, const Plan& p, const Slots& S, const Product& q, cudaStream_t st,
                       int sym) {
+    const int h = prof_begin(ctx, st, FO_STAGE_PRODUCTS);
+    fo_status r = run_product_impl(ctx, p, S, q, st, sym);
+    prof_end(ctx, st, h, product_flops(p), 1);
+    return r;
+}
+
+fo_status run_product_impl(fo_ctx* ctx, const Plan& p, const Slots& S, const Product& q,
+                           cudaStream_t st, int sym) {
     if (p.prec == FO_PREC_FP64) {
         const double* A = q.a_r ? S.Rd(q.a) : S.Td(q.a);
         const double* B = q.b_r ? S.Rd(q.b) : S.Td(q.b);
@@ -323,9 +398,8 @@ fo_status exact_moments(fo_ctx* ctx, const Plan& p, const Slots& S, cudaStream_t
     return FO_OK;
 }
 
-// Coefficients at the device mu, conversion to g, contraction and Clenshaw giant steps.
-fo_status expand(fo_ctx* ctx, const Plan& p, const Slots& S, double kT, double* dP, int64_t ldp,
-                 cudaStream_t st, int sym, int* n_gemm) {
+// Coefficients at the device mu and their conversion to giant-step coefficients g.
+fo_status coefficients(fo_ctx* ctx, const Plan& p, double kT, cudaStream_t st, int* launches) {
     char* W = wsb(ctx);
     double* ct = reinterpret_cast<double*>(W + p.off_ct);
     double* f = reinterpret_cast<double*>(W + p.off_f);
@@ -334,9 +408,19 @@ fo_status expand(fo_ctx* ctx, const Plan& p, const Slots& S, double kT, double* 
     FO_CUDA(launch_fermi_nodes(p.M, ct, ctx->res, kT, f, st), "fermi_nodes");
     FO_CUDA(launch_coeffs(f, ct, p.M, p.n_terms, p.km, c, st), "coeffs");
     FO_CUDA(launch_g_convert(c, p.k, p.m, g, st), "g_convert");
-    if (p.moments)
+    *launches += 3;
+    if (p.moments) {
         FO_CUDA(launch_poly_trace(c, reinterpret_cast<double*>(W + p.off_tau), p.n_terms, ctx->res, st),
                 "poly_trace");
+        *launches += 1;
+    }
+    return FO_OK;
+}
+
+// R_l = sum_i g_{i,l} T_i for every l (the S_j sums of the paper in the Chebyshev basis).
+fo_status contraction(fo_ctx* ctx, const Plan& p, const Slots& S, double* dP, int64_t ldp,
+                      cudaStream_t st, int* launches) {
+    const double* g = reinterpret_cast<const double*>(wsb(ctx) + p.off_g);
     if (p.prec == FO_PREC_FP64) {
         FO_CUDA(launch_contract_f64(g, p.k, p.m, S.Td(0), (int64_t)(p.slot_bytes / 8), S.Rd(0),
                                     (int64_t)(p.slot_bytes / 8), p.n, p.np, st),
@@ -347,14 +431,23 @@ fo_status expand(fo_ctx* ctx, const Plan& p, const Slots& S, double kT, double* 
                                     p.fp16, p.pscale_r, p.np * p.np, st, ctx->flag + 1),
                 "contract");
     }
-    const int ysl = giant_slot(p, 1);
+    *launches += 1;
     if (p.m == 1) {
         if (p.prec == FO_PREC_FP64)
             FO_CUDA(launch_copy_out(S.Rd(0), p.np, p.n, dP, ldp, st), "copy_out");
         else
             FO_CUDA(launch_copy_out_f32(S.R(0).x, p.np, p.n, dP, ldp, st), "copy_out");
-        return FO_OK;
+        *launches += 1;
     }
+    return FO_OK;
+}
+
+// Clenshaw recurrence in Y = T_k: b_{m-1} = R_{m-1}; b_l = 2 Y b_{l+1} - b_{l+2} + R_l;
+// P = Y b_1 - b_2 + R_0 (written as float64 into dP). b_l overwrites R_l in place.
+fo_status clenshaw(fo_ctx* ctx, const Plan& p, const Slots& S, double* dP, int64_t ldp,
+                   cudaStream_t st, int sym, int* n_gemm) {
+    if (p.m == 1) return FO_OK;
+    const int ysl = giant_slot(p, 1);
     for (int l = p.m - 2; l >= 1; --l) {
         Product q;
         q.a = ysl;
@@ -406,53 +499,91 @@ fo_status density_impl(fo_ctx* ctx, const double* dH, int64_t n, int64_t ld, dou
     FO_TRY(ensure_ws(ctx, p.total));
     Slots S{wsb(ctx) + p.off_t, wsb(ctx) + p.off_r, p.slot_bytes, p.np, p.planes};
     const int sym = 1;  // symmetric products (upper-triangle tiles, mirrored)
-    int n_gemm = 0;
+    int n_gemm = 0, launches = 0, lstage = 0;
     char* W = wsb(ctx);
     double* part = reinterpret_cast<double*>(W + p.off_part);
+    const int hcall = prof_begin(ctx, st, FO_STAGE_CALL);
+
+    // spectral bounds and X = scaled H (split into planes for the tensor-core forms)
+    int h = prof_begin(ctx, st, FO_STAGE_BOUNDS);
     FO_CUDA(cudaMemsetAsync(ctx->res, 0, sizeof(DevResult), st), "memset");
     FO_CUDA(launch_gershgorin(dH, n, ld, part, part + p.nparts, reinterpret_cast<int*>(part + 2 * p.nparts),
                               p.nparts, ctx->res, prm->use_given_bounds, prm->emin, prm->emax, st),
             "bounds");
     FO_TRY(pack_x(ctx, p, S, dH, ld, st));
+    lstage = (prm->use_given_bounds ? 1 : 2) + 1;
+    prof_end(ctx, st, h, 0.0, lstage);
+    launches += lstage;
+
+    // baby steps T_2 .. T_k
+    const int g0 = n_gemm;
     FO_TRY(baby_steps(ctx, p, S, p.k, st, sym, &n_gemm));
     double* ct = reinterpret_cast<double*>(W + p.off_ct);
     FO_CUDA(launch_cos_table(p.M, ct, st), "cos_table");
+    launches += 1;
     const int max_it = prm->max_bisect > 0 ? prm->max_bisect : 200;
     if (bisect) {
+        // giant steps T_{2k} .. T_{(m-1)k}, exact moments, bisection for mu
         if (p.giants) FO_TRY(giant_steps(ctx, p, S, st, sym, &n_gemm));
+        h = prof_begin(ctx, st, FO_STAGE_MOMENTS);
         FO_TRY(exact_moments(ctx, p, S, st));
+        lstage = 1 + ((p.m > 1 && p.k > 1) ? 2 : 0) + 1;
+        prof_end(ctx, st, h, 0.0, lstage);
+        launches += lstage;
+        h = prof_begin(ctx, st, FO_STAGE_MU);
         double* w = reinterpret_cast<double*>(W + p.off_w);
         FO_CUDA(launch_dos_weights(reinterpret_cast<double*>(W + p.off_tau), p.n_terms, p.M, ct, w, st),
                 "dos_weights");
         FO_CUDA(launch_bisect(w, ct, p.M, ctx->res, prm->kT, n_e, max_it, st), "bisect");
+        prof_end(ctx, st, h, 0.0, 2);
+        launches += 2;
     } else {
         // fixed mu: write it into the device record (kept after the bounds pass)
         FO_CUDA(launch_set_scalar(&ctx->res->mu, prm->mu, st), "mu");
+        launches += 1;
     }
-    FO_TRY(expand(ctx, p, S, prm->kT, dP, ldp, st, sym, &n_gemm));
+    h = prof_begin(ctx, st, FO_STAGE_COEFFS);
+    lstage = 0;
+    FO_TRY(coefficients(ctx, p, prm->kT, st, &lstage));
+    prof_end(ctx, st, h, 0.0, lstage);
+    launches += lstage;
+    h = prof_begin(ctx, st, FO_STAGE_CONTRACT);
+    lstage = 0;
+    FO_TRY(contraction(ctx, p, S, dP, ldp, st, &lstage));
+    prof_end(ctx, st, h, 0.0, lstage);
+    launches += lstage;
+    FO_TRY(clenshaw(ctx, p, S, dP, ldp, st, sym, &n_gemm));
+    launches += n_gemm - g0;
+    h = prof_begin(ctx, st, FO_STAGE_TRACE);
     FO_CUDA(launch_trace_frob(dP, n, ldp, part, p.nparts, ctx->res, st), "trace");
+    prof_end(ctx, st, h, 0.0, 2);
+    launches += 2;
+    prof_end(ctx, st, hcall, product_flops(p) * n_gemm, launches);
+    if (ctx->prof) ctx->prof_calls += 1;
+
     if (res && !(prm->flags & FO_FLAG_NO_RESULT_SYNC)) {
-        DevResult h;
+        DevResult hr;
         int flag[5] = {0, 0, 0, 0, 0};
-        FO_CUDA(cudaMemcpyAsync(&h, ctx->res, sizeof(DevResult), cudaMemcpyDeviceToHost, st), "readback");
+        FO_CUDA(cudaMemcpyAsync(&hr, ctx->res, sizeof(DevResult), cudaMemcpyDeviceToHost, st), "readback");
         FO_CUDA(cudaMemcpyAsync(flag, ctx->flag, sizeof(flag), cudaMemcpyDeviceToHost, st), "readback");
         FO_CUDA(cudaStreamSynchronize(st), "sync");
         if (flag[1] != 0)
             return fail(ctx, FO_ERR_CUDA, "self-check violation code " + std::to_string(flag[1]) + " (" +
                                               std::to_string(flag[2]) + ", " + std::to_string(flag[3]) + ")");
         std::memset(res, 0, sizeof(*res));
-        res->mu = h.mu;
-        res->trace = h.trace;
-        res->trace_poly = h.trace_poly;
-        res->frob2 = h.frob2;
-        res->emin = h.bounds[0];
-        res->emax = h.bounds[1];
+        res->mu = hr.mu;
+        res->trace = hr.trace;
+        res->trace_poly = hr.trace_poly;
+        res->frob2 = hr.frob2;
+        res->emin = hr.bounds[0];
+        res->emax = hr.bounds[1];
         res->k = p.k;
         res->m = p.m;
         res->n_gemm = n_gemm;
-        res->bisect_iters = h.iters;
+        res->bisect_iters = hr.iters;
         res->learned_accepted = 0;
-        int status = h.status;
+        res->n_launches = launches;
+        int status = hr.status;
         if (flag[0]) status = FO_ERR_DEVICE_TIMEOUT;
         res->status = status;
         if (status != FO_OK)
@@ -516,6 +647,8 @@ fo_status fo_destroy(fo_ctx* ctx) {
     {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
+        prof_collect(ctx);
+        for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
         if (ctx->ws) cudaFree(ctx->ws);
         if (ctx->stage) cudaFree(ctx->stage);
         if (ctx->res) cudaFree(ctx->res);
@@ -626,6 +759,41 @@ fo_status fo_moments(fo_ctx* ctx, const double* dH, int64_t n, int64_t ld, const
     FO_TRY(exact_moments(ctx, p, S, st));
     FO_CUDA(cudaMemcpyAsync(d_tau, wsb(ctx) + p.off_tau, 8 * (size_t)n_moments, cudaMemcpyDeviceToDevice, st),
             "tau copy");
+    return FO_OK;
+}
+
+fo_status fo_profile_enable(fo_ctx* ctx, int32_t enable) {
+    if (!ctx) return FO_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    prof_collect(ctx);
+    for (int i = 0; i < FO_PROFILE_STAGES; ++i) {
+        ctx->prof_ms[i] = 0.0;
+        ctx->prof_flops[i] = 0.0;
+        ctx->prof_launches[i] = 0;
+    }
+    ctx->prof_calls = 0;
+    ctx->prof = enable != 0;
+    return FO_OK;
+}
+
+fo_status fo_profile_read(fo_ctx* ctx, fo_profile* out, int32_t reset) {
+    if (!ctx || !out) return FO_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    prof_collect(ctx);
+    for (int i = 0; i < FO_PROFILE_STAGES; ++i) {
+        out->ms[i] = ctx->prof_ms[i];
+        out->flops[i] = ctx->prof_flops[i];
+        out->launches[i] = ctx->prof_launches[i];
+    }
+    out->calls = ctx->prof_calls;
+    if (reset) {
+        for (int i = 0; i < FO_PROFILE_STAGES; ++i) {
+            ctx->prof_ms[i] = 0.0;
+            ctx->prof_flops[i] = 0.0;
+            ctx->prof_launches[i] = 0;
+        }
+        ctx->prof_calls = 0;
+    }
     return FO_OK;
 }
 

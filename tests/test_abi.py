@@ -32,4 +32,5 @@ def test_host_only_calls(built_library):
 def test_struct_layouts_match_header():
     # fo_params: 2 ints, 2 doubles, 4 ints, 2 doubles, int, uint -> 64 bytes with padding
     assert ctypes.sizeof(fo.FoParams) == 64
-    assert ctypes.sizeof(fo.FoResult) == 6 * 8 + 6 * 4
+    assert ctypes.sizeof(fo.FoResult) == 6 * 8 + 8 * 4
+    assert ctypes.sizeof(fo.FoProfile) == 8 * 8 * 3 + 8

@@ -1,0 +1,112 @@
+"""Split-precision density matrices against the CPU FP64 oracle.
+
+Tolerances:
+* BF16x3: ||P - P_ref||_F / sqrt(N) <= 1e-6 (the stated mixed-precision bar), P_ref the oracle
+  polynomial at the bounds and mu the GPU used;
+* mu: |mu_gpu - mu_oracle| <= 1e-5 (the GPU moments come from float32 masters);
+* trace: |tr P - N_e| <= 2e-6 N for the split forms (float32 masters give ~1e-7 relative
+  error per diagonal entry; a sum of N of them), 1e-8 for FP64;
+* FP16x2 and BF16x1 are reported against their own arithmetic limits (1e-5 and 5e-2): they
+  do not meet the 1e-6 bar (FP16x2 keeps ~22 bits, BF16x1 8 bits per operand).
+At N = 5000 the oracle evaluates sampled columns P e_j by the three-term recursion applied
+to unit vectors; the RMS over the sampled columns estimates ||dP||_F / sqrt(N).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def to_dev(h):
+    return torch.from_numpy(np.ascontiguousarray(h)).to(DEV)
+
+
+def ref_at(h, res, kT, n_terms, eig=None):
+    c = O.chebyshev_coeffs(kT, res["mu"], res["emin"], res["emax"], n_terms)
+    return O.poly_eig(h, c, res["emin"], res["emax"], eig=eig)
+
+
+@pytest.mark.parametrize("n", [64, 300, 1000])
+def test_bf16x3_tight_binding_bisection(solver, n):
+    h = synth.tight_binding(n, 2000 + n)
+    prm = solver.params(400, 0.1, precision="bf16x3", mu_mode="bisect")
+    p, res = solver.density_matrix(to_dev(h), n / 2, prm)
+    p = p.cpu().numpy()
+    assert res["status"] == 0
+    err = np.linalg.norm(p - ref_at(h, res, 0.1, 400)) / math.sqrt(n)
+    assert err <= 1e-6, err
+    assert np.array_equal(p, p.T)
+    orc = O.density_matrix(h, n / 2, 0.1, 400, route="eig", want_p=False)
+    assert abs(res["mu"] - orc.mu) <= 1e-5
+    assert abs(np.trace(p) - n / 2) <= 2e-6 * n
+
+
+def test_bf16x3_random_config(solver):
+    # N = 256 random symmetric H, N_e = 128, kT = 0.05 (e_b - e_a), 256 terms (k = m = 16)
+    n = 256
+    h = synth.random_symmetric(n, 1)
+    ea, eb = O.gershgorin_bounds(h)
+    kT = 0.05 * (eb - ea)
+    prm = solver.params(256, kT, precision="bf16x3", mu_mode="bisect")
+    p, res = solver.density_matrix(to_dev(h), 128.0, prm)
+    err = np.linalg.norm(p.cpu().numpy() - ref_at(h, res, kT, 256)) / math.sqrt(n)
+    assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16x2", 1e-5), ("bf16x1", 5e-2)])
+def test_other_split_forms(solver, prec, tol):
+    n = 1000
+    h = synth.tight_binding(n, 2000 + n)
+    prm = solver.params(400, 0.1, precision=prec, mu_mode="bisect")
+    p, res = solver.density_matrix(to_dev(h), n / 2, prm)
+    err = np.linalg.norm(p.cpu().numpy() - ref_at(h, res, 0.1, 400)) / math.sqrt(n)
+    print(f"{prec}: ||dP||/sqrt(N) = {err:.3e}")
+    assert err <= tol, err
+
+
+def test_bf16x3_full_size_sampled_columns(solver):
+    n = 5000
+    h = synth.tight_binding(n, 2000 + n)
+    prm = solver.params(400, 0.1, precision="bf16x3", mu_mode="bisect")
+    p, res = solver.density_matrix(to_dev(h), n / 2, prm)
+    assert res["status"] == 0 and (res["k"], res["m"]) == (20, 20)
+    cols = np.arange(7, n, n // 8)
+    c = O.chebyshev_coeffs(0.1, res["mu"], res["emin"], res["emax"], 400)
+    x = O.scale_hamiltonian(h, res["emin"], res["emax"])
+    ref = O.chebyshev_apply(x, c, np.eye(n)[:, cols])
+    pc = p[:, cols].cpu().numpy()
+    err = math.sqrt(np.mean(np.sum((pc - ref) ** 2, axis=0)))
+    assert err <= 1e-6, err
+    # symmetric by construction; trace against the electron count
+    assert torch.equal(p, p.T)
+    assert abs(res["trace"] - n / 2) <= 2e-6 * n
+
+
+def test_deterministic_replay(solver):
+    n = 700
+    h = to_dev(synth.tight_binding(n, 77))
+    prm = solver.params(300, 0.1, precision="bf16x3", mu_mode="bisect")
+    p1, r1 = solver.density_matrix(h, n / 2, prm)
+    p2, r2 = solver.density_matrix(h, n / 2, prm)
+    assert torch.equal(p1, p2) and r1["mu"] == r2["mu"]
+
+
+def test_profiler_counts_products(solver):
+    n = 512
+    h = to_dev(synth.tight_binding(n, 5))
+    prm = solver.params(100, 0.1, precision="bf16x3", mu_mode="bisect")
+    solver.profile_enable(True)
+    _, res = solver.density_matrix(h, n / 2, prm)
+    prof = solver.profile_read(reset=True)
+    solver.profile_enable(False)
+    assert prof["products"]["launches"] == res["n_gemm"]
+    assert prof["call"]["launches"] == res["n_launches"]
+    assert prof["products"]["flops"] == pytest.approx(res["n_gemm"] * 6 * n * n * (n + 1))
+    assert 0 < prof["products"]["ms"] <= prof["call"]["ms"]
