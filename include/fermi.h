@@ -145,6 +145,28 @@ fo_status fo_spectral_bounds(fo_ctx *ctx, const double *dH, int64_t n, int64_t l
                              double *d_bounds, void *stream);
 
 /*
+ * Spectral bounds for callers that cannot allocate device memory when they need them (for
+ * example code running inside a memory pool it does not own, or an embedding that forbids
+ * cudaMalloc after start-up). The paper has no counterpart: this is a service entry point.
+ * It computes exactly what fo_spectral_bounds computes (same outputs in d_bounds[0..2]) but
+ * needs no context and allocates nothing: its per-block partial results live in a fixed
+ * 128 KiB array in device memory that is part of the library image, resident on every GPU
+ * that loads the library until the process exits.
+ *  - n must not exceed FO_NOALLOC_MAX_N (the capacity of that array); larger n, NULL
+ *    pointers or ld < n return FO_ERR_ARG, with nothing launched.
+ *  - The first call on a device looks up the array's device address (with that device
+ *    current) and caches it; make that first call before any stream capture.
+ *  - The call uses the current CUDA device; H and d_bounds must live on it.
+ *  - Every call on a device shares the array, which keeps the last call's contents; each
+ *    call overwrites what it reads, so no clearing is needed, but calls whose kernels
+ *    overlap on the GPU (different streams or host threads) race and must be serialised.
+ * Asynchronous on `stream`.
+ */
+#define FO_NOALLOC_MAX_N 32768
+fo_status fo_spectral_bounds_noalloc(const double *dH, int64_t n, int64_t ld, double *d_bounds,
+                                     void *stream);
+
+/*
  * Chebyshev coefficients of the Fermi-Dirac function on [emin, emax] (Sec. "Chebyshev
  * expansions", Eq. (fermifunc)): Chebyshev-Gauss interpolation on n_quad nodes
  * (0 = max(2048, 4 n_terms)), c_0 = (1/M) sum_j f_j, c_n = (2/M) sum_j f_j cos(n theta_j),

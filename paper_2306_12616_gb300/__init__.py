@@ -21,6 +21,7 @@ __all__ = [
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
     "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
+    "fo_spectral_bounds_noalloc", "FO_NOALLOC_MAX_N",
     "STAGE_NAMES", "Solver", "PRECISIONS", "MU_MODES",
 ]
 
@@ -40,7 +41,9 @@ EXPORTED_SYMBOLS = (
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
     "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read",
+    "fo_spectral_bounds_noalloc",
 )
+FO_NOALLOC_MAX_N = 32768
 
 
 class FoParams(ctypes.Structure):
@@ -124,6 +127,7 @@ def lib() -> ctypes.CDLL:
             "fo_moments": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_ptr, _c_i32, _c_i32,
                                           _c_ptr, _c_ptr]),
             "fo_profile_enable": (ctypes.c_int, [_c_ptr, _c_i32]),
+            "fo_spectral_bounds_noalloc": (ctypes.c_int, [_c_ptr, _c_i64, _c_i64, _c_ptr, _c_ptr]),
             "fo_profile_read": (ctypes.c_int, [_c_ptr, ctypes.POINTER(FoProfile), _c_i32]),
             "fo_recurrence_product": (ctypes.c_int, [_c_ptr, _c_i32, _c_i32, _c_i64, _c_i64, _c_ptr, _c_ptr,
                                                      _c_ptr, _c_ptr, _c_f, _c_f, _c_f, _c_ptr,
@@ -165,6 +169,11 @@ def fo_version() -> str:
 
 def fo_spectral_bounds(ctx, d_h, n, ld, d_bounds, stream=0) -> int:
     return lib().fo_spectral_bounds(ctx, d_h, n, ld, d_bounds, stream)
+
+
+def fo_spectral_bounds_noalloc(d_h, n, ld, d_bounds, stream=0) -> int:
+    """Spectral bounds without a context or any device allocation (see include/fermi.h)."""
+    return lib().fo_spectral_bounds_noalloc(d_h, n, ld, d_bounds, stream)
 
 
 def fo_chebyshev_coeffs(ctx, kT, mu, emin, emax, n_terms, n_quad, d_c, stream=0) -> int:
