@@ -183,6 +183,8 @@ fo_status make_plan(fo_ctx* ctx, int64_t n, int n_terms, int k_req, int prec, bo
     if (prec < FO_PREC_FP64 || prec > FO_PREC_BF16X1) return fail(ctx, FO_ERR_ARG, "unknown precision");
     p->n = n;
     p->np = ((n + kPad - 1) / kPad) * kPad;
+    // tensor-core tiles are 128 x 256: keep at least one full column tile
+    if (prec != FO_PREC_FP64 && p->np < 256) p->np = 256;
     p->n_terms = n_terms;
     if (!plan_km(n_terms, k_req, &p->k, &p->m)) return fail(ctx, FO_ERR_ARG, "bad k");
     if (p->k > 64 || p->m > 64) return fail(ctx, FO_ERR_ARG, "k and m must not exceed 64");
@@ -193,6 +195,7 @@ fo_status make_plan(fo_ctx* ctx, int64_t n, int n_terms, int k_req, int prec, bo
     p->planes = tc_planes(prec);
     p->fp16 = prec == FO_PREC_FP16X2;
     p->giants = giants && p->m > 2;
+    if (moments && p->k > 33) return fail(ctx, FO_ERR_UNSUPPORTED, "exact moments support k <= 33");
     p->moments = moments;
     const size_t np2 = (size_t)p->np * (size_t)p->np;
     p->slot_bytes = prec == FO_PREC_FP64 ? align256(np2 * 8) : align256(np2 * 4 + p->planes * np2 * 2);

@@ -49,47 +49,63 @@ __global__ void k_dos_weights(const double* __restrict__ tau, int n_terms, int M
     w[j] = (tau[0] + 2.0 * s) / (double)M;
 }
 
-// Sum over the M nodes of w_j f(e_j; mu), fixed order, result broadcast to the block.
-__device__ double trace_at(double mu, const double* __restrict__ w, const double* __restrict__ ct,
-                           int M, double mid, double half, double inv2kT, double* sh) {
-    double s = 0.0;
-    for (int j = threadIdx.x; j < M; j += blockDim.x)
-        s = fma(w[j], fermi(mid + half * ct[2 * j + 1], mu, inv2kT), s);
+// F(mu) + N_e = sum_j w_j f(e_j; mu) and dF/dmu = sum_j w_j f_j (1 - f_j) / kT over the M
+// nodes, fixed summation order, both broadcast to the block.
+__device__ void trace_at(double mu, const double* __restrict__ w, const double* __restrict__ ct,
+                         int M, double mid, double half, double inv2kT, double* sh, double* tr,
+                         double* dtr) {
+    double s = 0.0, d = 0.0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const double f = fermi(mid + half * ct[2 * j + 1], mu, inv2kT);
+        s = fma(w[j], f, s);
+        d = fma(w[j], f * (1.0 - f), d);
+    }
     s = warp_sum(s);
+    d = warp_sum(d);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
-    if (lane == 0) sh[warp] = s;
+    if (lane == 0) { sh[warp] = s; sh[32 + warp] = d; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < nw; ++i) t += sh[i];
-        sh[32] = t;
+        double t = 0.0, u = 0.0;
+        for (int i = 0; i < nw; ++i) { t += sh[i]; u += sh[32 + i]; }
+        sh[64] = t;
+        sh[65] = u * 2.0 * inv2kT;
     }
     __syncthreads();
-    return sh[32];
+    *tr = sh[64];
+    if (dtr) *dtr = sh[65];
 }
 
-// Bisection for F(mu) = sum_n c_n(mu) tau_n - N_e = 0 on one block: bracket [emin, emax]
-// widened by 10 kT (at most 8 times per side), stop when |F| <= 1e-12 max(1, N_e) or the
-// bracket is below 1e-15 (emax - emin), at most max_iter halvings; mu = last midpoint.
+// Root of F(mu) = sum_n c_n(mu) tau_n - N_e on one block. Bracket [emin, emax], widened by
+// 10 kT (at most 8 times per side). Inside the bracket a Newton step on the exact derivative
+// of the node sum is taken when it stays in the bracket, a halving otherwise; the bracket
+// shrinks with the sign of F at every evaluated point. Stop when |F| <= 1e-12 max(1, N_e)
+// (mu = that point) or the bracket is narrower than 1e-15 (emax - emin) (mu = midpoint), at
+// most max_iter evaluations.
 __global__ void __launch_bounds__(512) k_bisect(const double* __restrict__ w,
-                                                const double* __restrict__ ct, int M,
-                                                DevResult* res, double kT, double n_e,
-                                                int max_iter) {
-    __shared__ double sh[33];
+                                                 const double* __restrict__ ct, int M,
+                                                 DevResult* res, double kT, double n_e,
+                                                 int max_iter) {
+    __shared__ double sh[66];
     const double ea = res->bounds[0], eb = res->bounds[1];
     const double mid = 0.5 * (eb + ea), half = 0.5 * (eb - ea), inv2kT = 0.5 / kT;
-    double lo = ea, hi = eb;
-    for (int t = 0; t < 8; ++t) {
-        if (trace_at(lo, w, ct, M, mid, half, inv2kT, sh) - n_e <= 0.0) break;
+    double lo = ea, hi = eb, t;
+    for (int q = 0; q < 8; ++q) {
+        trace_at(lo, w, ct, M, mid, half, inv2kT, sh, &t, nullptr);
+        if (t - n_e <= 0.0) break;
         lo -= 10.0 * kT;
     }
-    for (int t = 0; t < 8; ++t) {
-        if (trace_at(hi, w, ct, M, mid, half, inv2kT, sh) - n_e >= 0.0) break;
+    for (int q = 0; q < 8; ++q) {
+        trace_at(hi, w, ct, M, mid, half, inv2kT, sh, &t, nullptr);
+        if (t - n_e >= 0.0) break;
         hi += 10.0 * kT;
     }
-    const double flo = trace_at(lo, w, ct, M, mid, half, inv2kT, sh) - n_e;
-    const double fhi = trace_at(hi, w, ct, M, mid, half, inv2kT, sh) - n_e;
+    double flo, fhi;
+    trace_at(lo, w, ct, M, mid, half, inv2kT, sh, &flo, nullptr);
+    trace_at(hi, w, ct, M, mid, half, inv2kT, sh, &fhi, nullptr);
+    flo -= n_e;
+    fhi -= n_e;
     int status = FO_OK, iters = 0;
     double mu = 0.5 * (lo + hi);
     if (flo > 0.0 || fhi < 0.0) {
@@ -98,13 +114,17 @@ __global__ void __launch_bounds__(512) k_bisect(const double* __restrict__ w,
         const double tol_f = 1e-12 * fmax(1.0, fabs(n_e));
         const double tol_w = 1e-15 * (eb - ea);
         bool done = false;
+        double x = 0.5 * (lo + hi);
         for (int it = 1; it <= max_iter; ++it) {
-            const double m = 0.5 * (lo + hi);
-            const double f = trace_at(m, w, ct, M, mid, half, inv2kT, sh) - n_e;
+            double f, df;
+            trace_at(x, w, ct, M, mid, half, inv2kT, sh, &f, &df);
+            f -= n_e;
             iters = it;
-            if (fabs(f) <= tol_f) { mu = m; done = true; break; }
-            if (f < 0.0) lo = m; else hi = m;
+            if (fabs(f) <= tol_f) { mu = x; done = true; break; }
+            if (f < 0.0) lo = x; else hi = x;
             if (hi - lo <= tol_w) { mu = 0.5 * (lo + hi); done = true; break; }
+            const double cand = (df > 0.0) ? x - f / df : lo;
+            x = (cand > lo && cand < hi) ? cand : 0.5 * (lo + hi);
         }
         if (!done) {
             mu = 0.5 * (lo + hi);
@@ -222,6 +242,7 @@ __device__ __forceinline__ uint16_t bf16_bits_c(float v) {
     return *reinterpret_cast<uint16_t*>(&h);
 }
 
+template <int MAXM>
 __global__ void __launch_bounds__(256) k_contract_f32(const double* __restrict__ gsrc, int k,
                                                       int m, const float* __restrict__ tbase,
                                                       int64_t tstride, float* __restrict__ rbase,
@@ -231,69 +252,67 @@ __global__ void __launch_bounds__(256) k_contract_f32(const double* __restrict__
     extern __shared__ float fsh[];
     for (int q = threadIdx.x; q < k * m; q += blockDim.x) fsh[q] = (float)gsrc[q];
     __syncthreads();
-    const int64_t total4 = np * np / 4;
-    for (int64_t i4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i4 < total4;
-         i4 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t idx = i4 * 4;
+    const int64_t total2 = np * np / 2;
+    for (int64_t i2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i2 < total2;
+         i2 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = i2 * 2;
         const int64_t r = idx / np, col0 = idx - r * np;
-        for (int l0 = 0; l0 < m; l0 += kGroup) {
-            float4 acc[kGroup];
+        float2 acc[MAXM];
 #pragma unroll
-            for (int q = 0; q < kGroup; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int i = 1; i < k; ++i) {
-                const float* tp = tbase + (int64_t)(i - 1) * tstride + idx;
-                if (!FO_CHK(dbg, (reinterpret_cast<uintptr_t>(tp) & 15) == 0 && idx + 4 <= np * np, 301, i, idx)) continue;
-                const float4 t = *reinterpret_cast<const float4*>(tp);
+        for (int l = 0; l < MAXM; ++l) acc[l] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int i = 1; i < k; ++i) {
+            const float2 t = *reinterpret_cast<const float2*>(tbase + (int64_t)(i - 1) * tstride + idx);
 #pragma unroll
-                for (int q = 0; q < kGroup; ++q) {
-                    if (l0 + q < m) {
-                        const float gv = fsh[(l0 + q) * k + i];
-                        acc[q].x = fmaf(gv, t.x, acc[q].x);
-                        acc[q].y = fmaf(gv, t.y, acc[q].y);
-                        acc[q].z = fmaf(gv, t.z, acc[q].z);
-                        acc[q].w = fmaf(gv, t.w, acc[q].w);
-                    }
+            for (int l = 0; l < MAXM; ++l) {
+                if (l < m) {
+                    const float gv = fsh[l * k + i];
+                    acc[l].x = fmaf(gv, t.x, acc[l].x);
+                    acc[l].y = fmaf(gv, t.y, acc[l].y);
                 }
             }
+        }
+        const bool d0 = (r < n) && (col0 == r), d1 = (r < n) && (col0 + 1 == r);
 #pragma unroll
-            for (int q = 0; q < kGroup; ++q) {
-                const int l = l0 + q;
-                if (l >= m) continue;
-                float v[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
-                if (r < n && r >= col0 && r < col0 + 4) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (col0 + e == r) v[e] += fsh[l * k];
+        for (int l = 0; l < MAXM; ++l) {
+            if (l >= m) break;
+            float v0 = acc[l].x, v1 = acc[l].y;
+            if (d0) v0 += fsh[l * k];
+            if (d1) v1 += fsh[l * k];
+            float* dst = rbase + (int64_t)l * rstride + idx;
+            if (!FO_CHK(dbg, (reinterpret_cast<uintptr_t>(dst) & 7) == 0, 302, l, idx)) continue;
+            *reinterpret_cast<float2*>(dst) = make_float2(v0, v1);
+            if (l == m - 1 && planes_last > 0) {
+                uint16_t* p = reinterpret_cast<uint16_t*>(rbase + (int64_t)l * rstride + plane_off) + idx;
+                const int64_t ps = np * np;
+                uint16_t a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+                if (!fp16) {
+                    __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
+                    float r1 = v0 - __bfloat162float(h0);
+                    __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                    a[0] = *reinterpret_cast<uint16_t*>(&h0);
+                    a[1] = *reinterpret_cast<uint16_t*>(&h1);
+                    a[2] = bf16_bits_c(r1 - __bfloat162float(h1));
+                    h0 = __float2bfloat16_rn(v1);
+                    r1 = v1 - __bfloat162float(h0);
+                    h1 = __float2bfloat16_rn(r1);
+                    b[0] = *reinterpret_cast<uint16_t*>(&h0);
+                    b[1] = *reinterpret_cast<uint16_t*>(&h1);
+                    b[2] = bf16_bits_c(r1 - __bfloat162float(h1));
+                } else {
+                    const float x0 = v0 * pscale, x1 = v1 * pscale;
+                    __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x0 - __half2float(__float2half_rn(x0)));
+                    a[0] = *reinterpret_cast<uint16_t*>(&h0);
+                    a[1] = *reinterpret_cast<uint16_t*>(&h1);
+                    h0 = __float2half_rn(x1);
+                    h1 = __float2half_rn(x1 - __half2float(h0));
+                    b[0] = *reinterpret_cast<uint16_t*>(&h0);
+                    b[1] = *reinterpret_cast<uint16_t*>(&h1);
                 }
-                float* dst = rbase + (int64_t)l * rstride + idx;
-                if (!FO_CHK(dbg, (reinterpret_cast<uintptr_t>(dst) & 15) == 0, 302, l, idx)) continue;
-                *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-                if (l == m - 1 && planes_last > 0) {
-                    uint16_t* p = reinterpret_cast<uint16_t*>(rbase + (int64_t)l * rstride + plane_off) + idx;
-                    const int64_t ps = np * np;
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (!fp16) {
-                            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[e]);
-                            p[e] = *reinterpret_cast<const uint16_t*>(&h0);
-                            if (planes_last > 1) {
-                                const float r1 = v[e] - __bfloat162float(h0);
-                                const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
-                                p[ps + e] = *reinterpret_cast<const uint16_t*>(&h1);
-                                if (planes_last > 2)
-                                    p[2 * ps + e] = bf16_bits_c(r1 - __bfloat162float(h1));
-                            }
-                        } else {
-                            const float vs = v[e] * pscale;
-                            const __half h0 = __float2half_rn(vs);
-                            p[e] = *reinterpret_cast<const uint16_t*>(&h0);
-                            if (planes_last > 1) {
-                                const __half h1 = __float2half_rn(vs - __half2float(h0));
-                                p[ps + e] = *reinterpret_cast<const uint16_t*>(&h1);
-                            }
-                        }
-                    }
-                }
+                for (int pl = 0; pl < 3; ++pl)
+                    if (pl < planes_last)
+                        *reinterpret_cast<uint32_t*>(p + pl * ps) = (uint32_t)a[pl] | ((uint32_t)b[pl] << 16);
             }
         }
     }
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(256) k_contract_f32(const double* __restrict__
 
 int grid_for(int64_t total, int threads) {
     int64_t b = (total + threads - 1) / threads;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > 152 * 16) b = 152 * 16;
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -366,11 +385,13 @@ cudaError_t launch_contract_f32(const double* g, int k, int m, const float* tbas
                                 int64_t np, int planes_last, int fp16, float pscale,
                                 int64_t plane_off_f, cudaStream_t s, int* dbg) {
     const size_t smem = (size_t)k * m * sizeof(float);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_contract_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_contract_f32<<<grid_for(np * np / 4, 256), 256, smem, s>>>(
-        g, k, m, tbase, tstride_f, rbase, rstride_f, n, np, planes_last, fp16, pscale,
-        plane_off_f, dbg);
+    const int blocks = grid_for(np * np / 2, 256);
+    if (m <= 32)
+        k_contract_f32<32><<<blocks, 256, smem, s>>>(g, k, m, tbase, tstride_f, rbase, rstride_f, n,
+                                                      np, planes_last, fp16, pscale, plane_off_f, dbg);
+    else
+        k_contract_f32<64><<<blocks, 256, smem, s>>>(g, k, m, tbase, tstride_f, rbase, rstride_f, n,
+                                                      np, planes_last, fp16, pscale, plane_off_f, dbg);
     return cudaGetLastError();
 }
 

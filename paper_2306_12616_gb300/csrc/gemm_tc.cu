@@ -4,30 +4,36 @@
 //
 // A_p, B_q are the 16-bit planes of float32 working matrices (A = sum_p A_p), staged by
 // TMA (cp.async.bulk.tensor, 64-byte swizzle) into a multi-stage shared-memory ring and
-// multiplied by tcgen05.mma (kind::f16, M = N = 128, K = 16) into float32 accumulators in
-// tensor memory. The epilogue applies the recurrence update (2 T_1 T_i - T_{i-1}, or
+// multiplied by tcgen05.mma (kind::f16, M = 128, N = 256, K = 16) into float32 accumulators
+// in tensor memory. The epilogue applies the recurrence update (2 T_1 T_i - T_{i-1}, or
 // 2 Y b_{l+1} - b_{l+2} + R_l for the Clenshaw giant steps) and writes the float32 master,
 // the split planes of the result (the next product's operand) or the final float64 P.
 //
 // Symmetric mode. Every matrix of the method is a polynomial in the symmetric X, so every
-// product of two of them is symmetric. Only the 128 x 128 tiles on or above the diagonal
-// are computed and each is written twice, at (r, c) and (c, r); the stored matrices are
-// then exactly symmetric, so reading B^T is exact, and half of the tensor work is saved.
+// product of two of them is symmetric. Only the tiles that hold an element on or above the
+// diagonal are computed, and each such element is written twice, at (r, c) and (c, r); the
+// stored matrices are then exactly symmetric, so reading B^T is exact, and about half of
+// the tensor work is saved.
 // (Reading B^T of a matrix that is only symmetric up to rounding makes the recurrence
 // unstable: in the eigenbasis of X the pair (T_ab, T_ba) is multiplied by a matrix with
 // eigenvalues +-2 sqrt(l_a l_b), which grows geometrically whenever l_a l_b < 0.)
 //
 // Accumulation. The tensor core rounds its float32 accumulator once per instruction, so a
-// long chain of MMAs into one accumulator loses accuracy linearly in K. The leading
-// product a_0 b_0 is therefore accumulated in segments of kSeg k-blocks, alternating
-// between two TMEM accumulators; the epilogue warps drain each finished segment into
-// float32 registers while the next one accumulates. The correction products (a_0 b_1,
-// a_1 b_0, ...), 2^-8 smaller, share a third accumulator for the whole K range.
+// long chain of MMAs into one accumulator loses accuracy linearly in K. Each k-block (32 k)
+// is therefore accumulated afresh into one of two TMEM accumulators (ping-pong) and drained
+// by the epilogue warps into float32 registers while the next k-block accumulates into the
+// other one. Within a k-block the correction products (a_0 b_1, a_1 b_0, ..., 2^-8 smaller)
+// are issued first, while the accumulator is still small, and the leading product a_0 b_0
+// last, so only two roundings per k-block happen at full magnitude.
 //
-// Roles (192 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs (warp 1 owns
-// the TMEM allocation), warps 2-5 drain TMEM lane quadrants (warp & 3) = tile rows. Every
-// mbarrier wait is bounded by a %globaltimer deadline: on expiry the CTA raises a device
-// error flag, drains what it has in flight (again bounded), frees its TMEM and exits.
+// Tiles are 128 x 256 (M x N): per MMA cycle this moves half the B bytes of a 128 x 128
+// tile, which matters because the split forms load 2 to 6 operand planes per k-block.
+//
+// Roles (320 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs (warp 1 owns the
+// TMEM allocation), warps 2-9 drain TMEM: warp w reads lane quadrant (w & 3) = 32 tile rows
+// and column half (w - 2) / 4. Every mbarrier wait is bounded by a %globaltimer deadline: on
+// expiry the CTA raises a device error flag, drains what it has in flight (again bounded),
+// frees its TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -161,15 +167,16 @@ __device__ __forceinline__ uint16_t bits_bf16(float v) {
     return *reinterpret_cast<uint16_t*>(&h);
 }
 
-constexpr int kBN = 128;          // tile columns (UMMA N)
-constexpr int kTmemCols = 512;    // main accumulators at columns 0 and 128, corrections at 256
+constexpr int kBN = 256;          // tile columns (UMMA N)
+constexpr int kTmemCols = 512;    // two accumulators of 256 columns
+constexpr int kDrainWarps = 8;    // 2 per TMEM lane quadrant, one per 128-column half
+constexpr int kThreads = 32 * (2 + kDrainWarps);
 
 template <int PA, int PB, int NPROD, bool F16>
 struct TcCfg {
-    static constexpr int kStageBytes = (PA + PB) * kBM * kRowBytes;
-    static constexpr int kStagesRaw = (200 * 1024) / kStageBytes;
+    static constexpr int kStageBytes = PA * kBM * kRowBytes + PB * kBN * kRowBytes;
+    static constexpr int kStagesRaw = (216 * 1024) / kStageBytes;
     static constexpr int kStages = kStagesRaw > 8 ? 8 : (kStagesRaw < 2 ? 2 : kStagesRaw);
-    static constexpr int kSeg = NPROD >= 3 ? 2 : 8;   // k-blocks per drained segment
     static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
     static constexpr uint32_t kIdesc = idesc_f16(kBN, F16);
     static_assert(kSmem <= 232448 - 64, "shared memory budget of one CTA exceeded");
@@ -226,12 +233,30 @@ __device__ __forceinline__ void split3(float x, bool f16, float pscale, uint16_t
     }
 }
 
+// Tile decode. Symmetric mode: the tiles of the 128-row block I that hold an element with
+// col >= row, i.e. column tiles J >= (128 I) / 256, enumerated row by row.
+__device__ __forceinline__ void tile_of(int bid, int tm, int tn, bool sym, int& I, int& J) {
+    if (sym) {
+        I = 0;
+        int b = bid;
+        for (;;) {
+            const int first = (I * kBM) / kBN;
+            const int cnt = tn - first;
+            if (b < cnt) { J = first + b; return; }
+            b -= cnt;
+            ++I;
+        }
+    }
+    I = bid / tn;
+    J = bid - I * tn;
+}
+
 template <int PA, int PB, int NPROD, bool F16, bool SYM>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const Epilogue ep, int np, int* err_flag) {
     using Cfg = TcCfg<PA, PB, NPROD, F16>;
-    constexpr int S = Cfg::kStages, G = Cfg::kSeg;
+    constexpr int S = Cfg::kStages;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -244,20 +269,11 @@ __global__ void __launch_bounds__(192, 1)
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = np / kBM;
+    const int tm = np / kBM, tn = (np + kBN - 1) / kBN;
     int I, J;
-    if (SYM) {
-        int b = blockIdx.x;
-        I = 0;
-        while (b >= t - I) { b -= t - I; ++I; }
-        J = I + b;
-    } else {
-        I = blockIdx.x / t;
-        J = blockIdx.x - I * t;
-    }
+    tile_of(blockIdx.x, tm, tn, SYM, I, J);
     const int m0 = I * kBM, n0 = J * kBN;
     const int nk = np / kBK;
-    const int nseg = (nk + G - 1) / G;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -267,7 +283,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&seg_full[b], 1);
-            mbar_init(&seg_empty[b], 128);
+            mbar_init(&seg_empty[b], 32 * kDrainWarps);
         }
         mbar_init(acc_full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -288,12 +304,12 @@ __global__ void __launch_bounds__(192, 1)
 
     auto stage_a = [&](int s, int p) { return smem + s * Cfg::kStageBytes + p * kBM * kRowBytes; };
     auto stage_b = [&](int s, int p) {
-        return smem + s * Cfg::kStageBytes + (PA + p) * kBM * kRowBytes;
+        return smem + s * Cfg::kStageBytes + PA * kBM * kRowBytes + p * kBN * kRowBytes;
     };
 
-    float sum[kBN];  // accumulated tile row of an epilogue thread
+    float sum[kBN / 2];  // a drain thread's 128 accumulated columns of its tile row
 #pragma unroll
-    for (int j = 0; j < kBN; ++j) sum[j] = 0.0f;
+    for (int j = 0; j < kBN / 2; ++j) sum[j] = 0.0f;
     bool ok = true;
 
     if (warp == 0) {
@@ -309,7 +325,7 @@ __global__ void __launch_bounds__(192, 1)
                         break;
                     }
                 }
-                if (!FO_CHK(ep.dbg, kb * kBK < np && m0 + kBM <= np && n0 + kBN <= np, 108, m0, n0)) {
+                if (!FO_CHK(ep.dbg, kb * kBK < np && m0 + kBM <= np && n0 < np, 108, m0, n0)) {
                     atomicExch(&abort_flag, 1);
                     break;
                 }
@@ -324,10 +340,8 @@ __global__ void __launch_bounds__(192, 1)
                 for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
                     mbar_wait(&full[kb % S], (kb / S) & 1, kDrainNs, nullptr);
             } else {
-                // Producer tail: wait until the MMA warp has released every stage, i.e. until
-                // the tcgen05.commit arrivals of the last S k-blocks have landed. Otherwise the
-                // CTA could exit with mbarrier arrivals in flight, which would then land in the
-                // shared memory of the next CTA scheduled on this SM.
+                // Producer tail: wait until the MMA warp has released every stage (the commit
+                // arrivals of the last S k-blocks have landed) before the CTA may exit.
                 for (int kb = (nk > S ? nk - S : 0); kb < nk; ++kb)
                     if (!mbar_wait(&empty[kb % S], (kb / S) & 1, kWaitNs, vabort)) {
                         atomicExch(err_flag, 1);
@@ -338,12 +352,11 @@ __global__ void __launch_bounds__(192, 1)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer
+            // ---------------- MMA issuer: one k-block per accumulator, corrections first
             for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % S, seg = kb / G, buf = seg & 1;
-                const bool seg_first = (kb % G) == 0;
-                if (seg_first && seg >= 2) {
-                    if (!mbar_wait(&seg_empty[buf], ((seg >> 1) - 1) & 1, kWaitNs, vabort)) {
+                const int s = kb % S, buf = kb & 1;
+                if (kb >= 2) {
+                    if (!mbar_wait(&seg_empty[buf], ((kb >> 1) - 1) & 1, kWaitNs, vabort)) {
                         atomicExch(&abort_flag, 1);
                         atomicExch(err_flag, 1);
                         break;
@@ -355,40 +368,43 @@ __global__ void __launch_bounds__(192, 1)
                     break;
                 }
                 fence_after();
+                const uint32_t d = tmem + buf * kBN;
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
-                    umma_f16(tmem + buf * kBN, sdesc_sw64(smem_u32(stage_a(s, 0)) + kk * 32),
-                             sdesc_sw64(smem_u32(stage_b(s, 0)) + kk * 32), Cfg::kIdesc,
-                             !(seg_first && kk == 0));
 #pragma unroll
                     for (int pr = 1; pr < NPROD; ++pr) {
-                        umma_f16(tmem + 2 * kBN,
-                                 sdesc_sw64(smem_u32(stage_a(s, prod_a(pr))) + kk * 32),
+                        umma_f16(d, sdesc_sw64(smem_u32(stage_a(s, prod_a(pr))) + kk * 32),
                                  sdesc_sw64(smem_u32(stage_b(s, prod_b(pr))) + kk * 32), Cfg::kIdesc,
-                                 !(kb == 0 && kk == 0 && pr == 1));
+                                 !(kk == 0 && pr == 1));
                     }
                 }
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    umma_f16(d, sdesc_sw64(smem_u32(stage_a(s, 0)) + kk * 32),
+                             sdesc_sw64(smem_u32(stage_b(s, 0)) + kk * 32), Cfg::kIdesc,
+                             (NPROD > 1) || kk > 0);
+                }
                 umma_commit(&empty[s]);
-                if ((kb % G) == G - 1 || kb == nk - 1) umma_commit(&seg_full[buf]);
+                umma_commit(&seg_full[buf]);
             }
             // arrives once every issued MMA has completed (also after an abort)
             umma_commit(acc_full);
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue warps, main loop: drain finished segments into registers
-        const int q = warp & 3;
-        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
-        for (int seg = 0; seg < nseg && ok; ++seg) {
-            const int buf = seg & 1;
-            if (!mbar_wait_warp(&seg_full[buf], (seg >> 1) & 1, kWaitNs, vabort)) {
+        // ---------------- drain warps: add every finished k-block to registers
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16) + half * (kBN / 2);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int buf = kb & 1;
+            if (!mbar_wait_warp(&seg_full[buf], (kb >> 1) & 1, kWaitNs, vabort)) {
                 ok = false;
                 break;
             }
             __syncwarp();
             fence_after();
 #pragma unroll
-            for (int cb = 0; cb < kBN / 32; ++cb) {
+            for (int cb = 0; cb < kBN / 64; ++cb) {
                 uint32_t r[32];
                 tmem_ld32(t_row + buf * kBN + cb * 32, r);
 #pragma unroll
@@ -397,19 +413,9 @@ __global__ void __launch_bounds__(192, 1)
             fence_before();
             mbar_arrive(&seg_empty[buf]);
         }
-        // every MMA has completed (corrections final) before TMEM is read for the last time
+        // every MMA has completed before TMEM is freed
         if (!mbar_wait_warp(acc_full, 0, kWaitNs, nullptr)) ok = false;
         __syncwarp();
-        fence_after();
-        if (ok && NPROD > 1) {
-#pragma unroll
-            for (int cb = 0; cb < kBN / 32; ++cb) {
-                uint32_t r[32];
-                tmem_ld32(t_row + 2 * kBN + cb * 32, r);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
-            }
-        }
         if (!ok && lane == 0) {
             atomicExch(&abort_flag, 1);
             atomicExch(err_flag, 1);
@@ -423,57 +429,75 @@ __global__ void __launch_bounds__(192, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
     }
-    if (warp < 2 || *vabort) return;  // uniform across the four epilogue warps
+    if (warp < 2 || *vabort) return;  // uniform across the drain warps
 
-    // ---------------- epilogue warps: update and store through shared memory. The stage ring
-    // is idle (every TMA load was consumed, every MMA completed), so it holds the 128 x 128
+    // ---------------- drain warps: update and store through shared memory. The stage ring
+    // is idle (every TMA load was consumed, every MMA completed), so it holds the 128 x 256
     // float32 result tile; all global traffic below is coalesced across the warp.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     constexpr int LD = kBN + 1;
     float* tile = reinterpret_cast<float*>(smem);
-    const int q = warp & 3;
-    const int rl = q * 32 + lane;
+    {
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int rl = q * 32 + lane;
 #pragma unroll
-    for (int c = 0; c < kBN; ++c) tile[rl * LD + c] = ep.alpha * sum[c];
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+        for (int c = 0; c < kBN / 2; ++c) tile[rl * LD + half * (kBN / 2) + c] = ep.alpha * sum[c];
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kDrainWarps) : "memory");
 
-    const bool diag = SYM && (I == J);
     const int64_t ld = ep.ld;
-    // store of the element pair (grow, gcol), (grow, gcol + 1); gcol even
-    auto store_pair = [&](int64_t grow, int64_t gcol, float v0, float v1) {
+    const int ew = warp - 2;  // 0..7
+    // store of the pair (grow, gcol), (grow, gcol + 1) for the elements whose flag is set
+    auto store_pair = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1) {
+        if (!(w0 || w1)) return;
         if (ep.out64) {
             if (grow < ep.n_real) {
                 double* dst = ep.out64 + grow * ep.ldo + gcol;
-                if (gcol < ep.n_real) dst[0] = (double)v0;
-                if (gcol + 1 < ep.n_real) dst[1] = (double)v1;
+                if (w0 && gcol < ep.n_real) dst[0] = (double)v0;
+                if (w1 && gcol + 1 < ep.n_real) dst[1] = (double)v1;
             }
             return;
         }
         const int64_t o = grow * ld + gcol;
         if (!FO_CHK(ep.dbg, o >= 0 && o + 2 <= ld * ld, 111, grow, gcol)) return;
-        if (ep.out.x) *reinterpret_cast<float2*>(ep.out.x + o) = make_float2(v0, v1);
+        uint16_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
         if (ep.planes > 0) {
-            uint16_t a0, a1, a2, b0, b1, b2;
             split3(v0, F16, ep.plane_scale, a0, a1, a2);
             split3(v1, F16, ep.plane_scale, b0, b1, b2);
-            uint16_t* pl = ep.out.planes + o;
-            *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0 << 16);
-            if (ep.planes > 1)
-                *reinterpret_cast<uint32_t*>(pl + ep.out.plane_stride) = (uint32_t)a1 | ((uint32_t)b1 << 16);
-            if (ep.planes > 2)
-                *reinterpret_cast<uint32_t*>(pl + 2 * ep.out.plane_stride) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+        }
+        if (w0 && w1) {
+            if (ep.out.x) *reinterpret_cast<float2*>(ep.out.x + o) = make_float2(v0, v1);
+            if (ep.planes > 0) {
+                uint16_t* pl = ep.out.planes + o;
+                *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0 << 16);
+                if (ep.planes > 1)
+                    *reinterpret_cast<uint32_t*>(pl + ep.out.plane_stride) = (uint32_t)a1 | ((uint32_t)b1 << 16);
+                if (ep.planes > 2)
+                    *reinterpret_cast<uint32_t*>(pl + 2 * ep.out.plane_stride) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+            }
+        } else {
+            const int e = w0 ? 0 : 1;
+            const float v = w0 ? v0 : v1;
+            if (ep.out.x) ep.out.x[o + e] = v;
+            if (ep.planes > 0) {
+                uint16_t* pl = ep.out.planes + o + e;
+                pl[0] = w0 ? a0 : b0;
+                if (ep.planes > 1) pl[ep.out.plane_stride] = w0 ? a1 : b1;
+                if (ep.planes > 2) pl[2 * ep.out.plane_stride] = w0 ? a2 : b2;
+            }
         }
     };
 
-    // row pass: this warp's 32 tile rows, lanes on column pairs; applies beta C + D + shift
-    const int r0 = q * 32;
-    for (int rr = 0; rr < 32; ++rr) {
-        const int r = r0 + rr;
+    // row pass: each drain warp takes 16 tile rows, lanes on column pairs; applies
+    // beta C + D + shift and stores the entries with col >= row (all of them when not SYM)
+    for (int rr = 0; rr < kBM / kDrainWarps; ++rr) {
+        const int r = ew * (kBM / kDrainWarps) + rr;
         const int64_t grow = (int64_t)m0 + r;
 #pragma unroll
         for (int h = 0; h < kBN / 64; ++h) {
             const int c = h * 64 + 2 * lane;
             const int64_t gcol = (int64_t)n0 + c;
+            if (gcol >= np) continue;
             const int64_t o = grow * ld + gcol;
             float v0 = tile[r * LD + c], v1 = tile[r * LD + c + 1];
             if (ep.C) {
@@ -492,40 +516,22 @@ __global__ void __launch_bounds__(192, 1)
             }
             tile[r * LD + c] = v0;
             tile[r * LD + c + 1] = v1;
-            if (!diag) store_pair(grow, gcol, v0, v1);
+            store_pair(grow, gcol, v0, v1, !SYM || gcol >= grow, !SYM || gcol + 1 >= grow);
         }
     }
     if (!SYM) return;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    if (diag) {
-        // diagonal tile: the lower triangle takes the values of the upper one
-        for (int rr = 0; rr < 32; ++rr) {
-            const int r = r0 + rr;
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kDrainWarps) : "memory");
+    // mirror pass: output row n0 + c holds tile column c for the entries with col > row;
+    // each drain warp takes 32 tile columns, lanes on row pairs
+    for (int cc = 0; cc < kBN / kDrainWarps; ++cc) {
+        const int c = ew * (kBN / kDrainWarps) + cc;
+        const int64_t grow = (int64_t)n0 + c;       // output row
+        if (grow >= np) break;
 #pragma unroll
-            for (int h = 0; h < kBN / 64; ++h) {
-                const int c = h * 64 + 2 * lane;
-                if (c < r) tile[r * LD + c] = tile[c * LD + r];
-                if (c + 1 < r) tile[r * LD + c + 1] = tile[(c + 1) * LD + r];
-            }
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        for (int rr = 0; rr < 32; ++rr) {
-            const int r = r0 + rr;
-#pragma unroll
-            for (int h = 0; h < kBN / 64; ++h) {
-                const int c = h * 64 + 2 * lane;
-                store_pair((int64_t)m0 + r, (int64_t)n0 + c, tile[r * LD + c], tile[r * LD + c + 1]);
-            }
-        }
-    } else {
-        // mirror of an off-diagonal tile: output row n0 + c holds tile column c
-        for (int cc = 0; cc < 32; ++cc) {
-            const int c = r0 + cc;
-#pragma unroll
-            for (int h = 0; h < kBN / 64; ++h) {
-                const int r = h * 64 + 2 * lane;
-                store_pair((int64_t)n0 + c, (int64_t)m0 + r, tile[r * LD + c], tile[(r + 1) * LD + c]);
-            }
+        for (int h = 0; h < kBM / 64; ++h) {
+            const int r = h * 64 + 2 * lane;
+            const int64_t gcol = (int64_t)m0 + r;   // output column
+            store_pair(grow, gcol, tile[r * LD + c], tile[(r + 1) * LD + c], grow > gcol, grow > gcol + 1);
         }
     }
 }
@@ -548,14 +554,14 @@ EncodeFn get_encode(std::string* err) {
     return fn;
 }
 
-// 3-D tensor map over a slot's planes: (column k, row, plane), 16-bit elements, 32 x 128 box.
+// 3-D tensor map over a slot's planes: (column k, row, plane), 16-bit elements, 32 x rows box.
 bool make_map(CUtensorMap* map, const uint16_t* planes, int64_t np, int64_t plane_stride,
-              int nplanes, bool fp16, std::string* err) {
+              int nplanes, int box_rows, bool fp16, std::string* err) {
     EncodeFn enc = get_encode(err);
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)np, (cuuint64_t)np, (cuuint64_t)nplanes};
     cuuint64_t strides[2] = {(cuuint64_t)np * 2, (cuuint64_t)plane_stride * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)kBM, 1};
+    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                      const_cast<uint16_t*>(planes), dims, strides, box, estr,
@@ -568,6 +574,14 @@ bool make_map(CUtensorMap* map, const uint16_t* planes, int64_t np, int64_t plan
     return true;
 }
 
+int64_t tiles_for(int64_t np, int sym) {
+    const int64_t tm = np / kBM, tn = (np + kBN - 1) / kBN;
+    if (!sym) return tm * tn;
+    int64_t c = 0;
+    for (int64_t I = 0; I < tm; ++I) c += tn - (I * kBM) / kBN;
+    return c;
+}
+
 template <int PA, int PB, int NPROD, bool F16, bool SYM>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Epilogue& ep, int64_t np,
                       int* err_flag, cudaStream_t s) {
@@ -575,9 +589,7 @@ cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Epilog
     auto kern = k_tc_gemm<PA, PB, NPROD, F16, SYM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
     if (e != cudaSuccess) return e;
-    const int64_t t = np / kBM;
-    const int64_t tiles = SYM ? t * (t + 1) / 2 : t * t;
-    kern<<<(unsigned)tiles, 192, Cfg::kSmem, s>>>(ma, mb, ep, (int)np, err_flag);
+    kern<<<(unsigned)tiles_for(np, SYM ? 1 : 0), kThreads, Cfg::kSmem, s>>>(ma, mb, ep, (int)np, err_flag);
     return cudaGetLastError();
 }
 
@@ -599,23 +611,20 @@ int tc_planes(int prec) {
     }
 }
 
-int64_t tc_tiles(int64_t np, int sym) {
-    const int64_t t = np / kBM;
-    return sym ? t * (t + 1) / 2 : t * t;
-}
+int64_t tc_tiles(int64_t np, int sym) { return tiles_for(np, sym); }
 
 cudaError_t tc_gemm(int prec, int64_t np, const MatF32& A, const MatF32& B, const Epilogue& ep,
                     int sym, int* flag, cudaStream_t s, std::string* err) {
     const int planes = tc_planes(prec);
-    if (planes == 0 || np % kBM != 0 || np % kBN != 0) {
+    if (planes == 0 || np % kBM != 0) {
         if (err) *err = "tc_gemm: unsupported precision or size";
         return cudaErrorInvalidValue;
     }
     if (!flag) return cudaErrorInvalidValue;
     const bool f16 = prec == FO_PREC_FP16X2;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A.planes, np, A.plane_stride, planes, f16, err)) return cudaErrorInvalidValue;
-    if (!make_map(&mb, B.planes, np, B.plane_stride, planes, f16, err)) return cudaErrorInvalidValue;
+    if (!make_map(&ma, A.planes, np, A.plane_stride, planes, kBM, f16, err)) return cudaErrorInvalidValue;
+    if (!make_map(&mb, B.planes, np, B.plane_stride, planes, kBN, f16, err)) return cudaErrorInvalidValue;
     switch (prec) {
         case FO_PREC_BF16X3: return dispatch_sym<3, 3, 6, false>(sym, ma, mb, ep, np, flag, s);
         case FO_PREC_FP16X2: return dispatch_sym<2, 2, 3, true>(sym, ma, mb, ep, np, flag, s);

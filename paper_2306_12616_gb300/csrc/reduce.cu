@@ -248,81 +248,101 @@ __global__ void k_diag_sums(const char* base, int64_t slot_stride_bytes, int64_t
 
 // --------------------------------------------------------- Frobenius inner products
 // gram[g * nbaby + b] = <S_{giant0+g}, S_{baby0+b}>_F over all np*np entries (the zero
-// border contributes nothing). Each block stages kChunk entries of every matrix in shared
-// memory (entry-major, so one entry's values are contiguous), then each thread owns a
-// 4 x 4 tile of (giant, baby) pairs and a slice of the chunk. float32 products are summed
-// in float32 within a chunk and in float64 across chunks.
-constexpr int kChunk = 128;
+// border contributes nothing). A block stages kChunk consecutive entries of every matrix in
+// shared memory, matrix-major (row s holds the chunk of matrix s), with float4 loads. Each
+// warp owns up to kTPW 4 x 4 tiles of (giant, baby) pairs; its lanes walk consecutive
+// entries of a row, so shared-memory reads are conflict free. Within a chunk the products
+// are summed in T; across chunks float32 sums are compensated (Kahan), float64 sums are
+// plain. Lanes are reduced by shuffles at the end into per-block float64 partials.
+constexpr int kChunk = 256;
+constexpr int kRowPad = 4;
+constexpr int kTPW = 2;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram(const char* base, int64_t slot_stride_bytes,
-                                              int giant0, int ngiant, int baby0, int nbaby,
-                                              int64_t total, double* partials) {
+__global__ void __launch_bounds__(512) k_gram(const char* base, int64_t slot_stride_bytes,
+                                               int giant0, int ngiant, int baby0, int nbaby,
+                                               int64_t total, double* partials) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
+    constexpr int RS = kChunk + kRowPad;                 // row stride (elements)
     const int ng4 = (ngiant + 3) / 4, nb4 = (nbaby + 3) / 4;
-    const int width = 4 * (ng4 + nb4);       // values per entry in shared memory
+    const int nrows = 4 * (ng4 + nb4);
     const int ntiles = ng4 * nb4;
-    const int nsub = blockDim.x / ntiles;    // >= 1 (host guarantees ntiles <= blockDim.x)
-    const int tid = threadIdx.x;
-    const int tile = tid % ntiles, sub = tid / ntiles;
-    const bool active = sub < nsub;
-    const int tg = tile / nb4, tb = tile % nb4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-    double accd[16];
+    T acc[kTPW][16];
+    T cmp[kTPW][16];   // Kahan compensation (float32 only)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) accd[q] = 0.0;
+    for (int t = 0; t < kTPW; ++t)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) { acc[t][q] = T(0); cmp[t][q] = T(0); }
 
+    constexpr int V = 16 / sizeof(T);                    // elements per 16-byte load
     const int64_t nchunks = (total + kChunk - 1) / kChunk;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int64_t e0 = ch * kChunk;
-        // stage: entry e, matrix column s (giants first, then babies, padded to 4)
-        for (int q = tid; q < kChunk * width; q += blockDim.x) {
-            const int e = q % kChunk, s = q / kChunk;
-            T v = T(0);
+        for (int q = threadIdx.x; q < nrows * (kChunk / V); q += blockDim.x) {
+            const int srow = q / (kChunk / V), ev = (q % (kChunk / V)) * V;
             int slot = -1;
-            if (s < 4 * ng4) { if (s < ngiant) slot = giant0 + s; }
-            else { const int b = s - 4 * ng4; if (b < nbaby) slot = baby0 + b; }
-            if (slot >= 0 && e0 + e < total)
-                v = reinterpret_cast<const T*>(base + slot_stride_bytes * slot)[e0 + e];
-            sm[e * width + s] = v;
+            if (srow < 4 * ng4) { if (srow < ngiant) slot = giant0 + srow; }
+            else { const int bb = srow - 4 * ng4; if (bb < nbaby) slot = baby0 + bb; }
+            T* dst = sm + srow * RS + ev;
+            if (slot >= 0 && e0 + ev + V <= total) {
+                const T* src = reinterpret_cast<const T*>(base + slot_stride_bytes * slot) + e0 + ev;
+                *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) dst[v] = T(0);
+            }
         }
         __syncthreads();
-        if (active) {
-            T acc[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = T(0);
-            for (int e = sub; e < kChunk; e += nsub) {
-                const T* row = sm + e * width;
+        for (int t = 0; t < kTPW; ++t) {
+            const int tile = warp + t * nwarps;
+            if (tile >= ntiles) break;                   // uniform across the warp
+            const int g0 = 4 * (tile / nb4), b0 = 4 * ng4 + 4 * (tile % nb4);
+            T c16[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) c16[q] = T(0);
+            for (int e = lane; e < kChunk; e += 32) {
                 T gv[4], bv[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) gv[a] = row[4 * tg + a];
+                for (int a = 0; a < 4; ++a) gv[a] = sm[(g0 + a) * RS + e];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) bv[b] = row[4 * ng4 + 4 * tb + b];
+                for (int b = 0; b < 4; ++b) bv[b] = sm[(b0 + b) * RS + e];
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[4 * a + b] = fma(gv[a], bv[b], acc[4 * a + b]);
+                    for (int b = 0; b < 4; ++b) c16[4 * a + b] = fma(gv[a], bv[b], c16[4 * a + b]);
             }
 #pragma unroll
-            for (int q = 0; q < 16; ++q) accd[q] += (double)acc[q];
+            for (int q = 0; q < 16; ++q) {
+                if (sizeof(T) == 4) {
+                    const T y = c16[q] - cmp[t][q];
+                    const T s2 = acc[t][q] + y;
+                    cmp[t][q] = (s2 - acc[t][q]) - y;
+                    acc[t][q] = s2;
+                } else {
+                    acc[t][q] += c16[q];
+                }
+            }
         }
         __syncthreads();
     }
-    // reduce the nsub slices of each tile in a fixed order through shared memory
-    double* red = reinterpret_cast<double*>(smem_raw);
-    if (active) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) red[(sub * ntiles + tile) * 16 + q] = accd[q];
-    }
-    __syncthreads();
     const int npairs = ngiant * nbaby;
-    for (int pq = tid; pq < npairs; pq += blockDim.x) {
-        const int g = pq / nbaby, b = pq % nbaby;
-        const int t = (g / 4) * nb4 + (b / 4), q = (g % 4) * 4 + (b % 4);
-        double s = 0.0;
-        for (int u = 0; u < nsub; ++u) s += red[(u * ntiles + t) * 16 + q];
-        partials[(int64_t)blockIdx.x * npairs + pq] = s;
+#pragma unroll
+    for (int t = 0; t < kTPW; ++t) {
+        const int tile = warp + t * nwarps;
+        if (tile >= ntiles) break;
+        const int tg = tile / nb4, tb = tile % nb4;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            double v = (double)acc[t][q] - (double)cmp[t][q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            const int g = 4 * tg + q / 4, b = 4 * tb + q % 4;
+            if (lane == 0 && g < ngiant && b < nbaby)
+                partials[(int64_t)blockIdx.x * npairs + g * nbaby + b] = v;
+        }
     }
 }
 
@@ -483,17 +503,26 @@ cudaError_t launch_gram(const void* base, int64_t slot_stride_bytes, int giant0,
                         int baby0, int nbaby, int64_t np, int is_f64, double* partials,
                         int max_blocks, double* out, cudaStream_t s) {
     if (ngiant <= 0 || nbaby <= 0) return cudaSuccess;
-    const int ng4 = (ngiant + 3) / 4, nb4 = (nbaby + 3) / 4;
-    if (ng4 * nb4 > 256) return cudaErrorInvalidValue;
-    const int width = 4 * (ng4 + nb4);
-    const int threads = 256;
-    const int nsub = threads / (ng4 * nb4);
+    if (nbaby > 32) return cudaErrorInvalidValue;
+    const int threads = 512;
+    const int max_tiles = (threads / 32) * kTPW;
+    const int nb4 = (nbaby + 3) / 4;
+    const int gmax = 4 * (max_tiles / nb4);           // giants per launch
+    if (ngiant > gmax) {
+        // giant-major output: one launch per group of giants
+        for (int g = 0; g < ngiant; g += gmax) {
+            const int ng = ngiant - g < gmax ? ngiant - g : gmax;
+            cudaError_t e = launch_gram(base, slot_stride_bytes, giant0 + g, ng, baby0, nbaby, np,
+                                        is_f64, partials, max_blocks, out + (int64_t)g * nbaby, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const int ng4 = (ngiant + 3) / 4;
     const size_t elem = is_f64 ? 8 : 4;
-    size_t stage = (size_t)kChunk * width * elem;
-    size_t red = (size_t)nsub * ng4 * nb4 * 16 * 8;
-    size_t smem = stage > red ? stage : red;
-    const int blocks = gram_blocks(np, ngiant, nbaby) < max_blocks ? gram_blocks(np, ngiant, nbaby)
-                                                                   : max_blocks;
+    const size_t smem = (size_t)4 * (ng4 + nb4) * (kChunk + kRowPad) * elem;
+    int blocks = gram_blocks(np, ngiant, nbaby);
+    if (blocks > max_blocks) blocks = max_blocks;
     const char* b = reinterpret_cast<const char*>(base);
     if (is_f64) {
         cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
