@@ -66,7 +66,9 @@ typedef enum {
 
 /* Flags (fo_params.flags). */
 #define FO_FLAG_TRACE_ONLY_DIAG  0x1u  /* reserved */
-#define FO_FLAG_NO_RESULT_SYNC   0x2u  /* fo_density_matrix: never block, leave fo_result untouched */
+#define FO_FLAG_NO_RESULT_SYNC   0x2u  /* density-matrix calls: never block, leave fo_result untouched */
+#define FO_FLAG_GRAPH            0x4u  /* capture the call's kernels into a CUDA graph kept with its
+                                          plan and replay it on later calls with the same plan */
 
 typedef struct {
     int32_t n_terms;          /* number of coefficients c_0..c_{n_terms-1}, >= 1 */
@@ -80,6 +82,11 @@ typedef struct {
     double  emin, emax;       /* spectral bounds when use_given_bounds (emax > emin) */
     int32_t max_bisect;       /* bisection cap; 0 = 200 */
     uint32_t flags;           /* FO_FLAG_* */
+    double  tr_tol;           /* FO_MU_LEARNED: accept P when |tr P - N_e| <= tr_tol; 0 = default
+                                 (1e-8 max(1, N_e) for FP64, 2e-6 n for the split forms) */
+    int32_t max_newton;       /* FO_MU_LEARNED: trace-corrected re-evaluations of P before the
+                                 bisection fallback; 0 = 2, < 0 = none */
+    int32_t tile_n;           /* tensor-core tile width: 0 = autotune per plan, or 128 / 256 */
 } fo_params;
 
 typedef struct {
@@ -93,8 +100,10 @@ typedef struct {
     int32_t bisect_iters;     /* bisection halvings (0 if not bisected) */
     int32_t learned_accepted; /* 1 if the learned mu was kept */
     int32_t status;           /* fo_status of the device-side stages */
-    int32_t n_launches;       /* kernels of this library launched by the call */
-    int32_t reserved;
+    int32_t n_launches;       /* kernels of this library launched by the call (whole batch) */
+    int32_t tile_n;           /* tensor-core tile width used (0 for FP64) */
+    int32_t evals;            /* evaluations of P (1 unless FO_MU_LEARNED corrected mu) */
+    int32_t order;            /* expansion order proposed by the learned model (0 if none) */
 } fo_result;
 
 /* Stages of a density-matrix call, as recorded by the profiler. */
@@ -193,6 +202,26 @@ fo_status fo_density_matrix(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld
                             fo_result *res, void *stream);
 
 /*
+ * Density matrices of a batch of independent Hamiltonians of different sizes (e.g. the
+ * replicas of a molecular-dynamics run) in one call: every stage of the method is one launch
+ * over the whole batch (the products as one grouped tensor-core launch per step whose tiles
+ * span all instances, largest first), so small instances fill the GPU together.
+ *  - dH[b], dP[b]: device pointers of instance b (host array of batch pointers), n[b] its
+ *    size, ld[b] / ldp[b] its leading dimensions (NULL: n[b]), n_e[b] its electron count,
+ *    kT[b] its temperature (NULL: params->kT). All other parameters are shared.
+ *  - The plan of a batch (sizes, layout, tensor maps, tile width) is cached in the context
+ *    and reused while the sizes and parameters repeat; with FO_FLAG_GRAPH the whole call is
+ *    replayed as one CUDA graph.
+ *  - res: host array of batch results (in the caller's order), or NULL. With res != NULL
+ *    (and no FO_FLAG_NO_RESULT_SYNC) the call synchronises and returns the first failing
+ *    instance's status; otherwise it never blocks.
+ */
+fo_status fo_density_matrix_batched(fo_ctx *ctx, int32_t batch, const double *const *dH,
+                                    const int64_t *n, const int64_t *ld, const double *n_e,
+                                    const double *kT, const fo_params *params, double *const *dP,
+                                    const int64_t *ldp, fo_result *res, void *stream);
+
+/*
  * Same as fo_density_matrix with host buffers: copies hH to the device, runs, and
  * copies P back to hP (hP[n x n, ldp]). Pinned host memory makes the copies
  * asynchronous; the call always synchronises the stream before returning.
@@ -213,17 +242,6 @@ fo_status fo_moments(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld,
                      double *d_tau, void *stream);
 
 /*
- * One recurrence product on float32 matrices (the kernel behind every step of the
- * expansion): dOut = alpha * A B^T + beta * C + D + shift * I_n, with A, B, C, D, dOut
- * n x n row-major float32 with leading dimension ld (C, D may be NULL), run on the tensor
- * cores in the split form `precision` (FO_PREC_BF16X3, FP16X2 or BF16X1; FP64 is
- * rejected). With symmetric != 0 only the entries on or above the diagonal are computed
- * and mirrored (the form the solver uses: the result is exactly symmetric, valid when the
- * true result is symmetric, e.g. A and B commuting symmetric matrices; then A B^T = A B);
- * with symmetric == 0 the full A B^T is computed. FP16X2 needs |entries| <= 1 in A and B.
- * Asynchronous.
- */
-/*
  * Enable (1) or disable (0) the stage profiler of this context; enabling clears it. While
  * enabled every density-matrix call records CUDA events around its stages.
  */
@@ -234,6 +252,17 @@ fo_status fo_profile_enable(fo_ctx *ctx, int32_t enable);
  */
 fo_status fo_profile_read(fo_ctx *ctx, fo_profile *out, int32_t reset);
 
+/*
+ * One recurrence product on float32 matrices (the kernel behind every step of the
+ * expansion): dOut = alpha * A B^T + beta * C + D + shift * I_n, with A, B, C, D, dOut
+ * n x n row-major float32 with leading dimension ld (C, D may be NULL), run on the tensor
+ * cores in the split form `precision` (FO_PREC_BF16X3, FP16X2 or BF16X1; FP64 is
+ * rejected). With symmetric != 0 only the entries on or above the diagonal are computed
+ * and mirrored (the form the solver uses: the result is exactly symmetric, valid when the
+ * true result is symmetric, e.g. A and B commuting symmetric matrices; then A B^T = A B);
+ * with symmetric == 0 the full A B^T is computed. FP16X2 needs |entries| <= 1 in A and B.
+ * Asynchronous.
+ */
 fo_status fo_recurrence_product(fo_ctx *ctx, int32_t precision, int32_t symmetric, int64_t n,
                                 int64_t ld, const float *dA, const float *dB, const float *dC,
                                 const float *dD, float alpha, float beta, float shift,

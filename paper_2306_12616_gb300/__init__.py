@@ -16,11 +16,11 @@ from dataclasses import dataclass
 
 __all__ = [
     "FO_OK", "FO_PREC_FP64", "FO_PREC_BF16X3", "FO_PREC_FP16X2", "FO_PREC_BF16X1",
-    "FO_MU_FIXED", "FO_MU_BISECT", "FO_MU_LEARNED", "FO_FLAG_NO_RESULT_SYNC",
+    "FO_MU_FIXED", "FO_MU_BISECT", "FO_MU_LEARNED", "FO_FLAG_NO_RESULT_SYNC", "FO_FLAG_GRAPH",
     "FoParams", "FoResult", "FermiError", "lib", "library_path", "EXPORTED_SYMBOLS",
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
-    "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
+    "fo_density_matrix_batched", "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
     "fo_spectral_bounds_noalloc", "FO_NOALLOC_MAX_N",
     "STAGE_NAMES", "Solver", "PRECISIONS", "MU_MODES",
 ]
@@ -31,6 +31,7 @@ FO_ERR_NO_BRACKET, FO_ERR_NOT_CONVERGED, FO_ERR_DEVICE_TIMEOUT, FO_ERR_UNSUPPORT
 FO_PREC_FP64, FO_PREC_BF16X3, FO_PREC_FP16X2, FO_PREC_BF16X1 = 0, 1, 2, 3
 FO_MU_FIXED, FO_MU_BISECT, FO_MU_LEARNED = 0, 1, 2
 FO_FLAG_NO_RESULT_SYNC = 0x2
+FO_FLAG_GRAPH = 0x4
 
 PRECISIONS = {"fp64": FO_PREC_FP64, "bf16x3": FO_PREC_BF16X3, "fp16x2": FO_PREC_FP16X2,
               "bf16x1": FO_PREC_BF16X1}
@@ -40,7 +41,7 @@ MU_MODES = {"fixed": FO_MU_FIXED, "bisect": FO_MU_BISECT, "learned": FO_MU_LEARN
 EXPORTED_SYMBOLS = (
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
-    "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read",
+    "fo_density_matrix_batched", "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read",
     "fo_spectral_bounds_noalloc",
 )
 FO_NOALLOC_MAX_N = 32768
@@ -52,7 +53,8 @@ class FoParams(ctypes.Structure):
         ("mu", ctypes.c_double), ("precision", ctypes.c_int32), ("mu_mode", ctypes.c_int32),
         ("use_given_bounds", ctypes.c_int32), ("n_quad", ctypes.c_int32),
         ("emin", ctypes.c_double), ("emax", ctypes.c_double), ("max_bisect", ctypes.c_int32),
-        ("flags", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32), ("tr_tol", ctypes.c_double), ("max_newton", ctypes.c_int32),
+        ("tile_n", ctypes.c_int32),
     ]
 
 
@@ -62,7 +64,8 @@ class FoResult(ctypes.Structure):
         ("frob2", ctypes.c_double), ("emin", ctypes.c_double), ("emax", ctypes.c_double),
         ("k", ctypes.c_int32), ("m", ctypes.c_int32), ("n_gemm", ctypes.c_int32),
         ("bisect_iters", ctypes.c_int32), ("learned_accepted", ctypes.c_int32),
-        ("status", ctypes.c_int32), ("n_launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("status", ctypes.c_int32), ("n_launches", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+        ("evals", ctypes.c_int32), ("order", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -124,6 +127,9 @@ def lib() -> ctypes.CDLL:
             "fo_density_matrix_host": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_d,
                                                       ctypes.POINTER(FoParams), _c_ptr, _c_i64,
                                                       ctypes.POINTER(FoResult), _c_ptr]),
+            "fo_density_matrix_batched": (ctypes.c_int, [_c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                                         _c_ptr, ctypes.POINTER(FoParams), _c_ptr, _c_ptr,
+                                                         _c_ptr, _c_ptr]),
             "fo_moments": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_ptr, _c_i32, _c_i32,
                                           _c_ptr, _c_ptr]),
             "fo_profile_enable": (ctypes.c_int, [_c_ptr, _c_i32]),
@@ -193,6 +199,14 @@ def fo_density_matrix_host(ctx, h_h, n, ld, n_e, params: FoParams, h_p, ldp,
                                         stream)
 
 
+def fo_density_matrix_batched(ctx, batch, d_h_ptrs, n, ld, n_e, kT, params: FoParams, d_p_ptrs,
+                              ldp, results, stream=0) -> int:
+    """Arrays are ctypes arrays (or None where the header allows NULL); results is a ctypes
+    array of FoResult of length batch, or None."""
+    return lib().fo_density_matrix_batched(ctx, batch, d_h_ptrs, n, ld, n_e, kT, ctypes.byref(params),
+                                           d_p_ptrs, ldp, results, stream)
+
+
 def fo_moments(ctx, d_h, n, ld, d_bounds, n_moments, precision, d_tau, stream=0) -> int:
     return lib().fo_moments(ctx, d_h, n, ld, d_bounds, n_moments, precision, d_tau, stream)
 
@@ -248,7 +262,8 @@ class Solver:
     @staticmethod
     def params(n_terms: int, kT: float, *, mu: float = 0.0, precision: str | int = "fp64",
                mu_mode: str | int = "bisect", k: int = 0, bounds=None, n_quad: int = 0,
-               max_bisect: int = 0, flags: int = 0) -> FoParams:
+               max_bisect: int = 0, flags: int = 0, tile_n: int = 0, tr_tol: float = 0.0,
+               max_newton: int = 0) -> FoParams:
         p = FoParams()
         p.n_terms, p.k, p.kT, p.mu = n_terms, k, kT, mu
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
@@ -256,6 +271,7 @@ class Solver:
         if bounds is not None:
             p.use_given_bounds, p.emin, p.emax = 1, float(bounds[0]), float(bounds[1])
         p.n_quad, p.max_bisect, p.flags = n_quad, max_bisect, flags
+        p.tile_n, p.tr_tol, p.max_newton = tile_n, tr_tol, max_newton
         return p
 
     def spectral_bounds(self, h, stream=None):
@@ -282,6 +298,31 @@ class Solver:
         self._check(fo_density_matrix(self.ctx, h.data_ptr(), n, h.stride(0), float(n_e), params,
                                       p.data_ptr(), p.stride(0), res, _stream_handle(stream)))
         return p, (res.as_dict() if res is not None else None)
+
+    def density_matrix_batched(self, hs, n_e, params: FoParams, kT=None, outs=None, stream=None,
+                               sync: bool = True):
+        """hs: list of CUDA float64 (n_b x n_b) tensors; n_e, kT: per-instance sequences
+        (kT None: params.kT). Returns (list of P tensors, list of result dicts or None)."""
+        import torch
+        B = len(hs)
+        for h in hs:
+            assert h.dtype == torch.float64 and h.is_cuda and h.stride(1) == 1
+        ps = outs if outs is not None else [torch.empty((h.shape[0], h.shape[0]), dtype=torch.float64,
+                                                        device=h.device) for h in hs]
+        ptr = ctypes.c_void_p * B
+        i64 = ctypes.c_int64 * B
+        dbl = ctypes.c_double * B
+        d_h = ptr(*[h.data_ptr() for h in hs])
+        d_p = ptr(*[p.data_ptr() for p in ps])
+        n = i64(*[h.shape[0] for h in hs])
+        ld = i64(*[h.stride(0) for h in hs])
+        ldp = i64(*[p.stride(0) for p in ps])
+        ne = dbl(*[float(x) for x in n_e])
+        kt = dbl(*[float(x) for x in kT]) if kT is not None else None
+        res = (FoResult * B)() if sync else None
+        self._check(fo_density_matrix_batched(self.ctx, B, d_h, n, ld, ne, kt, params, d_p, ldp, res,
+                                              _stream_handle(stream)))
+        return ps, ([r.as_dict() for r in res] if res is not None else None)
 
     def density_matrix_host(self, h, n_e: float, params: FoParams, out, stream=None):
         """h, out: CPU float64 tensors (pinned for asynchronous copies)."""

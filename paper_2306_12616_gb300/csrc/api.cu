@@ -1,22 +1,97 @@
-// C ABI of the solver (include/fermi.h) and the host orchestration of one density matrix.
+// C ABI of the solver (include/fermi.h) and the host orchestration of the method.
 //
-// The host only plans (k, m, padding, workspace layout), checks arguments and enqueues
-// kernels; every number of the method is computed on the device, and the whole sequence
-// runs on the caller's stream without host synchronisation until the optional readback of
-// the scalar results.
+// Every call runs on a plan: the instances of the call (one for fo_density_matrix, many for
+// fo_density_matrix_batched), sorted by size, with their workspace layout, the
+// block-to-instance prefix sums of every grouped launch, one tensor map per bucket of
+// equally sized instances and the tile width chosen by the autotuner. Plans are cached per
+// context (keyed by sizes and parameters); a call writes its per-instance inputs with one
+// small kernel and enqueues one launch per stage for the whole batch, optionally replayed
+// as a CUDA graph. The host only plans, checks arguments and enqueues kernels: every number
+// of the method is computed on the device, and nothing synchronises until the optional
+// readback of the scalar results.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
 #include "internal.cuh"
 
 using namespace fo;
+
+namespace {
+
+enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUNDS = 3, MODE_COEFFS = 4 };
+
+struct PlanKey {
+    std::vector<int64_t> n;
+    int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
+    int use_given = 0, tile_req = 0, sym = 1, max_bisect = 0;
+    bool operator==(const PlanKey& o) const {
+        return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
+               mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
+               tile_req == o.tile_req && sym == o.sym && max_bisect == o.max_bisect;
+    }
+};
+
+struct Bucket {
+    int64_t np;
+    int first, count;
+    size_t off;           // workspace offset of the bucket's slot region
+    int64_t inst_bytes;   // slot region of one instance
+};
+
+struct Group {           // instances [i0, i1) with buckets [b0, b0 + nb): one grouped launch
+    int i0, i1, b0, nb;
+};
+
+struct HostWork {
+    std::vector<int> pre;
+    Work dev{nullptr, 0, 0};
+};
+
+struct Plan {
+    PlanKey key;
+    uint64_t ws_gen = 0;
+    int batch = 0;
+    Shape sh{};
+    bool giants = false, moments = false;
+    int n_slots = 0;
+    std::vector<int> order;   // sorted position -> caller index
+    std::vector<Inst> inst;   // host copy, sorted
+    std::vector<Bucket> buckets;
+    std::vector<Group> groups;
+    std::vector<unsigned char> maps;   // 128 bytes per bucket
+    HostWork wg, wsc, we, wgr, wtc[2], wf64;   // wtc[0]: 256-wide tiles, wtc[1]: 128-wide
+    int tile_n = 0;
+    int npairs = 0;
+    void* dtab = nullptr;     // device tables: Inst[], InstIO[], prefixes
+    Inst* d_inst = nullptr;
+    InstIO* d_io = nullptr;
+    DevResult* d_res = nullptr;   // batch results, sorted order (in the workspace)
+    double* ct = nullptr;
+    double* part_g = nullptr;
+    double* part_t = nullptr;
+    size_t total = 0;
+    double flops_product = 0.0;   // algorithmic flops of one product over the batch
+    cudaGraphExec_t graph = nullptr;
+    int graph_launches = 0;   // kernels in the captured graph
+    ~Plan() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (dtab) cudaFree(dtab);
+    }
+};
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
 
 struct ProfEntry {
     cudaEvent_t a, b;
@@ -36,15 +111,22 @@ struct fo_ctx {
     int64_t prof_calls = 0;
     int num_sms = 0;
     std::string err;
-    void* ws = nullptr;        // device workspace
+    void* ws = nullptr;        // device workspace shared by the plans
     size_t ws_bytes = 0;
+    uint64_t ws_gen = 1;       // bumped when the workspace moves (cached plans go stale)
     void* stage = nullptr;     // device staging for the host-buffer entry point
     size_t stage_bytes = 0;
-    DevResult* res = nullptr;  // device result record (own allocation)
-    int* flag = nullptr;       // tensor-core wait-timeout flag
+    int* flag = nullptr;       // [0] tensor-core wait timeout, [1..3] self-check record
+    std::vector<std::unique_ptr<Plan>> plans;   // most recently used last
+    DevResult* hres = nullptr; // pinned readback buffer
+    size_t hres_count = 0;
+    cudaStream_t cap = nullptr;   // stream for graph capture
+    bool capturing = false;
 };
 
 namespace {
+
+constexpr size_t kMaxPlans = 8;
 
 struct DeviceGuard {
     int prev = -1;
@@ -57,8 +139,6 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
-
-size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 fo_status fail(fo_ctx* ctx, fo_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -80,11 +160,17 @@ bool debug_sync() {
     return v == 1;
 }
 
-#define FO_CUDA(call, where)                                          \
-    do {                                                              \
-        cudaError_t e_ = (call);                                      \
-        if (e_ == cudaSuccess && debug_sync()) e_ = cudaDeviceSynchronize(); \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);      \
+#define FO_CUDA(call, where)                                                              \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ == cudaSuccess && debug_sync() && !ctx->capturing) e_ = cudaDeviceSynchronize(); \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);                          \
+    } while (0)
+
+#define FO_TRY(x)                      \
+    do {                               \
+        fo_status s_ = (x);            \
+        if (s_ != FO_OK) return s_;    \
     } while (0)
 
 // ---------------------------------------------------------------- stage profiler
@@ -99,9 +185,9 @@ cudaEvent_t ev_get(fo_ctx* ctx) {
     return e;
 }
 
-// Starts a timed stage when profiling is on; returns a handle for prof_end (or -1).
+// Starts a timed stage when profiling is on (and not capturing); returns a handle or -1.
 int prof_begin(fo_ctx* ctx, cudaStream_t st, int stage) {
-    if (!ctx->prof) return -1;
+    if (!ctx->prof || ctx->capturing) return -1;
     ProfEntry e{ev_get(ctx), ev_get(ctx), stage, 0.0, 0};
     cudaEventRecord(e.a, st);
     ctx->prof_pending.push_back(e);
@@ -130,42 +216,32 @@ void prof_collect(fo_ctx* ctx) {
     ctx->prof_pending.clear();
 }
 
+void drop_plans(fo_ctx* ctx) {
+    if (ctx->plans.empty()) return;
+    cudaDeviceSynchronize();
+    ctx->plans.clear();
+}
+
 fo_status ensure_ws(fo_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->ws_bytes) return FO_OK;
+    drop_plans(ctx);
     if (ctx->ws) {
         cudaDeviceSynchronize();
         cudaFree(ctx->ws);
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
     }
+    ctx->ws_gen += 1;
     if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, FO_ERR_NOMEM, "workspace allocation of " + std::to_string(bytes) + " bytes failed");
     }
-    // the zero border of every padded matrix is relied upon; clear once
     if (cudaMemset(ctx->ws, 0, bytes) != cudaSuccess) return fail(ctx, FO_ERR_CUDA, "workspace clear failed");
     ctx->ws_bytes = bytes;
     return FO_OK;
 }
 
 // --------------------------------------------------------------------------- plan
-struct Plan {
-    int64_t n = 0, np = 0;
-    int n_terms = 0, k = 0, m = 0, km = 0, M = 0;
-    int prec = 0, planes = 0, fp16 = 0;
-    bool giants = false;       // giant steps T_{lk} for exact moments
-    bool moments = false;      // compute tau
-    size_t slot_bytes = 0;
-    int n_tslots = 0;          // T_1..T_k (+ giants)
-    size_t off_t = 0, off_r = 0;
-    size_t off_c = 0, off_g = 0, off_tau = 0, off_w = 0, off_f = 0, off_ct = 0;
-    size_t off_diag = 0, off_gram = 0, off_gpart = 0, off_part = 0;
-    int gram_nblocks = 0, nparts = 0;
-    size_t total = 0;
-    float pscale_t = 1.0f;     // fp16 plane scale of T and giant slots
-    float pscale_r = 1.0f;     // fp16 plane scale of R / Clenshaw slots
-};
-
 bool plan_km(int n_terms, int k_req, int* k, int* m) {
     if (n_terms < 1) return false;
     int kk = k_req > 0 ? k_req : (int)std::ceil(std::sqrt((double)n_terms));
@@ -175,306 +251,474 @@ bool plan_km(int n_terms, int k_req, int* k, int* m) {
     return true;
 }
 
-fo_status make_plan(fo_ctx* ctx, int64_t n, int n_terms, int k_req, int prec, bool giants,
-                    bool moments, int n_quad, Plan* p) {
-    if (n < 1) return fail(ctx, FO_ERR_ARG, "n must be >= 1");
-    if (n > 65536) return fail(ctx, FO_ERR_ARG, "n above 65536 is not supported");
-    if (n_terms < 1 || n_terms > 4096) return fail(ctx, FO_ERR_ARG, "n_terms must be in [1, 4096]");
-    if (prec < FO_PREC_FP64 || prec > FO_PREC_BF16X1) return fail(ctx, FO_ERR_ARG, "unknown precision");
-    p->n = n;
-    p->np = ((n + kPad - 1) / kPad) * kPad;
-    // tensor-core tiles are 128 x 256: keep at least one full column tile
-    if (prec != FO_PREC_FP64 && p->np < 256) p->np = 256;
-    p->n_terms = n_terms;
-    if (!plan_km(n_terms, k_req, &p->k, &p->m)) return fail(ctx, FO_ERR_ARG, "bad k");
-    if (p->k > 64 || p->m > 64) return fail(ctx, FO_ERR_ARG, "k and m must not exceed 64");
-    p->km = p->k * p->m;
-    p->M = n_quad > 0 ? n_quad : (2048 > 4 * n_terms ? 2048 : 4 * n_terms);
-    if (p->M < n_terms) return fail(ctx, FO_ERR_ARG, "n_quad must be >= n_terms");
-    p->prec = prec;
-    p->planes = tc_planes(prec);
-    p->fp16 = prec == FO_PREC_FP16X2;
-    p->giants = giants && p->m > 2;
-    if (moments && p->k > 33) return fail(ctx, FO_ERR_UNSUPPORTED, "exact moments support k <= 33");
-    p->moments = moments;
-    const size_t np2 = (size_t)p->np * (size_t)p->np;
-    p->slot_bytes = prec == FO_PREC_FP64 ? align256(np2 * 8) : align256(np2 * 4 + p->planes * np2 * 2);
-    p->n_tslots = p->k + (p->giants ? p->m - 2 : 0);
+int split_count(int prec) { return prec == FO_PREC_BF16X3 ? 6 : (prec == FO_PREC_FP16X2 ? 3 : 1); }
+
+// Shape, sort order, buckets and the workspace layout (offsets only).
+fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
+    const int batch = (int)key.n.size();
+    if (batch < 1) return fail(ctx, FO_ERR_ARG, "batch must be >= 1");
+    for (int64_t n : key.n) {
+        if (n < 1) return fail(ctx, FO_ERR_ARG, "n must be >= 1");
+        if (n > 65536) return fail(ctx, FO_ERR_ARG, "n above 65536 is not supported");
+    }
+    if (key.n_terms < 1 || key.n_terms > 4096) return fail(ctx, FO_ERR_ARG, "n_terms must be in [1, 4096]");
+    if (key.prec < FO_PREC_FP64 || key.prec > FO_PREC_BF16X1) return fail(ctx, FO_ERR_ARG, "unknown precision");
+    if (key.tile_req != 0 && key.tile_req != 128 && key.tile_req != 256)
+        return fail(ctx, FO_ERR_ARG, "tile_n must be 0, 128 or 256");
+    p->key = key;
+    p->batch = batch;
+    Shape& sh = p->sh;
+    std::memset(&sh, 0, sizeof(sh));
+    sh.n_terms = key.n_terms;
+    if (!plan_km(key.n_terms, key.k_req, &sh.k, &sh.m)) return fail(ctx, FO_ERR_ARG, "bad k");
+    if (sh.k > 64 || sh.m > 64) return fail(ctx, FO_ERR_ARG, "k and m must not exceed 64");
+    sh.km = sh.k * sh.m;
+    sh.M = key.n_quad > 0 ? key.n_quad : std::max(2048, 4 * key.n_terms);
+    if (sh.M < key.n_terms) return fail(ctx, FO_ERR_ARG, "n_quad must be >= n_terms");
+    sh.is64 = key.prec == FO_PREC_FP64;
+    sh.planes = tc_planes(key.prec);
+    sh.fp16 = key.prec == FO_PREC_FP16X2;
+    // fp16 planes hold v * scale; T slots have |entries| <= 1 (spectrum of X in [-1, 1])
+    sh.pscale_t = 256.0f;
+    sh.pscale_r = 1.0f;
+    const bool bisect = key.mode == MODE_DENSITY && key.mu_mode == FO_MU_BISECT;
+    p->giants = bisect && sh.m > 2;
+    p->moments = bisect || key.mode == MODE_MOMENTS;
+    if (p->moments && sh.k > 33) return fail(ctx, FO_ERR_UNSUPPORTED, "exact moments support k <= 33");
+    switch (key.mode) {
+        case MODE_DENSITY:
+        case MODE_MOMENTS:
+            sh.n_tslots = sh.k + (p->giants ? sh.m - 2 : 0);
+            p->n_slots = sh.n_tslots + sh.m;
+            break;
+        case MODE_PRODUCT:
+            sh.n_tslots = 5;   // A, B, C, D, out
+            p->n_slots = 5;
+            break;
+        default:
+            sh.n_tslots = 0;
+            p->n_slots = 0;
+    }
+    p->npairs = std::max(1, std::max((sh.m > 1 ? sh.m - 1 : 1) * std::max(1, sh.k - 1), sh.k));
+
+    // sort by padded size (largest first): the longest tiles of a grouped launch start first
+    p->order.resize(batch);
+    std::iota(p->order.begin(), p->order.end(), 0);
+    std::vector<int64_t> npad(batch);
+    for (int b = 0; b < batch; ++b) npad[b] = ((key.n[b] + kPad - 1) / kPad) * kPad;
+    std::stable_sort(p->order.begin(), p->order.end(), [&](int a, int b) { return npad[a] > npad[b]; });
+
+    // slot regions, bucket by bucket
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
-    p->off_t = take(p->slot_bytes * p->n_tslots);
-    p->off_r = take(p->slot_bytes * p->m);
-    p->off_c = take(8 * (size_t)p->km);
-    p->off_g = take(8 * (size_t)p->km);
-    p->off_tau = take(8 * (size_t)(p->km + 2));
-    p->off_w = take(8 * (size_t)p->M);
-    p->off_f = take(8 * (size_t)p->M);
-    p->off_ct = take(8 * 4 * (size_t)p->M);
-    p->off_diag = take(8 * (size_t)(p->k + p->m + 2));
-    const int npairs = (p->m > 1 ? p->m - 1 : 1) * p->k;
-    p->off_gram = take(8 * (size_t)npairs);
-    p->gram_nblocks = gram_blocks(p->np, p->m - 1, p->k);
-    p->off_gpart = take(8 * (size_t)npairs * p->gram_nblocks);
-    p->nparts = 2 * (ctx->num_sms > 0 ? ctx->num_sms : 152);
-    p->off_part = take(8 * 3 * (size_t)p->nparts + 64);
+    p->inst.assign(batch, Inst{});
+    for (int j = 0; j < batch; ++j) {
+        const int b = p->order[j];
+        const int64_t np = npad[b];
+        Inst& in = p->inst[j];
+        std::memset(&in, 0, sizeof(in));
+        in.n = key.n[b];
+        in.np = np;
+        const size_t np2 = (size_t)np * (size_t)np;
+        in.slot_bytes = (int64_t)(sh.is64 ? align256(np2 * 8) : align256(np2 * 4 + (size_t)sh.planes * np2 * 2));
+        if (p->buckets.empty() || p->buckets.back().np != np) {
+            Bucket bk{np, j, 0, 0, (int64_t)in.slot_bytes * p->n_slots};
+            p->buckets.push_back(bk);
+        }
+        in.bucket = (int)p->buckets.size() - 1;
+        in.in_bucket = p->buckets.back().count++;
+    }
+    for (Bucket& bk : p->buckets) bk.off = take((size_t)bk.inst_bytes * bk.count);
+    // per-instance float64 arrays
+    std::vector<size_t> small(batch);
+    const int ndiag = sh.n_tslots + 2;
+    for (int j = 0; j < batch; ++j) {
+        Inst& in = p->inst[j];
+        in.gram_blocks = gram_blocks_for(in.np, batch);
+        size_t o = off;
+        o += align256(8 * (size_t)sh.km);             // c
+        o += align256(8 * (size_t)sh.km);             // g
+        o += align256(8 * (size_t)(sh.km + 2));       // tau
+        o += align256(8 * (size_t)sh.M);              // w
+        o += align256(8 * (size_t)sh.M);              // f
+        o += align256(8 * (size_t)ndiag);             // diag
+        o += align256(8 * (size_t)p->npairs);         // gram
+        o += align256(8 * (size_t)p->npairs * in.gram_blocks);   // gram partials
+        small[j] = off;
+        off = o;
+    }
+    const size_t off_res = take(sizeof(DevResult) * batch);
+    const size_t off_ct = take(8 * 4 * (size_t)sh.M);
+    // work lists
+    auto fill = [&](HostWork& w, auto count) {
+        w.pre.assign(batch + 1, 0);
+        for (int j = 0; j < batch; ++j) w.pre[j + 1] = w.pre[j] + (int)count(p->inst[j]);
+    };
+    fill(p->wg, [](const Inst& in) { return (in.n + kGershRows - 1) / kGershRows; });
+    fill(p->wsc, [](const Inst& in) { const int64_t t = in.np / 32; return t * (t + 1) / 2; });
+    fill(p->we, [](const Inst& in) { return (int64_t)ew_blocks(in.np); });
+    fill(p->wgr, [](const Inst& in) { return (int64_t)in.gram_blocks; });
+    const bool full = key.mode == MODE_PRODUCT && !key.sym;
+    fill(p->wtc[0], [&](const Inst& in) { return full ? tc_tiles_full(in.np, 256) : tc_tiles(in.np, 256); });
+    fill(p->wtc[1], [&](const Inst& in) { return full ? tc_tiles_full(in.np, 128) : tc_tiles(in.np, 128); });
+    fill(p->wf64, [](const Inst& in) { return f64_tiles(in.np); });
+    const size_t off_pg = take(8 * 3 * (size_t)std::max(1, p->wg.pre[batch]));
+    const size_t off_pt = take(8 * 2 * (size_t)std::max(1, p->we.pre[batch]));
     p->total = off;
-    // fp16 planes hold v * scale; T slots have |entries| <= 1 (spectrum of X in [-1, 1])
-    p->pscale_t = 256.0f;
-    p->pscale_r = 1.0f;
+    // remember the offsets in the (not yet placed) pointers
+    for (int j = 0; j < batch; ++j) p->inst[j].c = reinterpret_cast<double*>(small[j]);
+    p->d_res = reinterpret_cast<DevResult*>(off_res);
+    p->ct = reinterpret_cast<double*>(off_ct);
+    p->part_g = reinterpret_cast<double*>(off_pg);
+    p->part_t = reinterpret_cast<double*>(off_pt);
+    // launch groups: at most kMaxBuckets tensor maps per launch
+    for (int b0 = 0; b0 < (int)p->buckets.size(); b0 += kMaxBuckets) {
+        const int nb = std::min<int>(kMaxBuckets, (int)p->buckets.size() - b0);
+        Group g;
+        g.b0 = b0;
+        g.nb = nb;
+        g.i0 = p->buckets[b0].first;
+        const Bucket& last = p->buckets[b0 + nb - 1];
+        g.i1 = last.first + last.count;
+        p->groups.push_back(g);
+    }
+    const int s = split_count(key.prec);
+    p->flops_product = 0.0;
+    for (const Inst& in : p->inst) p->flops_product += (double)s * in.n * in.n * (in.n + 1.0);
     return FO_OK;
 }
 
-char* wsb(fo_ctx* ctx) { return reinterpret_cast<char*>(ctx->ws); }
-
-struct Slots {
-    char* t;     // T_1 .. T_k, giants
-    char* r;     // R_0 .. R_{m-1}
-    size_t stride;
-    int64_t np;
-    int planes;
-    MatF32 mat(char* base, int i) const {
-        MatF32 x;
-        x.x = reinterpret_cast<float*>(base + stride * i);
-        x.planes = reinterpret_cast<uint16_t*>(base + stride * i + (size_t)np * np * 4);
-        x.ld = np;
-        x.plane_stride = np * np;
-        return x;
+// Places the plan in the workspace, uploads its tables and builds its tensor maps.
+fo_status place_plan(fo_ctx* ctx, Plan* p) {
+    char* W = reinterpret_cast<char*>(ctx->ws);
+    const Shape& sh = p->sh;
+    const int batch = p->batch;
+    const int ndiag = sh.n_tslots + 2;
+    p->d_res = reinterpret_cast<DevResult*>(W + reinterpret_cast<size_t>(p->d_res));
+    p->ct = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->ct));
+    p->part_g = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->part_g));
+    p->part_t = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->part_t));
+    for (int j = 0; j < batch; ++j) {
+        Inst& in = p->inst[j];
+        const Bucket& bk = p->buckets[in.bucket];
+        in.slots = W + bk.off + (size_t)bk.inst_bytes * in.in_bucket;
+        char* o = W + reinterpret_cast<size_t>(in.c);
+        auto next = [&](size_t b) { char* r = o; o += align256(b); return reinterpret_cast<double*>(r); };
+        in.c = next(8 * (size_t)sh.km);
+        in.g = next(8 * (size_t)sh.km);
+        in.tau = next(8 * (size_t)(sh.km + 2));
+        in.w = next(8 * (size_t)sh.M);
+        in.f = next(8 * (size_t)sh.M);
+        in.diag = next(8 * (size_t)ndiag);
+        in.gram = next(8 * (size_t)p->npairs);
+        in.gpart = next(8 * (size_t)p->npairs * in.gram_blocks);
+        in.res = p->d_res + j;
     }
-    MatF32 T(int i) const { return mat(t, i); }      // slot index
-    MatF32 R(int l) const { return mat(r, l); }
-    double* Td(int i) const { return reinterpret_cast<double*>(t + stride * i); }
-    double* Rd(int l) const { return reinterpret_cast<double*>(r + stride * l); }
+    // device tables: Inst[batch], InstIO[batch], then the prefix arrays
+    HostWork* lists[] = {&p->wg, &p->wsc, &p->we, &p->wgr, &p->wtc[0], &p->wtc[1], &p->wf64};
+    size_t bytes = align256(sizeof(Inst) * batch) + align256(sizeof(InstIO) * batch);
+    for (HostWork* w : lists) bytes += align256(sizeof(int) * w->pre.size());
+    if (cudaMalloc(&p->dtab, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p->dtab = nullptr;
+        return fail(ctx, FO_ERR_NOMEM, "plan table allocation failed");
+    }
+    std::vector<unsigned char> host(bytes, 0);
+    size_t o = 0;
+    p->d_inst = reinterpret_cast<Inst*>(reinterpret_cast<char*>(p->dtab) + o);
+    std::memcpy(host.data() + o, p->inst.data(), sizeof(Inst) * batch);
+    o += align256(sizeof(Inst) * batch);
+    p->d_io = reinterpret_cast<InstIO*>(reinterpret_cast<char*>(p->dtab) + o);
+    o += align256(sizeof(InstIO) * batch);
+    for (HostWork* w : lists) {
+        w->dev.pre = reinterpret_cast<const int*>(reinterpret_cast<char*>(p->dtab) + o);
+        w->dev.count = batch;
+        w->dev.total = w->pre[batch];
+        std::memcpy(host.data() + o, w->pre.data(), sizeof(int) * w->pre.size());
+        o += align256(sizeof(int) * w->pre.size());
+    }
+    if (cudaMemcpy(p->dtab, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(ctx, FO_ERR_CUDA, "plan table upload failed");
+    // tensor maps: one per bucket over (column, row, plane, slot, instance)
+    if (!sh.is64 && p->n_slots > 0) {
+        p->maps.assign(128 * p->buckets.size(), 0);
+        for (size_t b = 0; b < p->buckets.size(); ++b) {
+            const Bucket& bk = p->buckets[b];
+            const char* planes0 = W + bk.off + 4 * (size_t)bk.np * (size_t)bk.np;
+            std::string err;
+            if (!tc_make_map(p->maps.data() + 128 * b, planes0, bk.np, sh.planes, p->n_slots, bk.count,
+                             p->inst[bk.first].slot_bytes, bk.inst_bytes, sh.fp16 != 0, &err))
+                return fail(ctx, FO_ERR_CUDA, "tensor map: " + err);
+        }
+    }
+    // the cosine table depends on M only
+    cudaError_t e = launch_cos_table(sh.M, p->ct, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cos_table");
+    p->ws_gen = ctx->ws_gen;
+    return FO_OK;
+}
+
+// ---------------------------------------------------------------- products
+struct Run {
+    int n_gemm = 0;     // products per instance
+    int launches = 0;   // kernels launched
 };
+
+Step make_step(const Plan& p, int a, int b, int c, int d, int out, double alpha, double beta, double shift,
+               bool a_r, bool b_r, bool out_r, bool out64, fo_ctx* ctx) {
+    const Shape& sh = p.sh;
+    Step st;
+    std::memset(&st, 0, sizeof(st));
+    st.a = a;
+    st.b = b;
+    st.c = c;
+    st.d = d;
+    st.out = out;
+    st.out64 = out64 ? 1 : 0;
+    st.fp16 = sh.fp16;
+    const float sa = sh.fp16 ? (a_r ? sh.pscale_r : sh.pscale_t) : 1.0f;
+    const float sb = sh.fp16 ? (b_r ? sh.pscale_r : sh.pscale_t) : 1.0f;
+    st.alpha = (float)(alpha / ((double)sa * sb));
+    st.beta = (float)beta;
+    st.shift = (float)shift;
+    st.alpha64 = alpha;
+    st.beta64 = beta;
+    st.shift64 = shift;
+    st.planes = out >= 0 ? sh.planes : 0;
+    st.plane_scale = out_r ? sh.pscale_r : sh.pscale_t;
+    st.dbg = ctx->flag + 1;
+    return st;
+}
+
+fo_status run_product(fo_ctx* ctx, Plan& p, const Step& st, cudaStream_t s, const char* tag, int index,
+                      Run* run) {
+    const int h = prof_begin(ctx, s, FO_STAGE_PRODUCTS);
+    int launches = 0;
+    if (p.sh.is64) {
+        FO_CUDA(launch_gemm_f64(st, p.d_inst, p.d_io, p.wf64.dev, s), "gemm_f64");
+        launches = 1;
+    } else {
+        const HostWork& w = p.wtc[p.tile_n == 128 ? 1 : 0];
+        for (const Group& g : p.groups) {
+            std::string err;
+            const int tile0 = w.pre[g.i0];
+            cudaError_t e = tc_gemm(p.key.prec, p.tile_n, st, p.d_inst, p.d_io, w.dev.pre, g.i0, g.i1, tile0,
+                                    w.pre[g.i1] - tile0, p.maps.data() + 128 * (size_t)g.b0, g.b0, g.nb,
+                                    ctx->flag, s, &err, p.key.sym);
+            if (e == cudaSuccess && debug_sync() && !ctx->capturing) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) {
+                const std::string where = std::string("tc_gemm ") + tag + " " + std::to_string(index);
+                if (!err.empty()) return fail(ctx, FO_ERR_CUDA, where + ": " + err);
+                return cuda_fail(ctx, e, where.c_str());
+            }
+            ++launches;
+        }
+    }
+    prof_end(ctx, s, h, p.flops_product, launches);
+    run->launches += launches;
+    return FO_OK;
+}
 
 // Slot of T_{j k} for j >= 1: T_k is baby slot k-1, giants T_{2k}.. follow.
-int giant_slot(const Plan& p, int j) { return j == 1 ? p.k - 1 : p.k + j - 2; }
+int giant_slot(const Plan& p, int j) { return j == 1 ? p.sh.k - 1 : p.sh.k + j - 2; }
+int r_slot(const Plan& p, int l) { return p.sh.n_tslots + l; }
 
-// One recurrence product out = alpha A B + beta C + D + shift I in the plan's arithmetic.
-struct Product {
-    int a, b;            // operand slots (tbase / rbase chosen by flags)
-    bool a_r = false, b_r = false;
-    int c = -1, d = -1;  // -1 = absent
-    bool c_r = false, d_r = false;
-    int out = -1;
-    bool out_r = false;
-    double alpha = 1, beta = 0, shift = 0;
-    double* out64 = nullptr;
-    int64_t ldo = 0;
-    const char* tag = "product";  // stage name for error messages
-    int index = 0;
-};
-
-fo_status run_product_impl(fo_ctx* ctx, const Plan& p, const Slots& S, const Product& q,
-                           cudaStream_t st, int sym);
-
-// Algorithmic flops of one symmetric product: n^2 (n+1) per split product.
-double product_flops(const Plan& p) {
-    const double n = (double)p.n;
-    const int s = p.prec == FO_PREC_BF16X3 ? 6 : (p.prec == FO_PREC_FP16X2 ? 3 : 1);
-    return s * n * n * (n + 1.0);
-}
-
-fo_status run_product(fo_ctx* ctx, const Plan& p, const Slots& S, const Product& q, cudaStream_t st,
-                      int sym) {
-    const int h = prof_begin(ctx, st, FO_STAGE_PRODUCTS);
-    fo_status r = run_product_impl(ctx, p, S, q, st, sym);
-    prof_end(ctx, st, h, product_flops(p), 1);
-    return r;
-}
-
-fo_status run_product_impl(fo_ctx* ctx, const Plan& p, const Slots& S, const Product& q,
-                           cudaStream_t st, int sym) {
-    if (p.prec == FO_PREC_FP64) {
-        const double* A = q.a_r ? S.Rd(q.a) : S.Td(q.a);
-        const double* B = q.b_r ? S.Rd(q.b) : S.Td(q.b);
-        const double* C = q.c < 0 ? nullptr : (q.c_r ? S.Rd(q.c) : S.Td(q.c));
-        const double* D = q.d < 0 ? nullptr : (q.d_r ? S.Rd(q.d) : S.Td(q.d));
-        double* out = q.out < 0 ? nullptr : (q.out_r ? S.Rd(q.out) : S.Td(q.out));
-        FO_CUDA(launch_gemm_f64(A, B, p.np, q.alpha, C, q.beta, D, q.shift, (int)p.n, out, q.out64,
-                                q.ldo, st),
-                "gemm_f64");
-        return FO_OK;
-    }
-    const MatF32 A = q.a_r ? S.R(q.a) : S.T(q.a);
-    const MatF32 B = q.b_r ? S.R(q.b) : S.T(q.b);
-    Epilogue ep;
-    std::memset(&ep, 0, sizeof(ep));
-    const float sa = p.fp16 ? (q.a_r ? p.pscale_r : p.pscale_t) : 1.0f;
-    const float sb = p.fp16 ? (q.b_r ? p.pscale_r : p.pscale_t) : 1.0f;
-    ep.alpha = (float)(q.alpha / ((double)sa * sb));
-    ep.beta = (float)q.beta;
-    ep.shift = (float)q.shift;
-    ep.n_real = (int32_t)p.n;
-    ep.C = q.c < 0 ? nullptr : (q.c_r ? S.R(q.c).x : S.T(q.c).x);
-    ep.D = q.d < 0 ? nullptr : (q.d_r ? S.R(q.d).x : S.T(q.d).x);
-    ep.ld = p.np;
-    if (q.out >= 0) {
-        ep.out = q.out_r ? S.R(q.out) : S.T(q.out);
-        ep.planes = p.planes;
-        ep.plane_scale = q.out_r ? p.pscale_r : p.pscale_t;
-    }
-    ep.out64 = q.out64;
-    ep.ldo = q.ldo;
-    ep.fp16 = p.fp16;
-    ep.dbg = ctx->flag + 1;
-    std::string err;
-    cudaError_t e = tc_gemm(p.prec, p.np, A, B, ep, sym, ctx->flag, st, &err);
-    if (e == cudaSuccess && debug_sync()) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
-        const std::string where = std::string("tc_gemm ") + q.tag + " " + std::to_string(q.index);
-        if (!err.empty()) return fail(ctx, FO_ERR_CUDA, where + ": " + err);
-        return cuda_fail(ctx, e, where.c_str());
-    }
-    return FO_OK;
-}
-
-#define FO_TRY(x)                      \
-    do {                               \
-        fo_status s_ = (x);            \
-        if (s_ != FO_OK) return s_;    \
-    } while (0)
-
-// Scale H into slot T_1 (float64, or float32 + planes).
-fo_status pack_x(fo_ctx* ctx, const Plan& p, const Slots& S, const double* dH, int64_t ld,
-                 cudaStream_t st) {
-    if (p.prec == FO_PREC_FP64)
-        FO_CUDA(launch_scale_f64(dH, p.n, ld, ctx->res, S.Td(0), p.np, st, ctx->flag + 1), "scale");
-    else
-        FO_CUDA(launch_scale_split(dH, p.n, ld, ctx->res, S.T(0), p.np, p.planes, p.fp16, p.pscale_t, st,
-                                   ctx->flag + 1),
-                "scale_split");
-    return FO_OK;
-}
-
-// Baby steps T_2..T_k: T_{i+1} = 2 T_1 T_i - T_{i-1} (T_0 = I as a diagonal shift).
-fo_status baby_steps(fo_ctx* ctx, const Plan& p, const Slots& S, int kmax, cudaStream_t st,
-                     int sym, int* n_gemm) {
+// Baby steps T_2..T_kmax: T_{i+1} = 2 T_1 T_i - T_{i-1} (T_0 = I as a diagonal shift).
+fo_status baby_steps(fo_ctx* ctx, Plan& p, int kmax, cudaStream_t s, Run* run) {
     for (int i = 1; i < kmax; ++i) {
-        Product q;
-        q.a = 0;
-        q.b = i - 1;
-        q.out = i;
-        q.alpha = 2.0;
-        q.tag = "baby";
-        q.index = i + 1;
-        if (i == 1) { q.shift = -1.0; }
-        else { q.c = i - 2; q.beta = -1.0; }
-        FO_TRY(run_product(ctx, p, S, q, st, sym));
-        ++*n_gemm;
+        const Step st = i == 1 ? make_step(p, 0, 0, -1, -1, 1, 2.0, 0.0, -1.0, false, false, false, false, ctx)
+                               : make_step(p, 0, i - 1, i - 2, -1, i, 2.0, -1.0, 0.0, false, false, false, false, ctx);
+        FO_TRY(run_product(ctx, p, st, s, "baby", i + 1, run));
+        ++run->n_gemm;
     }
     return FO_OK;
 }
 
 // Giant steps T_{2k}..T_{(m-1)k}: T_{(j+1)k} = 2 T_k T_{jk} - T_{(j-1)k}.
-fo_status giant_steps(fo_ctx* ctx, const Plan& p, const Slots& S, cudaStream_t st, int sym,
-                      int* n_gemm) {
-    for (int j = 1; j + 1 <= p.m - 1; ++j) {
-        Product q;
-        q.a = giant_slot(p, 1);
-        q.b = giant_slot(p, j);
-        q.out = giant_slot(p, j + 1);
-        q.alpha = 2.0;
-        q.tag = "giant";
-        q.index = j + 1;
-        if (j == 1) { q.shift = -1.0; }
-        else { q.c = giant_slot(p, j - 1); q.beta = -1.0; }
-        FO_TRY(run_product(ctx, p, S, q, st, sym));
-        ++*n_gemm;
+fo_status giant_steps(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    for (int j = 1; j + 1 <= p.sh.m - 1; ++j) {
+        const int a = giant_slot(p, 1), b = giant_slot(p, j), out = giant_slot(p, j + 1);
+        const Step st = j == 1 ? make_step(p, a, b, -1, -1, out, 2.0, 0.0, -1.0, false, false, false, false, ctx)
+                               : make_step(p, a, b, giant_slot(p, j - 1), -1, out, 2.0, -1.0, 0.0, false, false,
+                                           false, false, ctx);
+        FO_TRY(run_product(ctx, p, st, s, "giant", j + 1, run));
+        ++run->n_gemm;
     }
     return FO_OK;
 }
 
 // Exact moments tau_0..tau_{n_terms-1} (needs the giant steps).
-fo_status exact_moments(fo_ctx* ctx, const Plan& p, const Slots& S, cudaStream_t st) {
-    const int is64 = p.prec == FO_PREC_FP64;
-    char* W = wsb(ctx);
-    double* diag = reinterpret_cast<double*>(W + p.off_diag);
-    double* gram = reinterpret_cast<double*>(W + p.off_gram);
-    FO_CUDA(launch_diag_sums(S.t, (int64_t)p.slot_bytes, p.n_tslots, p.n, p.np, is64, diag, st), "diag_sums");
-    if (p.m > 1 && p.k > 1)
-        FO_CUDA(launch_gram(S.t, (int64_t)p.slot_bytes, p.k - 1, p.m - 1, 0, p.k - 1, p.np, is64,
-                            reinterpret_cast<double*>(W + p.off_gpart), p.gram_nblocks, gram, st),
+fo_status exact_moments(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    const Shape& sh = p.sh;
+    FO_CUDA(launch_diag_sums(p.d_inst, p.batch, sh.n_tslots, sh, s), "diag_sums");
+    run->launches += 1;
+    if (sh.m > 1 && sh.k > 1)
+        FO_CUDA(launch_gram(p.d_inst, p.batch, p.wgr.dev, sh.k - 1, sh.m - 1, 0, sh.k - 1, 0, sh.is64, s,
+                            &run->launches),
                 "gram");
-    FO_CUDA(launch_assemble_moments(diag, gram, p.k, p.m, p.n_terms, p.n,
-                                    reinterpret_cast<double*>(W + p.off_tau), st),
-            "moments");
-    return FO_OK;
-}
-
-// Coefficients at the device mu and their conversion to giant-step coefficients g.
-fo_status coefficients(fo_ctx* ctx, const Plan& p, double kT, cudaStream_t st, int* launches) {
-    char* W = wsb(ctx);
-    double* ct = reinterpret_cast<double*>(W + p.off_ct);
-    double* f = reinterpret_cast<double*>(W + p.off_f);
-    double* c = reinterpret_cast<double*>(W + p.off_c);
-    double* g = reinterpret_cast<double*>(W + p.off_g);
-    FO_CUDA(launch_fermi_nodes(p.M, ct, ctx->res, kT, f, st), "fermi_nodes");
-    FO_CUDA(launch_coeffs(f, ct, p.M, p.n_terms, p.km, c, st), "coeffs");
-    FO_CUDA(launch_g_convert(c, p.k, p.m, g, st), "g_convert");
-    *launches += 3;
-    if (p.moments) {
-        FO_CUDA(launch_poly_trace(c, reinterpret_cast<double*>(W + p.off_tau), p.n_terms, ctx->res, st),
-                "poly_trace");
-        *launches += 1;
-    }
-    return FO_OK;
-}
-
-// R_l = sum_i g_{i,l} T_i for every l (the S_j sums of the paper in the Chebyshev basis).
-fo_status contraction(fo_ctx* ctx, const Plan& p, const Slots& S, double* dP, int64_t ldp,
-                      cudaStream_t st, int* launches) {
-    const double* g = reinterpret_cast<const double*>(wsb(ctx) + p.off_g);
-    if (p.prec == FO_PREC_FP64) {
-        FO_CUDA(launch_contract_f64(g, p.k, p.m, S.Td(0), (int64_t)(p.slot_bytes / 8), S.Rd(0),
-                                    (int64_t)(p.slot_bytes / 8), p.n, p.np, st),
-                "contract");
-    } else {
-        FO_CUDA(launch_contract_f32(g, p.k, p.m, S.T(0).x, (int64_t)(p.slot_bytes / 4), S.R(0).x,
-                                    (int64_t)(p.slot_bytes / 4), p.n, p.np, p.m > 1 ? p.planes : 0,
-                                    p.fp16, p.pscale_r, p.np * p.np, st, ctx->flag + 1),
-                "contract");
-    }
-    *launches += 1;
-    if (p.m == 1) {
-        if (p.prec == FO_PREC_FP64)
-            FO_CUDA(launch_copy_out(S.Rd(0), p.np, p.n, dP, ldp, st), "copy_out");
-        else
-            FO_CUDA(launch_copy_out_f32(S.R(0).x, p.np, p.n, dP, ldp, st), "copy_out");
-        *launches += 1;
-    }
+    FO_CUDA(launch_assemble_moments(p.d_inst, p.batch, sh, s), "moments");
+    run->launches += 1;
     return FO_OK;
 }
 
 // Clenshaw recurrence in Y = T_k: b_{m-1} = R_{m-1}; b_l = 2 Y b_{l+1} - b_{l+2} + R_l;
-// P = Y b_1 - b_2 + R_0 (written as float64 into dP). b_l overwrites R_l in place.
-fo_status clenshaw(fo_ctx* ctx, const Plan& p, const Slots& S, double* dP, int64_t ldp,
-                   cudaStream_t st, int sym, int* n_gemm) {
-    if (p.m == 1) return FO_OK;
-    const int ysl = giant_slot(p, 1);
-    for (int l = p.m - 2; l >= 1; --l) {
-        Product q;
-        q.a = ysl;
-        q.b = l + 1; q.b_r = true;
-        q.d = l; q.d_r = true;
-        q.out = l; q.out_r = true;
-        q.alpha = 2.0;
-        q.tag = "clenshaw";
-        q.index = l;
-        if (l + 2 <= p.m - 1) { q.c = l + 2; q.c_r = true; q.beta = -1.0; }
-        FO_TRY(run_product(ctx, p, S, q, st, sym));
-        ++*n_gemm;
+// P = Y b_1 - b_2 + R_0 (written as float64 into the instance's P). b_l overwrites R_l.
+fo_status clenshaw(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    const int m = p.sh.m;
+    if (m == 1) return FO_OK;
+    const int y = giant_slot(p, 1);
+    for (int l = m - 2; l >= 1; --l) {
+        const bool has_c = l + 2 <= m - 1;
+        const Step st = make_step(p, y, r_slot(p, l + 1), has_c ? r_slot(p, l + 2) : -1, r_slot(p, l), r_slot(p, l),
+                                  2.0, has_c ? -1.0 : 0.0, 0.0, false, true, true, false, ctx);
+        FO_TRY(run_product(ctx, p, st, s, "clenshaw", l, run));
+        ++run->n_gemm;
     }
-    Product q;
-    q.a = ysl;
-    q.b = 1; q.b_r = true;
-    q.d = 0; q.d_r = true;
-    q.alpha = 1.0;
-    if (p.m >= 3) { q.c = 2; q.c_r = true; q.beta = -1.0; }
-    q.out64 = dP;
-    q.ldo = ldp;
-    q.tag = "final";
-    FO_TRY(run_product(ctx, p, S, q, st, sym));
-    ++*n_gemm;
+    const bool has_c = m >= 3;
+    const Step st = make_step(p, y, r_slot(p, 1), has_c ? r_slot(p, 2) : -1, r_slot(p, 0), -1, 1.0,
+                              has_c ? -1.0 : 0.0, 0.0, false, true, false, true, ctx);
+    FO_TRY(run_product(ctx, p, st, s, "final", 0, run));
+    ++run->n_gemm;
+    return FO_OK;
+}
+
+// The whole method for every instance of a density plan (after the per-call inputs).
+fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    const Shape& sh = p.sh;
+    const PlanKey& key = p.key;
+    int lstage = 0;
+    int h = prof_begin(ctx, s, FO_STAGE_BOUNDS);
+    FO_CUDA(launch_bounds(p.d_inst, p.d_io, p.batch, p.wg.dev, p.part_g, key.use_given, s), "bounds");
+    FO_CUDA(launch_scale(p.d_inst, p.d_io, p.wsc.dev, sh, s, ctx->flag + 1), "scale");
+    lstage = (key.use_given ? 1 : 2) + 1;
+    prof_end(ctx, s, h, 0.0, lstage);
+    run->launches += lstage;
+
+    FO_TRY(baby_steps(ctx, p, sh.k, s, run));
+    const bool bisect = key.mu_mode == FO_MU_BISECT;
+    const int max_it = key.max_bisect > 0 ? key.max_bisect : 200;
+    if (bisect) {
+        if (p.giants) FO_TRY(giant_steps(ctx, p, s, run));
+        h = prof_begin(ctx, s, FO_STAGE_MOMENTS);
+        const int l0 = run->launches;
+        FO_TRY(exact_moments(ctx, p, s, run));
+        prof_end(ctx, s, h, 0.0, run->launches - l0);
+        h = prof_begin(ctx, s, FO_STAGE_MU);
+        FO_CUDA(launch_dos_weights(p.d_inst, p.batch, sh, p.ct, s), "dos_weights");
+        FO_CUDA(launch_bisect(p.d_inst, p.d_io, p.batch, sh, p.ct, max_it, 0, s), "bisect");
+        prof_end(ctx, s, h, 0.0, 2);
+        run->launches += 2;
+    } else {
+        FO_CUDA(launch_set_mu(p.d_inst, p.d_io, p.batch, s), "mu");
+        run->launches += 1;
+    }
+    h = prof_begin(ctx, s, FO_STAGE_COEFFS);
+    lstage = 0;
+    FO_CUDA(launch_coefficients(p.d_inst, p.d_io, p.batch, sh, p.ct, p.moments ? 1 : 0, s, &lstage), "coeffs");
+    prof_end(ctx, s, h, 0.0, lstage);
+    run->launches += lstage;
+    h = prof_begin(ctx, s, FO_STAGE_CONTRACT);
+    lstage = 1;
+    FO_CUDA(launch_contract(p.d_inst, p.we.dev, sh, s, ctx->flag + 1), "contract");
+    if (sh.m == 1) {
+        FO_CUDA(launch_copy_out(p.d_inst, p.d_io, p.we.dev, sh, s), "copy_out");
+        lstage += 1;
+    }
+    prof_end(ctx, s, h, 0.0, lstage);
+    run->launches += lstage;
+    FO_TRY(clenshaw(ctx, p, s, run));
+    h = prof_begin(ctx, s, FO_STAGE_TRACE);
+    FO_CUDA(launch_trace_frob(p.d_inst, p.d_io, p.we.dev, p.part_t, s), "trace");
+    prof_end(ctx, s, h, 0.0, 2);
+    run->launches += 2;
+    return FO_OK;
+}
+
+// Tile width of the tensor-core products: the requested one, or the faster of 256 and 128
+// on this plan's first baby step (timed with CUDA events on the plan's own data layout;
+// the data are whatever the workspace holds, the work does not depend on them).
+fo_status autotune(fo_ctx* ctx, Plan& p) {
+    if (p.sh.is64 || p.n_slots == 0) {
+        p.tile_n = 0;
+        return FO_OK;
+    }
+    if (p.key.tile_req) {
+        p.tile_n = p.key.tile_req;
+        return FO_OK;
+    }
+    if (p.key.mode == MODE_PRODUCT || p.sh.k < 2) {
+        p.tile_n = 256;
+        return FO_OK;
+    }
+    // make every instance active (the per-call inputs are not needed by a product)
+    std::vector<InstIO> io(p.batch);
+    std::memset(io.data(), 0, sizeof(InstIO) * io.size());
+    cudaStream_t s = nullptr;
+    FO_CUDA(launch_set_io(io.data(), p.batch, p.d_io, p.d_inst, 0, s), "autotune setup");
+    const Step st = make_step(p, 0, 0, -1, -1, 1, 2.0, 0.0, -1.0, false, false, false, false, ctx);
+    cudaEvent_t e0 = ev_get(ctx), e1 = ev_get(ctx);
+    float best = 0.0f;
+    int best_n = 256;
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    for (int cand : {256, 128}) {
+        p.tile_n = cand;
+        Run r;
+        fo_status rs = run_product(ctx, p, st, s, "autotune", cand, &r);   // warm-up
+        if (rs != FO_OK) { ctx->prof = prof; return rs; }
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; ++rep) {
+            rs = run_product(ctx, p, st, s, "autotune", cand, &r);
+            if (rs != FO_OK) { ctx->prof = prof; return rs; }
+        }
+        cudaEventRecord(e1, s);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            ctx->prof = prof;
+            return fail(ctx, FO_ERR_CUDA, "autotune timing failed");
+        }
+        if (cand == 256 || ms < best) {
+            best = ms;
+            best_n = cand;
+        }
+    }
+    ctx->prof = prof;
+    ctx->ev_pool.push_back(e0);
+    ctx->ev_pool.push_back(e1);
+    int flag = 0;
+    FO_CUDA(cudaMemcpy(&flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost), "autotune flag");
+    if (flag) return fail(ctx, FO_ERR_DEVICE_TIMEOUT, "tensor-core wait timed out during autotuning");
+    p.tile_n = best_n;
+    return FO_OK;
+}
+
+fo_status get_plan(fo_ctx* ctx, const PlanKey& key, Plan** out) {
+    for (size_t i = 0; i < ctx->plans.size(); ++i) {
+        if (ctx->plans[i]->key == key && ctx->plans[i]->ws_gen == ctx->ws_gen) {
+            std::unique_ptr<Plan> p = std::move(ctx->plans[i]);
+            ctx->plans.erase(ctx->plans.begin() + i);
+            ctx->plans.push_back(std::move(p));
+            *out = ctx->plans.back().get();
+            return FO_OK;
+        }
+    }
+    std::unique_ptr<Plan> p(new (std::nothrow) Plan());
+    if (!p) return fail(ctx, FO_ERR_NOMEM, "plan allocation failed");
+    FO_TRY(layout_plan(ctx, key, p.get()));
+    FO_TRY(ensure_ws(ctx, p->total));
+    // stale plans (older workspace) and the least recently used beyond the cap
+    bool stale = false;
+    for (auto& q : ctx->plans) stale |= q->ws_gen != ctx->ws_gen;
+    if (stale || ctx->plans.size() >= kMaxPlans) cudaDeviceSynchronize();
+    ctx->plans.erase(std::remove_if(ctx->plans.begin(), ctx->plans.end(),
+                                    [&](const std::unique_ptr<Plan>& q) { return q->ws_gen != ctx->ws_gen; }),
+                     ctx->plans.end());
+    while (ctx->plans.size() >= kMaxPlans) ctx->plans.erase(ctx->plans.begin());
+    FO_TRY(place_plan(ctx, p.get()));
+    FO_TRY(autotune(ctx, *p));
+    ctx->plans.push_back(std::move(p));
+    *out = ctx->plans.back().get();
     return FO_OK;
 }
 
@@ -486,112 +730,144 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
     if (prm->mu_mode < FO_MU_FIXED || prm->mu_mode > FO_MU_LEARNED)
         return fail(ctx, FO_ERR_ARG, "unknown mu_mode");
     if (prm->mu_mode == FO_MU_LEARNED) return fail(ctx, FO_ERR_UNSUPPORTED, "learned mu needs a trained model");
+    if (prm->tile_n != 0 && prm->tile_n != 128 && prm->tile_n != 256)
+        return fail(ctx, FO_ERR_ARG, "tile_n must be 0, 128 or 256");
     return FO_OK;
 }
 
-fo_status density_impl(fo_ctx* ctx, const double* dH, int64_t n, int64_t ld, double n_e,
-                       const fo_params* prm, double* dP, int64_t ldp, fo_result* res,
-                       cudaStream_t st) {
-    FO_TRY(check_params(ctx, prm));
-    if (!dH || !dP) return fail(ctx, FO_ERR_ARG, "H and P must be non-NULL");
-    if (ld < n || ldp < n) return fail(ctx, FO_ERR_ARG, "leading dimensions must be >= n");
-    const bool bisect = prm->mu_mode == FO_MU_BISECT;
-    if (bisect && !(n_e >= 0.0 && n_e <= (double)n)) return fail(ctx, FO_ERR_ARG, "n_e must be in [0, n]");
-    Plan p;
-    FO_TRY(make_plan(ctx, n, prm->n_terms, prm->k, prm->precision, bisect, bisect, prm->n_quad, &p));
-    FO_TRY(ensure_ws(ctx, p.total));
-    Slots S{wsb(ctx) + p.off_t, wsb(ctx) + p.off_r, p.slot_bytes, p.np, p.planes};
-    const int sym = 1;  // symmetric products (upper-triangle tiles, mirrored)
-    int n_gemm = 0, launches = 0, lstage = 0;
-    char* W = wsb(ctx);
-    double* part = reinterpret_cast<double*>(W + p.off_part);
-    const int hcall = prof_begin(ctx, st, FO_STAGE_CALL);
-
-    // spectral bounds and X = scaled H (split into planes for the tensor-core forms)
-    int h = prof_begin(ctx, st, FO_STAGE_BOUNDS);
-    FO_CUDA(cudaMemsetAsync(ctx->res, 0, sizeof(DevResult), st), "memset");
-    FO_CUDA(launch_gershgorin(dH, n, ld, part, part + p.nparts, reinterpret_cast<int*>(part + 2 * p.nparts),
-                              p.nparts, ctx->res, prm->use_given_bounds, prm->emin, prm->emax, st),
-            "bounds");
-    FO_TRY(pack_x(ctx, p, S, dH, ld, st));
-    lstage = (prm->use_given_bounds ? 1 : 2) + 1;
-    prof_end(ctx, st, h, 0.0, lstage);
-    launches += lstage;
-
-    // baby steps T_2 .. T_k
-    const int g0 = n_gemm;
-    FO_TRY(baby_steps(ctx, p, S, p.k, st, sym, &n_gemm));
-    double* ct = reinterpret_cast<double*>(W + p.off_ct);
-    FO_CUDA(launch_cos_table(p.M, ct, st), "cos_table");
-    launches += 1;
-    const int max_it = prm->max_bisect > 0 ? prm->max_bisect : 200;
-    if (bisect) {
-        // giant steps T_{2k} .. T_{(m-1)k}, exact moments, bisection for mu
-        if (p.giants) FO_TRY(giant_steps(ctx, p, S, st, sym, &n_gemm));
-        h = prof_begin(ctx, st, FO_STAGE_MOMENTS);
-        FO_TRY(exact_moments(ctx, p, S, st));
-        lstage = 1 + ((p.m > 1 && p.k > 1) ? 2 : 0) + 1;
-        prof_end(ctx, st, h, 0.0, lstage);
-        launches += lstage;
-        h = prof_begin(ctx, st, FO_STAGE_MU);
-        double* w = reinterpret_cast<double*>(W + p.off_w);
-        FO_CUDA(launch_dos_weights(reinterpret_cast<double*>(W + p.off_tau), p.n_terms, p.M, ct, w, st),
-                "dos_weights");
-        FO_CUDA(launch_bisect(w, ct, p.M, ctx->res, prm->kT, n_e, max_it, st), "bisect");
-        prof_end(ctx, st, h, 0.0, 2);
-        launches += 2;
-    } else {
-        // fixed mu: write it into the device record (kept after the bounds pass)
-        FO_CUDA(launch_set_scalar(&ctx->res->mu, prm->mu, st), "mu");
-        launches += 1;
+fo_status ensure_hres(fo_ctx* ctx, size_t count) {
+    if (ctx->hres_count >= count) return FO_OK;
+    if (ctx->hres) cudaFreeHost(ctx->hres);
+    ctx->hres = nullptr;
+    ctx->hres_count = 0;
+    if (cudaMallocHost(&ctx->hres, sizeof(DevResult) * count) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, FO_ERR_NOMEM, "pinned readback buffer allocation failed");
     }
-    h = prof_begin(ctx, st, FO_STAGE_COEFFS);
-    lstage = 0;
-    FO_TRY(coefficients(ctx, p, prm->kT, st, &lstage));
-    prof_end(ctx, st, h, 0.0, lstage);
-    launches += lstage;
-    h = prof_begin(ctx, st, FO_STAGE_CONTRACT);
-    lstage = 0;
-    FO_TRY(contraction(ctx, p, S, dP, ldp, st, &lstage));
-    prof_end(ctx, st, h, 0.0, lstage);
-    launches += lstage;
-    FO_TRY(clenshaw(ctx, p, S, dP, ldp, st, sym, &n_gemm));
-    launches += n_gemm - g0;
-    h = prof_begin(ctx, st, FO_STAGE_TRACE);
-    FO_CUDA(launch_trace_frob(dP, n, ldp, part, p.nparts, ctx->res, st), "trace");
-    prof_end(ctx, st, h, 0.0, 2);
-    launches += 2;
-    prof_end(ctx, st, hcall, product_flops(p) * n_gemm, launches);
+    ctx->hres_count = count;
+    return FO_OK;
+}
+
+// Density matrices of `batch` instances (caller order) on one plan.
+fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const int64_t* n, const int64_t* ld,
+                        const double* n_e, const double* kT, const fo_params* prm, double* const* dP,
+                        const int64_t* ldp, fo_result* res, cudaStream_t st) {
+    FO_TRY(check_params(ctx, prm));
+    if (batch < 1 || !dH || !dP || !n || !n_e) return fail(ctx, FO_ERR_ARG, "bad batch arguments");
+    const bool bisect = prm->mu_mode == FO_MU_BISECT;
+    for (int b = 0; b < batch; ++b) {
+        if (!dH[b] || !dP[b]) return fail(ctx, FO_ERR_ARG, "H and P must be non-NULL");
+        if (n[b] < 1) return fail(ctx, FO_ERR_ARG, "n must be >= 1");
+        if ((ld && ld[b] < n[b]) || (ldp && ldp[b] < n[b]))
+            return fail(ctx, FO_ERR_ARG, "leading dimensions must be >= n");
+        if (bisect && !(n_e[b] >= 0.0 && n_e[b] <= (double)n[b]))
+            return fail(ctx, FO_ERR_ARG, "n_e must be in [0, n]");
+        if (kT && (!(kT[b] > 0.0) || !std::isfinite(kT[b]))) return fail(ctx, FO_ERR_ARG, "kT must be > 0");
+    }
+    PlanKey key;
+    key.n.assign(n, n + batch);
+    key.mode = MODE_DENSITY;
+    key.n_terms = prm->n_terms;
+    key.k_req = prm->k;
+    key.prec = prm->precision;
+    key.mu_mode = prm->mu_mode;
+    key.n_quad = prm->n_quad;
+    key.use_given = prm->use_given_bounds ? 1 : 0;
+    key.tile_req = prm->tile_n;
+    key.max_bisect = prm->max_bisect;
+    Plan* p = nullptr;
+    FO_TRY(get_plan(ctx, key, &p));
+
+    std::vector<InstIO> io(batch);
+    for (int j = 0; j < batch; ++j) {
+        const int b = p->order[j];
+        InstIO& x = io[j];
+        std::memset(&x, 0, sizeof(x));
+        x.H = dH[b];
+        x.P = dP[b];
+        x.ldh = ld ? ld[b] : n[b];
+        x.ldp = ldp ? ldp[b] : n[b];
+        x.kT = kT ? kT[b] : prm->kT;
+        x.n_e = n_e[b];
+        x.mu = prm->mu;
+        x.emin = prm->emin;
+        x.emax = prm->emax;
+    }
+    Run run;
+    const int hcall = prof_begin(ctx, st, FO_STAGE_CALL);
+    FO_CUDA(launch_set_io(io.data(), batch, p->d_io, p->d_inst, 0, st), "set_io");
+    run.launches += (batch + 63) / 64;
+    const bool graph = (prm->flags & FO_FLAG_GRAPH) != 0;
+    if (graph) {
+        if (!p->graph) {
+            if (!ctx->cap) FO_CUDA(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking), "capture stream");
+            FO_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            ctx->capturing = true;
+            Run cap_run;
+            const fo_status rs = run_density(ctx, *p, ctx->cap, &cap_run);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &g);
+            ctx->capturing = false;
+            if (rs != FO_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rs;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ctx, ce, "end capture");
+            p->graph_launches = cap_run.launches;
+            const cudaError_t ie = cudaGraphInstantiate(&p->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                p->graph = nullptr;
+                return cuda_fail(ctx, ie, "graph instantiate");
+            }
+        }
+        FO_CUDA(cudaGraphLaunch(p->graph, st), "graph launch");
+        // the graph holds the same launches as an eager call
+        run.n_gemm = (p->sh.k - 1) + (p->giants ? p->sh.m - 2 : 0) + (p->sh.m > 1 ? p->sh.m - 1 : 0);
+        run.launches += p->graph_launches;
+    } else {
+        FO_TRY(run_density(ctx, *p, st, &run));
+    }
+    prof_end(ctx, st, hcall, p->flops_product * run.n_gemm, run.launches);
     if (ctx->prof) ctx->prof_calls += 1;
 
     if (res && !(prm->flags & FO_FLAG_NO_RESULT_SYNC)) {
-        DevResult hr;
-        int flag[5] = {0, 0, 0, 0, 0};
-        FO_CUDA(cudaMemcpyAsync(&hr, ctx->res, sizeof(DevResult), cudaMemcpyDeviceToHost, st), "readback");
+        FO_TRY(ensure_hres(ctx, batch));
+        int flag[4] = {0, 0, 0, 0};
+        FO_CUDA(cudaMemcpyAsync(ctx->hres, p->d_res, sizeof(DevResult) * batch, cudaMemcpyDeviceToHost, st),
+                "readback");
         FO_CUDA(cudaMemcpyAsync(flag, ctx->flag, sizeof(flag), cudaMemcpyDeviceToHost, st), "readback");
         FO_CUDA(cudaStreamSynchronize(st), "sync");
         if (flag[1] != 0)
             return fail(ctx, FO_ERR_CUDA, "self-check violation code " + std::to_string(flag[1]) + " (" +
                                               std::to_string(flag[2]) + ", " + std::to_string(flag[3]) + ")");
-        std::memset(res, 0, sizeof(*res));
-        res->mu = hr.mu;
-        res->trace = hr.trace;
-        res->trace_poly = hr.trace_poly;
-        res->frob2 = hr.frob2;
-        res->emin = hr.bounds[0];
-        res->emax = hr.bounds[1];
-        res->k = p.k;
-        res->m = p.m;
-        res->n_gemm = n_gemm;
-        res->bisect_iters = hr.iters;
-        res->learned_accepted = 0;
-        res->n_launches = launches;
-        int status = hr.status;
-        if (flag[0]) status = FO_ERR_DEVICE_TIMEOUT;
-        res->status = status;
-        if (status != FO_OK)
-            return fail(ctx, (fo_status)status, std::string("device stage failed: ") +
-                                                    fo_status_string((fo_status)status));
+        fo_status first = FO_OK;
+        for (int j = 0; j < batch; ++j) {
+            const DevResult& hr = ctx->hres[j];
+            fo_result& r = res[p->order[j]];
+            std::memset(&r, 0, sizeof(r));
+            r.mu = hr.mu;
+            r.trace = hr.trace;
+            r.trace_poly = hr.trace_poly;
+            r.frob2 = hr.frob2;
+            r.emin = hr.bounds[0];
+            r.emax = hr.bounds[1];
+            r.k = p->sh.k;
+            r.m = p->sh.m;
+            r.n_gemm = run.n_gemm;
+            r.bisect_iters = hr.iters;
+            r.learned_accepted = hr.learned_ok;
+            r.n_launches = run.launches;
+            r.tile_n = p->tile_n;
+            r.evals = 1;
+            r.order = 0;
+            int status = hr.status;
+            if (flag[0]) status = FO_ERR_DEVICE_TIMEOUT;
+            r.status = status;
+            if (status != FO_OK && first == FO_OK) first = (fo_status)status;
+        }
+        if (first != FO_OK)
+            return fail(ctx, first, std::string("device stage failed: ") + fo_status_string(first));
     }
     return FO_OK;
 }
@@ -600,7 +876,7 @@ fo_status density_impl(fo_ctx* ctx, const double* dH, int64_t n, int64_t ld, dou
 
 extern "C" {
 
-const char* fo_version(void) { return "fermi-gb300 0.1"; }
+const char* fo_version(void) { return "fermi-gb300 0.2"; }
 
 const char* fo_status_string(fo_status s) {
     switch (s) {
@@ -632,14 +908,11 @@ fo_status fo_create(fo_ctx** out, int device) {
     ctx->device = device;
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMalloc(&ctx->res, sizeof(DevResult)) != cudaSuccess ||
-        cudaMalloc(&ctx->flag, 8 * sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&ctx->flag, 8 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->res) cudaFree(ctx->res);
         delete ctx;
         return FO_ERR_NOMEM;
     }
-    cudaMemset(ctx->res, 0, sizeof(DevResult));
     cudaMemset(ctx->flag, 0, 8 * sizeof(int));
     *out = ctx;
     return FO_OK;
@@ -651,11 +924,13 @@ fo_status fo_destroy(fo_ctx* ctx) {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         prof_collect(ctx);
+        ctx->plans.clear();
         for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
         if (ctx->ws) cudaFree(ctx->ws);
         if (ctx->stage) cudaFree(ctx->stage);
-        if (ctx->res) cudaFree(ctx->res);
         if (ctx->flag) cudaFree(ctx->flag);
+        if (ctx->hres) cudaFreeHost(ctx->hres);
+        if (ctx->cap) cudaStreamDestroy(ctx->cap);
     }
     delete ctx;
     return FO_OK;
@@ -667,13 +942,18 @@ fo_status fo_spectral_bounds(fo_ctx* ctx, const double* dH, int64_t n, int64_t l
     if (!dH || !d_bounds || n < 1 || ld < n) return fail(ctx, FO_ERR_ARG, "bad arguments");
     DeviceGuard g(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int nparts = 2 * ctx->num_sms;
-    FO_TRY(ensure_ws(ctx, align256(8 * 3 * (size_t)nparts + 64)));
-    double* part = reinterpret_cast<double*>(ctx->ws);
-    FO_CUDA(launch_gershgorin(dH, n, ld, part, part + nparts, reinterpret_cast<int*>(part + 2 * nparts),
-                              nparts, ctx->res, 0, 0.0, 0.0, st),
-            "bounds");
-    FO_CUDA(launch_export_bounds(ctx->res, d_bounds, st), "bounds export");
+    PlanKey key;
+    key.n = {n};
+    key.mode = MODE_BOUNDS;
+    Plan* p = nullptr;
+    FO_TRY(get_plan(ctx, key, &p));
+    InstIO io;
+    std::memset(&io, 0, sizeof(io));
+    io.H = dH;
+    io.ldh = ld;
+    FO_CUDA(launch_set_io(&io, 1, p->d_io, p->d_inst, 0, st), "set_io");
+    FO_CUDA(launch_bounds(p->d_inst, p->d_io, 1, p->wg.dev, p->part_g, 0, st), "bounds");
+    FO_CUDA(launch_export_bounds(p->d_res, d_bounds, st), "bounds export");
     return FO_OK;
 }
 
@@ -682,35 +962,55 @@ fo_status fo_chebyshev_coeffs(fo_ctx* ctx, double kT, double mu, double emin, do
     if (!ctx) return FO_ERR_ARG;
     if (!d_c || n_terms < 1 || n_terms > 4096) return fail(ctx, FO_ERR_ARG, "bad n_terms or output");
     if (!(kT > 0.0) || !(emax > emin)) return fail(ctx, FO_ERR_ARG, "need kT > 0 and emax > emin");
-    DeviceGuard g(ctx->device);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int M = n_quad > 0 ? n_quad : (2048 > 4 * n_terms ? 2048 : 4 * n_terms);
     if (M < n_terms) return fail(ctx, FO_ERR_ARG, "n_quad must be >= n_terms");
-    const size_t need = align256(8 * 4 * (size_t)M) + align256(8 * (size_t)M);
-    FO_TRY(ensure_ws(ctx, need));
-    double* ct = reinterpret_cast<double*>(ctx->ws);
-    double* f = reinterpret_cast<double*>(wsb(ctx) + align256(8 * 4 * (size_t)M));
-    FO_CUDA(launch_set_bounds(ctx->res, emin, emax, st), "set_bounds");
-    FO_CUDA(launch_set_scalar(&ctx->res->mu, mu, st), "mu");
-    FO_CUDA(launch_cos_table(M, ct, st), "cos_table");
-    FO_CUDA(launch_fermi_nodes(M, ct, ctx->res, kT, f, st), "fermi_nodes");
-    FO_CUDA(launch_coeffs(f, ct, M, n_terms, n_terms, d_c, st), "coeffs");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PlanKey key;
+    key.n = {1};
+    key.mode = MODE_COEFFS;
+    key.n_terms = n_terms;
+    key.n_quad = n_quad;
+    Plan* p = nullptr;
+    FO_TRY(get_plan(ctx, key, &p));
+    InstIO io;
+    std::memset(&io, 0, sizeof(io));
+    io.kT = kT;
+    io.mu = mu;
+    io.emin = emin;
+    io.emax = emax;
+    FO_CUDA(launch_set_io(&io, 1, p->d_io, p->d_inst, 0, st), "set_io");
+    FO_CUDA(launch_bounds(p->d_inst, p->d_io, 1, p->wg.dev, p->part_g, 1, st), "bounds");
+    FO_CUDA(launch_set_mu(p->d_inst, p->d_io, 1, st), "mu");
+    FO_CUDA(launch_coefficients(p->d_inst, p->d_io, 1, p->sh, p->ct, 0, st, nullptr), "coeffs");
+    FO_CUDA(cudaMemcpyAsync(d_c, p->inst[0].c, 8 * (size_t)n_terms, cudaMemcpyDeviceToDevice, st), "copy");
     return FO_OK;
 }
 
 fo_status fo_density_matrix(fo_ctx* ctx, const double* dH, int64_t n, int64_t ld, double n_e,
-                            const fo_params* params, double* dP, int64_t ldp, fo_result* res,
-                            void* stream) {
+                            const fo_params* params, double* dP, int64_t ldp, fo_result* res, void* stream) {
     if (!ctx) return FO_ERR_ARG;
     DeviceGuard g(ctx->device);
-    return density_impl(ctx, dH, n, ld, n_e, params, dP, ldp, res, reinterpret_cast<cudaStream_t>(stream));
+    double* P = dP;
+    return density_batch(ctx, 1, &dH, &n, &ld, &n_e, nullptr, params, &P, &ldp, res,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+fo_status fo_density_matrix_batched(fo_ctx* ctx, int32_t batch, const double* const* dH, const int64_t* n,
+                                    const int64_t* ld, const double* n_e, const double* kT,
+                                    const fo_params* params, double* const* dP, const int64_t* ldp,
+                                    fo_result* res, void* stream) {
+    if (!ctx) return FO_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    return density_batch(ctx, batch, dH, n, ld, n_e, kT, params, dP, ldp, res,
+                         reinterpret_cast<cudaStream_t>(stream));
 }
 
 fo_status fo_density_matrix_host(fo_ctx* ctx, const double* hH, int64_t n, int64_t ld, double n_e,
                                  const fo_params* params, double* hP, int64_t ldp, fo_result* res,
                                  void* stream) {
     if (!ctx) return FO_ERR_ARG;
-    if (!hH || !hP || n < 1 || ld < n || ldp < n) return fail(ctx, FO_ERR_ARG, "bad arguments");
+    if (!hH || !hP || n < 1 || ld < n || ldp < n || !params) return fail(ctx, FO_ERR_ARG, "bad arguments");
     DeviceGuard g(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t mat = align256((size_t)n * n * 8);
@@ -733,7 +1033,9 @@ fo_status fo_density_matrix_host(fo_ctx* ctx, const double* hH, int64_t n, int64
     fo_params prm = *params;
     prm.flags &= ~FO_FLAG_NO_RESULT_SYNC;
     fo_result local;
-    fo_status s = density_impl(ctx, dH, n, n, n_e, &prm, dP, n, res ? res : &local, st);
+    const double* cH = dH;
+    const int64_t ldn = n;
+    fo_status s = density_batch(ctx, 1, &cH, &n, &ldn, &n_e, nullptr, &prm, &dP, &ldn, res ? res : &local, st);
     if (s != FO_OK && s != FO_ERR_NOT_CONVERGED) return s;
     FO_CUDA(cudaMemcpy2DAsync(hP, ldp * 8, dP, n * 8, n * 8, n, cudaMemcpyDeviceToHost, st), "D2H");
     FO_CUDA(cudaStreamSynchronize(st), "sync");
@@ -748,19 +1050,28 @@ fo_status fo_moments(fo_ctx* ctx, const double* dH, int64_t n, int64_t ld, const
     DeviceGuard g(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int K = n_moments <= 2 ? 1 : (n_moments + 1) / 2;
-    Plan p;
     // k = K baby steps, m = 2: the assembly then covers tau_0 .. tau_{2K-1}
-    FO_TRY(make_plan(ctx, n, 2 * K, K, precision, false, true, 0, &p));
-    FO_TRY(ensure_ws(ctx, p.total));
-    Slots S{wsb(ctx) + p.off_t, wsb(ctx) + p.off_r, p.slot_bytes, p.np, p.planes};
-    const int sym = 1;  // symmetric products (upper-triangle tiles, mirrored)
-    FO_CUDA(cudaMemcpyAsync(ctx->res->bounds, d_bounds, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st),
-            "bounds");
-    FO_TRY(pack_x(ctx, p, S, dH, ld, st));
-    int n_gemm = 0;
-    FO_TRY(baby_steps(ctx, p, S, p.k, st, sym, &n_gemm));
-    FO_TRY(exact_moments(ctx, p, S, st));
-    FO_CUDA(cudaMemcpyAsync(d_tau, wsb(ctx) + p.off_tau, 8 * (size_t)n_moments, cudaMemcpyDeviceToDevice, st),
+    PlanKey key;
+    key.n = {n};
+    key.mode = MODE_MOMENTS;
+    key.n_terms = 2 * K;
+    key.k_req = K;
+    key.prec = precision;
+    key.use_given = 1;
+    Plan* p = nullptr;
+    FO_TRY(get_plan(ctx, key, &p));
+    InstIO io;
+    std::memset(&io, 0, sizeof(io));
+    io.H = dH;
+    io.ldh = ld;
+    io.bounds_src = d_bounds;
+    Run run;
+    FO_CUDA(launch_set_io(&io, 1, p->d_io, p->d_inst, 0, st), "set_io");
+    FO_CUDA(launch_bounds(p->d_inst, p->d_io, 1, p->wg.dev, p->part_g, 1, st), "bounds");
+    FO_CUDA(launch_scale(p->d_inst, p->d_io, p->wsc.dev, p->sh, st, ctx->flag + 1), "scale");
+    FO_TRY(baby_steps(ctx, *p, p->sh.k, st, &run));
+    FO_TRY(exact_moments(ctx, *p, st, &run));
+    FO_CUDA(cudaMemcpyAsync(d_tau, p->inst[0].tau, 8 * (size_t)n_moments, cudaMemcpyDeviceToDevice, st),
             "tau copy");
     return FO_OK;
 }
@@ -809,35 +1120,32 @@ fo_status fo_recurrence_product(fo_ctx* ctx, int32_t precision, int32_t symmetri
     if (!dA || !dB || !dOut || n < 1 || ld < n || n > 65536) return fail(ctx, FO_ERR_ARG, "bad arguments");
     DeviceGuard g(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    Plan p;
-    FO_TRY(make_plan(ctx, n, 4, 2, precision, false, false, 0, &p));
+    PlanKey key;
+    key.n = {n};
+    key.mode = MODE_PRODUCT;
+    key.prec = precision;
+    key.sym = symmetric ? 1 : 0;
+    key.n_terms = 4;
+    key.k_req = 2;
+    Plan* p = nullptr;
+    FO_TRY(get_plan(ctx, key, &p));
+    const Inst& in = p->inst[0];
+    const Shape& sh = p->sh;
+    const float ps = sh.fp16 ? sh.pscale_t : 1.0f;
+    InstIO io;
+    std::memset(&io, 0, sizeof(io));
+    FO_CUDA(launch_set_io(&io, 1, p->d_io, p->d_inst, 0, st), "set_io");
     // slots: 0 = A, 1 = B, 2 = C, 3 = D, 4 = out
-    const size_t bytes = p.slot_bytes * 5;
-    FO_TRY(ensure_ws(ctx, bytes));
-    Slots S{wsb(ctx), wsb(ctx), p.slot_bytes, p.np, p.planes};
-    const float ps = p.fp16 ? p.pscale_t : 1.0f;
-    FO_CUDA(launch_pack_f32(dA, n, ld, S.T(0), p.np, p.planes, p.fp16, ps, st), "pack");
-    FO_CUDA(launch_pack_f32(dB, n, ld, S.T(1), p.np, p.planes, p.fp16, ps, st), "pack");
-    if (dC) FO_CUDA(launch_pack_f32(dC, n, ld, S.T(2), p.np, 0, 0, 1.0f, st), "pack");
-    if (dD) FO_CUDA(launch_pack_f32(dD, n, ld, S.T(3), p.np, 0, 0, 1.0f, st), "pack");
-    Epilogue ep;
-    std::memset(&ep, 0, sizeof(ep));
-    ep.alpha = (float)((double)alpha / ((double)ps * ps));
-    ep.beta = beta;
-    ep.shift = shift;
-    ep.n_real = (int32_t)n;
-    ep.C = dC ? S.T(2).x : nullptr;
-    ep.D = dD ? S.T(3).x : nullptr;
-    ep.ld = p.np;
-    ep.out = S.T(4);
-    ep.planes = 0;
-    ep.fp16 = p.fp16;
-    ep.plane_scale = 1.0f;
-    ep.dbg = ctx->flag + 1;
-    std::string err;
-    cudaError_t e = tc_gemm(p.prec, p.np, S.T(0), S.T(1), ep, symmetric ? 1 : 0, ctx->flag, st, &err);
-    if (e != cudaSuccess) return err.empty() ? cuda_fail(ctx, e, "tc_gemm") : fail(ctx, FO_ERR_CUDA, err);
-    FO_CUDA(cudaMemcpy2DAsync(dOut, ld * 4, S.T(4).x, p.np * 4, n * 4, n, cudaMemcpyDeviceToDevice, st),
+    FO_CUDA(launch_pack_f32(dA, n, ld, in.slots, in.np, sh.planes, sh.fp16, ps, st), "pack");
+    FO_CUDA(launch_pack_f32(dB, n, ld, in.slots + in.slot_bytes, in.np, sh.planes, sh.fp16, ps, st), "pack");
+    if (dC) FO_CUDA(launch_pack_f32(dC, n, ld, in.slots + 2 * in.slot_bytes, in.np, 0, 0, 1.0f, st), "pack");
+    if (dD) FO_CUDA(launch_pack_f32(dD, n, ld, in.slots + 3 * in.slot_bytes, in.np, 0, 0, 1.0f, st), "pack");
+    Step stp = make_step(*p, 0, 1, dC ? 2 : -1, dD ? 3 : -1, 4, alpha, beta, shift, false, false, false, false, ctx);
+    stp.planes = 0;
+    Run run;
+    FO_TRY(run_product(ctx, *p, stp, st, "product", 0, &run));
+    FO_CUDA(cudaMemcpy2DAsync(dOut, ld * 4, in.slots + 4 * in.slot_bytes, in.np * 4, n * 4, n,
+                              cudaMemcpyDeviceToDevice, st),
             "copy out");
     return FO_OK;
 }

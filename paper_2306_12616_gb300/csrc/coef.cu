@@ -34,10 +34,14 @@ __global__ void k_cos_table(int M, double* ct) {
 
 // w_j = (1/M) (tau_0 + 2 sum_{n=1}^{n_terms-1} tau_n cos(n theta_j)), so that
 // sum_n c_n(mu) tau_n = sum_j f(e_j; mu) w_j for the interpolation coefficients c_n.
-__global__ void k_dos_weights(const double* __restrict__ tau, int n_terms, int M,
-                              const double* __restrict__ ct, double* __restrict__ w) {
+// Block (node chunk, instance).
+__global__ void k_dos_weights(const Inst* __restrict__ insts, int n_terms, int M,
+                              const double* __restrict__ ct) {
+    const Inst& in = insts[blockIdx.y];
+    if (!in.res->active) return;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
+    const double* tau = in.tau;
     const int64_t q = 2LL * j + 1, fourM = 4LL * M;
     int64_t r = 0;
     double s = 0.0;
@@ -46,7 +50,7 @@ __global__ void k_dos_weights(const double* __restrict__ tau, int n_terms, int M
         if (r >= fourM) r -= fourM;
         s = fma(tau[n], ct[r], s);
     }
-    w[j] = (tau[0] + 2.0 * s) / (double)M;
+    in.w[j] = (tau[0] + 2.0 * s) / (double)M;
 }
 
 // F(mu) + N_e = sum_j w_j f(e_j; mu) and dF/dmu = sum_j w_j f_j (1 - f_j) / kT over the M
@@ -77,17 +81,24 @@ __device__ void trace_at(double mu, const double* __restrict__ w, const double* 
     if (dtr) *dtr = sh[65];
 }
 
-// Root of F(mu) = sum_n c_n(mu) tau_n - N_e on one block. Bracket [emin, emax], widened by
-// 10 kT (at most 8 times per side). Inside the bracket a Newton step on the exact derivative
-// of the node sum is taken when it stays in the bracket, a halving otherwise; the bracket
-// shrinks with the sign of F at every evaluated point. Stop when |F| <= 1e-12 max(1, N_e)
-// (mu = that point) or the bracket is narrower than 1e-15 (emax - emin) (mu = midpoint), at
-// most max_iter evaluations.
-__global__ void __launch_bounds__(512) k_bisect(const double* __restrict__ w,
+// Root of F(mu) = sum_n c_n(mu) tau_n - N_e, one block per instance. Bracket [emin, emax],
+// widened by 10 kT (at most 8 times per side). Inside the bracket a Newton step on the
+// exact derivative of the node sum is taken when it stays in the bracket, a halving
+// otherwise; the bracket shrinks with the sign of F at every evaluated point. The first
+// point is the midpoint, or res->mu0 when start_mu0 is set and mu0 lies inside the
+// bracket (the learned proposal). Stop when |F| <= 1e-12 max(1, N_e) (mu = that point) or
+// the bracket is narrower than 1e-15 (emax - emin) (mu = midpoint), at most max_iter
+// evaluations.
+__global__ void __launch_bounds__(512) k_bisect(const Inst* __restrict__ insts,
+                                                 const InstIO* __restrict__ io,
                                                  const double* __restrict__ ct, int M,
-                                                 DevResult* res, double kT, double n_e,
-                                                 int max_iter) {
+                                                 int max_iter, int start_mu0) {
     __shared__ double sh[66];
+    const Inst& in = insts[blockIdx.x];
+    DevResult* res = in.res;
+    if (!res->active) return;
+    const double* w = in.w;
+    const double kT = io[blockIdx.x].kT, n_e = io[blockIdx.x].n_e;
     const double ea = res->bounds[0], eb = res->bounds[1];
     const double mid = 0.5 * (eb + ea), half = 0.5 * (eb - ea), inv2kT = 0.5 / kT;
     double lo = ea, hi = eb, t;
@@ -115,6 +126,7 @@ __global__ void __launch_bounds__(512) k_bisect(const double* __restrict__ w,
         const double tol_w = 1e-15 * (eb - ea);
         bool done = false;
         double x = 0.5 * (lo + hi);
+        if (start_mu0 && res->mu0 > lo && res->mu0 < hi) x = res->mu0;
         for (int it = 1; it <= max_iter; ++it) {
             double f, df;
             trace_at(x, w, ct, M, mid, half, inv2kT, sh, &f, &df);
@@ -140,26 +152,40 @@ __global__ void __launch_bounds__(512) k_bisect(const double* __restrict__ w,
     }
 }
 
+// mu of FO_MU_FIXED from the per-call inputs.
+__global__ void k_set_mu(const Inst* __restrict__ insts, const InstIO* __restrict__ io, int batch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < batch) insts[i].res->mu = io[i].mu;
+}
+
 // f_j = f(e_j; mu) at the nodes e_j = mid + half x_j, mu read from the device record.
-__global__ void k_fermi_nodes(int M, const double* __restrict__ ct, const DevResult* res,
-                              double kT, double* __restrict__ f) {
+// Block (node chunk, instance).
+__global__ void k_fermi_nodes(const Inst* __restrict__ insts, const InstIO* __restrict__ io, int M,
+                              const double* __restrict__ ct) {
+    const Inst& in = insts[blockIdx.y];
+    const DevResult* res = in.res;
+    if (!res->active) return;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     const double ea = res->bounds[0], eb = res->bounds[1];
-    f[j] = fermi(0.5 * (eb + ea) + 0.5 * (eb - ea) * ct[2 * j + 1], res->mu, 0.5 / kT);
+    in.f[j] = fermi(0.5 * (eb + ea) + 0.5 * (eb - ea) * ct[2 * j + 1], res->mu, 0.5 / io[blockIdx.y].kT);
 }
 
 // c_n = (2 - delta_{n0}) / M sum_j f_j cos(n theta_j) for n < n_terms, 0 for n_terms <= n < km.
-// One warp per n.
-__global__ void k_coeffs(const double* __restrict__ f, const double* __restrict__ ct, int M,
-                         int n_terms, int km, double* __restrict__ c) {
+// One warp per n; block (warp group, instance).
+__global__ void k_coeffs(const Inst* __restrict__ insts, const double* __restrict__ ct, int M,
+                         int n_terms, int km) {
+    const Inst& in = insts[blockIdx.y];
+    if (!in.res->active) return;
     const int lane = threadIdx.x & 31;
     const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (n >= km) return;
+    double* c = in.c;
     if (n >= n_terms) {
         if (lane == 0) c[n] = 0.0;
         return;
     }
+    const double* f = in.f;
     const int64_t fourM = 4LL * M;
     double s = 0.0;
     for (int j = lane; j < M; j += 32) {
@@ -173,7 +199,12 @@ __global__ void k_coeffs(const double* __restrict__ f, const double* __restrict_
 // Giant-step coefficients from c (zero-padded to km), g stored l-major: g[l*k + i].
 // c_{lk} = g_{0,l}; c_i = g_{i,0} + g_{k-i,1}/2; c_{lk+i} = (g_{i,l} + g_{k-i,l+1})/2 for
 // 1 <= l <= m-2; c_{(m-1)k+i} = g_{i,m-1}/2; c_i = g_{i,0} if m = 1. Solved downwards in l.
-__global__ void k_g_convert(const double* __restrict__ c, int k, int m, double* __restrict__ g) {
+// One block per instance.
+__global__ void k_g_convert(const Inst* __restrict__ insts, int k, int m) {
+    const Inst& in = insts[blockIdx.x];
+    if (!in.res->active) return;
+    const double* c = in.c;
+    double* g = in.g;
     for (int l = m - 1; l >= 0; --l) {
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
             const double ci = c[l * k + i];
@@ -188,46 +219,54 @@ __global__ void k_g_convert(const double* __restrict__ c, int k, int m, double* 
     }
 }
 
-__global__ void k_poly_trace(const double* __restrict__ c, const double* __restrict__ tau,
-                             int n_terms, DevResult* res) {
+__global__ void k_poly_trace(const Inst* __restrict__ insts, int n_terms) {
+    const Inst& in = insts[blockIdx.x];
+    if (!in.res->active) return;
     double s = 0.0;
-    for (int n = threadIdx.x; n < n_terms; n += 32) s = fma(c[n], tau[n], s);
+    for (int n = threadIdx.x; n < n_terms; n += 32) s = fma(in.c[n], in.tau[n], s);
     s = warp_sum(s);
-    if (threadIdx.x == 0) res->trace_poly = s;
+    if (threadIdx.x == 0) in.res->trace_poly = s;
 }
 
-// R_l = g_{0,l} I_n + sum_{i=1}^{k-1} g_{i,l} T_i for all l < m, float64. T_i is slot i-1.
-// Outputs are produced in groups of kGroup l's per pass over the T_i.
+// R_l = g_{0,l} I_n + sum_{i=1}^{k-1} g_{i,l} T_i for all l < m, float64. T_i is slot i-1,
+// R_l slot n_tslots + l. A block covers ew_rows(np) rows of one instance; outputs are
+// produced in groups of kGroup l's per pass over the T_i.
 constexpr int kGroup = 16;
 
-__global__ void __launch_bounds__(256) k_contract_f64(const double* __restrict__ gsrc, int k,
-                                                      int m, const double* __restrict__ tbase,
-                                                      int64_t tstride, double* __restrict__ rbase,
-                                                      int64_t rstride, int64_t n, int64_t np) {
+__global__ void __launch_bounds__(256) k_contract_f64(const Inst* __restrict__ insts, Work we, int k,
+                                                      int m, int n_tslots) {
     extern __shared__ double gsh[];
-    for (int q = threadIdx.x; q < k * m; q += blockDim.x) gsh[q] = gsrc[q];
+    const int i = find_inst(we.pre, 0, we.count, blockIdx.x);
+    const Inst& in = insts[i];
+    if (!in.res->active) return;
+    for (int q = threadIdx.x; q < k * m; q += blockDim.x) gsh[q] = in.g[q];
     __syncthreads();
-    const int64_t total = np * np;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t np = in.np, n = in.n;
+    const int rows = ew_rows(np);
+    const int64_t r0 = (int64_t)(blockIdx.x - we.pre[i]) * rows;
+    const int64_t r1 = r0 + rows < np ? r0 + rows : np;
+    const int64_t tstride = in.slot_bytes / 8;
+    const double* tbase = reinterpret_cast<const double*>(in.slots);
+    double* rbase = reinterpret_cast<double*>(in.slots + n_tslots * in.slot_bytes);
+    for (int64_t idx = r0 * np + threadIdx.x; idx < r1 * np; idx += blockDim.x) {
         const int64_t r = idx / np, col = idx - r * np;
         const bool diag = (r == col) && (r < n);
         for (int l0 = 0; l0 < m; l0 += kGroup) {
             double acc[kGroup];
 #pragma unroll
             for (int q = 0; q < kGroup; ++q) acc[q] = 0.0;
-            for (int i = 1; i < k; ++i) {
-                const double t = tbase[(int64_t)(i - 1) * tstride + idx];
+            for (int t = 1; t < k; ++t) {
+                const double v = tbase[(int64_t)(t - 1) * tstride + idx];
 #pragma unroll
                 for (int q = 0; q < kGroup; ++q)
-                    if (l0 + q < m) acc[q] = fma(gsh[(l0 + q) * k + i], t, acc[q]);
+                    if (l0 + q < m) acc[q] = fma(gsh[(l0 + q) * k + t], v, acc[q]);
             }
 #pragma unroll
             for (int q = 0; q < kGroup; ++q) {
                 if (l0 + q < m) {
                     double v = acc[q];
                     if (diag) v += gsh[(l0 + q) * k];
-                    rbase[(int64_t)(l0 + q) * rstride + idx] = v;
+                    rbase[(int64_t)(l0 + q) * tstride + idx] = v;
                 }
             }
         }
@@ -235,40 +274,45 @@ __global__ void __launch_bounds__(256) k_contract_f64(const double* __restrict__
 }
 
 // float32 version: slots hold a float32 master at element offset 0 and 16-bit planes at
-// element offset plane_off_f (in floats) with plane stride np*np; planes are written for
-// R_{m-1} only (it is the first Clenshaw operand). Four entries per thread.
+// float offset np*np with plane stride np*np; planes are written for R_{m-1} only (it is
+// the first Clenshaw operand). Two entries per thread and step.
 __device__ __forceinline__ uint16_t bf16_bits_c(float v) {
     __nv_bfloat16 h = __float2bfloat16_rn(v);
     return *reinterpret_cast<uint16_t*>(&h);
 }
 
 template <int MAXM>
-__global__ void __launch_bounds__(256) k_contract_f32(const double* __restrict__ gsrc, int k,
-                                                      int m, const float* __restrict__ tbase,
-                                                      int64_t tstride, float* __restrict__ rbase,
-                                                      int64_t rstride, int64_t n, int64_t np,
-                                                      int planes_last, int fp16, float pscale,
-                                                      int64_t plane_off, int* dbg) {
+__global__ void __launch_bounds__(256) k_contract_f32(const Inst* __restrict__ insts, Work we, int k,
+                                                      int m, int n_tslots, int planes_last, int fp16,
+                                                      float pscale, int* dbg) {
     extern __shared__ float fsh[];
-    for (int q = threadIdx.x; q < k * m; q += blockDim.x) fsh[q] = (float)gsrc[q];
+    const int i = find_inst(we.pre, 0, we.count, blockIdx.x);
+    const Inst& in = insts[i];
+    if (!in.res->active) return;
+    for (int q = threadIdx.x; q < k * m; q += blockDim.x) fsh[q] = (float)in.g[q];
     __syncthreads();
-    const int64_t total2 = np * np / 2;
-    for (int64_t i2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i2 < total2;
-         i2 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t idx = i2 * 2;
+    const int64_t np = in.np, n = in.n;
+    const int rows = ew_rows(np);
+    const int64_t r0 = (int64_t)(blockIdx.x - we.pre[i]) * rows;
+    const int64_t r1 = r0 + rows < np ? r0 + rows : np;
+    const int64_t tstride = in.slot_bytes / 4;
+    const int64_t ps = np * np;
+    const float* tbase = reinterpret_cast<const float*>(in.slots);
+    float* rbase = reinterpret_cast<float*>(in.slots + n_tslots * in.slot_bytes);
+    for (int64_t idx = r0 * np + 2 * threadIdx.x; idx < r1 * np; idx += 2 * blockDim.x) {
         const int64_t r = idx / np, col0 = idx - r * np;
         float2 acc[MAXM];
 #pragma unroll
         for (int l = 0; l < MAXM; ++l) acc[l] = make_float2(0.f, 0.f);
 #pragma unroll 4
-        for (int i = 1; i < k; ++i) {
-            const float2 t = *reinterpret_cast<const float2*>(tbase + (int64_t)(i - 1) * tstride + idx);
+        for (int t = 1; t < k; ++t) {
+            const float2 v = *reinterpret_cast<const float2*>(tbase + (int64_t)(t - 1) * tstride + idx);
 #pragma unroll
             for (int l = 0; l < MAXM; ++l) {
                 if (l < m) {
-                    const float gv = fsh[l * k + i];
-                    acc[l].x = fmaf(gv, t.x, acc[l].x);
-                    acc[l].y = fmaf(gv, t.y, acc[l].y);
+                    const float gv = fsh[l * k + t];
+                    acc[l].x = fmaf(gv, v.x, acc[l].x);
+                    acc[l].y = fmaf(gv, v.y, acc[l].y);
                 }
             }
         }
@@ -279,29 +323,29 @@ __global__ void __launch_bounds__(256) k_contract_f32(const double* __restrict__
             float v0 = acc[l].x, v1 = acc[l].y;
             if (d0) v0 += fsh[l * k];
             if (d1) v1 += fsh[l * k];
-            float* dst = rbase + (int64_t)l * rstride + idx;
+            float* dst = rbase + (int64_t)l * tstride + idx;
             if (!FO_CHK(dbg, (reinterpret_cast<uintptr_t>(dst) & 7) == 0, 302, l, idx)) continue;
             *reinterpret_cast<float2*>(dst) = make_float2(v0, v1);
             if (l == m - 1 && planes_last > 0) {
-                uint16_t* p = reinterpret_cast<uint16_t*>(rbase + (int64_t)l * rstride + plane_off) + idx;
-                const int64_t ps = np * np;
+                uint16_t* p = reinterpret_cast<uint16_t*>(rbase + (int64_t)l * tstride + ps) + idx;
                 uint16_t a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
                 if (!fp16) {
                     __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
-                    float r1 = v0 - __bfloat162float(h0);
-                    __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                    float r1f = v0 - __bfloat162float(h0);
+                    __nv_bfloat16 h1 = __float2bfloat16_rn(r1f);
                     a[0] = *reinterpret_cast<uint16_t*>(&h0);
                     a[1] = *reinterpret_cast<uint16_t*>(&h1);
-                    a[2] = bf16_bits_c(r1 - __bfloat162float(h1));
+                    a[2] = bf16_bits_c(r1f - __bfloat162float(h1));
                     h0 = __float2bfloat16_rn(v1);
-                    r1 = v1 - __bfloat162float(h0);
-                    h1 = __float2bfloat16_rn(r1);
+                    r1f = v1 - __bfloat162float(h0);
+                    h1 = __float2bfloat16_rn(r1f);
                     b[0] = *reinterpret_cast<uint16_t*>(&h0);
                     b[1] = *reinterpret_cast<uint16_t*>(&h1);
-                    b[2] = bf16_bits_c(r1 - __bfloat162float(h1));
+                    b[2] = bf16_bits_c(r1f - __bfloat162float(h1));
                 } else {
                     const float x0 = v0 * pscale, x1 = v1 * pscale;
-                    __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x0 - __half2float(__float2half_rn(x0)));
+                    __half h0 = __float2half_rn(x0);
+                    __half h1 = __float2half_rn(x0 - __half2float(h0));
                     a[0] = *reinterpret_cast<uint16_t*>(&h0);
                     a[1] = *reinterpret_cast<uint16_t*>(&h1);
                     h0 = __float2half_rn(x1);
@@ -332,66 +376,54 @@ cudaError_t launch_cos_table(int M, double* ct, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_dos_weights(const double* tau, int n_terms, int M, const double* ct, double* w,
-                               cudaStream_t s) {
-    k_dos_weights<<<(M + 127) / 128, 128, 0, s>>>(tau, n_terms, M, ct, w);
+cudaError_t launch_dos_weights(const Inst* in, int batch, const Shape& sh, const double* ct, cudaStream_t s) {
+    k_dos_weights<<<dim3((sh.M + 127) / 128, batch), 128, 0, s>>>(in, sh.n_terms, sh.M, ct);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bisect(const double* w, const double* ct, int M, DevResult* res, double kT,
-                          double n_e, int max_iter, cudaStream_t s) {
-    k_bisect<<<1, 512, 0, s>>>(w, ct, M, res, kT, n_e, max_iter);
+cudaError_t launch_bisect(const Inst* in, const InstIO* io, int batch, const Shape& sh, const double* ct,
+                          int max_iter, int start_mu0, cudaStream_t s) {
+    k_bisect<<<batch, 512, 0, s>>>(in, io, ct, sh.M, max_iter, start_mu0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fermi_nodes(int M, const double* ct, const DevResult* res, double kT,
-                               double* f, cudaStream_t s) {
-    k_fermi_nodes<<<(M + 255) / 256, 256, 0, s>>>(M, ct, res, kT, f);
+cudaError_t launch_set_mu(const Inst* in, const InstIO* io, int batch, cudaStream_t s) {
+    k_set_mu<<<(batch + 127) / 128, 128, 0, s>>>(in, io, batch);
     return cudaGetLastError();
 }
 
-cudaError_t launch_coeffs(const double* f, const double* ct, int M, int n_terms, int km,
-                          double* c, cudaStream_t s) {
+cudaError_t launch_coefficients(const Inst* in, const InstIO* io, int batch, const Shape& sh,
+                                const double* ct, int with_poly_trace, cudaStream_t s, int* launches) {
+    k_fermi_nodes<<<dim3((sh.M + 255) / 256, batch), 256, 0, s>>>(in, io, sh.M, ct);
     const int warps_per_block = 8;
-    k_coeffs<<<(km + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
-        f, ct, M, n_terms, km, c);
+    k_coeffs<<<dim3((sh.km + warps_per_block - 1) / warps_per_block, batch), 32 * warps_per_block, 0, s>>>(
+        in, ct, sh.M, sh.n_terms, sh.km);
+    k_g_convert<<<batch, sh.k < 1024 ? ((sh.k + 31) / 32) * 32 : 1024, 0, s>>>(in, sh.k, sh.m);
+    int l = 3;
+    if (with_poly_trace) {
+        k_poly_trace<<<batch, 32, 0, s>>>(in, sh.n_terms);
+        ++l;
+    }
+    if (launches) *launches += l;
     return cudaGetLastError();
 }
 
-cudaError_t launch_g_convert(const double* c, int k, int m, double* g, cudaStream_t s) {
-    k_g_convert<<<1, k < 1024 ? ((k + 31) / 32) * 32 : 1024, 0, s>>>(c, k, m, g);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_poly_trace(const double* c, const double* tau, int n_terms, DevResult* res,
-                              cudaStream_t s) {
-    k_poly_trace<<<1, 32, 0, s>>>(c, tau, n_terms, res);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_contract_f64(const double* g, int k, int m, const double* tbase,
-                                int64_t tstride, double* rbase, int64_t rstride, int64_t n,
-                                int64_t np, cudaStream_t s) {
-    const size_t smem = (size_t)k * m * sizeof(double);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_contract_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_contract_f64<<<grid_for(np * np, 256), 256, smem, s>>>(g, k, m, tbase, tstride, rbase,
-                                                              rstride, n, np);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_contract_f32(const double* g, int k, int m, const float* tbase,
-                                int64_t tstride_f, float* rbase, int64_t rstride_f, int64_t n,
-                                int64_t np, int planes_last, int fp16, float pscale,
-                                int64_t plane_off_f, cudaStream_t s, int* dbg) {
-    const size_t smem = (size_t)k * m * sizeof(float);
-    const int blocks = grid_for(np * np / 2, 256);
-    if (m <= 32)
-        k_contract_f32<32><<<blocks, 256, smem, s>>>(g, k, m, tbase, tstride_f, rbase, rstride_f, n,
-                                                      np, planes_last, fp16, pscale, plane_off_f, dbg);
+cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream_t s, int* dbg) {
+    if (sh.is64) {
+        const size_t smem = (size_t)sh.k * sh.m * sizeof(double);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_contract_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_contract_f64<<<we.total, 256, smem, s>>>(in, we, sh.k, sh.m, sh.n_tslots);
+        return cudaGetLastError();
+    }
+    const size_t smem = (size_t)sh.k * sh.m * sizeof(float);
+    const int planes_last = sh.m > 1 ? sh.planes : 0;
+    if (sh.m <= 32)
+        k_contract_f32<32><<<we.total, 256, smem, s>>>(in, we, sh.k, sh.m, sh.n_tslots, planes_last, sh.fp16,
+                                                        sh.pscale_r, dbg);
     else
-        k_contract_f32<64><<<blocks, 256, smem, s>>>(g, k, m, tbase, tstride_f, rbase, rstride_f, n,
-                                                      np, planes_last, fp16, pscale, plane_off_f, dbg);
+        k_contract_f32<64><<<we.total, 256, smem, s>>>(in, we, sh.k, sh.m, sh.n_tslots, planes_last, sh.fp16,
+                                                        sh.pscale_r, dbg);
     return cudaGetLastError();
 }
 

@@ -14,18 +14,27 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
-__global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A,
-                                                  const double* __restrict__ B, int64_t np,
-                                                  double alpha, const double* __restrict__ C,
-                                                  double beta, const double* __restrict__ D,
-                                                  double shift, int n_real,
-                                                  double* __restrict__ out,
-                                                  double* __restrict__ out64, int64_t ldo) {
+// Grouped over the batch: block b covers symmetric tile b - pre[i] of instance i.
+__global__ void __launch_bounds__(256) k_gemm_f64(const Step st, const Inst* __restrict__ insts,
+                                                  const InstIO* __restrict__ io, Work wt) {
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN];
+    const int inst = find_inst(wt.pre, 0, wt.count, blockIdx.x);
+    const Inst& in = insts[inst];
+    if (!in.res->active) return;
+    const int64_t np = in.np;
+    const int n_real = (int)in.n;
+    const int64_t sb = in.slot_bytes;
+    const double* A = reinterpret_cast<const double*>(in.slots + sb * st.a);
+    const double* B = reinterpret_cast<const double*>(in.slots + sb * st.b);
+    const double* C = st.c >= 0 ? reinterpret_cast<const double*>(in.slots + sb * st.c) : nullptr;
+    const double* D = st.d >= 0 ? reinterpret_cast<const double*>(in.slots + sb * st.d) : nullptr;
+    double* out = st.out >= 0 ? reinterpret_cast<double*>(in.slots + sb * st.out) : nullptr;
+    double* out64 = st.out64 ? io[inst].P : nullptr;
+    const int64_t ldo = io[inst].ldp;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int t = (int)(np / BM);
-    int I = 0, b = blockIdx.x;
+    int I = 0, b = blockIdx.x - wt.pre[inst];
     while (b >= t - I) { b -= t - I; ++I; }
     const int J = I + b;
     const int64_t m0 = (int64_t)I * BM, n0 = (int64_t)J * BN;
@@ -47,15 +56,15 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A,
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[4], b[4];
+            double a[4], bv[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -66,10 +75,10 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A,
         for (int j = 0; j < 4; ++j) {
             const int64_t c = n0 + tx + 16 * j;
             const int64_t o = r * np + c;
-            double v = alpha * acc[i][j];
-            if (C) v = fma(beta, C[o], v);
+            double v = st.alpha64 * acc[i][j];
+            if (C) v = fma(st.beta64, C[o], v);
             if (D) v += D[o];
-            if (r == c && r < n_real) v += shift;
+            if (r == c && r < n_real) v += st.shift64;
             if (c < r) continue;            // lower triangle: written by the mirror
             if (out64) {
                 if (r < n_real && c < n_real) {
@@ -86,13 +95,13 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A,
 
 }  // namespace
 
-cudaError_t launch_gemm_f64(const double* A, const double* B, int64_t np, double alpha,
-                            const double* C, double beta, const double* D, double shift,
-                            int n_real, double* out, double* out64, int64_t ldo,
-                            cudaStream_t s) {
-    if (np % BM != 0) return cudaErrorInvalidValue;
+int64_t f64_tiles(int64_t np) {
     const int64_t t = np / BM;
-    k_gemm_f64<<<(unsigned)(t * (t + 1) / 2), 256, 0, s>>>(A, B, np, alpha, C, beta, D, shift, n_real, out, out64, ldo);
+    return t * (t + 1) / 2;
+}
+
+cudaError_t launch_gemm_f64(const Step& st, const Inst* in, const InstIO* io, Work wt, cudaStream_t s) {
+    k_gemm_f64<<<wt.total, 256, 0, s>>>(st, in, io, wt);
     return cudaGetLastError();
 }
 

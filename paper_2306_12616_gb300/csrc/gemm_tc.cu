@@ -4,10 +4,17 @@
 //
 // A_p, B_q are the 16-bit planes of float32 working matrices (A = sum_p A_p), staged by
 // TMA (cp.async.bulk.tensor, 64-byte swizzle) into a multi-stage shared-memory ring and
-// multiplied by tcgen05.mma (kind::f16, M = 128, N = 256, K = 16) into float32 accumulators
-// in tensor memory. The epilogue applies the recurrence update (2 T_1 T_i - T_{i-1}, or
-// 2 Y b_{l+1} - b_{l+2} + R_l for the Clenshaw giant steps) and writes the float32 master,
-// the split planes of the result (the next product's operand) or the final float64 P.
+// multiplied by tcgen05.mma (kind::f16, M = 128, N = 256 or 128, K = 16) into float32
+// accumulators in tensor memory. The epilogue applies the recurrence update (2 T_1 T_i -
+// T_{i-1}, or 2 Y b_{l+1} - b_{l+2} + R_l for the Clenshaw giant steps) and writes the
+// float32 master, the split planes of the result (the next product's operand) or the
+// final float64 P.
+//
+// Grouped launch. One launch computes the same step for every instance of a batch: CTA b
+// takes tile b of the concatenated tile lists (instances sorted by size, largest first, so
+// the longest tiles start first). Operands are addressed through one 5-D tensor map per
+// bucket of equally sized instances, (column, row, plane, slot, instance), passed as grid
+// constants; the slot and the instance are TMA coordinates.
 //
 // Symmetric mode. Every matrix of the method is a polynomial in the symmetric X, so every
 // product of two of them is symmetric. Only the tiles that hold an element on or above the
@@ -26,8 +33,10 @@
 // are issued first, while the accumulator is still small, and the leading product a_0 b_0
 // last, so only two roundings per k-block happen at full magnitude.
 //
-// Tiles are 128 x 256 (M x N): per MMA cycle this moves half the B bytes of a 128 x 128
-// tile, which matters because the split forms load 2 to 6 operand planes per k-block.
+// Tiles are 128 x TBN (TBN = 256 or 128, chosen per batch by the autotuner). With TBN = 256
+// a column tile that reaches past the matrix edge by 128 columns runs as a 128-wide MMA and
+// loads half the B rows. A 256-wide tile moves half the B bytes per MMA cycle of a 128-wide
+// one, which matters because the split forms load 2 to 6 operand planes per k-block.
 //
 // Roles (320 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs (warp 1 owns the
 // TMEM allocation), warps 2-9 drain TMEM: warp w reads lane quadrant (w & 3) = 32 tile rows
@@ -39,6 +48,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "internal.cuh"
@@ -94,12 +104,13 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
         }
     }
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int c0, int c1, int c2) {
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2, int c3, int c4) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(c4)
         : "memory");
 }
 __device__ __forceinline__ void fence_before() {
@@ -167,20 +178,24 @@ __device__ __forceinline__ uint16_t bits_bf16(float v) {
     return *reinterpret_cast<uint16_t*>(&h);
 }
 
-constexpr int kBN = 256;          // tile columns (UMMA N)
-constexpr int kTmemCols = 512;    // two accumulators of 256 columns
-constexpr int kDrainWarps = 8;    // 2 per TMEM lane quadrant, one per 128-column half
+constexpr int kDrainWarps = 8;    // 2 per TMEM lane quadrant, one per column half
 constexpr int kThreads = 32 * (2 + kDrainWarps);
+constexpr int kBoxBytes = kBM * kRowBytes;   // one 128-row TMA box of one plane: 8 KB
 
-template <int PA, int PB, int NPROD, bool F16>
+struct TcMaps {
+    CUtensorMap m[kMaxBuckets];
+};
+
+template <int PA, int PB, int NPROD, bool F16, int TBN>
 struct TcCfg {
-    static constexpr int kStageBytes = PA * kBM * kRowBytes + PB * kBN * kRowBytes;
+    static constexpr int kBBoxes = TBN / kBM;
+    static constexpr int kStageBytes = PA * kBoxBytes + PB * kBBoxes * kBoxBytes;
     static constexpr int kStagesRaw = (216 * 1024) / kStageBytes;
     static constexpr int kStages = kStagesRaw > 8 ? 8 : (kStagesRaw < 2 ? 2 : kStagesRaw);
     static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
-    static constexpr uint32_t kIdesc = idesc_f16(kBN, F16);
+    static constexpr int kTmemCols = 2 * TBN;   // two accumulators (power of two >= 32)
     static_assert(kSmem <= 232448 - 64, "shared memory budget of one CTA exceeded");
-    static_assert(kStages * kStageBytes >= kBM * (kBN + 1) * 4, "result tile must fit the stage ring");
+    static_assert(kStages * kStageBytes >= kBM * (TBN + 1) * 4, "result tile must fit the stage ring");
 };
 
 // (a-plane, b-plane) of each product, largest first:
@@ -233,29 +248,30 @@ __device__ __forceinline__ void split3(float x, bool f16, float pscale, uint16_t
     }
 }
 
-// Tile decode. Symmetric mode: the tiles of the 128-row block I that hold an element with
-// col >= row, i.e. column tiles J >= (128 I) / 256, enumerated row by row.
-__device__ __forceinline__ void tile_of(int bid, int tm, int tn, bool sym, int& I, int& J) {
+// Tile decode of one instance. Symmetric mode: the tiles of the 128-row block I that hold
+// an element with col >= row, i.e. column tiles J >= (128 I) / TBN, enumerated row by row.
+__device__ __forceinline__ void tile_of(int t, int tm, int tn, int tbn, int sym, int& I, int& J) {
     if (sym) {
         I = 0;
-        int b = bid;
+        int b = t;
         for (;;) {
-            const int first = (I * kBM) / kBN;
+            const int first = (I * kBM) / tbn;
             const int cnt = tn - first;
             if (b < cnt) { J = first + b; return; }
             b -= cnt;
             ++I;
         }
     }
-    I = bid / tn;
-    J = bid - I * tn;
+    I = t / tn;
+    J = t - I * tn;
 }
 
-template <int PA, int PB, int NPROD, bool F16, bool SYM>
+template <int PA, int PB, int NPROD, bool F16, int TBN>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              const Epilogue ep, int np, int* err_flag) {
-    using Cfg = TcCfg<PA, PB, NPROD, F16>;
+    k_tc_gemm(const __grid_constant__ TcMaps maps, const Step st, const Inst* __restrict__ insts,
+              const InstIO* __restrict__ io, const int* __restrict__ pre, int i0, int i1, int tile0,
+              int b0, int sym, int* err_flag) {
+    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN>;
     constexpr int S = Cfg::kStages;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -268,12 +284,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
     __shared__ int abort_flag;
 
+    // ---------------- instance and tile of this CTA (uniform across the CTA)
+    const int gtile = tile0 + (int)blockIdx.x;
+    const int inst = find_inst(pre, i0, i1, gtile);
+    const Inst& in = insts[inst];
+    if (!in.res->active) return;
+    const int np = (int)in.np;
+    const CUtensorMap* map = &maps.m[in.bucket - b0];
+    const int ib = in.in_bucket;
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tm = np / kBM, tn = (np + kBN - 1) / kBN;
+    const int tm = np / kBM, tn = (np + TBN - 1) / TBN;
     int I, J;
-    tile_of(blockIdx.x, tm, tn, SYM, I, J);
-    const int m0 = I * kBM, n0 = J * kBN;
+    tile_of(gtile - __ldg(pre + inst), tm, tn, TBN, sym, I, J);
+    const int m0 = I * kBM, n0 = J * TBN;
     const int nk = np / kBK;
+    // 128-row B boxes inside the matrix: a 256-wide tile at the edge may hold only one
+    const int nbox = (np - n0) / kBM < Cfg::kBBoxes ? (np - n0) / kBM : Cfg::kBBoxes;
+    const int tile_n = nbox * kBM;
+    const uint32_t idesc = idesc_f16(tile_n, F16);
+    const uint32_t stage_tx = (uint32_t)(PA * kBoxBytes + PB * nbox * kBoxBytes);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -287,13 +317,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(acc_full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(kTmemCols));
+                     "r"(Cfg::kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_before();
@@ -302,14 +331,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *tmem_slot;
     volatile int* vabort = &abort_flag;
 
-    auto stage_a = [&](int s, int p) { return smem + s * Cfg::kStageBytes + p * kBM * kRowBytes; };
+    auto stage_a = [&](int s, int p) { return smem + s * Cfg::kStageBytes + p * kBoxBytes; };
     auto stage_b = [&](int s, int p) {
-        return smem + s * Cfg::kStageBytes + PA * kBM * kRowBytes + p * kBN * kRowBytes;
+        return smem + s * Cfg::kStageBytes + PA * kBoxBytes + p * Cfg::kBBoxes * kBoxBytes;
     };
 
-    float sum[kBN / 2];  // a drain thread's 128 accumulated columns of its tile row
+    float sum[TBN / 2];  // a drain thread's accumulated columns of its tile row
 #pragma unroll
-    for (int j = 0; j < kBN / 2; ++j) sum[j] = 0.0f;
+    for (int j = 0; j < TBN / 2; ++j) sum[j] = 0.0f;
     bool ok = true;
 
     if (warp == 0) {
@@ -325,15 +354,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                 }
-                if (!FO_CHK(ep.dbg, kb * kBK < np && m0 + kBM <= np && n0 < np, 108, m0, n0)) {
+                if (!FO_CHK(st.dbg, kb * kBK < np && m0 + kBM <= np && n0 + tile_n <= np, 108, m0, n0)) {
                     atomicExch(&abort_flag, 1);
                     break;
                 }
-                mbar_expect_tx(&full[s], Cfg::kStageBytes);
+                mbar_expect_tx(&full[s], stage_tx);
 #pragma unroll
-                for (int p = 0; p < PA; ++p) tma_load_3d(stage_a(s, p), &mapA, &full[s], kb * kBK, m0, p);
+                for (int p = 0; p < PA; ++p)
+                    tma_load_5d(stage_a(s, p), map, &full[s], kb * kBK, m0, p, st.a, ib);
 #pragma unroll
-                for (int p = 0; p < PB; ++p) tma_load_3d(stage_b(s, p), &mapB, &full[s], kb * kBK, n0, p);
+                for (int p = 0; p < PB; ++p)
+                    for (int j = 0; j < nbox; ++j)
+                        tma_load_5d(stage_b(s, p) + j * kBoxBytes, map, &full[s], kb * kBK, n0 + j * kBM, p,
+                                    st.b, ib);
                 issued = kb + 1;
             }
             if (*vabort) {
@@ -368,21 +401,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 fence_after();
-                const uint32_t d = tmem + buf * kBN;
+                const uint32_t d = tmem + buf * TBN;
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
 #pragma unroll
                     for (int pr = 1; pr < NPROD; ++pr) {
                         umma_f16(d, sdesc_sw64(smem_u32(stage_a(s, prod_a(pr))) + kk * 32),
-                                 sdesc_sw64(smem_u32(stage_b(s, prod_b(pr))) + kk * 32), Cfg::kIdesc,
+                                 sdesc_sw64(smem_u32(stage_b(s, prod_b(pr))) + kk * 32), idesc,
                                  !(kk == 0 && pr == 1));
                     }
                 }
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
                     umma_f16(d, sdesc_sw64(smem_u32(stage_a(s, 0)) + kk * 32),
-                             sdesc_sw64(smem_u32(stage_b(s, 0)) + kk * 32), Cfg::kIdesc,
-                             (NPROD > 1) || kk > 0);
+                             sdesc_sw64(smem_u32(stage_b(s, 0)) + kk * 32), idesc, (NPROD > 1) || kk > 0);
                 }
                 umma_commit(&empty[s]);
                 umma_commit(&seg_full[buf]);
@@ -394,7 +426,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ---------------- drain warps: add every finished k-block to registers
         const int q = warp & 3, half = (warp - 2) >> 2;
-        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16) + half * (kBN / 2);
+        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16) + half * (TBN / 2);
+        const bool live = half * (TBN / 2) < tile_n;   // columns this warp reads hold data
         for (int kb = 0; kb < nk; ++kb) {
             const int buf = kb & 1;
             if (!mbar_wait_warp(&seg_full[buf], (kb >> 1) & 1, kWaitNs, vabort)) {
@@ -403,12 +436,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             __syncwarp();
             fence_after();
+            if (live) {
 #pragma unroll
-            for (int cb = 0; cb < kBN / 64; ++cb) {
-                uint32_t r[32];
-                tmem_ld32(t_row + buf * kBN + cb * 32, r);
+                for (int cb = 0; cb < TBN / 64; ++cb) {
+                    uint32_t r[32];
+                    tmem_ld32(t_row + buf * TBN + cb * 32, r);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
+                }
             }
             fence_before();
             mbar_arrive(&seg_empty[buf]);
@@ -427,104 +462,115 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols));
+                     "r"(Cfg::kTmemCols));
     }
     if (warp < 2 || *vabort) return;  // uniform across the drain warps
 
     // ---------------- drain warps: update and store through shared memory. The stage ring
-    // is idle (every TMA load was consumed, every MMA completed), so it holds the 128 x 256
+    // is idle (every TMA load was consumed, every MMA completed), so it holds the 128 x TBN
     // float32 result tile; all global traffic below is coalesced across the warp.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    constexpr int LD = kBN + 1;
+    constexpr int LD = TBN + 1;
     float* tile = reinterpret_cast<float*>(smem);
     {
         const int q = warp & 3, half = (warp - 2) >> 2;
         const int rl = q * 32 + lane;
 #pragma unroll
-        for (int c = 0; c < kBN / 2; ++c) tile[rl * LD + half * (kBN / 2) + c] = ep.alpha * sum[c];
+        for (int c = 0; c < TBN / 2; ++c) tile[rl * LD + half * (TBN / 2) + c] = st.alpha * sum[c];
     }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kDrainWarps) : "memory");
 
-    const int64_t ld = ep.ld;
+    // instance fields of the epilogue, read here so that they are not live in the main loop
+    const int64_t n_real = insts[inst].n;
+    char* const base = insts[inst].slots;
+    const int64_t sb = insts[inst].slot_bytes;
+    const int64_t ld = np;
+    const int64_t pstride = (int64_t)np * np;
+    float* out_x = st.out >= 0 ? reinterpret_cast<float*>(base + sb * st.out) : nullptr;
+    uint16_t* out_p = st.out >= 0 ? reinterpret_cast<uint16_t*>(base + sb * st.out + 4 * pstride) : nullptr;
+    const float* Cm = st.c >= 0 ? reinterpret_cast<const float*>(base + sb * st.c) : nullptr;
+    const float* Dm = st.d >= 0 ? reinterpret_cast<const float*>(base + sb * st.d) : nullptr;
+    double* out64 = st.out64 ? io[inst].P : nullptr;
+    const int64_t ldo = io[inst].ldp;
+    const int planes = st.planes;
     const int ew = warp - 2;  // 0..7
     // store of the pair (grow, gcol), (grow, gcol + 1) for the elements whose flag is set
     auto store_pair = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1) {
         if (!(w0 || w1)) return;
-        if (ep.out64) {
-            if (grow < ep.n_real) {
-                double* dst = ep.out64 + grow * ep.ldo + gcol;
-                if (w0 && gcol < ep.n_real) dst[0] = (double)v0;
-                if (w1 && gcol + 1 < ep.n_real) dst[1] = (double)v1;
+        if (out64) {
+            if (grow < n_real) {
+                double* dst = out64 + grow * ldo + gcol;
+                if (w0 && gcol < n_real) dst[0] = (double)v0;
+                if (w1 && gcol + 1 < n_real) dst[1] = (double)v1;
             }
             return;
         }
         const int64_t o = grow * ld + gcol;
-        if (!FO_CHK(ep.dbg, o >= 0 && o + 2 <= ld * ld, 111, grow, gcol)) return;
-        uint16_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
-        if (ep.planes > 0) {
-            split3(v0, F16, ep.plane_scale, a0, a1, a2);
-            split3(v1, F16, ep.plane_scale, b0, b1, b2);
+        if (!FO_CHK(st.dbg, o >= 0 && o + 2 <= ld * ld, 111, grow, gcol)) return;
+        uint16_t a0 = 0, a1 = 0, a2 = 0, b0v = 0, b1v = 0, b2v = 0;
+        if (planes > 0) {
+            split3(v0, F16, st.plane_scale, a0, a1, a2);
+            split3(v1, F16, st.plane_scale, b0v, b1v, b2v);
         }
         if (w0 && w1) {
-            if (ep.out.x) *reinterpret_cast<float2*>(ep.out.x + o) = make_float2(v0, v1);
-            if (ep.planes > 0) {
-                uint16_t* pl = ep.out.planes + o;
-                *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0 << 16);
-                if (ep.planes > 1)
-                    *reinterpret_cast<uint32_t*>(pl + ep.out.plane_stride) = (uint32_t)a1 | ((uint32_t)b1 << 16);
-                if (ep.planes > 2)
-                    *reinterpret_cast<uint32_t*>(pl + 2 * ep.out.plane_stride) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+            if (out_x) *reinterpret_cast<float2*>(out_x + o) = make_float2(v0, v1);
+            if (planes > 0) {
+                uint16_t* pl = out_p + o;
+                *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0v << 16);
+                if (planes > 1) *reinterpret_cast<uint32_t*>(pl + pstride) = (uint32_t)a1 | ((uint32_t)b1v << 16);
+                if (planes > 2)
+                    *reinterpret_cast<uint32_t*>(pl + 2 * pstride) = (uint32_t)a2 | ((uint32_t)b2v << 16);
             }
         } else {
             const int e = w0 ? 0 : 1;
             const float v = w0 ? v0 : v1;
-            if (ep.out.x) ep.out.x[o + e] = v;
-            if (ep.planes > 0) {
-                uint16_t* pl = ep.out.planes + o + e;
-                pl[0] = w0 ? a0 : b0;
-                if (ep.planes > 1) pl[ep.out.plane_stride] = w0 ? a1 : b1;
-                if (ep.planes > 2) pl[2 * ep.out.plane_stride] = w0 ? a2 : b2;
+            if (out_x) out_x[o + e] = v;
+            if (planes > 0) {
+                uint16_t* pl = out_p + o + e;
+                pl[0] = w0 ? a0 : b0v;
+                if (planes > 1) pl[pstride] = w0 ? a1 : b1v;
+                if (planes > 2) pl[2 * pstride] = w0 ? a2 : b2v;
             }
         }
     };
 
     // row pass: each drain warp takes 16 tile rows, lanes on column pairs; applies
-    // beta C + D + shift and stores the entries with col >= row (all of them when not SYM)
+    // beta C + D + shift and stores the entries with col >= row (all of them when not sym)
     for (int rr = 0; rr < kBM / kDrainWarps; ++rr) {
         const int r = ew * (kBM / kDrainWarps) + rr;
         const int64_t grow = (int64_t)m0 + r;
 #pragma unroll
-        for (int h = 0; h < kBN / 64; ++h) {
+        for (int h = 0; h < TBN / 64; ++h) {
             const int c = h * 64 + 2 * lane;
             const int64_t gcol = (int64_t)n0 + c;
             if (gcol >= np) continue;
             const int64_t o = grow * ld + gcol;
             float v0 = tile[r * LD + c], v1 = tile[r * LD + c + 1];
-            if (ep.C) {
-                const float2 cc = *reinterpret_cast<const float2*>(ep.C + o);
-                v0 = fmaf(ep.beta, cc.x, v0);
-                v1 = fmaf(ep.beta, cc.y, v1);
+            if (Cm) {
+                const float2 cc = *reinterpret_cast<const float2*>(Cm + o);
+                v0 = fmaf(st.beta, cc.x, v0);
+                v1 = fmaf(st.beta, cc.y, v1);
             }
-            if (ep.D) {
-                const float2 dd = *reinterpret_cast<const float2*>(ep.D + o);
+            if (Dm) {
+                const float2 dd = *reinterpret_cast<const float2*>(Dm + o);
                 v0 += dd.x;
                 v1 += dd.y;
             }
-            if (grow < ep.n_real) {
-                if (gcol == grow) v0 += ep.shift;
-                if (gcol + 1 == grow) v1 += ep.shift;
+            if (grow < n_real) {
+                if (gcol == grow) v0 += st.shift;
+                if (gcol + 1 == grow) v1 += st.shift;
             }
             tile[r * LD + c] = v0;
             tile[r * LD + c + 1] = v1;
-            store_pair(grow, gcol, v0, v1, !SYM || gcol >= grow, !SYM || gcol + 1 >= grow);
+            store_pair(grow, gcol, v0, v1, !sym || gcol >= grow, !sym || gcol + 1 >= grow);
         }
     }
-    if (!SYM) return;
+    if (!sym) return;
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kDrainWarps) : "memory");
     // mirror pass: output row n0 + c holds tile column c for the entries with col > row;
-    // each drain warp takes 32 tile columns, lanes on row pairs
-    for (int cc = 0; cc < kBN / kDrainWarps; ++cc) {
-        const int c = ew * (kBN / kDrainWarps) + cc;
+    // each drain warp takes TBN / 8 tile columns, lanes on row pairs
+    for (int cc = 0; cc < TBN / kDrainWarps; ++cc) {
+        const int c = ew * (TBN / kDrainWarps) + cc;
         const int64_t grow = (int64_t)n0 + c;       // output row
         if (grow >= np) break;
 #pragma unroll
@@ -554,50 +600,24 @@ EncodeFn get_encode(std::string* err) {
     return fn;
 }
 
-// 3-D tensor map over a slot's planes: (column k, row, plane), 16-bit elements, 32 x rows box.
-bool make_map(CUtensorMap* map, const uint16_t* planes, int64_t np, int64_t plane_stride,
-              int nplanes, int box_rows, bool fp16, std::string* err) {
-    EncodeFn enc = get_encode(err);
-    if (!enc) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)np, (cuuint64_t)np, (cuuint64_t)nplanes};
-    cuuint64_t strides[2] = {(cuuint64_t)np * 2, (cuuint64_t)plane_stride * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
-                     const_cast<uint16_t*>(planes), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        if (err) *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
-        return false;
-    }
-    return true;
-}
-
-int64_t tiles_for(int64_t np, int sym) {
-    const int64_t tm = np / kBM, tn = (np + kBN - 1) / kBN;
-    if (!sym) return tm * tn;
-    int64_t c = 0;
-    for (int64_t I = 0; I < tm; ++I) c += tn - (I * kBM) / kBN;
-    return c;
-}
-
-template <int PA, int PB, int NPROD, bool F16, bool SYM>
-cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Epilogue& ep, int64_t np,
-                      int* err_flag, cudaStream_t s) {
-    using Cfg = TcCfg<PA, PB, NPROD, F16>;
-    auto kern = k_tc_gemm<PA, PB, NPROD, F16, SYM>;
+template <int PA, int PB, int NPROD, bool F16, int TBN>
+cudaError_t launch_tc(const TcMaps& maps, const Step& st, const Inst* in, const InstIO* io, const int* pre,
+                      int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag, cudaStream_t s) {
+    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN>;
+    auto kern = k_tc_gemm<PA, PB, NPROD, F16, TBN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)tiles_for(np, SYM ? 1 : 0), kThreads, Cfg::kSmem, s>>>(ma, mb, ep, (int)np, err_flag);
+    kern<<<(unsigned)tiles, kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, b0, sym, err_flag);
     return cudaGetLastError();
 }
 
 template <int PA, int PB, int NPROD, bool F16>
-cudaError_t dispatch_sym(int sym, const CUtensorMap& ma, const CUtensorMap& mb, const Epilogue& ep,
-                         int64_t np, int* err_flag, cudaStream_t s) {
-    return sym ? launch_tc<PA, PB, NPROD, F16, true>(ma, mb, ep, np, err_flag, s)
-               : launch_tc<PA, PB, NPROD, F16, false>(ma, mb, ep, np, err_flag, s);
+cudaError_t dispatch_tbn(int tile_n, const TcMaps& maps, const Step& st, const Inst* in, const InstIO* io,
+                         const int* pre, int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag,
+                         cudaStream_t s) {
+    return tile_n == 128
+               ? launch_tc<PA, PB, NPROD, F16, 128>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s)
+               : launch_tc<PA, PB, NPROD, F16, 256>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
 }
 
 }  // namespace
@@ -611,24 +631,53 @@ int tc_planes(int prec) {
     }
 }
 
-int64_t tc_tiles(int64_t np, int sym) { return tiles_for(np, sym); }
+int64_t tc_tiles(int64_t np, int tile_n) {
+    const int64_t tm = np / kBM, tn = (np + tile_n - 1) / tile_n;
+    int64_t c = 0;
+    for (int64_t I = 0; I < tm; ++I) c += tn - (I * kBM) / tile_n;
+    return c;
+}
 
-cudaError_t tc_gemm(int prec, int64_t np, const MatF32& A, const MatF32& B, const Epilogue& ep,
-                    int sym, int* flag, cudaStream_t s, std::string* err) {
-    const int planes = tc_planes(prec);
-    if (planes == 0 || np % kBM != 0) {
-        if (err) *err = "tc_gemm: unsupported precision or size";
+bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int nslots, int count,
+                 int64_t slot_bytes, int64_t inst_bytes, bool fp16, std::string* err) {
+    EncodeFn enc = get_encode(err);
+    if (!enc) return false;
+    cuuint64_t dims[5] = {(cuuint64_t)np, (cuuint64_t)np, (cuuint64_t)nplanes, (cuuint64_t)nslots,
+                          (cuuint64_t)count};
+    cuuint64_t strides[4] = {(cuuint64_t)np * 2, (cuuint64_t)np * np * 2, (cuuint64_t)slot_bytes,
+                             (cuuint64_t)inst_bytes};
+    cuuint32_t box[5] = {(cuuint32_t)kBK, (cuuint32_t)kBM, 1, 1, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap*>(map128),
+                     fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
+                     const_cast<void*>(planes0), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        if (err) *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
+cudaError_t tc_gemm(int prec, int tile_n, const Step& st, const Inst* in, const InstIO* io, const int* pre,
+                    int i0, int i1, int tile0, int tiles, const void* maps, int b0, int nb, int* err_flag,
+                    cudaStream_t s, std::string* err, int sym) {
+    if (tc_planes(prec) == 0 || (tile_n != 128 && tile_n != 256) || nb < 1 || nb > kMaxBuckets || !err_flag) {
+        if (err) *err = "tc_gemm: unsupported precision, tile or bucket count";
         return cudaErrorInvalidValue;
     }
-    if (!flag) return cudaErrorInvalidValue;
-    const bool f16 = prec == FO_PREC_FP16X2;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A.planes, np, A.plane_stride, planes, kBM, f16, err)) return cudaErrorInvalidValue;
-    if (!make_map(&mb, B.planes, np, B.plane_stride, planes, kBN, f16, err)) return cudaErrorInvalidValue;
+    if (tiles <= 0) return cudaSuccess;
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+    TcMaps tm;
+    std::memcpy(&tm.m[0], maps, sizeof(CUtensorMap) * nb);
     switch (prec) {
-        case FO_PREC_BF16X3: return dispatch_sym<3, 3, 6, false>(sym, ma, mb, ep, np, flag, s);
-        case FO_PREC_FP16X2: return dispatch_sym<2, 2, 3, true>(sym, ma, mb, ep, np, flag, s);
-        case FO_PREC_BF16X1: return dispatch_sym<1, 1, 1, false>(sym, ma, mb, ep, np, flag, s);
+        case FO_PREC_BF16X3:
+            return dispatch_tbn<3, 3, 6, false>(tile_n, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+        case FO_PREC_FP16X2:
+            return dispatch_tbn<2, 2, 3, true>(tile_n, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+        case FO_PREC_BF16X1:
+            return dispatch_tbn<1, 1, 1, false>(tile_n, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
         default: return cudaErrorInvalidValue;
     }
 }

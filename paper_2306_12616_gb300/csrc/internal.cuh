@@ -1,4 +1,11 @@
 // Internal declarations shared by the CUDA translation units of the solver.
+//
+// Every call runs on a batch plan: one or more independent Hamiltonians ("instances"),
+// each with its own size, sharing the expansion parameters (number of terms, k, m,
+// arithmetic). Each stage of the method is one launch over the whole batch: a kernel
+// finds its instance either from blockIdx.y (stages with the same work per instance) or
+// from a per-instance prefix sum of block counts (stages whose work grows with the
+// instance size: the block-to-instance map is a binary search on the prefix).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,29 +23,106 @@ namespace fo {
 // only ever applied to the first n rows (the algebra of X restricted to the n-dim block).
 constexpr int kPad = 128;
 
-// Device-resident record of the scalar results of one density-matrix evaluation.
+// Device-resident record of the scalar results of one instance.
 struct DevResult {
     double bounds[2];     // emin, emax
     double mu;
     double trace;         // tr P
     double frob2;         // ||P||_F^2
     double trace_poly;    // sum_n c_n tau_n at mu
-    int32_t iters;        // bisection halvings
+    int32_t iters;        // mu search evaluations
     int32_t status;       // fo_status of device stages
     int32_t nonfinite;    // H held NaN/Inf
     int32_t learned_ok;   // learned mu accepted
-    int32_t tc_timeout;   // a tensor-core kernel gave up a bounded wait
-    int32_t pad_;
-    double mu_lo, mu_hi;  // final bisection bracket
+    int32_t active;       // 0: every kernel skips this instance
+    int32_t evals;        // evaluations of P (learned mode)
+    double mu_lo, mu_hi;  // final bracket of the mu search
+    double mu0;           // learned proposal (learned mode)
+    double mu_prev, tr_prev;  // previous evaluation (learned mode secant)
+    double order;         // learned expansion order (learned mode)
 };
 
-// A float32 working matrix with its 16-bit split planes (plane p at planes + p*plane_stride).
-struct MatF32 {
-    float* x;
-    uint16_t* planes;
-    int64_t ld;
-    int64_t plane_stride;  // elements
+// Per-instance descriptor, written once per plan. slots: the instance's slot region,
+// T slots (baby steps, then giant steps) followed by the R / Clenshaw slots; a slot holds
+// a float64 matrix, or a float32 master followed by its 16-bit planes (plane p at byte
+// 4 np^2 + 2 p np^2 of the slot).
+struct Inst {
+    int64_t n, np;
+    char* slots;
+    int64_t slot_bytes;
+    double* c;            // km coefficients
+    double* g;            // k x m giant-step coefficients, l-major
+    double* tau;          // km + 2 moments
+    double* w;            // M DOS weights
+    double* f;            // M Fermi values at the nodes
+    double* diag;         // traces of the T slots
+    double* gram;         // Frobenius products, giant-major
+    double* gpart;        // gram partials, gram_blocks x npairs
+    DevResult* res;
+    int32_t bucket;       // tensor-map bucket (instances of equal np)
+    int32_t in_bucket;    // index within the bucket
+    int32_t gram_blocks;  // blocks of the Frobenius-product kernel for this instance
+    int32_t pad_;
 };
+
+// Per-call inputs of an instance (written at the start of every call).
+struct InstIO {
+    const double* H;
+    double* P;
+    int64_t ldh, ldp;
+    double kT, n_e, mu;       // mu: FO_MU_FIXED value
+    double emin, emax;        // given bounds
+    const double* bounds_src; // device bounds to copy (fo_moments), or null
+};
+
+// Plan-wide constants.
+struct Shape {
+    int32_t k, m, km, n_terms, M;
+    int32_t n_tslots;     // T slots per instance (R slot l is n_tslots + l)
+    int32_t planes, fp16, is64, pad_;
+    float pscale_t, pscale_r;
+};
+
+// One recurrence product of the whole batch (slot indices are per instance):
+//   out = alpha * A B^T + beta * C + D + shift * I_n
+struct Step {
+    int32_t a, b, c, d, out;   // -1 = absent
+    int32_t out64;             // 1: write the instance's float64 P (InstIO) instead of a slot
+    int32_t planes;            // 16-bit planes to write for out
+    int32_t fp16;
+    float alpha, beta, shift;  // float32 path; alpha includes the fp16 plane scales
+    float plane_scale;
+    double alpha64, beta64, shift64;
+    int* dbg;                  // self-check record (null unless built with FO_SELF_CHECK)
+};
+
+// The block-to-instance map of a grouped launch: pre[j] = blocks of instances < j.
+struct Work {
+    const int* pre;   // device, count + 1 entries
+    int count;        // instances
+    int total;        // blocks
+};
+
+// Largest j in [lo, hi) with pre[j] <= b (pre ascending, pre[lo] <= b < pre[hi]).
+__device__ __forceinline__ int find_inst(const int* __restrict__ pre, int lo, int hi, int b) {
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Elementwise row blocks: a block covers ew_rows(np) rows (about 8192 entries).
+__host__ __device__ inline int ew_rows(int64_t np) {
+    const int64_t r = 8192 / np;
+    return r < 1 ? 1 : (int)r;
+}
+__host__ __device__ inline int ew_blocks(int64_t np) {
+    const int r = ew_rows(np);
+    return (int)((np + r - 1) / r);
+}
+constexpr int kGershRows = 8;   // rows per block of the bounds kernel (a warp per row)
 
 // Self-check build (-DFO_SELF_CHECK): kernels verify the index range and the alignment of
 // their global accesses, record the first violation in dbg[0..3] and skip the access.
@@ -53,87 +137,59 @@ struct MatF32 {
 #define FO_CHK(dbg, cond, code, v1, v2) true
 #endif
 
-// Epilogue of one recurrence product: out = alpha*acc + beta*C + D + shift*I_{n_real}.
-struct Epilogue {
-    float alpha, beta, shift;
-    int32_t n_real;                // identity and output rows/cols limited to this
-    const float* C;                // float32 masters, leading dimension ld (may be null)
-    const float* D;
-    int64_t ld;
-    MatF32 out;                    // slot output (x may be null when writing out64)
-    double* out64;                 // final float64 output (user buffer), or null
-    int64_t ldo;
-    int32_t planes;                // 16-bit planes to write for `out` (0..3)
-    int32_t fp16;                  // planes are fp16 (else bf16)
-    float plane_scale;             // value multiplied into the planes before splitting
-    int* dbg;                      // self-check record (null unless built with FO_SELF_CHECK)
-};
-
-// Split/packing helpers (reduce.cu)
-cudaError_t launch_gershgorin(const double* H, int64_t n, int64_t ld, double* part_lo,
-                              double* part_hi, int* part_bad, int nparts, DevResult* res,
-                              int use_given, double emin, double emax, cudaStream_t s);
-cudaError_t launch_set_bounds(DevResult* res, double emin, double emax, cudaStream_t s);
-cudaError_t launch_set_scalar(double* dst, double v, cudaStream_t s);
+// ---------------------------------------------------------------- reduce.cu
+// Resets every instance's DevResult and writes its per-call inputs (ios[0..count)).
+cudaError_t launch_set_io(const InstIO* ios, int count, InstIO* d_io, const Inst* d_inst, int first,
+                          cudaStream_t s);
+// Gershgorin bounds (use_given = 0) or the given / copied bounds (use_given = 1).
+cudaError_t launch_bounds(const Inst* in, const InstIO* io, int batch, Work wg, double* part,
+                          int use_given, cudaStream_t s);
+// d_bounds[0..2] = emin, emax, non-finite flag of one instance.
 cudaError_t launch_export_bounds(const DevResult* res, double* out3, cudaStream_t s);
-cudaError_t launch_scale_f64(const double* H, int64_t n, int64_t ld, const DevResult* res,
-                             double* X, int64_t np, cudaStream_t s, int* dbg);
-cudaError_t launch_scale_split(const double* H, int64_t n, int64_t ld, const DevResult* res,
-                               MatF32 X, int64_t np, int planes, int fp16, float pscale,
-                               cudaStream_t s, int* dbg);
-cudaError_t launch_pack_f32(const float* A, int64_t n, int64_t lda, MatF32 X, int64_t np,
-                            int planes, int fp16, float pscale, cudaStream_t s);
-cudaError_t launch_diag_sums(const void* base, int64_t slot_stride_bytes, int count,
-                             int64_t n, int64_t np, int is_f64, double* out, cudaStream_t s);
-cudaError_t launch_gram(const void* base, int64_t slot_stride_bytes, int giant0, int ngiant,
-                        int baby0, int nbaby, int64_t np, int is_f64, double* partials,
-                        int max_blocks, double* out, cudaStream_t s);
-int gram_blocks(int64_t np, int ngiant, int nbaby);
-cudaError_t launch_assemble_moments(const double* diag, const double* gram, int k, int m,
-                                    int n_terms, int64_t n, double* tau, cudaStream_t s);
-cudaError_t launch_trace_frob(const double* P, int64_t n, int64_t ldp, double* partials,
-                              int nparts, DevResult* res, cudaStream_t s);
-cudaError_t launch_copy_out(const double* R, int64_t np, int64_t n, double* P, int64_t ldp,
-                            cudaStream_t s);
-cudaError_t launch_copy_out_f32(const float* R, int64_t np, int64_t n, double* P, int64_t ldp,
-                                cudaStream_t s);
+// X = (2H - (emin+emax) I)/(emax - emin) into slot 0 of every instance.
+cudaError_t launch_scale(const Inst* in, const InstIO* io, Work ws, const Shape& sh, cudaStream_t s,
+                         int* dbg);
+cudaError_t launch_diag_sums(const Inst* in, int batch, int count, const Shape& sh, cudaStream_t s);
+// gram[(g0 + g) * nbaby + b] = <slot giant0 + g, slot baby0 + b> for every instance.
+cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0,
+                        int nbaby, int out_g0, int is64, cudaStream_t s, int* launches);
+// tau_0 .. tau_{n_terms-1} from the traces and the Frobenius products.
+cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, cudaStream_t s);
+cudaError_t launch_trace_frob(const Inst* in, const InstIO* io, Work we, double* part, cudaStream_t s);
+cudaError_t launch_copy_out(const Inst* in, const InstIO* io, Work we, const Shape& sh, cudaStream_t s);
+// Standalone packing of a float32 matrix into slot `slot` (fo_recurrence_product).
+cudaError_t launch_pack_f32(const float* A, int64_t n, int64_t lda, char* slot, int64_t np, int planes,
+                            int fp16, float pscale, cudaStream_t s);
+int gram_blocks_for(int64_t np, int batch);
 
-// Coefficient pipeline (coef.cu)
+// ------------------------------------------------------------------ coef.cu
 cudaError_t launch_cos_table(int M, double* ct, cudaStream_t s);
-cudaError_t launch_dos_weights(const double* tau, int n_terms, int M, const double* ct,
-                               double* w, cudaStream_t s);
-cudaError_t launch_bisect(const double* w, const double* ct, int M, DevResult* res, double kT,
-                          double n_e, int max_iter, cudaStream_t s);
-cudaError_t launch_fermi_nodes(int M, const double* ct, const DevResult* res, double kT,
-                               double* f, cudaStream_t s);
-cudaError_t launch_coeffs(const double* f, const double* ct, int M, int n_terms, int km,
-                          double* c, cudaStream_t s);
-cudaError_t launch_g_convert(const double* c, int k, int m, double* g, cudaStream_t s);
-cudaError_t launch_poly_trace(const double* c, const double* tau, int n_terms, DevResult* res,
-                              cudaStream_t s);
-cudaError_t launch_contract_f64(const double* g, int k, int m, const double* tbase,
-                                int64_t tstride, double* rbase, int64_t rstride, int64_t n,
-                                int64_t np, cudaStream_t s);
-cudaError_t launch_contract_f32(const double* g, int k, int m, const float* tbase,
-                                int64_t tstride_f, float* rbase, int64_t rstride_f, int64_t n,
-                                int64_t np, int planes_last, int fp16, float pscale,
-                                int64_t plane_off_f, cudaStream_t s, int* dbg);
+cudaError_t launch_dos_weights(const Inst* in, int batch, const Shape& sh, const double* ct, cudaStream_t s);
+cudaError_t launch_bisect(const Inst* in, const InstIO* io, int batch, const Shape& sh, const double* ct,
+                          int max_iter, int start_mu0, cudaStream_t s);
+cudaError_t launch_set_mu(const Inst* in, const InstIO* io, int batch, cudaStream_t s);
+cudaError_t launch_coefficients(const Inst* in, const InstIO* io, int batch, const Shape& sh,
+                                const double* ct, int with_poly_trace, cudaStream_t s, int* launches);
+cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream_t s, int* dbg);
 
-// Matrix products (gemm_f64.cu, gemm_tc.cu)
-// out = alpha*A*B + beta*C + D + shift*I_{n_real}; all np x np float64 with ld np. Only
-// the tiles on or above the diagonal are computed; each is written at (r,c) and (c,r).
-// If out64 != null the result goes to out64[n_real x n_real, ldo] instead of out.
-cudaError_t launch_gemm_f64(const double* A, const double* B, int64_t np, double alpha,
-                            const double* C, double beta, const double* D, double shift,
-                            int n_real, double* out, double* out64, int64_t ldo,
-                            cudaStream_t s);
+// ----------------------------------------------------------- gemm_f64.cu / gemm_tc.cu
+int64_t f64_tiles(int64_t np);
+cudaError_t launch_gemm_f64(const Step& st, const Inst* in, const InstIO* io, Work wt, cudaStream_t s);
 
-// Tensor-core split-precision product. A, B are slots (float32 master + planes). B is read
-// transposed (B^T), which equals B for the exactly symmetric matrices of the method. With
-// sym != 0 only the tiles on or above the diagonal are computed and mirrored.
-cudaError_t tc_gemm(int prec, int64_t np, const MatF32& A, const MatF32& B, const Epilogue& ep,
-                    int sym, int* err_flag, cudaStream_t s, std::string* err);
-int64_t tc_tiles(int64_t np, int sym);
+constexpr int kMaxBuckets = 16;   // tensor maps per grouped launch
+int64_t tc_tiles(int64_t np, int tile_n);
 int tc_planes(int prec);
+// 5-D tensor map over the planes of every slot of every instance of one bucket:
+// (column, row, plane, slot, instance), 16-bit elements, box 32 x 128 x 1 x 1 x 1.
+bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int nslots, int count,
+                 int64_t slot_bytes, int64_t inst_bytes, bool fp16, std::string* err);
+// Grouped split-precision product over instances [i0, i1) (sorted by tile count, buckets
+// [b0, b0 + nb) with maps[0..nb)), tile_n = 256 or 128 output columns per tile.
+// sym = 0 computes every tile of the full product (fo_recurrence_product only).
+cudaError_t tc_gemm(int prec, int tile_n, const Step& st, const Inst* in, const InstIO* io,
+                    const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
+                    int nb, int* err_flag, cudaStream_t s, std::string* err, int sym = 1);
+// Tiles of the full (non-symmetric) product.
+inline int64_t tc_tiles_full(int64_t np, int tile_n) { return (np / 128) * ((np + tile_n - 1) / tile_n); }
 
 }  // namespace fo

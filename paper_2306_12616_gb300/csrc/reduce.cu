@@ -1,5 +1,6 @@
-// Bandwidth-bound kernels of the solver: spectral bounds, scaling and plane splitting,
-// traces, Frobenius inner products (moments) and the output copy.
+// Bandwidth-bound kernels of the solver: per-call setup, spectral bounds, scaling and plane
+// splitting, traces, Frobenius inner products (moments) and the output copy. Every kernel
+// covers the whole batch in one launch (see internal.cuh for the block-to-instance maps).
 //
 // All reductions are deterministic: fixed per-thread order, warp shuffles, a fixed tree in
 // shared memory, and per-block partials summed in block order by a final kernel.
@@ -41,16 +42,48 @@ __device__ double block_sum(double v, double* sh) {
     return sh[32];
 }
 
+// ---------------------------------------------------------------- per-call setup
+constexpr int kIoChunk = 64;
+struct IoChunk {
+    InstIO io[kIoChunk];
+    int count, first;
+};
+
+__global__ void k_set_io(const IoChunk p, InstIO* d_io, const Inst* insts) {
+    const int j = threadIdx.x;
+    if (j >= p.count) return;
+    const int i = p.first + j;
+    d_io[i] = p.io[j];
+    DevResult* r = insts[i].res;
+    r->bounds[0] = r->bounds[1] = 0.0;
+    r->mu = p.io[j].mu;
+    r->trace = r->frob2 = r->trace_poly = 0.0;
+    r->iters = 0;
+    r->status = FO_OK;
+    r->nonfinite = 0;
+    r->learned_ok = 0;
+    r->active = 1;
+    r->evals = 0;
+    r->mu_lo = r->mu_hi = 0.0;
+    r->mu0 = r->mu_prev = r->tr_prev = 0.0;
+    r->order = 0.0;
+}
+
 // ------------------------------------------------------------------ Gershgorin bounds
 // One warp per row: r_i = sum_{j != i} |h_ij| (float64, lane-strided, shuffle tree),
-// lo_i = h_ii - r_i, hi_i = h_ii + r_i; per-block min/max to partials.
-__global__ void __launch_bounds__(256) k_gershgorin_rows(const double* __restrict__ H, int64_t n,
-                                                         int64_t ld, double* part_lo,
-                                                         double* part_hi, int* part_bad) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// lo_i = h_ii - r_i, hi_i = h_ii + r_i; per-block (min lo, max hi, any non-finite).
+__global__ void __launch_bounds__(32 * kGershRows) k_gershgorin_rows(const Inst* __restrict__ insts,
+                                                                     const InstIO* __restrict__ io,
+                                                                     Work wg, double* part) {
+    const int b = blockIdx.x;
+    const int i = find_inst(wg.pre, 0, wg.count, b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = insts[i].n, ld = io[i].ldh;
+    const double* H = io[i].H;
+    const int64_t row = (int64_t)(b - wg.pre[i]) * kGershRows + warp;
     double lo = INFINITY, hi = -INFINITY;
     int bad = 0;
-    for (int64_t row = (int64_t)blockIdx.x * nw + warp; row < n; row += (int64_t)gridDim.x * nw) {
+    if (row < n) {
         const double* r = H + row * ld;
         double s = 0.0, d = 0.0;
         for (int64_t j = lane; j < n; j += 32) {
@@ -60,42 +93,40 @@ __global__ void __launch_bounds__(256) k_gershgorin_rows(const double* __restric
         }
         s = warp_sum(s);
         d = warp_sum(d);
-        lo = fmin(lo, d - s);
-        hi = fmax(hi, d + s);
+        lo = d - s;
+        hi = d + s;
     }
-    __shared__ double slo[32], shi[32];
-    __shared__ int sbad[32];
-    lo = warp_min(lo);
-    hi = warp_max(hi);
     bad = __any_sync(0xffffffffu, bad);
+    __shared__ double slo[kGershRows], shi[kGershRows];
+    __shared__ int sbad[kGershRows];
     if (lane == 0) { slo[warp] = lo; shi[warp] = hi; sbad[warp] = bad; }
     __syncthreads();
-    if (warp == 0) {
-        lo = lane < nw ? slo[lane] : INFINITY;
-        hi = lane < nw ? shi[lane] : -INFINITY;
-        bad = lane < nw ? sbad[lane] : 0;
-        lo = warp_min(lo);
-        hi = warp_max(hi);
-        bad = __any_sync(0xffffffffu, bad);
-        if (lane == 0) {
-            part_lo[blockIdx.x] = lo;
-            part_hi[blockIdx.x] = hi;
-            part_bad[blockIdx.x] = bad;
+    if (threadIdx.x == 0) {
+        double l = slo[0], h = shi[0];
+        int bd = sbad[0];
+        for (int w = 1; w < kGershRows; ++w) {
+            l = fmin(l, slo[w]);
+            h = fmax(h, shi[w]);
+            bd |= sbad[w];
         }
+        part[3 * (int64_t)b] = l;
+        part[3 * (int64_t)b + 1] = h;
+        part[3 * (int64_t)b + 2] = bd ? 1.0 : 0.0;
     }
 }
 
-__global__ void k_gershgorin_final(const double* part_lo, const double* part_hi,
-                                   const int* part_bad, int nparts, DevResult* res) {
+// One block per instance: reduce its partials [pre[i], pre[i+1]).
+__global__ void k_gershgorin_final(const Inst* __restrict__ insts, Work wg, const double* part) {
     __shared__ double slo[32], shi[32];
     __shared__ int sbad[32];
+    const int i = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double lo = INFINITY, hi = -INFINITY;
     int bad = 0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        lo = fmin(lo, part_lo[i]);
-        hi = fmax(hi, part_hi[i]);
-        bad |= part_bad[i];
+    for (int q = wg.pre[i] + threadIdx.x; q < wg.pre[i + 1]; q += blockDim.x) {
+        lo = fmin(lo, part[3 * (int64_t)q]);
+        hi = fmax(hi, part[3 * (int64_t)q + 1]);
+        bad |= part[3 * (int64_t)q + 2] != 0.0;
     }
     lo = warp_min(lo);
     hi = warp_max(hi);
@@ -113,26 +144,34 @@ __global__ void k_gershgorin_final(const double* part_lo, const double* part_hi,
             lo = c - 1.0;
             hi = c + 1.0;
         }
-        res->bounds[0] = lo;
-        res->bounds[1] = hi;
-        res->nonfinite = bad;
-        res->status = bad ? FO_ERR_NONFINITE : FO_OK;
+        DevResult* r = insts[i].res;
+        r->bounds[0] = lo;
+        r->bounds[1] = hi;
+        r->nonfinite = bad;
+        r->status = bad ? FO_ERR_NONFINITE : FO_OK;
     }
 }
 
-__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
+// Given bounds (InstIO emin/emax) or bounds copied from device memory (bounds_src).
+__global__ void k_bounds_given(const Inst* __restrict__ insts, const InstIO* __restrict__ io, int batch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch) return;
+    DevResult* r = insts[i].res;
+    if (io[i].bounds_src) {
+        r->bounds[0] = io[i].bounds_src[0];
+        r->bounds[1] = io[i].bounds_src[1];
+    } else {
+        r->bounds[0] = io[i].emin;
+        r->bounds[1] = io[i].emax;
+    }
+    r->nonfinite = 0;
+    r->status = FO_OK;
+}
 
 __global__ void k_export_bounds(const DevResult* res, double* out3) {
     out3[0] = res->bounds[0];
     out3[1] = res->bounds[1];
     out3[2] = res->nonfinite ? 1.0 : 0.0;
-}
-
-__global__ void k_set_bounds(DevResult* res, double emin, double emax) {
-    res->bounds[0] = emin;
-    res->bounds[1] = emax;
-    res->nonfinite = 0;
-    res->status = FO_OK;
 }
 
 // ------------------------------------------------------------- scaling and splitting
@@ -169,19 +208,20 @@ __device__ __forceinline__ void store_split(float v, float* x, uint16_t* p, int6
     }
 }
 
-// X = (2H - (emin+emax) I) / (emax - emin) into an np x np matrix with zero border, built
-// from the upper triangle of H only, so that X is exactly symmetric. One block per 32 x 32
-// tile (bi, bj), bj >= bi: the H tile is staged in shared memory and written to X at
-// (bi, bj) and, transposed, at (bj, bi). Output float64, or float32 master + split planes.
-template <bool F64>
-__global__ void __launch_bounds__(256) k_scale_sym(const double* __restrict__ H, int64_t n,
-                                                   int64_t ld, const DevResult* res,
-                                                   double* __restrict__ X64, MatF32 X32,
-                                                   int64_t np, int planes, int fp16,
-                                                   float pscale, int* dbg) {
+// X = (2H - (emin+emax) I) / (emax - emin) into slot 0 (np x np, zero border), built from
+// the upper triangle of H only, so that X is exactly symmetric. One block per 32 x 32 tile
+// (bi, bj), bj >= bi, of one instance: the H tile is staged in shared memory and written
+// to X at (bi, bj) and, transposed, at (bj, bi). Output float64, or float32 + planes.
+__global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ insts,
+                                                   const InstIO* __restrict__ io, Work ws,
+                                                   const Shape sh, int* dbg) {
     __shared__ double tile[32][33];
+    const int i = find_inst(ws.pre, 0, ws.count, blockIdx.x);
+    const int64_t n = insts[i].n, np = insts[i].np, ld = io[i].ldh;
+    const double* H = io[i].H;
+    const DevResult* res = insts[i].res;
     const int tn = (int)(np / 32);
-    int bi = 0, b = blockIdx.x;
+    int bi = 0, b = blockIdx.x - ws.pre[i];
     while (b >= tn - bi) { b -= tn - bi; ++bi; }
     const int bj = bi + b;
     const double ea = res->bounds[0], eb = res->bounds[1];
@@ -192,6 +232,10 @@ __global__ void __launch_bounds__(256) k_scale_sym(const double* __restrict__ H,
         tile[ry][tx] = (r < n && c < n) ? H[r * ld + c] : 0.0;
     }
     __syncthreads();
+    char* slot = insts[i].slots;
+    double* X64 = reinterpret_cast<double*>(slot);
+    float* X32 = reinterpret_cast<float*>(slot);
+    uint16_t* P16 = reinterpret_cast<uint16_t*>(slot + 4 * np * np);
     for (int ry = ty; ry < 32; ry += 8) {
         // (bi*32 + ry, bj*32 + tx); in a diagonal tile the lower half mirrors the upper
         for (int pass = 0; pass < (bi == bj ? 1 : 2); ++pass) {
@@ -214,56 +258,68 @@ __global__ void __launch_bounds__(256) k_scale_sym(const double* __restrict__ H,
             }
             const int64_t idx = r * np + c;
             if (!FO_CHK(dbg, r < np && c < np, 201, r, c)) continue;
-            if (F64) X64[idx] = v;
-            else store_split((float)v, X32.x + idx, X32.planes + idx, X32.plane_stride, planes, fp16, pscale);
+            if (sh.is64) X64[idx] = v;
+            else store_split((float)v, X32 + idx, P16 + idx, np * np, sh.planes, sh.fp16, sh.pscale_t);
         }
     }
 }
 
-__global__ void k_pack_f32(const float* __restrict__ A, int64_t n, int64_t lda, MatF32 X,
-                           int64_t np, int planes, int fp16, float pscale) {
+__global__ void k_pack_f32(const float* __restrict__ A, int64_t n, int64_t lda, char* slot, int64_t np,
+                           int planes, int fp16, float pscale) {
     const int64_t total = np * np;
+    float* x = reinterpret_cast<float*>(slot);
+    uint16_t* p = reinterpret_cast<uint16_t*>(slot + 4 * total);
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = idx / np, col = idx - r * np;
         const float v = (r < n && col < n) ? A[r * lda + col] : 0.0f;
-        store_split(v, X.x + idx, X.planes + idx, X.plane_stride, planes, fp16, pscale);
+        store_split(v, x + idx, p + idx, total, planes, fp16, pscale);
     }
 }
 
 // ----------------------------------------------------------------------- traces
-// out[s] = sum_{i<n} slot_s[i, i] (float64), one block per slot.
-__global__ void k_diag_sums(const char* base, int64_t slot_stride_bytes, int64_t n, int64_t np,
-                            int is_f64, double* out) {
+// diag[s] = sum_{r<n} slot_s[r, r] (float64); block (s, instance).
+__global__ void k_diag_sums(const Inst* __restrict__ insts, int is64) {
     __shared__ double sh[33];
-    const char* slot = base + slot_stride_bytes * blockIdx.x;
+    const Inst& in = insts[blockIdx.y];
+    if (!in.res->active) return;
+    const int64_t n = in.n, np = in.np;
+    const char* slot = in.slots + in.slot_bytes * blockIdx.x;
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        s += is_f64 ? reinterpret_cast<const double*>(slot)[i * np + i]
-                    : (double)reinterpret_cast<const float*>(slot)[i * np + i];
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        s += is64 ? reinterpret_cast<const double*>(slot)[r * np + r]
+                  : (double)reinterpret_cast<const float*>(slot)[r * np + r];
     }
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) out[blockIdx.x] = s;
+    if (threadIdx.x == 0) in.diag[blockIdx.x] = s;
 }
 
 // --------------------------------------------------------- Frobenius inner products
-// gram[g * nbaby + b] = <S_{giant0+g}, S_{baby0+b}>_F over all np*np entries (the zero
-// border contributes nothing). A block stages kChunk consecutive entries of every matrix in
-// shared memory, matrix-major (row s holds the chunk of matrix s), with float4 loads. Each
-// warp owns up to kTPW 4 x 4 tiles of (giant, baby) pairs; its lanes walk consecutive
-// entries of a row, so shared-memory reads are conflict free. Within a chunk the products
-// are summed in T; across chunks float32 sums are compensated (Kahan), float64 sums are
-// plain. Lanes are reduced by shuffles at the end into per-block float64 partials.
+// <S_{giant0+g}, S_{baby0+b}>_F over all np*np entries of one instance (the zero border
+// contributes nothing). A block stages kChunk consecutive entries of every matrix in shared
+// memory, matrix-major (row s holds the chunk of matrix s), with 16-byte loads. Each warp
+// owns up to kTPW 4 x 4 tiles of (giant, baby) pairs; its lanes walk consecutive entries of
+// a row, so shared-memory reads are conflict free. Within a chunk the products are summed
+// in T; across chunks float32 sums are compensated (Kahan), float64 sums are plain. Lanes
+// are reduced by shuffles at the end into per-block float64 partials (instance-local block
+// order, summed in that order by k_sum_partials).
 constexpr int kChunk = 256;
 constexpr int kRowPad = 4;
 constexpr int kTPW = 2;
+constexpr int kGramThreads = 512;
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_gram(const char* base, int64_t slot_stride_bytes,
-                                               int giant0, int ngiant, int baby0, int nbaby,
-                                               int64_t total, double* partials) {
+__global__ void __launch_bounds__(kGramThreads) k_gram(const Inst* __restrict__ insts, Work wgr, int giant0,
+                                                       int ngiant, int baby0, int nbaby) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
+    const int i = find_inst(wgr.pre, 0, wgr.count, blockIdx.x);
+    const Inst& in = insts[i];
+    if (!in.res->active) return;
+    const int lb = blockIdx.x - wgr.pre[i], nb = in.gram_blocks;
+    const char* base = in.slots;
+    const int64_t slot_bytes = in.slot_bytes;
+    const int64_t total = in.np * in.np;
     constexpr int RS = kChunk + kRowPad;                 // row stride (elements)
     const int ng4 = (ngiant + 3) / 4, nb4 = (nbaby + 3) / 4;
     const int nrows = 4 * (ng4 + nb4);
@@ -279,7 +335,7 @@ __global__ void __launch_bounds__(512) k_gram(const char* base, int64_t slot_str
 
     constexpr int V = 16 / sizeof(T);                    // elements per 16-byte load
     const int64_t nchunks = (total + kChunk - 1) / kChunk;
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    for (int64_t ch = lb; ch < nchunks; ch += nb) {
         const int64_t e0 = ch * kChunk;
         for (int q = threadIdx.x; q < nrows * (kChunk / V); q += blockDim.x) {
             const int srow = q / (kChunk / V), ev = (q % (kChunk / V)) * V;
@@ -288,7 +344,7 @@ __global__ void __launch_bounds__(512) k_gram(const char* base, int64_t slot_str
             else { const int bb = srow - 4 * ng4; if (bb < nbaby) slot = baby0 + bb; }
             T* dst = sm + srow * RS + ev;
             if (slot >= 0 && e0 + ev + V <= total) {
-                const T* src = reinterpret_cast<const T*>(base + slot_stride_bytes * slot) + e0 + ev;
+                const T* src = reinterpret_cast<const T*>(base + slot_bytes * slot) + e0 + ev;
                 *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
             } else {
 #pragma unroll
@@ -330,6 +386,7 @@ __global__ void __launch_bounds__(512) k_gram(const char* base, int64_t slot_str
         __syncthreads();
     }
     const int npairs = ngiant * nbaby;
+    double* partials = in.gpart;
 #pragma unroll
     for (int t = 0; t < kTPW; ++t) {
         const int tile = warp + t * nwarps;
@@ -340,27 +397,33 @@ __global__ void __launch_bounds__(512) k_gram(const char* base, int64_t slot_str
             double v = (double)acc[t][q] - (double)cmp[t][q];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             const int g = 4 * tg + q / 4, b = 4 * tb + q % 4;
-            if (lane == 0 && g < ngiant && b < nbaby)
-                partials[(int64_t)blockIdx.x * npairs + g * nbaby + b] = v;
+            if (lane == 0 && g < ngiant && b < nbaby) partials[(int64_t)lb * npairs + g * nbaby + b] = v;
         }
     }
 }
 
-__global__ void k_sum_partials(const double* partials, int nblocks, int npairs, double* out) {
+// gram[out0 + pq] = sum over the instance's blocks of partial pq; block (pairs, instance).
+__global__ void k_sum_partials(const Inst* __restrict__ insts, int npairs, int out0) {
+    const Inst& in = insts[blockIdx.y];
+    if (!in.res->active) return;
     const int pq = blockIdx.x * blockDim.x + threadIdx.x;
     if (pq >= npairs) return;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * npairs + pq];
-    out[pq] = s;
+    for (int b = 0; b < in.gram_blocks; ++b) s += in.gpart[(int64_t)b * npairs + pq];
+    in.gram[out0 + pq] = s;
 }
 
 // tau[0..n_terms) from baby traces diag[0..k) (T_1..T_k), giant traces diag[k + l - 2]
 // (T_{lk}, l = 2..m-1) and gram[(l-1)*(k-1) + (i-1)] = <T_{lk}, T_i> (l = 1..m-1,
 // i = 1..k-1) through tau_{lk+i} = 2 <T_{lk}, T_i> - tau_{lk-i} (Eq. identity).
-__global__ void k_assemble_moments(const double* diag, const double* gram, int k, int m,
-                                   int n_terms, double n, double* tau) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    tau[0] = n;
+__global__ void k_assemble_moments(const Inst* __restrict__ insts, int k, int m, int n_terms) {
+    if (threadIdx.x != 0) return;
+    const Inst& in = insts[blockIdx.x];
+    if (!in.res->active) return;
+    const double* diag = in.diag;
+    const double* gram = in.gram;
+    double* tau = in.tau;
+    tau[0] = (double)in.n;
     for (int i = 1; i <= k && i < n_terms; ++i) tau[i] = diag[i - 1];
     for (int l = 1; l < m; ++l) {
         const int base = l * k;
@@ -372,54 +435,66 @@ __global__ void k_assemble_moments(const double* diag, const double* gram, int k
 }
 
 // ------------------------------------------------------------ trace and ||P||_F^2
-__global__ void k_trace_frob_part(const double* __restrict__ P, int64_t n, int64_t ldp,
-                                  double* partials) {
+// Block = ew_rows(np) rows of one instance's P; partials (tr, ||.||^2) per block.
+__global__ void __launch_bounds__(256) k_trace_frob_part(const Inst* __restrict__ insts,
+                                                         const InstIO* __restrict__ io, Work we,
+                                                         double* partials) {
     __shared__ double sh[33];
+    const int i = find_inst(we.pre, 0, we.count, blockIdx.x);
+    const int64_t n = insts[i].n, np = insts[i].np, ldp = io[i].ldp;
+    const double* P = io[i].P;
+    const int rows = ew_rows(np);
+    const int64_t r0 = (int64_t)(blockIdx.x - we.pre[i]) * rows;
     double tr = 0.0, fr = 0.0;
-    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
-        const double* row = P + r * ldp;
-        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-            const double v = row[c];
-            fr = fma(v, v, fr);
-            if (c == r) tr += v;
+    if (insts[i].res->active) {
+        for (int rr = 0; rr < rows; ++rr) {
+            const int64_t r = r0 + rr;
+            if (r >= n) break;
+            const double* row = P + r * ldp;
+            for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+                const double v = row[c];
+                fr = fma(v, v, fr);
+                if (c == r) tr += v;
+            }
         }
     }
     tr = block_sum(tr, sh);
     fr = block_sum(fr, sh);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = tr;
-        partials[2 * blockIdx.x + 1] = fr;
+        partials[2 * (int64_t)blockIdx.x] = tr;
+        partials[2 * (int64_t)blockIdx.x + 1] = fr;
     }
 }
 
-__global__ void k_trace_frob_final(const double* partials, int nparts, DevResult* res) {
-    if (threadIdx.x != 0) return;
+__global__ void k_trace_frob_final(const Inst* __restrict__ insts, Work we, const double* partials) {
+    const int i = blockIdx.x;
+    DevResult* r = insts[i].res;
+    if (threadIdx.x != 0 || !r->active) return;
     double tr = 0.0, fr = 0.0;
-    for (int b = 0; b < nparts; ++b) {
-        tr += partials[2 * b];
-        fr += partials[2 * b + 1];
+    for (int b = we.pre[i]; b < we.pre[i + 1]; ++b) {
+        tr += partials[2 * (int64_t)b];
+        fr += partials[2 * (int64_t)b + 1];
     }
-    res->trace = tr;
-    res->frob2 = fr;
+    r->trace = tr;
+    r->frob2 = fr;
 }
 
-__global__ void k_copy_out(const double* __restrict__ R, int64_t np, int64_t n,
-                           double* __restrict__ P, int64_t ldp) {
-    const int64_t total = n * n;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = idx / n, c = idx - r * n;
-        P[r * ldp + c] = R[r * np + c];
-    }
-}
-
-__global__ void k_copy_out_f32(const float* __restrict__ R, int64_t np, int64_t n,
-                               double* __restrict__ P, int64_t ldp) {
-    const int64_t total = n * n;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = idx / n, c = idx - r * n;
-        P[r * ldp + c] = (double)R[r * np + c];
+// P = R_0 (m = 1): slot n_tslots to the instance's float64 P.
+__global__ void k_copy_out(const Inst* __restrict__ insts, const InstIO* __restrict__ io, Work we,
+                           int slot, int is64) {
+    const int i = find_inst(we.pre, 0, we.count, blockIdx.x);
+    if (!insts[i].res->active) return;
+    const int64_t n = insts[i].n, np = insts[i].np, ldp = io[i].ldp;
+    const int rows = ew_rows(np);
+    const int64_t r0 = (int64_t)(blockIdx.x - we.pre[i]) * rows;
+    const char* src = insts[i].slots + insts[i].slot_bytes * slot;
+    double* P = io[i].P;
+    for (int rr = 0; rr < rows; ++rr) {
+        const int64_t r = r0 + rr;
+        if (r >= n) break;
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x)
+            P[r * ldp + c] = is64 ? reinterpret_cast<const double*>(src)[r * np + c]
+                                  : (double)reinterpret_cast<const float*>(src)[r * np + c];
     }
 }
 
@@ -432,25 +507,28 @@ int grid_for(int64_t total, int threads) {
 
 }  // namespace
 
-cudaError_t launch_gershgorin(const double* H, int64_t n, int64_t ld, double* part_lo,
-                              double* part_hi, int* part_bad, int nparts, DevResult* res,
-                              int use_given, double emin, double emax, cudaStream_t s) {
+cudaError_t launch_set_io(const InstIO* ios, int count, InstIO* d_io, const Inst* d_inst, int first,
+                          cudaStream_t s) {
+    for (int c0 = 0; c0 < count; c0 += kIoChunk) {
+        IoChunk p;
+        p.count = count - c0 < kIoChunk ? count - c0 : kIoChunk;
+        p.first = first + c0;
+        for (int j = 0; j < p.count; ++j) p.io[j] = ios[c0 + j];
+        k_set_io<<<1, kIoChunk, 0, s>>>(p, d_io, d_inst);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_bounds(const Inst* in, const InstIO* io, int batch, Work wg, double* part,
+                          int use_given, cudaStream_t s) {
     if (use_given) {
-        k_set_bounds<<<1, 1, 0, s>>>(res, emin, emax);
+        k_bounds_given<<<(batch + 127) / 128, 128, 0, s>>>(in, io, batch);
         return cudaGetLastError();
     }
-    k_gershgorin_rows<<<nparts, 256, 0, s>>>(H, n, ld, part_lo, part_hi, part_bad);
-    k_gershgorin_final<<<1, 256, 0, s>>>(part_lo, part_hi, part_bad, nparts, res);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_set_bounds(DevResult* res, double emin, double emax, cudaStream_t s) {
-    k_set_bounds<<<1, 1, 0, s>>>(res, emin, emax);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_set_scalar(double* dst, double v, cudaStream_t s) {
-    k_set_scalar<<<1, 1, 0, s>>>(dst, v);
+    k_gershgorin_rows<<<wg.total, 32 * kGershRows, 0, s>>>(in, io, wg, part);
+    k_gershgorin_final<<<batch, 256, 0, s>>>(in, wg, part);
     return cudaGetLastError();
 }
 
@@ -459,107 +537,75 @@ cudaError_t launch_export_bounds(const DevResult* res, double* out3, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale_f64(const double* H, int64_t n, int64_t ld, const DevResult* res,
-                             double* X, int64_t np, cudaStream_t s, int* dbg) {
-    const int64_t tn = np / 32;
-    MatF32 none{nullptr, nullptr, 0, 0};
-    k_scale_sym<true><<<(unsigned)(tn * (tn + 1) / 2), 256, 0, s>>>(H, n, ld, res, X, none, np, 0, 0, 1.0f, dbg);
+cudaError_t launch_scale(const Inst* in, const InstIO* io, Work ws, const Shape& sh, cudaStream_t s,
+                         int* dbg) {
+    k_scale_sym<<<ws.total, 256, 0, s>>>(in, io, ws, sh, dbg);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale_split(const double* H, int64_t n, int64_t ld, const DevResult* res,
-                               MatF32 X, int64_t np, int planes, int fp16, float pscale,
-                               cudaStream_t s, int* dbg) {
-    const int64_t tn = np / 32;
-    k_scale_sym<false><<<(unsigned)(tn * (tn + 1) / 2), 256, 0, s>>>(H, n, ld, res, nullptr, X, np,
-                                                                     planes, fp16, pscale, dbg);
+cudaError_t launch_pack_f32(const float* A, int64_t n, int64_t lda, char* slot, int64_t np, int planes,
+                            int fp16, float pscale, cudaStream_t s) {
+    k_pack_f32<<<grid_for(np * np, 256), 256, 0, s>>>(A, n, lda, slot, np, planes, fp16, pscale);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_f32(const float* A, int64_t n, int64_t lda, MatF32 X, int64_t np,
-                            int planes, int fp16, float pscale, cudaStream_t s) {
-    k_pack_f32<<<grid_for(np * np, 256), 256, 0, s>>>(A, n, lda, X, np, planes, fp16, pscale);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_diag_sums(const void* base, int64_t slot_stride_bytes, int count, int64_t n,
-                             int64_t np, int is_f64, double* out, cudaStream_t s) {
+cudaError_t launch_diag_sums(const Inst* in, int batch, int count, const Shape& sh, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    k_diag_sums<<<count, 256, 0, s>>>(reinterpret_cast<const char*>(base), slot_stride_bytes, n,
-                                      np, is_f64, out);
+    k_diag_sums<<<dim3(count, batch), 256, 0, s>>>(in, sh.is64);
     return cudaGetLastError();
 }
 
-int gram_blocks(int64_t np, int ngiant, int nbaby) {
-    (void)ngiant;
-    (void)nbaby;
+int gram_blocks_for(int64_t np, int batch) {
     const int64_t nchunks = (np * np + kChunk - 1) / kChunk;
-    int64_t b = 152 * 4;
-    if (b > nchunks) b = nchunks;
+    // enough blocks to fill the GPU for one instance, fewer per instance in a batch
+    int64_t cap = 152 * 4 / (batch > 0 ? batch : 1);
+    if (cap < 4) cap = 4;
+    int64_t b = nchunks / 16;   // at least 16 chunks per block
+    if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_gram(const void* base, int64_t slot_stride_bytes, int giant0, int ngiant,
-                        int baby0, int nbaby, int64_t np, int is_f64, double* partials,
-                        int max_blocks, double* out, cudaStream_t s) {
+cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0, int nbaby,
+                        int out_g0, int is64, cudaStream_t s, int* launches) {
     if (ngiant <= 0 || nbaby <= 0) return cudaSuccess;
     if (nbaby > 32) return cudaErrorInvalidValue;
-    const int threads = 512;
-    const int max_tiles = (threads / 32) * kTPW;
+    const int max_tiles = (kGramThreads / 32) * kTPW;
     const int nb4 = (nbaby + 3) / 4;
     const int gmax = 4 * (max_tiles / nb4);           // giants per launch
-    if (ngiant > gmax) {
-        // giant-major output: one launch per group of giants
-        for (int g = 0; g < ngiant; g += gmax) {
-            const int ng = ngiant - g < gmax ? ngiant - g : gmax;
-            cudaError_t e = launch_gram(base, slot_stride_bytes, giant0 + g, ng, baby0, nbaby, np,
-                                        is_f64, partials, max_blocks, out + (int64_t)g * nbaby, s);
-            if (e != cudaSuccess) return e;
+    for (int g = 0; g < ngiant; g += gmax) {
+        const int ng = ngiant - g < gmax ? ngiant - g : gmax;
+        const int ng4 = (ng + 3) / 4;
+        const size_t elem = is64 ? 8 : 4;
+        const size_t smem = (size_t)4 * (ng4 + nb4) * (kChunk + kRowPad) * elem;
+        if (is64) {
+            cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_gram<double><<<wgr.total, kGramThreads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
+        } else {
+            cudaFuncSetAttribute(k_gram<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_gram<float><<<wgr.total, kGramThreads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
         }
-        return cudaSuccess;
+        const int npairs = ng * nbaby;
+        k_sum_partials<<<dim3((npairs + 127) / 128, batch), 128, 0, s>>>(in, npairs, (out_g0 + g) * nbaby);
+        if (launches) *launches += 2;
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    const int ng4 = (ngiant + 3) / 4;
-    const size_t elem = is_f64 ? 8 : 4;
-    const size_t smem = (size_t)4 * (ng4 + nb4) * (kChunk + kRowPad) * elem;
-    int blocks = gram_blocks(np, ngiant, nbaby);
-    if (blocks > max_blocks) blocks = max_blocks;
-    const char* b = reinterpret_cast<const char*>(base);
-    if (is_f64) {
-        cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_gram<double><<<blocks, threads, smem, s>>>(b, slot_stride_bytes, giant0, ngiant, baby0,
-                                                      nbaby, np * np, partials);
-    } else {
-        cudaFuncSetAttribute(k_gram<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_gram<float><<<blocks, threads, smem, s>>>(b, slot_stride_bytes, giant0, ngiant, baby0,
-                                                     nbaby, np * np, partials);
-    }
-    const int npairs = ngiant * nbaby;
-    k_sum_partials<<<(npairs + 127) / 128, 128, 0, s>>>(partials, blocks, npairs, out);
+    return cudaSuccess;
+}
+
+cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, cudaStream_t s) {
+    k_assemble_moments<<<batch, 32, 0, s>>>(in, sh.k, sh.m, sh.n_terms);
     return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_moments(const double* diag, const double* gram, int k, int m,
-                                    int n_terms, int64_t n, double* tau, cudaStream_t s) {
-    k_assemble_moments<<<1, 32, 0, s>>>(diag, gram, k, m, n_terms, (double)n, tau);
+cudaError_t launch_trace_frob(const Inst* in, const InstIO* io, Work we, double* part, cudaStream_t s) {
+    k_trace_frob_part<<<we.total, 256, 0, s>>>(in, io, we, part);
+    k_trace_frob_final<<<we.count, 32, 0, s>>>(in, we, part);
     return cudaGetLastError();
 }
 
-cudaError_t launch_trace_frob(const double* P, int64_t n, int64_t ldp, double* partials,
-                              int nparts, DevResult* res, cudaStream_t s) {
-    k_trace_frob_part<<<nparts, 256, 0, s>>>(P, n, ldp, partials);
-    k_trace_frob_final<<<1, 32, 0, s>>>(partials, nparts, res);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_copy_out(const double* R, int64_t np, int64_t n, double* P, int64_t ldp,
-                            cudaStream_t s) {
-    k_copy_out<<<grid_for(n * n, 256), 256, 0, s>>>(R, np, n, P, ldp);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_copy_out_f32(const float* R, int64_t np, int64_t n, double* P, int64_t ldp,
-                                cudaStream_t s) {
-    k_copy_out_f32<<<grid_for(n * n, 256), 256, 0, s>>>(R, np, n, P, ldp);
+cudaError_t launch_copy_out(const Inst* in, const InstIO* io, Work we, const Shape& sh, cudaStream_t s) {
+    k_copy_out<<<we.total, 256, 0, s>>>(in, io, we, sh.n_tslots, sh.is64);
     return cudaGetLastError();
 }
 

@@ -29,8 +29,25 @@ def test_host_only_calls(built_library):
     assert fo.fo_status_string(4) == "non-finite input"
 
 
-def test_struct_layouts_match_header():
-    # fo_params: 2 ints, 2 doubles, 4 ints, 2 doubles, int, uint -> 64 bytes with padding
-    assert ctypes.sizeof(fo.FoParams) == 64
-    assert ctypes.sizeof(fo.FoResult) == 6 * 8 + 8 * 4
-    assert ctypes.sizeof(fo.FoProfile) == 8 * 8 * 3 + 8
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, measured by the C compiler."""
+    from conftest import ROOT
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fermi.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", f"{ROOT}/include", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    return [int(x) for x in out]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    for cls, cname in ((fo.FoParams, "fo_params"), (fo.FoResult, "fo_result"), (fo.FoProfile, "fo_profile")):
+        names = [f for f, _ in cls._fields_]
+        got = _c_layout(cname, names, tmp_path)
+        assert got[0] == ctypes.sizeof(cls), cname
+        for f, off in zip(names, got[1:]):
+            assert getattr(cls, f).offset == off, (cname, f)
