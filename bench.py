@@ -4,8 +4,10 @@
 One step = one density matrix for each tight-binding Hamiltonian N in {1000, 2000, 5000}
 (4 orbitals per atom, 0.1 atoms / A^3, 400 Chebyshev terms, kT = 0.1 eV, N_e = N/2, mu by
 float64 bisection on exact moments), with the matrix products in BF16x3 split precision on
-the tensor cores. Inputs are resident in HBM; the L2 is flushed (256 MiB write) before every
-timed step. Prints one JSON line (rank 0).
+the tensor cores, the three instances computed by one batched call (one grouped launch per
+stage). Inputs are resident in HBM; the L2 is flushed (256 MiB write) before every timed
+step. Also reported: the 512-instance batch (N log-uniform in [64, 1024], kT ~ U(0.05, 0.2)
+eV, 300 terms) replayed as one CUDA graph per batch. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -48,7 +50,9 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", default="bf16x3", choices=("bf16x3", "fp16x2", "bf16x1", "fp64"))
     ap.add_argument("--ns", default=",".join(str(n) for n in NS))
+    ap.add_argument("--n-terms", type=int, default=N_TERMS, help="Chebyshev terms (profiling cases)")
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batch measurement")
     return ap.parse_args()
 
 
@@ -154,6 +158,59 @@ def traffic_record(kernel: str, source: str):
     return rec
 
 
+# ------------------------------------------------------------- 512-instance batch
+def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300):
+    """Density matrices per second of the batch of `count` tight-binding instances with N
+    log-uniform in [64, 1024] and kT ~ U(0.05, 0.2) eV, replayed as one CUDA graph per batch
+    (L2 flushed before each), plus one profiled eager pass for the product roofline."""
+    import torch
+    import synth
+    from paper_2306_12616_gb300 import FO_FLAG_GRAPH
+    ns = [int(n) for n in synth.batch_sizes(count, 4000)]
+    kts = [float(t) for t in synth.batch_temperatures(count, 4000)]
+    hs = [torch.from_numpy(synth.tight_binding(n, 4000 + i)).to(flush.device) for i, n in enumerate(ns)]
+    ps = [torch.empty_like(h) for h in hs]
+    ne = [n / 2 for n in ns]
+    prm = solver.params(n_terms, 0.1, precision=precision, mu_mode="bisect", flags=FO_FLAG_GRAPH)
+    _, res = solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps)   # plan, autotune, capture
+    ok = all(r["status"] == 0 for r in res)
+    worst_tr = max(abs(r["trace"] - n / 2) / n for r, n in zip(res, ns))
+    for _ in range(2):
+        solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps, sync=False)
+    times = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps, sync=False)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    # profiled eager pass: stage times and the product kernel's achieved rate
+    prm_e = solver.params(n_terms, 0.1, precision=precision, mu_mode="bisect")
+    solver.density_matrix_batched(hs, ne, prm_e, kT=kts, outs=ps, sync=False)
+    torch.cuda.synchronize()
+    solver.profile_enable(True)
+    flush.fill_(1.0)
+    solver.density_matrix_batched(hs, ne, prm_e, kT=kts, outs=ps, sync=False)
+    prof = solver.profile_read(reset=True)
+    solver.profile_enable(False)
+    pr = prof["products"]
+    del hs, ps
+    torch.cuda.empty_cache()
+    return {"workload": f"{count} tight-binding H, N log-uniform in [64, 1024] (multiples of 4), "
+                        f"kT ~ U(0.05, 0.2) eV, N_e = N/2, {n_terms} terms, {precision}, mu by bisection",
+            "dm_per_s": count / (ms * 1e-3), "ms_per_batch": ms, "steps": steps, "graph": True,
+            "sum_n3": float(sum(float(n) ** 3 for n in ns)), "all_status_ok": ok,
+            "worst_trace_err_over_N": worst_tr, "tile_n": res[0]["tile_n"],
+            "tile_ctas": res[0]["tile_ctas"],
+            "eager_ms_per_batch": prof["call"]["ms"],
+            "products_achieved_tflops": pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] > 0 else None,
+            "products_share": pr["ms"] / max(1e-9, prof["call"]["ms"]),
+            "stages_ms": {k: v["ms"] for k, v in prof.items() if isinstance(v, dict)}}
+
+
 # --------------------------------------------------------------------------- main
 def run_reference(args, rank, world):
     if rank != 0:
@@ -170,7 +227,7 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": len(ns) / value * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "n": ns, "n_terms": N_TERMS, "kT_eV": KT,
+           "config": {"workload": WORKLOAD, "n": ns, "n_terms": args.n_terms, "kT_eV": KT,
                       "precision": "fp64 (numpy/LAPACK oracle)"},
            "cpu_baseline": {"value": value, "unit": "density matrices/s", "cores": sample["cores"],
                             "kind": "oracle", "sample": sample["sample"]},
@@ -198,7 +255,7 @@ def main():
     ns = [int(x) for x in args.ns.split(",")]
     solver = Solver(local)
     stream = torch.cuda.current_stream()
-    prm = solver.params(N_TERMS, KT, precision=args.precision, mu_mode="bisect")
+    prm = solver.params(args.n_terms, KT, precision=args.precision, mu_mode="bisect")
 
     # inputs resident in HBM (a different replica per rank)
     hs, ps, hcpu = {}, {}, {}
@@ -209,14 +266,16 @@ def main():
         ps[n] = torch.empty((n, n), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    hl, pl, nel = [hs[n] for n in ns], [ps[n] for n in ns], [n / 2 for n in ns]
+
     # validation pass: status, trace, and the mixed result against the FP64 GPU path
     accuracy, fp64_ms, results = {}, {}, {}
-    for n in ns:
-        _, res = solver.density_matrix(hs[n], n / 2, prm, out=ps[n])
+    _, res_b = solver.density_matrix_batched(hl, nel, prm, outs=pl)
+    for n, res in zip(ns, res_b):
         results[n] = res
         if not args.no_fp64_check and args.precision != "fp64":
             p64 = torch.empty_like(ps[n])
-            prm64 = solver.params(N_TERMS, KT, precision="fp64", mu_mode="bisect")
+            prm64 = solver.params(args.n_terms, KT, precision="fp64", mu_mode="bisect")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, r64 = solver.density_matrix(hs[n], n / 2, prm64, out=p64)
@@ -227,8 +286,7 @@ def main():
             del p64
 
     def step():
-        for n in ns:
-            solver.density_matrix(hs[n], n / 2, prm, out=ps[n], sync=False)
+        solver.density_matrix_batched(hl, nel, prm, outs=pl, sync=False)
 
     for _ in range(args.warmup):
         step()
@@ -297,12 +355,15 @@ def main():
             "share_of_step": prod["ms"] / max(1e-9, prof["call"]["ms"]),
             "traffic": (trec["bytes_per_launch"] if trec else None),
             "traffic_note": (trec["note"] if trec else "no ncu capture of the current kernel source")}
+    batch = None if args.no_batch else bench_batch(solver, stream, flush, max(3, args.steps // 2),
+                                                    args.precision)
     cb = cpu_baseline(ns) if (rank == 0 and world == 1) else None
     per_n = {}
     for n in ns:
         per_n[str(n)] = {"n_gemm": results[n]["n_gemm"], "k": results[n]["k"], "m": results[n]["m"],
                          "bisect_iters": results[n]["bisect_iters"], "mu_eV": results[n]["mu"],
-                         "status": results[n]["status"]}
+                         "status": results[n]["status"], "tile_n": results[n]["tile_n"],
+                         "tile_ctas": results[n]["tile_ctas"]}
         if n in accuracy:
             per_n[str(n)].update(accuracy[n])
             per_n[str(n)]["fp64_gpu_ms"] = fp64_ms[n]
@@ -313,7 +374,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if args.precision != "fp64" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": ns, "n_terms": N_TERMS, "kT_eV": KT,
+        "config": {"workload": WORKLOAD, "n": ns, "n_terms": args.n_terms, "kT_eV": KT,
                    "precision": f"{args.precision} split products, fp32 accumulation; fp64 bounds, "
                                 f"coefficients, moments, traces and mu" if args.precision != "fp64"
                    else "fp64 throughout",
@@ -328,6 +389,7 @@ def main():
         "per_n": per_n,
         "stages": stages,
         "fp64_gpu_dm_per_s": (len(fp64_ms) / (sum(fp64_ms.values()) * 1e-3)) if fp64_ms else None,
+        "batch_512": batch,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

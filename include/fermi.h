@@ -87,6 +87,9 @@ typedef struct {
     int32_t max_newton;       /* FO_MU_LEARNED: trace-corrected re-evaluations of P before the
                                  bisection fallback; 0 = 2, < 0 = none */
     int32_t tile_n;           /* tensor-core tile width: 0 = autotune per plan, or 128 / 256 */
+    int32_t tile_ctas;        /* CTAs per SM of the product kernel: 0 = autotune, 1, or 2
+                                 (2 only with 128-wide tiles); set together with tile_n */
+    int32_t reserved;
 } fo_params;
 
 typedef struct {
@@ -102,8 +105,10 @@ typedef struct {
     int32_t status;           /* fo_status of the device-side stages */
     int32_t n_launches;       /* kernels of this library launched by the call (whole batch) */
     int32_t tile_n;           /* tensor-core tile width used (0 for FP64) */
+    int32_t tile_ctas;        /* CTAs per SM of the product kernel used (0 for FP64) */
     int32_t evals;            /* evaluations of P (1 unless FO_MU_LEARNED corrected mu) */
     int32_t order;            /* expansion order proposed by the learned model (0 if none) */
+    int32_t reserved;
 } fo_result;
 
 /* Stages of a density-matrix call, as recorded by the profiler. */

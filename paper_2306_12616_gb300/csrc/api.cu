@@ -33,11 +33,11 @@ enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUND
 struct PlanKey {
     std::vector<int64_t> n;
     int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
-    int use_given = 0, tile_req = 0, sym = 1, max_bisect = 0;
+    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0;
     bool operator==(const PlanKey& o) const {
         return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
                mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
-               tile_req == o.tile_req && sym == o.sym && max_bisect == o.max_bisect;
+               tile_req == o.tile_req && ctas_req == o.ctas_req && sym == o.sym && max_bisect == o.max_bisect;
     }
 };
 
@@ -69,8 +69,9 @@ struct Plan {
     std::vector<Bucket> buckets;
     std::vector<Group> groups;
     std::vector<unsigned char> maps;   // 128 bytes per bucket
-    HostWork wg, wsc, we, wgr, wtc[2], wf64;   // wtc[0]: 256-wide tiles, wtc[1]: 128-wide
+    HostWork wg, wsc, we, wr, wgr, wtc[2], wf64;   // wtc[0]: 256-wide tiles, wtc[1]: 128-wide
     int tile_n = 0;
+    int tile_ctas = 0;
     int npairs = 0;
     void* dtab = nullptr;     // device tables: Inst[], InstIO[], prefixes
     Inst* d_inst = nullptr;
@@ -357,13 +358,14 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     fill(p->wg, [](const Inst& in) { return (in.n + kGershRows - 1) / kGershRows; });
     fill(p->wsc, [](const Inst& in) { const int64_t t = in.np / 32; return t * (t + 1) / 2; });
     fill(p->we, [](const Inst& in) { return (int64_t)ew_blocks(in.np); });
+    fill(p->wr, [](const Inst& in) { return (int64_t)red_blocks(in.np); });
     fill(p->wgr, [](const Inst& in) { return (int64_t)in.gram_blocks; });
     const bool full = key.mode == MODE_PRODUCT && !key.sym;
     fill(p->wtc[0], [&](const Inst& in) { return full ? tc_tiles_full(in.np, 256) : tc_tiles(in.np, 256); });
     fill(p->wtc[1], [&](const Inst& in) { return full ? tc_tiles_full(in.np, 128) : tc_tiles(in.np, 128); });
     fill(p->wf64, [](const Inst& in) { return f64_tiles(in.np); });
     const size_t off_pg = take(8 * 3 * (size_t)std::max(1, p->wg.pre[batch]));
-    const size_t off_pt = take(8 * 2 * (size_t)std::max(1, p->we.pre[batch]));
+    const size_t off_pt = take(8 * 2 * (size_t)std::max(1, p->wr.pre[batch]));
     p->total = off;
     // remember the offsets in the (not yet placed) pointers
     for (int j = 0; j < batch; ++j) p->inst[j].c = reinterpret_cast<double*>(small[j]);
@@ -415,7 +417,7 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
         in.res = p->d_res + j;
     }
     // device tables: Inst[batch], InstIO[batch], then the prefix arrays
-    HostWork* lists[] = {&p->wg, &p->wsc, &p->we, &p->wgr, &p->wtc[0], &p->wtc[1], &p->wf64};
+    HostWork* lists[] = {&p->wg, &p->wsc, &p->we, &p->wr, &p->wgr, &p->wtc[0], &p->wtc[1], &p->wf64};
     size_t bytes = align256(sizeof(Inst) * batch) + align256(sizeof(InstIO) * batch);
     for (HostWork* w : lists) bytes += align256(sizeof(int) * w->pre.size());
     if (cudaMalloc(&p->dtab, bytes) != cudaSuccess) {
@@ -503,7 +505,7 @@ fo_status run_product(fo_ctx* ctx, Plan& p, const Step& st, cudaStream_t s, cons
         for (const Group& g : p.groups) {
             std::string err;
             const int tile0 = w.pre[g.i0];
-            cudaError_t e = tc_gemm(p.key.prec, p.tile_n, st, p.d_inst, p.d_io, w.dev.pre, g.i0, g.i1, tile0,
+            cudaError_t e = tc_gemm(p.key.prec, p.tile_n, p.tile_ctas, st, p.d_inst, p.d_io, w.dev.pre, g.i0, g.i1, tile0,
                                     w.pre[g.i1] - tile0, p.maps.data() + 128 * (size_t)g.b0, g.b0, g.nb,
                                     ctx->flag, s, &err, p.key.sym);
             if (e == cudaSuccess && debug_sync() && !ctx->capturing) e = cudaDeviceSynchronize();
@@ -629,26 +631,30 @@ fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     run->launches += lstage;
     FO_TRY(clenshaw(ctx, p, s, run));
     h = prof_begin(ctx, s, FO_STAGE_TRACE);
-    FO_CUDA(launch_trace_frob(p.d_inst, p.d_io, p.we.dev, p.part_t, s), "trace");
+    FO_CUDA(launch_trace_frob(p.d_inst, p.d_io, p.wr.dev, p.part_t, s), "trace");
     prof_end(ctx, s, h, 0.0, 2);
     run->launches += 2;
     return FO_OK;
 }
 
-// Tile width of the tensor-core products: the requested one, or the faster of 256 and 128
-// on this plan's first baby step (timed with CUDA events on the plan's own data layout;
-// the data are whatever the workspace holds, the work does not depend on them).
+// Tile configuration of the tensor-core products: the requested one, or the fastest of
+// (256 wide, 1 CTA/SM), (128 wide, 1 CTA/SM) and (128 wide, 2 CTAs/SM) on this plan's first
+// baby step, timed with CUDA events on the plan's own layout (the data are whatever the
+// workspace holds; the work does not depend on them).
 fo_status autotune(fo_ctx* ctx, Plan& p) {
     if (p.sh.is64 || p.n_slots == 0) {
         p.tile_n = 0;
+        p.tile_ctas = 0;
         return FO_OK;
     }
     if (p.key.tile_req) {
         p.tile_n = p.key.tile_req;
+        p.tile_ctas = p.key.ctas_req ? p.key.ctas_req : 1;
         return FO_OK;
     }
     if (p.key.mode == MODE_PRODUCT || p.sh.k < 2) {
         p.tile_n = 256;
+        p.tile_ctas = 1;
         return FO_OK;
     }
     // make every instance active (the per-call inputs are not needed by a product)
@@ -659,17 +665,19 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
     const Step st = make_step(p, 0, 0, -1, -1, 1, 2.0, 0.0, -1.0, false, false, false, false, ctx);
     cudaEvent_t e0 = ev_get(ctx), e1 = ev_get(ctx);
     float best = 0.0f;
-    int best_n = 256;
+    int best_n = 256, best_c = 1;
     const bool prof = ctx->prof;
     ctx->prof = false;
-    for (int cand : {256, 128}) {
-        p.tile_n = cand;
+    const int cands[3][2] = {{256, 1}, {128, 1}, {128, 2}};
+    for (int ci = 0; ci < 3; ++ci) {
+        p.tile_n = cands[ci][0];
+        p.tile_ctas = cands[ci][1];
         Run r;
-        fo_status rs = run_product(ctx, p, st, s, "autotune", cand, &r);   // warm-up
+        fo_status rs = run_product(ctx, p, st, s, "autotune", ci, &r);   // warm-up
         if (rs != FO_OK) { ctx->prof = prof; return rs; }
         cudaEventRecord(e0, s);
         for (int rep = 0; rep < 3; ++rep) {
-            rs = run_product(ctx, p, st, s, "autotune", cand, &r);
+            rs = run_product(ctx, p, st, s, "autotune", ci, &r);
             if (rs != FO_OK) { ctx->prof = prof; return rs; }
         }
         cudaEventRecord(e1, s);
@@ -678,9 +686,10 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
             ctx->prof = prof;
             return fail(ctx, FO_ERR_CUDA, "autotune timing failed");
         }
-        if (cand == 256 || ms < best) {
+        if (ci == 0 || ms < best) {
             best = ms;
-            best_n = cand;
+            best_n = cands[ci][0];
+            best_c = cands[ci][1];
         }
     }
     ctx->prof = prof;
@@ -690,6 +699,7 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
     FO_CUDA(cudaMemcpy(&flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost), "autotune flag");
     if (flag) return fail(ctx, FO_ERR_DEVICE_TIMEOUT, "tensor-core wait timed out during autotuning");
     p.tile_n = best_n;
+    p.tile_ctas = best_c;
     return FO_OK;
 }
 
@@ -732,6 +742,9 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
     if (prm->mu_mode == FO_MU_LEARNED) return fail(ctx, FO_ERR_UNSUPPORTED, "learned mu needs a trained model");
     if (prm->tile_n != 0 && prm->tile_n != 128 && prm->tile_n != 256)
         return fail(ctx, FO_ERR_ARG, "tile_n must be 0, 128 or 256");
+    if (prm->tile_ctas < 0 || prm->tile_ctas > 2 || (prm->tile_ctas == 2 && prm->tile_n != 128) ||
+        (prm->tile_ctas != 0 && prm->tile_n == 0))
+        return fail(ctx, FO_ERR_ARG, "tile_ctas must be 0, 1 or 2 (2 with tile_n = 128), set with tile_n");
     return FO_OK;
 }
 
@@ -774,6 +787,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
     key.n_quad = prm->n_quad;
     key.use_given = prm->use_given_bounds ? 1 : 0;
     key.tile_req = prm->tile_n;
+    key.ctas_req = prm->tile_ctas;
     key.max_bisect = prm->max_bisect;
     Plan* p = nullptr;
     FO_TRY(get_plan(ctx, key, &p));
@@ -859,6 +873,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
             r.learned_accepted = hr.learned_ok;
             r.n_launches = run.launches;
             r.tile_n = p->tile_n;
+            r.tile_ctas = p->tile_ctas;
             r.evals = 1;
             r.order = 0;
             int status = hr.status;

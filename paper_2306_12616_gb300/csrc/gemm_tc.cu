@@ -151,6 +151,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile with 64-byte swizzle: rows of
 // 64 bytes, 8-row core groups 512 bytes apart (stride byte offset), descriptor version 1,
 // layout type 4 = SWIZZLE_64B. The k16 slices inside the 64-byte row are addressed by
@@ -186,15 +198,19 @@ struct TcMaps {
     CUtensorMap m[kMaxBuckets];
 };
 
-template <int PA, int PB, int NPROD, bool F16, int TBN>
+// MINB CTAs share an SM (1, or 2 for 128-wide tiles: one CTA's epilogue then overlaps the
+// other's main loop); the shared-memory ring and the register budget are split accordingly.
+template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB>
 struct TcCfg {
     static constexpr int kBBoxes = TBN / kBM;
     static constexpr int kStageBytes = PA * kBoxBytes + PB * kBBoxes * kBoxBytes;
-    static constexpr int kStagesRaw = (216 * 1024) / kStageBytes;
+    static constexpr int kStagesRaw = (216 * 1024 / MINB) / kStageBytes;
     static constexpr int kStages = kStagesRaw > 8 ? 8 : (kStagesRaw < 2 ? 2 : kStagesRaw);
     static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
     static constexpr int kTmemCols = 2 * TBN;   // two accumulators (power of two >= 32)
     static_assert(kSmem <= 232448 - 64, "shared memory budget of one CTA exceeded");
+    static_assert(MINB * kTmemCols <= 512, "tensor memory of the co-resident CTAs exceeded");
+    static_assert(MINB * (kSmem + 1024) <= 233472, "shared memory of the co-resident CTAs exceeded");
     static_assert(kStages * kStageBytes >= kBM * (TBN + 1) * 4, "result tile must fit the stage ring");
 };
 
@@ -266,12 +282,12 @@ __device__ __forceinline__ void tile_of(int t, int tm, int tn, int tbn, int sym,
     J = t - I * tn;
 }
 
-template <int PA, int PB, int NPROD, bool F16, int TBN>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     k_tc_gemm(const __grid_constant__ TcMaps maps, const Step st, const Inst* __restrict__ insts,
               const InstIO* __restrict__ io, const int* __restrict__ pre, int i0, int i1, int tile0,
               int b0, int sym, int* err_flag) {
-    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN>;
+    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB>;
     constexpr int S = Cfg::kStages;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -437,12 +453,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             fence_after();
             if (live) {
+                if (MINB == 1) {
 #pragma unroll
-                for (int cb = 0; cb < TBN / 64; ++cb) {
-                    uint32_t r[32];
-                    tmem_ld32(t_row + buf * TBN + cb * 32, r);
+                    for (int cb = 0; cb < TBN / 64; ++cb) {
+                        uint32_t r[32];
+                        tmem_ld32(t_row + buf * TBN + cb * 32, r);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
+                        for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
+                    }
+                } else {
+                    // half the registers per thread: 16-column loads
+#pragma unroll
+                    for (int cb = 0; cb < TBN / 32; ++cb) {
+                        uint32_t r[16];
+                        tmem_ld16(t_row + buf * TBN + cb * 16, r);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) sum[cb * 16 + j] += __uint_as_float(r[j]);
+                    }
                 }
             }
             fence_before();
@@ -600,11 +627,11 @@ EncodeFn get_encode(std::string* err) {
     return fn;
 }
 
-template <int PA, int PB, int NPROD, bool F16, int TBN>
+template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB>
 cudaError_t launch_tc(const TcMaps& maps, const Step& st, const Inst* in, const InstIO* io, const int* pre,
                       int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag, cudaStream_t s) {
-    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN>;
-    auto kern = k_tc_gemm<PA, PB, NPROD, F16, TBN>;
+    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB>;
+    auto kern = k_tc_gemm<PA, PB, NPROD, F16, TBN, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)tiles, kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, b0, sym, err_flag);
@@ -612,12 +639,14 @@ cudaError_t launch_tc(const TcMaps& maps, const Step& st, const Inst* in, const 
 }
 
 template <int PA, int PB, int NPROD, bool F16>
-cudaError_t dispatch_tbn(int tile_n, const TcMaps& maps, const Step& st, const Inst* in, const InstIO* io,
-                         const int* pre, int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag,
-                         cudaStream_t s) {
-    return tile_n == 128
-               ? launch_tc<PA, PB, NPROD, F16, 128>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s)
-               : launch_tc<PA, PB, NPROD, F16, 256>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+cudaError_t dispatch_tbn(int tile_n, int ctas, const TcMaps& maps, const Step& st, const Inst* in,
+                         const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles, int b0, int sym,
+                         int* err_flag, cudaStream_t s) {
+    if (tile_n == 256)
+        return launch_tc<PA, PB, NPROD, F16, 256, 1>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+    if (ctas == 2)
+        return launch_tc<PA, PB, NPROD, F16, 128, 2>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+    return launch_tc<PA, PB, NPROD, F16, 128, 1>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
 }
 
 }  // namespace
@@ -660,10 +689,11 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
     return true;
 }
 
-cudaError_t tc_gemm(int prec, int tile_n, const Step& st, const Inst* in, const InstIO* io, const int* pre,
-                    int i0, int i1, int tile0, int tiles, const void* maps, int b0, int nb, int* err_flag,
-                    cudaStream_t s, std::string* err, int sym) {
-    if (tc_planes(prec) == 0 || (tile_n != 128 && tile_n != 256) || nb < 1 || nb > kMaxBuckets || !err_flag) {
+cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step& st, const Inst* in, const InstIO* io,
+                    const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0, int nb,
+                    int* err_flag, cudaStream_t s, std::string* err, int sym) {
+    if (tc_planes(prec) == 0 || (tile_n != 128 && tile_n != 256) || (ctas != 1 && ctas != 2) ||
+        (ctas == 2 && tile_n != 128) || nb < 1 || nb > kMaxBuckets || !err_flag) {
         if (err) *err = "tc_gemm: unsupported precision, tile or bucket count";
         return cudaErrorInvalidValue;
     }
@@ -673,11 +703,11 @@ cudaError_t tc_gemm(int prec, int tile_n, const Step& st, const Inst* in, const 
     std::memcpy(&tm.m[0], maps, sizeof(CUtensorMap) * nb);
     switch (prec) {
         case FO_PREC_BF16X3:
-            return dispatch_tbn<3, 3, 6, false>(tile_n, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            return dispatch_tbn<3, 3, 6, false>(tile_n, ctas, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
         case FO_PREC_FP16X2:
-            return dispatch_tbn<2, 2, 3, true>(tile_n, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            return dispatch_tbn<2, 2, 3, true>(tile_n, ctas, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
         case FO_PREC_BF16X1:
-            return dispatch_tbn<1, 1, 1, false>(tile_n, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            return dispatch_tbn<1, 1, 1, false>(tile_n, ctas, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -122,6 +122,15 @@ __host__ __device__ inline int ew_blocks(int64_t np) {
     const int r = ew_rows(np);
     return (int)((np + r - 1) / r);
 }
+// Reduction row blocks (traces of P): about 64K entries per block.
+__host__ __device__ inline int red_rows(int64_t np) {
+    const int64_t r = 65536 / np;
+    return r < 1 ? 1 : (int)r;
+}
+__host__ __device__ inline int red_blocks(int64_t np) {
+    const int r = red_rows(np);
+    return (int)((np + r - 1) / r);
+}
 constexpr int kGershRows = 8;   // rows per block of the bounds kernel (a warp per row)
 
 // Self-check build (-DFO_SELF_CHECK): kernels verify the index range and the alignment of
@@ -155,7 +164,7 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
                         int nbaby, int out_g0, int is64, cudaStream_t s, int* launches);
 // tau_0 .. tau_{n_terms-1} from the traces and the Frobenius products.
 cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, cudaStream_t s);
-cudaError_t launch_trace_frob(const Inst* in, const InstIO* io, Work we, double* part, cudaStream_t s);
+cudaError_t launch_trace_frob(const Inst* in, const InstIO* io, Work wr, double* part, cudaStream_t s);
 cudaError_t launch_copy_out(const Inst* in, const InstIO* io, Work we, const Shape& sh, cudaStream_t s);
 // Standalone packing of a float32 matrix into slot `slot` (fo_recurrence_product).
 cudaError_t launch_pack_f32(const float* A, int64_t n, int64_t lda, char* slot, int64_t np, int planes,
@@ -185,8 +194,9 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
                  int64_t slot_bytes, int64_t inst_bytes, bool fp16, std::string* err);
 // Grouped split-precision product over instances [i0, i1) (sorted by tile count, buckets
 // [b0, b0 + nb) with maps[0..nb)), tile_n = 256 or 128 output columns per tile.
-// sym = 0 computes every tile of the full product (fo_recurrence_product only).
-cudaError_t tc_gemm(int prec, int tile_n, const Step& st, const Inst* in, const InstIO* io,
+// ctas = CTAs per SM (2 only with tile_n = 128). sym = 0 computes every tile of the full
+// product (fo_recurrence_product only).
+cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step& st, const Inst* in, const InstIO* io,
                     const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
                     int nb, int* err_flag, cudaStream_t s, std::string* err, int sym = 1);
 // Tiles of the full (non-symmetric) product.

@@ -435,7 +435,7 @@ __global__ void k_assemble_moments(const Inst* __restrict__ insts, int k, int m,
 }
 
 // ------------------------------------------------------------ trace and ||P||_F^2
-// Block = ew_rows(np) rows of one instance's P; partials (tr, ||.||^2) per block.
+// Block = red_rows(np) rows of one instance's P; partials (tr, ||.||^2) per block.
 __global__ void __launch_bounds__(256) k_trace_frob_part(const Inst* __restrict__ insts,
                                                          const InstIO* __restrict__ io, Work we,
                                                          double* partials) {
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(256) k_trace_frob_part(const Inst* __restrict_
     const int i = find_inst(we.pre, 0, we.count, blockIdx.x);
     const int64_t n = insts[i].n, np = insts[i].np, ldp = io[i].ldp;
     const double* P = io[i].P;
-    const int rows = ew_rows(np);
+    const int rows = red_rows(np);
     const int64_t r0 = (int64_t)(blockIdx.x - we.pre[i]) * rows;
     double tr = 0.0, fr = 0.0;
     if (insts[i].res->active) {

@@ -66,17 +66,20 @@ def test_batch_equals_single_calls(solver):
         assert torch.max(torch.abs(p1 - p)).item() <= 1e-9
 
 
-def test_tile_widths_bit_identical(solver):
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x2", "bf16x1"])
+def test_tile_configs_bit_identical(solver, prec):
+    """Every tile configuration the autotuner may pick gives the same bits."""
     ns, kts, hs = batch(5, 3, 100, 700)
     hd = [to_dev(h) for h in hs]
     out = {}
-    for t in (128, 256):
-        prm = solver.params(300, 0.1, precision="bf16x3", mu_mode="bisect", tile_n=t)
+    for t, c in ((256, 1), (128, 1), (128, 2)):
+        prm = solver.params(300, 0.1, precision=prec, mu_mode="bisect", tile_n=t, tile_ctas=c)
         ps, res = solver.density_matrix_batched(hd, [n / 2 for n in ns], prm, kT=kts)
-        assert all(r["tile_n"] == t for r in res)
-        out[t] = ps
-    for a, b in zip(out[128], out[256]):
-        assert torch.equal(a, b)
+        assert all(r["tile_n"] == t and r["tile_ctas"] == c for r in res)
+        out[(t, c)] = ps
+    for key in ((128, 1), (128, 2)):
+        for a, b in zip(out[(256, 1)], out[key]):
+            assert torch.equal(a, b), key
 
 
 def test_graph_replay_equals_eager(solver):
@@ -142,3 +145,5 @@ def test_batch_argument_errors(solver):
         solver.density_matrix_batched([h], [100.0], solver.params(64, 0.1))   # n_e > n
     with pytest.raises(Exception):
         solver.density_matrix_batched([h], [32.0], solver.params(64, 0.1, tile_n=64))
+    with pytest.raises(Exception):
+        solver.density_matrix_batched([h], [32.0], solver.params(64, 0.1, tile_n=256, tile_ctas=2))
