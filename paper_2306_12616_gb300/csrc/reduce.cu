@@ -296,93 +296,114 @@ __global__ void k_diag_sums(const Inst* __restrict__ insts, int is64) {
 
 // --------------------------------------------------------- Frobenius inner products
 // <S_{giant0+g}, S_{baby0+b}>_F over all np*np entries of one instance (the zero border
-// contributes nothing). A block stages kChunk consecutive entries of every matrix in shared
-// memory, matrix-major (row s holds the chunk of matrix s), with 16-byte loads. Each warp
-// owns up to kTPW 4 x 4 tiles of (giant, baby) pairs; its lanes walk consecutive entries of
-// a row, so shared-memory reads are conflict free. Within a chunk the products are summed
-// in T; across chunks float32 sums are compensated (Kahan), float64 sums are plain. Lanes
-// are reduced by shuffles at the end into per-block float64 partials (instance-local block
-// order, summed in that order by k_sum_partials).
-constexpr int kChunk = 256;
-constexpr int kRowPad = 4;
+// contributes nothing). A block covers kGChunks consecutive chunks of kChunk entries. Each
+// chunk of every matrix is staged in shared memory, matrix-major (row s holds the chunk of
+// matrix s, rows padded by 16 bytes), double-buffered: the next chunk is loaded into
+// registers before the current one is multiplied, and stored to the other buffer after, so
+// one barrier per chunk separates the phases and the global loads overlap the arithmetic.
+// Each warp owns up to kTPW 4 x 4 tiles of (giant, baby) pairs; a lane reads 16-byte
+// vectors of 8 rows and accumulates 4 x 4 x (16 / sizeof(T)) products per step. Every lane
+// sums at most kGChunks * kChunk / 32 products per pair in T; lanes are combined by float64
+// shuffles and blocks by the partial sums (instance-local block order, k_sum_partials).
+constexpr int kChunkBytes = 1024;   // one chunk of one matrix
+constexpr int kBlockBytes = 16384;  // entries of one matrix per block, in bytes of float32
+constexpr int kMaxQuads = 12;       // staged rows <= 48
 constexpr int kTPW = 2;
 constexpr int kGramThreads = 512;
 
 template <typename T>
-__global__ void __launch_bounds__(kGramThreads) k_gram(const Inst* __restrict__ insts, Work wgr, int giant0,
-                                                       int ngiant, int baby0, int nbaby) {
+__global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict__ insts, Work wgr, int giant0,
+                                                          int ngiant, int baby0, int nbaby) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
+    constexpr int kChunk = kChunkBytes / (int)sizeof(T);      // entries per chunk
+    constexpr int kGChunks = kBlockBytes / 4 / kChunk;        // chunks per block
+    constexpr int V = 16 / sizeof(T);          // elements per 16-byte vector
+    constexpr int RS = kChunk + V;             // row stride (elements)
+    constexpr int VPR = kChunk / V;            // vectors per row
     const int i = find_inst(wgr.pre, 0, wgr.count, blockIdx.x);
     const Inst& in = insts[i];
     if (!in.res->active) return;
-    const int lb = blockIdx.x - wgr.pre[i], nb = in.gram_blocks;
+    const int lb = blockIdx.x - wgr.pre[i];
     const char* base = in.slots;
     const int64_t slot_bytes = in.slot_bytes;
-    const int64_t total = in.np * in.np;
-    constexpr int RS = kChunk + kRowPad;                 // row stride (elements)
+    const int64_t nchunks = in.np * in.np / kChunk;   // np^2 is a multiple of 16384
+    const int64_t c0 = (int64_t)lb * kGChunks;
+    const int64_t c1 = c0 + kGChunks < nchunks ? c0 + kGChunks : nchunks;
     const int ng4 = (ngiant + 3) / 4, nb4 = (nbaby + 3) / 4;
     const int nrows = 4 * (ng4 + nb4);
     const int ntiles = ng4 * nb4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    T* buf0 = reinterpret_cast<T*>(smem_raw);
+    T* buf1 = buf0 + nrows * RS;
+
+    // vectors this thread loads per chunk: q = threadIdx.x + j * blockDim.x < nrows * VPR
+    constexpr int kMaxLoads = (4 * kMaxQuads * VPR + kGramThreads - 1) / kGramThreads;
+    const int nq = nrows * VPR;
+    auto src_of = [&](int q, int64_t chunk) -> const float4* {
+        const int srow = q / VPR, ev = (q % VPR) * V;
+        int slot = -1;
+        if (srow < 4 * ng4) { if (srow < ngiant) slot = giant0 + srow; }
+        else { const int bb = srow - 4 * ng4; if (bb < nbaby) slot = baby0 + bb; }
+        if (slot < 0) return nullptr;
+        return reinterpret_cast<const float4*>(reinterpret_cast<const T*>(base + slot_bytes * slot) +
+                                               chunk * kChunk + ev);
+    };
+    float4 pre[kMaxLoads];
+    auto load = [&](int64_t chunk) {
+#pragma unroll
+        for (int j = 0; j < kMaxLoads; ++j) {
+            const int q = threadIdx.x + j * kGramThreads;
+            const float4* src = q < nq ? src_of(q, chunk) : nullptr;
+            pre[j] = src ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store = [&](T* buf) {
+#pragma unroll
+        for (int j = 0; j < kMaxLoads; ++j) {
+            const int q = threadIdx.x + j * kGramThreads;
+            if (q < nq) *reinterpret_cast<float4*>(buf + (q / VPR) * RS + (q % VPR) * V) = pre[j];
+        }
+    };
 
     T acc[kTPW][16];
-    T cmp[kTPW][16];   // Kahan compensation (float32 only)
 #pragma unroll
     for (int t = 0; t < kTPW; ++t)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) { acc[t][q] = T(0); cmp[t][q] = T(0); }
+        for (int q = 0; q < 16; ++q) acc[t][q] = T(0);
 
-    constexpr int V = 16 / sizeof(T);                    // elements per 16-byte load
-    const int64_t nchunks = (total + kChunk - 1) / kChunk;
-    for (int64_t ch = lb; ch < nchunks; ch += nb) {
-        const int64_t e0 = ch * kChunk;
-        for (int q = threadIdx.x; q < nrows * (kChunk / V); q += blockDim.x) {
-            const int srow = q / (kChunk / V), ev = (q % (kChunk / V)) * V;
-            int slot = -1;
-            if (srow < 4 * ng4) { if (srow < ngiant) slot = giant0 + srow; }
-            else { const int bb = srow - 4 * ng4; if (bb < nbaby) slot = baby0 + bb; }
-            T* dst = sm + srow * RS + ev;
-            if (slot >= 0 && e0 + ev + V <= total) {
-                const T* src = reinterpret_cast<const T*>(base + slot_bytes * slot) + e0 + ev;
-                *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v) dst[v] = T(0);
-            }
-        }
-        __syncthreads();
+    if (c0 < c1) {
+        load(c0);
+        store(buf0);
+    }
+    __syncthreads();
+    for (int64_t c = c0; c < c1; ++c) {
+        T* cur = ((c - c0) & 1) ? buf1 : buf0;
+        T* nxt = ((c - c0) & 1) ? buf0 : buf1;
+        const bool more = c + 1 < c1;
+        if (more) load(c + 1);
 #pragma unroll
         for (int t = 0; t < kTPW; ++t) {
             const int tile = warp + t * nwarps;
             if (tile >= ntiles) break;                   // uniform across the warp
-            const int g0 = 4 * (tile / nb4), b0 = 4 * ng4 + 4 * (tile % nb4);
-            T c16[16];
+            const T* g0 = cur + 4 * (tile / nb4) * RS;
+            const T* b0 = cur + (4 * ng4 + 4 * (tile % nb4)) * RS;
+            for (int e = lane * V; e < kChunk; e += 32 * V) {
+                T gv[4][V], bv[4][V];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) c16[q] = T(0);
-            for (int e = lane; e < kChunk; e += 32) {
-                T gv[4], bv[4];
+                for (int a = 0; a < 4; ++a)
+                    *reinterpret_cast<float4*>(gv[a]) = *reinterpret_cast<const float4*>(g0 + a * RS + e);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) gv[a] = sm[(g0 + a) * RS + e];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) bv[b] = sm[(b0 + b) * RS + e];
+                for (int b = 0; b < 4; ++b)
+                    *reinterpret_cast<float4*>(bv[b]) = *reinterpret_cast<const float4*>(b0 + b * RS + e);
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) c16[4 * a + b] = fma(gv[a], bv[b], c16[4 * a + b]);
-            }
+                    for (int b = 0; b < 4; ++b)
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                if (sizeof(T) == 4) {
-                    const T y = c16[q] - cmp[t][q];
-                    const T s2 = acc[t][q] + y;
-                    cmp[t][q] = (s2 - acc[t][q]) - y;
-                    acc[t][q] = s2;
-                } else {
-                    acc[t][q] += c16[q];
-                }
+                        for (int v = 0; v < V; ++v) acc[t][4 * a + b] = fma(gv[a][v], bv[b][v], acc[t][4 * a + b]);
             }
         }
+        if (more) store(nxt);
         __syncthreads();
     }
     const int npairs = ngiant * nbaby;
@@ -394,7 +415,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const Inst* __restrict__ 
         const int tg = tile / nb4, tb = tile % nb4;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            double v = (double)acc[t][q] - (double)cmp[t][q];
+            double v = (double)acc[t][q];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             const int g = 4 * tg + q / 4, b = 4 * tb + q % 4;
             if (lane == 0 && g < ngiant && b < nbaby) partials[(int64_t)lb * npairs + g * nbaby + b] = v;
@@ -402,15 +423,17 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const Inst* __restrict__ 
     }
 }
 
-// gram[out0 + pq] = sum over the instance's blocks of partial pq; block (pairs, instance).
+// gram[out0 + pq] = sum over the instance's blocks of partial pq, in a fixed order; one
+// block per (pair, instance), threads strided over the partials.
 __global__ void k_sum_partials(const Inst* __restrict__ insts, int npairs, int out0) {
+    __shared__ double sh[33];
     const Inst& in = insts[blockIdx.y];
     if (!in.res->active) return;
-    const int pq = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pq >= npairs) return;
+    const int pq = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < in.gram_blocks; ++b) s += in.gpart[(int64_t)b * npairs + pq];
-    in.gram[out0 + pq] = s;
+    for (int b = threadIdx.x; b < in.gram_blocks; b += blockDim.x) s += in.gpart[(int64_t)b * npairs + pq];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) in.gram[out0 + pq] = s;
 }
 
 // tau[0..n_terms) from baby traces diag[0..k) (T_1..T_k), giant traces diag[k + l - 2]
@@ -556,13 +579,10 @@ cudaError_t launch_diag_sums(const Inst* in, int batch, int count, const Shape& 
 }
 
 int gram_blocks_for(int64_t np, int batch) {
-    const int64_t nchunks = (np * np + kChunk - 1) / kChunk;
-    // enough blocks to fill the GPU for one instance, fewer per instance in a batch
-    int64_t cap = 152 * 4 / (batch > 0 ? batch : 1);
-    if (cap < 4) cap = 4;
-    int64_t b = nchunks / 16;   // at least 16 chunks per block
-    if (b > cap) b = cap;
-    return (int)(b < 1 ? 1 : b);
+    (void)batch;
+    // kBlockBytes / 4 entries per block (for float32 and float64 alike)
+    const int64_t per = kBlockBytes / 4;
+    return (int)((np * np + per - 1) / per);
 }
 
 cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0, int nbaby,
@@ -571,12 +591,15 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
     if (nbaby > 32) return cudaErrorInvalidValue;
     const int max_tiles = (kGramThreads / 32) * kTPW;
     const int nb4 = (nbaby + 3) / 4;
-    const int gmax = 4 * (max_tiles / nb4);           // giants per launch
+    // giants per launch: the tiles fit the warps, and the staged rows stay <= 64
+    int gmax = 4 * (max_tiles / nb4);
+    if (gmax > 4 * (kMaxQuads - nb4)) gmax = 4 * (kMaxQuads - nb4);
+    if (gmax < 4) return cudaErrorInvalidValue;
     for (int g = 0; g < ngiant; g += gmax) {
         const int ng = ngiant - g < gmax ? ngiant - g : gmax;
         const int ng4 = (ng + 3) / 4;
         const size_t elem = is64 ? 8 : 4;
-        const size_t smem = (size_t)4 * (ng4 + nb4) * (kChunk + kRowPad) * elem;
+        const size_t smem = (size_t)2 * 4 * (ng4 + nb4) * (kChunkBytes / elem + 16 / elem) * elem;
         if (is64) {
             cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_gram<double><<<wgr.total, kGramThreads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
@@ -585,7 +608,7 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
             k_gram<float><<<wgr.total, kGramThreads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
         }
         const int npairs = ng * nbaby;
-        k_sum_partials<<<dim3((npairs + 127) / 128, batch), 128, 0, s>>>(in, npairs, (out_g0 + g) * nbaby);
+        k_sum_partials<<<dim3(npairs, batch), 128, 0, s>>>(in, npairs, (out_g0 + g) * nbaby);
         if (launches) *launches += 2;
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
