@@ -247,6 +247,72 @@ fo_status fo_moments(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld,
                      double *d_tau, void *stream);
 
 /*
+ * Learned chemical potential (FO_MU_LEARNED). A small fully connected network, float32,
+ * 68 inputs -> 256 -> 256 -> 2 outputs with SiLU activations, held by the context:
+ *   inputs  tau_1 .. tau_64 / N (Chebyshev moments tau_j = tr T_j(X) of the scaled
+ *           Hamiltonian; only tau_j with j <= 2k are available from the k baby steps, the
+ *           others are 0), N_e / N, kT_x = 2 kT / (emax - emin), emin / 100, emax / 100;
+ *   outputs mu_x = (2 mu - (emin + emax)) / (emax - emin) and log2(L*) / log2(n_terms),
+ *           L* the number of terms after which every trace tail |sum_{j>=L'} c_j tau_j|
+ *           stays below 1e-4 N (the proposed expansion order, reported in fo_result.order).
+ * Inputs and outputs are standardised with the training set's mean and standard deviation
+ * (the normalisation vector: feature mean[68], feature std[68], target mean[2], target
+ * std[2]). Parameters are stored W1 (256 x 68), b1 (256), W2 (256 x 256), b2 (256),
+ * W3 (2 x 256), b3 (2): FO_MLP_PARAMS floats. The loss of training is the mean over the
+ * batch of (mu_x error)^2 + 0.1 (order error)^2 in standardised units, minimised by Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8); all of forward, backward and update run in this
+ * library's kernels. In a FO_MU_LEARNED call the proposed mu is kept when the float64
+ * trace of P meets params.tr_tol; otherwise mu is corrected from tr P and ||P||_F^2
+ * (Newton, then secant) and P re-evaluated up to params.max_newton times, and instances
+ * still outside the tolerance fall back to exact moments and bisection (started at the
+ * proposal). The call fails with FO_ERR_UNSUPPORTED while the context holds no model.
+ */
+#define FO_MLP_INPUTS  68
+#define FO_MLP_OUTPUTS 2
+#define FO_MLP_PARAMS  83970
+#define FO_MLP_NORM    140
+
+/*
+ * Training pairs generated by the method itself: for every instance of the batch the exact
+ * path (baby and giant steps, exact moments, bisection) finds mu, and the call writes the
+ * network inputs into d_feat[batch x 68] and, if d_target != NULL, the targets
+ * (mu_x, order) into d_target[batch x 2] (device float32, rows in the caller's order).
+ * P is not formed. Arguments as in fo_density_matrix_batched (params->mu_mode is ignored).
+ * res (optional, host array of batch) receives mu, bounds and status; the call then
+ * synchronises.
+ */
+fo_status fo_learned_features(fo_ctx *ctx, int32_t batch, const double *const *dH,
+                              const int64_t *n, const int64_t *ld, const double *n_e,
+                              const double *kT, const fo_params *params, float *d_feat,
+                              float *d_target, fo_result *res, void *stream);
+/* Fresh parameters: Uniform(-a, a) weights, a = sqrt(6 / (fan_in + fan_out)), drawn with
+ * splitmix64 from `seed`; zero biases; identity normalisation. Synchronous. */
+fo_status fo_mlp_init(fo_ctx *ctx, uint64_t seed);
+/* Copy parameters (FO_MLP_PARAMS floats) and normalisation (FO_MLP_NORM floats, NULL =
+ * identity) from host memory into the context's model; resets the Adam state. */
+fo_status fo_mlp_set_params(fo_ctx *ctx, const float *h_params, const float *h_norm);
+/* Copy the model's parameters and normalisation to host memory (either may be NULL). */
+fo_status fo_mlp_get_params(fo_ctx *ctx, float *h_params, float *h_norm);
+/* Network outputs d_y[n x 2] for standardised inputs d_x[n x 68] (device). Asynchronous. */
+fo_status fo_mlp_forward(fo_ctx *ctx, const float *d_x, int32_t n, float *d_y, void *stream);
+/* Loss and gradient for standardised inputs d_x[n x 68] and targets d_t[n x 2]: every
+ * parameter's gradient into d_grad[FO_MLP_PARAMS] (device, parameter layout), the loss into
+ * *h_loss (host; the call then synchronises) unless h_loss == NULL. */
+fo_status fo_mlp_gradients(fo_ctx *ctx, const float *d_x, const float *d_t, int32_t n,
+                           float *d_grad, float *h_loss, void *stream);
+/* Train on raw features d_feat[n x 68] and targets d_target[n x 2] (device): standardise
+ * with their column statistics, then `epochs` passes of Adam steps over mini-batches of
+ * `batch` rows in a splitmix64-shuffled order (seeded by `seed`); starts from the current
+ * model, or a fresh one drawn from `seed` if the context has none. h_loss (host, epochs
+ * floats, may be NULL) receives the mean mini-batch loss of every epoch. Synchronous. */
+fo_status fo_mlp_train(fo_ctx *ctx, const float *d_feat, const float *d_target, int32_t n,
+                       int32_t epochs, int32_t batch, float lr, uint64_t seed, float *h_loss,
+                       void *stream);
+/* Save / load the model (layout header, normalisation, parameters) to / from a file. */
+fo_status fo_mlp_save(fo_ctx *ctx, const char *path);
+fo_status fo_mlp_load(fo_ctx *ctx, const char *path);
+
+/*
  * Enable (1) or disable (0) the stage profiler of this context; enabling clears it. While
  * enabled every density-matrix call records CUDA events around its stages.
  */

@@ -21,7 +21,9 @@ __all__ = [
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
     "fo_density_matrix_batched", "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
-    "fo_spectral_bounds_noalloc", "FO_NOALLOC_MAX_N",
+    "fo_spectral_bounds_noalloc", "FO_NOALLOC_MAX_N", "fo_learned_features", "fo_mlp_init",
+    "fo_mlp_set_params", "fo_mlp_get_params", "fo_mlp_forward", "fo_mlp_gradients", "fo_mlp_train",
+    "fo_mlp_save", "fo_mlp_load", "FO_MLP_INPUTS", "FO_MLP_OUTPUTS", "FO_MLP_PARAMS", "FO_MLP_NORM",
     "STAGE_NAMES", "Solver", "PRECISIONS", "MU_MODES",
 ]
 
@@ -42,9 +44,11 @@ EXPORTED_SYMBOLS = (
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
     "fo_density_matrix_batched", "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read",
-    "fo_spectral_bounds_noalloc",
+    "fo_spectral_bounds_noalloc", "fo_learned_features", "fo_mlp_init", "fo_mlp_set_params",
+    "fo_mlp_get_params", "fo_mlp_forward", "fo_mlp_gradients", "fo_mlp_train", "fo_mlp_save", "fo_mlp_load",
 )
 FO_NOALLOC_MAX_N = 32768
+FO_MLP_INPUTS, FO_MLP_OUTPUTS, FO_MLP_PARAMS, FO_MLP_NORM = 68, 2, 83970, 140
 
 
 class FoParams(ctypes.Structure):
@@ -131,6 +135,17 @@ def lib() -> ctypes.CDLL:
             "fo_density_matrix_batched": (ctypes.c_int, [_c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                                          _c_ptr, ctypes.POINTER(FoParams), _c_ptr, _c_ptr,
                                                          _c_ptr, _c_ptr]),
+            "fo_learned_features": (ctypes.c_int, [_c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                                   ctypes.POINTER(FoParams), _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
+            "fo_mlp_init": (ctypes.c_int, [_c_ptr, ctypes.c_uint64]),
+            "fo_mlp_set_params": (ctypes.c_int, [_c_ptr, _c_ptr, _c_ptr]),
+            "fo_mlp_get_params": (ctypes.c_int, [_c_ptr, _c_ptr, _c_ptr]),
+            "fo_mlp_forward": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i32, _c_ptr, _c_ptr]),
+            "fo_mlp_gradients": (ctypes.c_int, [_c_ptr, _c_ptr, _c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr]),
+            "fo_mlp_train": (ctypes.c_int, [_c_ptr, _c_ptr, _c_ptr, _c_i32, _c_i32, _c_i32, _c_f,
+                                            ctypes.c_uint64, _c_ptr, _c_ptr]),
+            "fo_mlp_save": (ctypes.c_int, [_c_ptr, ctypes.c_char_p]),
+            "fo_mlp_load": (ctypes.c_int, [_c_ptr, ctypes.c_char_p]),
             "fo_moments": (ctypes.c_int, [_c_ptr, _c_ptr, _c_i64, _c_i64, _c_ptr, _c_i32, _c_i32,
                                           _c_ptr, _c_ptr]),
             "fo_profile_enable": (ctypes.c_int, [_c_ptr, _c_i32]),
@@ -206,6 +221,44 @@ def fo_density_matrix_batched(ctx, batch, d_h_ptrs, n, ld, n_e, kT, params: FoPa
     array of FoResult of length batch, or None."""
     return lib().fo_density_matrix_batched(ctx, batch, d_h_ptrs, n, ld, n_e, kT, ctypes.byref(params),
                                            d_p_ptrs, ldp, results, stream)
+
+
+def fo_learned_features(ctx, batch, d_h_ptrs, n, ld, n_e, kT, params: FoParams, d_feat, d_target,
+                        results, stream=0) -> int:
+    return lib().fo_learned_features(ctx, batch, d_h_ptrs, n, ld, n_e, kT, ctypes.byref(params), d_feat,
+                                     d_target, results, stream)
+
+
+def fo_mlp_init(ctx, seed) -> int:
+    return lib().fo_mlp_init(ctx, seed)
+
+
+def fo_mlp_set_params(ctx, h_params, h_norm) -> int:
+    return lib().fo_mlp_set_params(ctx, h_params, h_norm)
+
+
+def fo_mlp_get_params(ctx, h_params, h_norm) -> int:
+    return lib().fo_mlp_get_params(ctx, h_params, h_norm)
+
+
+def fo_mlp_forward(ctx, d_x, n, d_y, stream=0) -> int:
+    return lib().fo_mlp_forward(ctx, d_x, n, d_y, stream)
+
+
+def fo_mlp_gradients(ctx, d_x, d_t, n, d_grad, h_loss, stream=0) -> int:
+    return lib().fo_mlp_gradients(ctx, d_x, d_t, n, d_grad, h_loss, stream)
+
+
+def fo_mlp_train(ctx, d_feat, d_target, n, epochs, batch, lr, seed, h_loss, stream=0) -> int:
+    return lib().fo_mlp_train(ctx, d_feat, d_target, n, epochs, batch, lr, seed, h_loss, stream)
+
+
+def fo_mlp_save(ctx, path: str) -> int:
+    return lib().fo_mlp_save(ctx, path.encode())
+
+
+def fo_mlp_load(ctx, path: str) -> int:
+    return lib().fo_mlp_load(ctx, path.encode())
 
 
 def fo_moments(ctx, d_h, n, ld, d_bounds, n_moments, precision, d_tau, stream=0) -> int:
@@ -324,6 +377,67 @@ class Solver:
         self._check(fo_density_matrix_batched(self.ctx, B, d_h, n, ld, ne, kt, params, d_p, ldp, res,
                                               _stream_handle(stream)))
         return ps, ([r.as_dict() for r in res] if res is not None else None)
+
+    # ------------------------------------------------------------ learned mu
+    def learned_features(self, hs, n_e, params: FoParams, kT=None, stream=None):
+        """Training pairs of a batch by the exact method: (features [B, 68], targets [B, 2],
+        results) as float32 CUDA tensors and result dicts."""
+        import torch
+        B = len(hs)
+        ptr, i64, dbl = ctypes.c_void_p * B, ctypes.c_int64 * B, ctypes.c_double * B
+        feat = torch.empty((B, FO_MLP_INPUTS), dtype=torch.float32, device=hs[0].device)
+        tgt = torch.empty((B, FO_MLP_OUTPUTS), dtype=torch.float32, device=hs[0].device)
+        res = (FoResult * B)()
+        self._check(fo_learned_features(
+            self.ctx, B, ptr(*[h.data_ptr() for h in hs]), i64(*[h.shape[0] for h in hs]),
+            i64(*[h.stride(0) for h in hs]), dbl(*[float(x) for x in n_e]),
+            dbl(*[float(x) for x in kT]) if kT is not None else None, params, feat.data_ptr(), tgt.data_ptr(),
+            res, _stream_handle(stream)))
+        return feat, tgt, [r.as_dict() for r in res]
+
+    def mlp_init(self, seed: int = 0):
+        self._check(fo_mlp_init(self.ctx, seed))
+
+    def mlp_set_params(self, params, norm=None):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == FO_MLP_PARAMS
+        nrm = np.ascontiguousarray(norm, dtype=np.float32) if norm is not None else None
+        self._check(fo_mlp_set_params(self.ctx, p.ctypes.data, nrm.ctypes.data if nrm is not None else None))
+
+    def mlp_get_params(self):
+        import numpy as np
+        p = np.empty(FO_MLP_PARAMS, dtype=np.float32)
+        nrm = np.empty(FO_MLP_NORM, dtype=np.float32)
+        self._check(fo_mlp_get_params(self.ctx, p.ctypes.data, nrm.ctypes.data))
+        return p, nrm
+
+    def mlp_forward(self, x, stream=None):
+        import torch
+        y = torch.empty((x.shape[0], FO_MLP_OUTPUTS), dtype=torch.float32, device=x.device)
+        self._check(fo_mlp_forward(self.ctx, x.data_ptr(), x.shape[0], y.data_ptr(), _stream_handle(stream)))
+        return y
+
+    def mlp_gradients(self, x, t, stream=None):
+        import torch
+        g = torch.empty(FO_MLP_PARAMS, dtype=torch.float32, device=x.device)
+        loss = ctypes.c_float()
+        self._check(fo_mlp_gradients(self.ctx, x.data_ptr(), t.data_ptr(), x.shape[0], g.data_ptr(),
+                                     ctypes.byref(loss), _stream_handle(stream)))
+        return g, loss.value
+
+    def mlp_train(self, feat, target, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0,
+                  stream=None):
+        losses = (ctypes.c_float * epochs)()
+        self._check(fo_mlp_train(self.ctx, feat.data_ptr(), target.data_ptr(), feat.shape[0], epochs, batch,
+                                 lr, seed, losses, _stream_handle(stream)))
+        return list(losses)
+
+    def mlp_save(self, path: str):
+        self._check(fo_mlp_save(self.ctx, path))
+
+    def mlp_load(self, path: str):
+        self._check(fo_mlp_load(self.ctx, path))
 
     def density_matrix_host(self, h, n_e: float, params: FoParams, out, stream=None):
         """h, out: CPU float64 tensors (pinned for asynchronous copies)."""

@@ -33,11 +33,13 @@ enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUND
 struct PlanKey {
     std::vector<int64_t> n;
     int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
-    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0;
+    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0, max_newton = 0;
+    double tr_tol = 0.0;
     bool operator==(const PlanKey& o) const {
         return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
                mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
-               tile_req == o.tile_req && ctas_req == o.ctas_req && sym == o.sym && max_bisect == o.max_bisect;
+               tile_req == o.tile_req && ctas_req == o.ctas_req && sym == o.sym && max_bisect == o.max_bisect &&
+               max_newton == o.max_newton && tr_tol == o.tr_tol;
     }
 };
 
@@ -80,6 +82,8 @@ struct Plan {
     double* ct = nullptr;
     double* part_g = nullptr;
     double* part_t = nullptr;
+    float* lscratch = nullptr;    // learned mu: features, normalised features, activations, outputs
+    int* lcount = nullptr;        // learned mu: instances still active after a judge
     size_t total = 0;
     double flops_product = 0.0;   // algorithmic flops of one product over the batch
     cudaGraphExec_t graph = nullptr;
@@ -123,6 +127,13 @@ struct fo_ctx {
     size_t hres_count = 0;
     cudaStream_t cap = nullptr;   // stream for graph capture
     bool capturing = false;
+    int* hcount = nullptr;        // pinned readback of the learned judge's active count
+    // learned-mu model (device, float32): parameters, gradients, Adam moments, normalisation
+    float* mlp = nullptr;         // params | grad | m | v | norm
+    bool mlp_ready = false;       // trained, loaded or set
+    int mlp_step = 0;             // Adam steps taken
+    float* mlp_scratch = nullptr; // training buffers
+    size_t mlp_scratch_floats = 0;
 };
 
 namespace {
@@ -283,9 +294,11 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     sh.pscale_t = 256.0f;
     sh.pscale_r = 1.0f;
     const bool bisect = key.mode == MODE_DENSITY && key.mu_mode == FO_MU_BISECT;
-    p->giants = bisect && sh.m > 2;
-    p->moments = bisect || key.mode == MODE_MOMENTS;
+    const bool learned = key.mode == MODE_DENSITY && key.mu_mode == FO_MU_LEARNED;
+    p->giants = (bisect || learned) && sh.m > 2;   // the learned mode falls back to exact moments
+    p->moments = bisect || learned || key.mode == MODE_MOMENTS;
     if (p->moments && sh.k > 33) return fail(ctx, FO_ERR_UNSUPPORTED, "exact moments support k <= 33");
+    if (learned && sh.k > 32) return fail(ctx, FO_ERR_UNSUPPORTED, "learned mu supports k <= 32");
     switch (key.mode) {
         case MODE_DENSITY:
         case MODE_MOMENTS:
@@ -320,6 +333,7 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
         std::memset(&in, 0, sizeof(in));
         in.n = key.n[b];
         in.np = np;
+        in.user = b;
         const size_t np2 = (size_t)np * (size_t)np;
         in.slot_bytes = (int64_t)(sh.is64 ? align256(np2 * 8) : align256(np2 * 4 + (size_t)sh.planes * np2 * 2));
         if (p->buckets.empty() || p->buckets.back().np != np) {
@@ -366,6 +380,8 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     fill(p->wf64, [](const Inst& in) { return f64_tiles(in.np); });
     const size_t off_pg = take(8 * 3 * (size_t)std::max(1, p->wg.pre[batch]));
     const size_t off_pt = take(8 * 2 * (size_t)std::max(1, p->wr.pre[batch]));
+    const size_t off_ls = take(4 * (size_t)batch * (2 * kMlpIn + 4 * kMlpHidden + kMlpOut));
+    const size_t off_lc = take(sizeof(int));
     p->total = off;
     // remember the offsets in the (not yet placed) pointers
     for (int j = 0; j < batch; ++j) p->inst[j].c = reinterpret_cast<double*>(small[j]);
@@ -373,6 +389,8 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     p->ct = reinterpret_cast<double*>(off_ct);
     p->part_g = reinterpret_cast<double*>(off_pg);
     p->part_t = reinterpret_cast<double*>(off_pt);
+    p->lscratch = reinterpret_cast<float*>(off_ls);
+    p->lcount = reinterpret_cast<int*>(off_lc);
     // launch groups: at most kMaxBuckets tensor maps per launch
     for (int b0 = 0; b0 < (int)p->buckets.size(); b0 += kMaxBuckets) {
         const int nb = std::min<int>(kMaxBuckets, (int)p->buckets.size() - b0);
@@ -400,6 +418,8 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
     p->ct = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->ct));
     p->part_g = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->part_g));
     p->part_t = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->part_t));
+    p->lscratch = reinterpret_cast<float*>(W + reinterpret_cast<size_t>(p->lscratch));
+    p->lcount = reinterpret_cast<int*>(W + reinterpret_cast<size_t>(p->lcount));
     for (int j = 0; j < batch; ++j) {
         Inst& in = p->inst[j];
         const Bucket& bk = p->buckets[in.bucket];
@@ -585,39 +605,40 @@ fo_status clenshaw(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     return FO_OK;
 }
 
-// The whole method for every instance of a density plan (after the per-call inputs).
-fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
-    const Shape& sh = p.sh;
-    const PlanKey& key = p.key;
-    int lstage = 0;
-    int h = prof_begin(ctx, s, FO_STAGE_BOUNDS);
-    FO_CUDA(launch_bounds(p.d_inst, p.d_io, p.batch, p.wg.dev, p.part_g, key.use_given, s), "bounds");
-    FO_CUDA(launch_scale(p.d_inst, p.d_io, p.wsc.dev, sh, s, ctx->flag + 1), "scale");
-    lstage = (key.use_given ? 1 : 2) + 1;
-    prof_end(ctx, s, h, 0.0, lstage);
-    run->launches += lstage;
+// Spectral bounds, X and the baby steps T_2..T_k of every instance.
+fo_status front(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    const int h = prof_begin(ctx, s, FO_STAGE_BOUNDS);
+    FO_CUDA(launch_bounds(p.d_inst, p.d_io, p.batch, p.wg.dev, p.part_g, p.key.use_given, s), "bounds");
+    FO_CUDA(launch_scale(p.d_inst, p.d_io, p.wsc.dev, p.sh, s, ctx->flag + 1), "scale");
+    const int l = (p.key.use_given ? 1 : 2) + 1;
+    prof_end(ctx, s, h, 0.0, l);
+    run->launches += l;
+    return baby_steps(ctx, p, p.sh.k, s, run);
+}
 
-    FO_TRY(baby_steps(ctx, p, sh.k, s, run));
-    const bool bisect = key.mu_mode == FO_MU_BISECT;
-    const int max_it = key.max_bisect > 0 ? key.max_bisect : 200;
-    if (bisect) {
-        if (p.giants) FO_TRY(giant_steps(ctx, p, s, run));
-        h = prof_begin(ctx, s, FO_STAGE_MOMENTS);
-        const int l0 = run->launches;
-        FO_TRY(exact_moments(ctx, p, s, run));
-        prof_end(ctx, s, h, 0.0, run->launches - l0);
-        h = prof_begin(ctx, s, FO_STAGE_MU);
-        FO_CUDA(launch_dos_weights(p.d_inst, p.batch, sh, p.ct, s), "dos_weights");
-        FO_CUDA(launch_bisect(p.d_inst, p.d_io, p.batch, sh, p.ct, max_it, 0, s), "bisect");
-        prof_end(ctx, s, h, 0.0, 2);
-        run->launches += 2;
-    } else {
-        FO_CUDA(launch_set_mu(p.d_inst, p.d_io, p.batch, s), "mu");
-        run->launches += 1;
-    }
-    h = prof_begin(ctx, s, FO_STAGE_COEFFS);
-    lstage = 0;
-    FO_CUDA(launch_coefficients(p.d_inst, p.d_io, p.batch, sh, p.ct, p.moments ? 1 : 0, s, &lstage), "coeffs");
+// mu of every active instance from exact moments: giant steps, moments, DOS weights and the
+// bracketed search (starting from the learned proposal when start_mu0 is set).
+fo_status exact_mu(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int start_mu0) {
+    if (p.giants) FO_TRY(giant_steps(ctx, p, s, run));
+    int h = prof_begin(ctx, s, FO_STAGE_MOMENTS);
+    const int l0 = run->launches;
+    FO_TRY(exact_moments(ctx, p, s, run));
+    prof_end(ctx, s, h, 0.0, run->launches - l0);
+    h = prof_begin(ctx, s, FO_STAGE_MU);
+    const int max_it = p.key.max_bisect > 0 ? p.key.max_bisect : 200;
+    FO_CUDA(launch_dos_weights(p.d_inst, p.batch, p.sh, p.ct, s), "dos_weights");
+    FO_CUDA(launch_bisect(p.d_inst, p.d_io, p.batch, p.sh, p.ct, max_it, start_mu0, s), "bisect");
+    prof_end(ctx, s, h, 0.0, 2);
+    run->launches += 2;
+    return FO_OK;
+}
+
+// P of every active instance at its current mu: coefficients, R_l, Clenshaw, tr P, ||P||^2.
+fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trace) {
+    const Shape& sh = p.sh;
+    int h = prof_begin(ctx, s, FO_STAGE_COEFFS);
+    int lstage = 0;
+    FO_CUDA(launch_coefficients(p.d_inst, p.d_io, p.batch, sh, p.ct, poly_trace, s, &lstage), "coeffs");
     prof_end(ctx, s, h, 0.0, lstage);
     run->launches += lstage;
     h = prof_begin(ctx, s, FO_STAGE_CONTRACT);
@@ -635,6 +656,74 @@ fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     prof_end(ctx, s, h, 0.0, 2);
     run->launches += 2;
     return FO_OK;
+}
+
+// Learned mu: moments up to 2k from the baby steps, the network's proposal, evaluation of P
+// and the trace judge; corrected re-evaluations; exact moments and bisection for whatever
+// is still rejected. Eager calls stop as soon as every instance is accepted; a captured
+// graph runs every round (rejected-free instances skip the work of each kernel).
+fo_status learned(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    const Shape& sh = p.sh;
+    const int B = p.batch;
+    const MlpOffsets mo = mlp_offsets();
+    const float* params = ctx->mlp;
+    const float* norm = ctx->mlp + 4 * (size_t)mo.total;
+    float* feat = p.lscratch;
+    float* xn = feat + (size_t)B * kMlpIn;
+    float* z1 = xn + (size_t)B * kMlpIn;
+    float* a1 = z1 + (size_t)B * kMlpHidden;
+    float* z2 = a1 + (size_t)B * kMlpHidden;
+    float* a2 = z2 + (size_t)B * kMlpHidden;
+    float* y = a2 + (size_t)B * kMlpHidden;
+    int h = prof_begin(ctx, s, FO_STAGE_MOMENTS);
+    int l0 = run->launches;
+    FO_CUDA(launch_diag_sums(p.d_inst, B, sh.k, sh, s), "diag_sums");
+    FO_CUDA(launch_gram(p.d_inst, B, p.wgr.dev, sh.k - 1, 1, 0, sh.k, 0, sh.is64, s, &run->launches), "gram");
+    FO_CUDA(launch_assemble_low(p.d_inst, B, sh.k, s), "low moments");
+    run->launches += 2;
+    prof_end(ctx, s, h, 0.0, run->launches - l0);
+    h = prof_begin(ctx, s, FO_STAGE_MU);
+    FO_CUDA(launch_features(p.d_inst, p.d_io, B, sh.k, 0, feat, s), "features");
+    FO_CUDA(mlp_gather_norm(feat, nullptr, B, kMlpIn, norm, norm + kMlpIn, xn, s), "normalise");
+    FO_CUDA(mlp_forward(params, xn, B, z1, a1, z2, a2, y, s), "network");
+    FO_CUDA(launch_learned_mu(p.d_inst, B, y, norm, sh.n_terms, s), "proposal");
+    prof_end(ctx, s, h, 0.0, 6);
+    run->launches += 6;
+    const int R = p.key.max_newton == 0 ? 2 : (p.key.max_newton < 0 ? 0 : p.key.max_newton);
+    bool any = true;
+    for (int r = 0; r <= R; ++r) {
+        FO_TRY(evaluate(ctx, p, s, run, 0));
+        FO_CUDA(cudaMemsetAsync(p.lcount, 0, sizeof(int), s), "judge");
+        FO_CUDA(launch_learned_check(p.d_inst, p.d_io, B, r, R, p.key.tr_tol, sh.is64, p.lcount, s), "judge");
+        run->launches += 1;
+        if (!ctx->capturing) {
+            FO_CUDA(cudaMemcpyAsync(ctx->hcount, p.lcount, sizeof(int), cudaMemcpyDeviceToHost, s), "judge");
+            FO_CUDA(cudaStreamSynchronize(s), "judge");
+            any = *ctx->hcount > 0;
+            if (!any) break;
+        }
+    }
+    if (any) {
+        FO_TRY(exact_mu(ctx, p, s, run, 1));
+        FO_TRY(evaluate(ctx, p, s, run, 1));
+    }
+    return FO_OK;
+}
+
+// The whole method for every instance of a density plan (after the per-call inputs).
+fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    FO_TRY(front(ctx, p, s, run));
+    switch (p.key.mu_mode) {
+        case FO_MU_BISECT:
+            FO_TRY(exact_mu(ctx, p, s, run, 0));
+            return evaluate(ctx, p, s, run, 1);
+        case FO_MU_LEARNED:
+            return learned(ctx, p, s, run);
+        default:
+            FO_CUDA(launch_set_mu(p.d_inst, p.d_io, p.batch, s), "mu");
+            run->launches += 1;
+            return evaluate(ctx, p, s, run, 0);
+    }
 }
 
 // Tile configuration of the tensor-core products: the requested one, or the fastest of
@@ -739,7 +828,9 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
         return fail(ctx, FO_ERR_ARG, "emax must exceed emin");
     if (prm->mu_mode < FO_MU_FIXED || prm->mu_mode > FO_MU_LEARNED)
         return fail(ctx, FO_ERR_ARG, "unknown mu_mode");
-    if (prm->mu_mode == FO_MU_LEARNED) return fail(ctx, FO_ERR_UNSUPPORTED, "learned mu needs a trained model");
+    if (prm->mu_mode == FO_MU_LEARNED && !ctx->mlp_ready)
+        return fail(ctx, FO_ERR_UNSUPPORTED, "learned mu needs a trained, loaded or set model");
+    if (prm->mu_mode == FO_MU_LEARNED && !(prm->tr_tol >= 0.0)) return fail(ctx, FO_ERR_ARG, "tr_tol must be >= 0");
     if (prm->tile_n != 0 && prm->tile_n != 128 && prm->tile_n != 256)
         return fail(ctx, FO_ERR_ARG, "tile_n must be 0, 128 or 256");
     if (prm->tile_ctas < 0 || prm->tile_ctas > 2 || (prm->tile_ctas == 2 && prm->tile_n != 128) ||
@@ -767,7 +858,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
                         const int64_t* ldp, fo_result* res, cudaStream_t st) {
     FO_TRY(check_params(ctx, prm));
     if (batch < 1 || !dH || !dP || !n || !n_e) return fail(ctx, FO_ERR_ARG, "bad batch arguments");
-    const bool bisect = prm->mu_mode == FO_MU_BISECT;
+    const bool bisect = prm->mu_mode != FO_MU_FIXED;
     for (int b = 0; b < batch; ++b) {
         if (!dH[b] || !dP[b]) return fail(ctx, FO_ERR_ARG, "H and P must be non-NULL");
         if (n[b] < 1) return fail(ctx, FO_ERR_ARG, "n must be >= 1");
@@ -789,6 +880,10 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
     key.tile_req = prm->tile_n;
     key.ctas_req = prm->tile_ctas;
     key.max_bisect = prm->max_bisect;
+    if (prm->mu_mode == FO_MU_LEARNED) {
+        key.max_newton = prm->max_newton;
+        key.tr_tol = prm->tr_tol;
+    }
     Plan* p = nullptr;
     FO_TRY(get_plan(ctx, key, &p));
 
@@ -876,6 +971,17 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
             r.tile_ctas = p->tile_ctas;
             r.evals = 1;
             r.order = 0;
+            if (prm->mu_mode == FO_MU_LEARNED) {
+                // products of this instance: baby steps, one Clenshaw pass per evaluation,
+                // and the giant steps of the exact fallback
+                const int ev = hr.evals + (hr.learned_ok ? 0 : 1);
+                const int km1 = p->sh.m > 1 ? p->sh.m - 1 : 0;
+                r.evals = ev;
+                r.n_gemm = (p->sh.k - 1) + ev * km1 + (hr.learned_ok ? 0 : (p->giants ? p->sh.m - 2 : 0));
+                r.order = (int)std::lround(hr.order);
+                if (!hr.learned_ok) r.bisect_iters = hr.iters;
+                else r.bisect_iters = 0;
+            }
             int status = hr.status;
             if (flag[0]) status = FO_ERR_DEVICE_TIMEOUT;
             r.status = status;
@@ -883,6 +989,160 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
         }
         if (first != FO_OK)
             return fail(ctx, first, std::string("device stage failed: ") + fo_status_string(first));
+    }
+    return FO_OK;
+}
+
+// ---------------------------------------------------------------- learned model
+size_t mlp_floats() { return 4 * (size_t)mlp_offsets().total + kMlpNorm; }
+float* mlp_params(fo_ctx* ctx) { return ctx->mlp; }
+float* mlp_grad(fo_ctx* ctx) { return ctx->mlp + mlp_offsets().total; }
+float* mlp_m(fo_ctx* ctx) { return ctx->mlp + 2 * (size_t)mlp_offsets().total; }
+float* mlp_v(fo_ctx* ctx) { return ctx->mlp + 3 * (size_t)mlp_offsets().total; }
+float* mlp_norm(fo_ctx* ctx) { return ctx->mlp + 4 * (size_t)mlp_offsets().total; }
+
+fo_status ensure_mlp(fo_ctx* ctx) {
+    if (ctx->mlp) return FO_OK;
+    if (cudaMalloc(&ctx->mlp, sizeof(float) * mlp_floats()) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->mlp = nullptr;
+        return fail(ctx, FO_ERR_NOMEM, "model allocation failed");
+    }
+    if (cudaMemset(ctx->mlp, 0, sizeof(float) * mlp_floats()) != cudaSuccess)
+        return fail(ctx, FO_ERR_CUDA, "model clear failed");
+    return FO_OK;
+}
+
+fo_status ensure_mlp_scratch(fo_ctx* ctx, size_t floats) {
+    if (ctx->mlp_scratch_floats >= floats) return FO_OK;
+    if (ctx->mlp_scratch) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->mlp_scratch);
+    }
+    ctx->mlp_scratch = nullptr;
+    ctx->mlp_scratch_floats = 0;
+    if (cudaMalloc(&ctx->mlp_scratch, sizeof(float) * floats) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, FO_ERR_NOMEM, "model scratch allocation failed");
+    }
+    ctx->mlp_scratch_floats = floats;
+    return FO_OK;
+}
+
+// splitmix64 (Steele, Lea and Flood 2014): the counter-based generator of the weight
+// initialisation and of the mini-batch order.
+uint64_t splitmix64(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double unit_uniform(uint64_t& x) { return (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0); }
+
+// Uniform(-a, a) weights, a = sqrt(6 / (fan_in + fan_out)); zero biases; identity normalisation.
+void init_host_params(uint64_t seed, std::vector<float>& prm, std::vector<float>& norm) {
+    const MlpOffsets o = mlp_offsets();
+    prm.assign(o.total, 0.0f);
+    uint64_t st = seed;
+    auto fill = [&](int off, int fan_out, int fan_in) {
+        const double a = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int q = 0; q < fan_out * fan_in; ++q) prm[off + q] = (float)((2.0 * unit_uniform(st) - 1.0) * a);
+    };
+    fill(o.W1, kMlpHidden, kMlpIn);
+    fill(o.W2, kMlpHidden, kMlpHidden);
+    fill(o.W3, kMlpOut, kMlpHidden);
+    norm.assign(kMlpNorm, 0.0f);
+    for (int c = 0; c < kMlpIn; ++c) norm[kMlpIn + c] = 1.0f;
+    for (int c = 0; c < kMlpOut; ++c) norm[2 * kMlpIn + kMlpOut + c] = 1.0f;
+}
+
+fo_status upload_model(fo_ctx* ctx, const float* prm, const float* norm) {
+    FO_TRY(ensure_mlp(ctx));
+    const MlpOffsets o = mlp_offsets();
+    if (cudaMemcpy(mlp_params(ctx), prm, sizeof(float) * o.total, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(mlp_norm(ctx), norm, sizeof(float) * kMlpNorm, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(mlp_m(ctx), 0, sizeof(float) * o.total) != cudaSuccess ||
+        cudaMemset(mlp_v(ctx), 0, sizeof(float) * o.total) != cudaSuccess)
+        return fail(ctx, FO_ERR_CUDA, "model upload failed");
+    ctx->mlp_step = 0;
+    ctx->mlp_ready = true;
+    return FO_OK;
+}
+
+// Training pairs of a batch: the exact method (bisection on exact moments) gives mu; the
+// features come from the same moments, the targets from mu, the coefficients at mu and the
+// moments. P is not formed.
+fo_status features_batch(fo_ctx* ctx, int batch, const double* const* dH, const int64_t* n, const int64_t* ld,
+                         const double* n_e, const double* kT, const fo_params* prm, float* d_feat, float* d_tgt,
+                         fo_result* res, cudaStream_t st) {
+    fo_params q = *prm;
+    q.mu_mode = FO_MU_BISECT;
+    q.flags = 0;
+    FO_TRY(check_params(ctx, &q));
+    if (batch < 1 || !dH || !n || !n_e || !d_feat) return fail(ctx, FO_ERR_ARG, "bad batch arguments");
+    for (int b = 0; b < batch; ++b) {
+        if (!dH[b] || n[b] < 1 || (ld && ld[b] < n[b])) return fail(ctx, FO_ERR_ARG, "bad instance arguments");
+        if (!(n_e[b] >= 0.0 && n_e[b] <= (double)n[b])) return fail(ctx, FO_ERR_ARG, "n_e must be in [0, n]");
+        if (kT && (!(kT[b] > 0.0) || !std::isfinite(kT[b]))) return fail(ctx, FO_ERR_ARG, "kT must be > 0");
+    }
+    PlanKey key;
+    key.n.assign(n, n + batch);
+    key.mode = MODE_DENSITY;
+    key.n_terms = q.n_terms;
+    key.k_req = q.k;
+    key.prec = q.precision;
+    key.mu_mode = FO_MU_BISECT;
+    key.n_quad = q.n_quad;
+    key.use_given = q.use_given_bounds ? 1 : 0;
+    key.tile_req = q.tile_n;
+    key.ctas_req = q.tile_ctas;
+    key.max_bisect = q.max_bisect;
+    Plan* p = nullptr;
+    FO_TRY(get_plan(ctx, key, &p));
+    std::vector<InstIO> io(batch);
+    for (int j = 0; j < batch; ++j) {
+        const int b = p->order[j];
+        InstIO& x = io[j];
+        std::memset(&x, 0, sizeof(x));
+        x.H = dH[b];
+        x.ldh = ld ? ld[b] : n[b];
+        x.kT = kT ? kT[b] : q.kT;
+        x.n_e = n_e[b];
+        x.emin = q.emin;
+        x.emax = q.emax;
+    }
+    Run run;
+    FO_CUDA(launch_set_io(io.data(), batch, p->d_io, p->d_inst, 0, st), "set_io");
+    FO_TRY(front(ctx, *p, st, &run));
+    FO_TRY(exact_mu(ctx, *p, st, &run, 0));
+    int l = 0;
+    FO_CUDA(launch_coefficients(p->d_inst, p->d_io, batch, p->sh, p->ct, 1, st, &l), "coeffs");
+    FO_CUDA(launch_features(p->d_inst, p->d_io, batch, p->sh.k, 1, d_feat, st), "features");
+    if (d_tgt) FO_CUDA(launch_targets(p->d_inst, batch, p->sh.n_terms, d_tgt, st), "targets");
+    if (res) {
+        FO_TRY(ensure_hres(ctx, batch));
+        FO_CUDA(cudaMemcpyAsync(ctx->hres, p->d_res, sizeof(DevResult) * batch, cudaMemcpyDeviceToHost, st),
+                "readback");
+        FO_CUDA(cudaStreamSynchronize(st), "sync");
+        fo_status first = FO_OK;
+        for (int j = 0; j < batch; ++j) {
+            const DevResult& hr = ctx->hres[j];
+            fo_result& r = res[p->order[j]];
+            std::memset(&r, 0, sizeof(r));
+            r.mu = hr.mu;
+            r.trace_poly = hr.trace_poly;
+            r.emin = hr.bounds[0];
+            r.emax = hr.bounds[1];
+            r.k = p->sh.k;
+            r.m = p->sh.m;
+            r.n_gemm = (p->sh.k - 1) + (p->giants ? p->sh.m - 2 : 0);
+            r.bisect_iters = hr.iters;
+            r.status = hr.status;
+            r.tile_n = p->tile_n;
+            r.tile_ctas = p->tile_ctas;
+            if (hr.status != FO_OK && first == FO_OK) first = (fo_status)hr.status;
+        }
+        if (first != FO_OK) return fail(ctx, first, std::string("device stage failed: ") + fo_status_string(first));
     }
     return FO_OK;
 }
@@ -929,6 +1189,12 @@ fo_status fo_create(fo_ctx** out, int device) {
         return FO_ERR_NOMEM;
     }
     cudaMemset(ctx->flag, 0, 8 * sizeof(int));
+    if (cudaMallocHost(&ctx->hcount, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->flag);
+        delete ctx;
+        return FO_ERR_NOMEM;
+    }
     *out = ctx;
     return FO_OK;
 }
@@ -946,6 +1212,9 @@ fo_status fo_destroy(fo_ctx* ctx) {
         if (ctx->flag) cudaFree(ctx->flag);
         if (ctx->hres) cudaFreeHost(ctx->hres);
         if (ctx->cap) cudaStreamDestroy(ctx->cap);
+        if (ctx->hcount) cudaFreeHost(ctx->hcount);
+        if (ctx->mlp) cudaFree(ctx->mlp);
+        if (ctx->mlp_scratch) cudaFree(ctx->mlp_scratch);
     }
     delete ctx;
     return FO_OK;
@@ -1163,6 +1432,190 @@ fo_status fo_recurrence_product(fo_ctx* ctx, int32_t precision, int32_t symmetri
                               cudaMemcpyDeviceToDevice, st),
             "copy out");
     return FO_OK;
+}
+
+fo_status fo_learned_features(fo_ctx* ctx, int32_t batch, const double* const* dH, const int64_t* n,
+                              const int64_t* ld, const double* n_e, const double* kT, const fo_params* params,
+                              float* d_feat, float* d_target, fo_result* res, void* stream) {
+    if (!ctx) return FO_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    return features_batch(ctx, batch, dH, n, ld, n_e, kT, params, d_feat, d_target, res,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+fo_status fo_mlp_init(fo_ctx* ctx, uint64_t seed) {
+    if (!ctx) return FO_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    std::vector<float> prm, norm;
+    init_host_params(seed, prm, norm);
+    return upload_model(ctx, prm.data(), norm.data());
+}
+
+fo_status fo_mlp_set_params(fo_ctx* ctx, const float* h_params, const float* h_norm) {
+    if (!ctx || !h_params) return FO_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    std::vector<float> prm, norm;
+    init_host_params(0, prm, norm);
+    return upload_model(ctx, h_params, h_norm ? h_norm : norm.data());
+}
+
+fo_status fo_mlp_get_params(fo_ctx* ctx, float* h_params, float* h_norm) {
+    if (!ctx) return FO_ERR_ARG;
+    if (!ctx->mlp) return fail(ctx, FO_ERR_UNSUPPORTED, "no model");
+    DeviceGuard g(ctx->device);
+    if (h_params && cudaMemcpy(h_params, mlp_params(ctx), sizeof(float) * mlp_offsets().total,
+                               cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, FO_ERR_CUDA, "model download failed");
+    if (h_norm && cudaMemcpy(h_norm, mlp_norm(ctx), sizeof(float) * kMlpNorm, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, FO_ERR_CUDA, "model download failed");
+    return FO_OK;
+}
+
+fo_status fo_mlp_forward(fo_ctx* ctx, const float* d_x, int32_t n, float* d_y, void* stream) {
+    if (!ctx || !d_x || !d_y || n < 1) return ctx ? fail(ctx, FO_ERR_ARG, "bad arguments") : FO_ERR_ARG;
+    if (!ctx->mlp_ready) return fail(ctx, FO_ERR_UNSUPPORTED, "no model");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    FO_TRY(ensure_mlp_scratch(ctx, (size_t)n * 4 * kMlpHidden));
+    float* z1 = ctx->mlp_scratch;
+    float* a1 = z1 + (size_t)n * kMlpHidden;
+    float* z2 = a1 + (size_t)n * kMlpHidden;
+    float* a2 = z2 + (size_t)n * kMlpHidden;
+    FO_CUDA(mlp_forward(mlp_params(ctx), d_x, n, z1, a1, z2, a2, d_y, st), "network");
+    return FO_OK;
+}
+
+fo_status fo_mlp_gradients(fo_ctx* ctx, const float* d_x, const float* d_t, int32_t n, float* d_grad,
+                           float* h_loss, void* stream) {
+    if (!ctx || !d_x || !d_t || !d_grad || n < 1) return ctx ? fail(ctx, FO_ERR_ARG, "bad arguments") : FO_ERR_ARG;
+    if (!ctx->mlp_ready) return fail(ctx, FO_ERR_UNSUPPORTED, "no model");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t B = (size_t)n;
+    FO_TRY(ensure_mlp_scratch(ctx, B * (6 * kMlpHidden + 2 * kMlpOut) + 1));
+    float* z1 = ctx->mlp_scratch;
+    float* a1 = z1 + B * kMlpHidden;
+    float* z2 = a1 + B * kMlpHidden;
+    float* a2 = z2 + B * kMlpHidden;
+    float* dz2 = a2 + B * kMlpHidden;
+    float* dz1 = dz2 + B * kMlpHidden;
+    float* y = dz1 + B * kMlpHidden;
+    float* dy = y + B * kMlpOut;
+    float* loss = dy + B * kMlpOut;
+    FO_CUDA(mlp_forward(mlp_params(ctx), d_x, n, z1, a1, z2, a2, y, st), "network");
+    FO_CUDA(mlp_backward(mlp_params(ctx), d_x, d_t, n, z1, a1, z2, a2, y, dy, dz2, dz1, d_grad, loss, st),
+            "backward");
+    if (h_loss) {
+        FO_CUDA(cudaMemcpyAsync(h_loss, loss, sizeof(float), cudaMemcpyDeviceToHost, st), "loss");
+        FO_CUDA(cudaStreamSynchronize(st), "sync");
+    }
+    return FO_OK;
+}
+
+fo_status fo_mlp_train(fo_ctx* ctx, const float* d_feat, const float* d_target, int32_t n, int32_t epochs,
+                       int32_t batch, float lr, uint64_t seed, float* h_loss, void* stream) {
+    if (!ctx) return FO_ERR_ARG;
+    if (!d_feat || !d_target || n < 2 || epochs < 1 || batch < 1 || !(lr > 0.0f))
+        return fail(ctx, FO_ERR_ARG, "bad training arguments");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!ctx->mlp_ready) FO_TRY(fo_mlp_init(ctx, seed));
+    const int B = batch < n ? batch : n;
+    const int steps = (n + B - 1) / B;
+    const size_t total_steps = (size_t)steps * epochs;
+    const size_t Bz = (size_t)B;
+    const size_t need = Bz * (kMlpIn + kMlpOut + 6 * kMlpHidden + 2 * kMlpOut) + total_steps + (size_t)n;
+    FO_TRY(ensure_mlp_scratch(ctx, need));
+    float* xb = ctx->mlp_scratch;
+    float* tb = xb + Bz * kMlpIn;
+    float* z1 = tb + Bz * kMlpOut;
+    float* a1 = z1 + Bz * kMlpHidden;
+    float* z2 = a1 + Bz * kMlpHidden;
+    float* a2 = z2 + Bz * kMlpHidden;
+    float* dz2 = a2 + Bz * kMlpHidden;
+    float* dz1 = dz2 + Bz * kMlpHidden;
+    float* y = dz1 + Bz * kMlpHidden;
+    float* dy = y + Bz * kMlpOut;
+    float* losses = dy + Bz * kMlpOut;
+    int* idx = reinterpret_cast<int*>(losses + total_steps);
+    float* norm = mlp_norm(ctx);
+    // normalisation from the training set
+    FO_CUDA(mlp_col_stats(d_feat, n, kMlpIn, norm, norm + kMlpIn, st), "stats");
+    FO_CUDA(mlp_col_stats(d_target, n, kMlpOut, norm + 2 * kMlpIn, norm + 2 * kMlpIn + kMlpOut, st), "stats");
+    const int P = mlp_offsets().total;
+    std::vector<int> perm(n);
+    uint64_t rs = seed ^ 0x5DEECE66Dull;
+    size_t step_i = 0;
+    for (int e = 0; e < epochs; ++e) {
+        std::iota(perm.begin(), perm.end(), 0);
+        for (int q = n - 1; q > 0; --q) {   // Fisher-Yates
+            const int r = (int)(splitmix64(rs) % (uint64_t)(q + 1));
+            std::swap(perm[q], perm[r]);
+        }
+        FO_CUDA(cudaStreamSynchronize(st), "sync");
+        FO_CUDA(cudaMemcpy(idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "order");
+        for (int j = 0; j < steps; ++j, ++step_i) {
+            const int Bj = (j + 1) * B <= n ? B : n - j * B;
+            FO_CUDA(mlp_gather_norm(d_feat, idx + j * B, Bj, kMlpIn, norm, norm + kMlpIn, xb, st), "batch");
+            FO_CUDA(mlp_gather_norm(d_target, idx + j * B, Bj, kMlpOut, norm + 2 * kMlpIn,
+                                    norm + 2 * kMlpIn + kMlpOut, tb, st),
+                    "batch");
+            FO_CUDA(mlp_forward(mlp_params(ctx), xb, Bj, z1, a1, z2, a2, y, st), "network");
+            FO_CUDA(mlp_backward(mlp_params(ctx), xb, tb, Bj, z1, a1, z2, a2, y, dy, dz2, dz1, mlp_grad(ctx),
+                                 losses + step_i, st),
+                    "backward");
+            ctx->mlp_step += 1;
+            FO_CUDA(mlp_adam(mlp_params(ctx), mlp_grad(ctx), mlp_m(ctx), mlp_v(ctx), P, lr, ctx->mlp_step, st),
+                    "adam");
+        }
+    }
+    std::vector<float> hl(total_steps);
+    FO_CUDA(cudaStreamSynchronize(st), "sync");
+    FO_CUDA(cudaMemcpy(hl.data(), losses, sizeof(float) * total_steps, cudaMemcpyDeviceToHost), "losses");
+    if (h_loss)
+        for (int e = 0; e < epochs; ++e) {
+            double a = 0.0;
+            for (int j = 0; j < steps; ++j) a += hl[(size_t)e * steps + j];
+            h_loss[e] = (float)(a / steps);
+        }
+    ctx->mlp_ready = true;
+    return FO_OK;
+}
+
+fo_status fo_mlp_save(fo_ctx* ctx, const char* path) {
+    if (!ctx || !path) return FO_ERR_ARG;
+    if (!ctx->mlp_ready) return fail(ctx, FO_ERR_UNSUPPORTED, "no model");
+    const int P = mlp_offsets().total;
+    std::vector<float> prm(P), norm(kMlpNorm);
+    FO_TRY(fo_mlp_get_params(ctx, prm.data(), norm.data()));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, FO_ERR_ARG, std::string("cannot write ") + path);
+    const char magic[8] = {'F', 'O', 'M', 'L', 'P', '1', 0, 0};
+    const int32_t dims[5] = {kMlpIn, kMlpHidden, kMlpOut, P, kMlpNorm};
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(dims, sizeof(int32_t), 5, f) == 5 &&
+              std::fwrite(norm.data(), sizeof(float), kMlpNorm, f) == (size_t)kMlpNorm &&
+              std::fwrite(prm.data(), sizeof(float), P, f) == (size_t)P;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? FO_OK : fail(ctx, FO_ERR_ARG, std::string("write failed: ") + path);
+}
+
+fo_status fo_mlp_load(fo_ctx* ctx, const char* path) {
+    if (!ctx || !path) return FO_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, FO_ERR_ARG, std::string("cannot read ") + path);
+    char magic[8];
+    int32_t dims[5];
+    const int P = mlp_offsets().total;
+    std::vector<float> prm(P), norm(kMlpNorm);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "FOMLP1", 6) == 0 &&
+              std::fread(dims, sizeof(int32_t), 5, f) == 5 && dims[0] == kMlpIn && dims[1] == kMlpHidden &&
+              dims[2] == kMlpOut && dims[3] == P && dims[4] == kMlpNorm &&
+              std::fread(norm.data(), sizeof(float), kMlpNorm, f) == (size_t)kMlpNorm &&
+              std::fread(prm.data(), sizeof(float), P, f) == (size_t)P;
+    std::fclose(f);
+    if (!ok) return fail(ctx, FO_ERR_ARG, std::string("not a model file of this layout: ") + path);
+    return upload_model(ctx, prm.data(), norm.data());
 }
 
 }  // extern "C"

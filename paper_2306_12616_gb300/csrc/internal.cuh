@@ -62,7 +62,7 @@ struct Inst {
     int32_t bucket;       // tensor-map bucket (instances of equal np)
     int32_t in_bucket;    // index within the bucket
     int32_t gram_blocks;  // blocks of the Frobenius-product kernel for this instance
-    int32_t pad_;
+    int32_t user;         // index of the instance in the caller's arrays
 };
 
 // Per-call inputs of an instance (written at the start of every call).
@@ -170,6 +170,51 @@ cudaError_t launch_copy_out(const Inst* in, const InstIO* io, Work we, const Sha
 cudaError_t launch_pack_f32(const float* A, int64_t n, int64_t lda, char* slot, int64_t np, int planes,
                             int fp16, float pscale, cudaStream_t s);
 int gram_blocks_for(int64_t np, int batch);
+
+// ------------------------------------------------------------------- mlp.cu
+// Learned chemical potential: 68 inputs (64 moments, N_e/N, kT_x, e_a/100, e_b/100),
+// two hidden layers of 256 SiLU units, 2 outputs (mu_x, order), float32 parameters stored
+// W1 (256 x 68), b1, W2 (256 x 256), b2, W3 (2 x 256), b3; normalisation vector
+// [feature mean (68), feature std (68), target mean (2), target std (2)].
+constexpr int kMlpMoments = 64;
+constexpr int kMlpIn = kMlpMoments + 4;
+constexpr int kMlpHidden = 256;
+constexpr int kMlpOut = 2;
+constexpr int kMlpNorm = 2 * kMlpIn + 2 * kMlpOut;
+constexpr float kMlpLossW0 = 1.0f;   // weight of the mu_x error
+constexpr float kMlpLossW1 = 0.1f;   // weight of the order error
+struct MlpOffsets {
+    int W1, b1, W2, b2, W3, b3, total;
+};
+inline MlpOffsets mlp_offsets() {
+    MlpOffsets o;
+    o.W1 = 0;
+    o.b1 = o.W1 + kMlpHidden * kMlpIn;
+    o.W2 = o.b1 + kMlpHidden;
+    o.b2 = o.W2 + kMlpHidden * kMlpHidden;
+    o.W3 = o.b2 + kMlpHidden;
+    o.b3 = o.W3 + kMlpOut * kMlpHidden;
+    o.total = o.b3 + kMlpOut;
+    return o;
+}
+cudaError_t mlp_forward(const float* params, const float* x, int B, float* z1, float* a1, float* z2, float* a2,
+                        float* y, cudaStream_t s);
+// Loss of (y, t) into *loss, dL/dy into dy and every parameter gradient into grad.
+cudaError_t mlp_backward(const float* params, const float* x, const float* t, int B, const float* z1,
+                         const float* a1, const float* z2, const float* a2, const float* y, float* dy, float* dz2,
+                         float* dz1, float* grad, float* loss, cudaStream_t s);
+cudaError_t mlp_adam(float* p, const float* g, float* m, float* v, int n, float lr, int step, cudaStream_t s);
+cudaError_t mlp_gather_norm(const float* src, const int* idx, int B, int C, const float* mean, const float* stdv,
+                            float* dst, cudaStream_t s);
+cudaError_t mlp_col_stats(const float* X, int n, int C, float* mean, float* stdv, cudaStream_t s);
+cudaError_t launch_features(const Inst* in, const InstIO* io, int batch, int k, int rows_by_user, float* feat,
+                            cudaStream_t s);
+cudaError_t launch_targets(const Inst* in, int batch, int n_terms, float* tgt, cudaStream_t s);
+cudaError_t launch_assemble_low(const Inst* in, int batch, int k, cudaStream_t s);
+cudaError_t launch_learned_mu(const Inst* in, int batch, const float* y, const float* norm, int n_terms,
+                              cudaStream_t s);
+cudaError_t launch_learned_check(const Inst* in, const InstIO* io, int batch, int round, int max_rounds,
+                                 double tol, int is64, int* active_count, cudaStream_t s);
 
 // ------------------------------------------------------------------ coef.cu
 cudaError_t launch_cos_table(int M, double* ct, cudaStream_t s);
