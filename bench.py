@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--n-terms", type=int, default=N_TERMS, help="Chebyshev terms (profiling cases)")
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batch measurement")
+    ap.add_argument("--batch-count", type=int, default=512, help="instances of the batch measurement")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="measure only the batch (profiling runs); the JSON line then describes the batch")
     return ap.parse_args()
 
 
@@ -175,7 +178,7 @@ def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300)
     _, res = solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps)   # plan, autotune, capture
     ok = all(r["status"] == 0 for r in res)
     worst_tr = max(abs(r["trace"] - n / 2) / n for r, n in zip(res, ns))
-    for _ in range(2):
+    for _ in range(3):
         solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps, sync=False)
     times = []
     for _ in range(steps):
@@ -252,6 +255,19 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.batch_only:
+        solver = Solver(local)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        b = bench_batch(solver, torch.cuda.current_stream(), flush, max(1, args.steps), args.precision,
+                        count=args.batch_count)
+        if rank == 0:
+            print(json.dumps({"metric": "density matrices/s (batch)", "value": b["dm_per_s"],
+                              "unit": "density matrices/s", "n_gpus": world, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": b["ms_per_batch"], "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                              "config": {"workload": b["workload"]}, "batch": b}), flush=True)
+        solver.close()
+        return
     ns = [int(x) for x in args.ns.split(",")]
     solver = Solver(local)
     stream = torch.cuda.current_stream()
@@ -356,7 +372,7 @@ def main():
             "traffic": (trec["bytes_per_launch"] if trec else None),
             "traffic_note": (trec["note"] if trec else "no ncu capture of the current kernel source")}
     batch = None if args.no_batch else bench_batch(solver, stream, flush, max(3, args.steps // 2),
-                                                    args.precision)
+                                                    args.precision, count=args.batch_count)
     cb = cpu_baseline(ns) if (rank == 0 and world == 1) else None
     per_n = {}
     for n in ns:
