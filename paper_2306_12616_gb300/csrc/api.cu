@@ -642,7 +642,7 @@ fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trac
     prof_end(ctx, s, h, 0.0, lstage);
     run->launches += lstage;
     h = prof_begin(ctx, s, FO_STAGE_CONTRACT);
-    lstage = 1;
+    lstage = (!sh.is64 && sh.m > 24) ? (sh.m + 31) / 32 : 1;
     FO_CUDA(launch_contract(p.d_inst, p.we.dev, sh, s, ctx->flag + 1), "contract");
     if (sh.m == 1) {
         FO_CUDA(launch_copy_out(p.d_inst, p.d_io, p.we.dev, sh, s), "copy_out");

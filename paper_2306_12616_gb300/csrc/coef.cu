@@ -281,15 +281,48 @@ __device__ __forceinline__ uint16_t bf16_bits_c(float v) {
     return *reinterpret_cast<uint16_t*>(&h);
 }
 
+struct Split3 {
+    uint16_t p[3];
+};
+__device__ __forceinline__ Split3 split_value(float v, int fp16, float pscale) {
+    Split3 o;
+    if (!fp16) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v);
+        const float r1 = v - __bfloat162float(h0);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+        o.p[0] = *reinterpret_cast<const uint16_t*>(&h0);
+        o.p[1] = *reinterpret_cast<const uint16_t*>(&h1);
+        o.p[2] = bf16_bits_c(r1 - __bfloat162float(h1));
+    } else {
+        const float x = v * pscale;
+        const __half h0 = __float2half_rn(x);
+        const __half h1 = __float2half_rn(x - __half2float(h0));
+        o.p[0] = *reinterpret_cast<const uint16_t*>(&h0);
+        o.p[1] = *reinterpret_cast<const uint16_t*>(&h1);
+        o.p[2] = 0;
+    }
+    return o;
+}
+
+// R_l for l0 <= l < min(l0 + MAXM, m) (MAXM a multiple of 4; m > 32 takes two launches).
+// The coefficients are staged transposed, gsh[t * MAXM + j] = g_{t,l0+j} (zero beyond m),
+// so that one 16-byte shared load serves four R_l (8 FMAs on two entries). Each thread takes
+// two consecutive entries and loads them from eight T_t at a time before using them, which
+// keeps enough bytes in flight for the HBM bandwidth at 2-3 blocks per SM.
+constexpr int kCtDepth = 8;
+
 template <int MAXM>
 __global__ void __launch_bounds__(256) k_contract_f32(const Inst* __restrict__ insts, Work we, int k,
-                                                      int m, int n_tslots, int planes_last, int fp16,
+                                                      int m, int l0, int n_tslots, int planes_last, int fp16,
                                                       float pscale, int* dbg) {
-    extern __shared__ float fsh[];
+    extern __shared__ __align__(16) float fsh[];
     const int i = find_inst(we.pre, 0, we.count, blockIdx.x);
     const Inst& in = insts[i];
     if (!in.res->active) return;
-    for (int q = threadIdx.x; q < k * m; q += blockDim.x) fsh[q] = (float)in.g[q];
+    for (int q = threadIdx.x; q < k * MAXM; q += blockDim.x) {
+        const int t = q / MAXM, l = l0 + q - t * MAXM;
+        fsh[q] = l < m ? (float)in.g[l * k + t] : 0.0f;
+    }
     __syncthreads();
     const int64_t np = in.np, n = in.n;
     const int rows = ew_rows(np);
@@ -300,63 +333,53 @@ __global__ void __launch_bounds__(256) k_contract_f32(const Inst* __restrict__ i
     const float* tbase = reinterpret_cast<const float*>(in.slots);
     float* rbase = reinterpret_cast<float*>(in.slots + n_tslots * in.slot_bytes);
     for (int64_t idx = r0 * np + 2 * threadIdx.x; idx < r1 * np; idx += 2 * blockDim.x) {
-        const int64_t r = idx / np, col0 = idx - r * np;
         float2 acc[MAXM];
 #pragma unroll
-        for (int l = 0; l < MAXM; ++l) acc[l] = make_float2(0.f, 0.f);
-#pragma unroll 4
-        for (int t = 1; t < k; ++t) {
-            const float2 v = *reinterpret_cast<const float2*>(tbase + (int64_t)(t - 1) * tstride + idx);
+        for (int j = 0; j < MAXM; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int t0 = 1; t0 < k; t0 += kCtDepth) {
+            float2 v[kCtDepth];
 #pragma unroll
-            for (int l = 0; l < MAXM; ++l) {
-                if (l < m) {
-                    const float gv = fsh[l * k + t];
-                    acc[l].x = fmaf(gv, v.x, acc[l].x);
-                    acc[l].y = fmaf(gv, v.y, acc[l].y);
+            for (int u = 0; u < kCtDepth; ++u)
+                v[u] = t0 + u < k ? __ldg(reinterpret_cast<const float2*>(tbase + (int64_t)(t0 + u - 1) * tstride + idx))
+                                  : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kCtDepth; ++u) {
+                if (t0 + u >= k) break;
+                const float* gt = fsh + (t0 + u) * MAXM;
+#pragma unroll
+                for (int j4 = 0; j4 < MAXM; j4 += 4) {
+                    const float4 g4 = *reinterpret_cast<const float4*>(gt + j4);
+                    acc[j4].x = fmaf(g4.x, v[u].x, acc[j4].x);
+                    acc[j4].y = fmaf(g4.x, v[u].y, acc[j4].y);
+                    acc[j4 + 1].x = fmaf(g4.y, v[u].x, acc[j4 + 1].x);
+                    acc[j4 + 1].y = fmaf(g4.y, v[u].y, acc[j4 + 1].y);
+                    acc[j4 + 2].x = fmaf(g4.z, v[u].x, acc[j4 + 2].x);
+                    acc[j4 + 2].y = fmaf(g4.z, v[u].y, acc[j4 + 2].y);
+                    acc[j4 + 3].x = fmaf(g4.w, v[u].x, acc[j4 + 3].x);
+                    acc[j4 + 3].y = fmaf(g4.w, v[u].y, acc[j4 + 3].y);
                 }
             }
         }
-        const bool d0 = (r < n) && (col0 == r), d1 = (r < n) && (col0 + 1 == r);
+        const int64_t r = idx / np, c0 = idx - r * np;
+        const bool d0 = (r < n) && (c0 == r), d1 = (r < n) && (c0 + 1 == r);
 #pragma unroll
-        for (int l = 0; l < MAXM; ++l) {
+        for (int j = 0; j < MAXM; ++j) {
+            const int l = l0 + j;
             if (l >= m) break;
-            float v0 = acc[l].x, v1 = acc[l].y;
-            if (d0) v0 += fsh[l * k];
-            if (d1) v1 += fsh[l * k];
+            float2 v = acc[j];
+            if (d0) v.x += fsh[j];   // g_{0,l}: the t = 0 row
+            if (d1) v.y += fsh[j];
             float* dst = rbase + (int64_t)l * tstride + idx;
             if (!FO_CHK(dbg, (reinterpret_cast<uintptr_t>(dst) & 7) == 0, 302, l, idx)) continue;
-            *reinterpret_cast<float2*>(dst) = make_float2(v0, v1);
+            *reinterpret_cast<float2*>(dst) = v;
             if (l == m - 1 && planes_last > 0) {
+                const Split3 a = split_value(v.x, fp16, pscale), b2 = split_value(v.y, fp16, pscale);
                 uint16_t* p = reinterpret_cast<uint16_t*>(rbase + (int64_t)l * tstride + ps) + idx;
-                uint16_t a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
-                if (!fp16) {
-                    __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
-                    float r1f = v0 - __bfloat162float(h0);
-                    __nv_bfloat16 h1 = __float2bfloat16_rn(r1f);
-                    a[0] = *reinterpret_cast<uint16_t*>(&h0);
-                    a[1] = *reinterpret_cast<uint16_t*>(&h1);
-                    a[2] = bf16_bits_c(r1f - __bfloat162float(h1));
-                    h0 = __float2bfloat16_rn(v1);
-                    r1f = v1 - __bfloat162float(h0);
-                    h1 = __float2bfloat16_rn(r1f);
-                    b[0] = *reinterpret_cast<uint16_t*>(&h0);
-                    b[1] = *reinterpret_cast<uint16_t*>(&h1);
-                    b[2] = bf16_bits_c(r1f - __bfloat162float(h1));
-                } else {
-                    const float x0 = v0 * pscale, x1 = v1 * pscale;
-                    __half h0 = __float2half_rn(x0);
-                    __half h1 = __float2half_rn(x0 - __half2float(h0));
-                    a[0] = *reinterpret_cast<uint16_t*>(&h0);
-                    a[1] = *reinterpret_cast<uint16_t*>(&h1);
-                    h0 = __float2half_rn(x1);
-                    h1 = __float2half_rn(x1 - __half2float(h0));
-                    b[0] = *reinterpret_cast<uint16_t*>(&h0);
-                    b[1] = *reinterpret_cast<uint16_t*>(&h1);
-                }
-#pragma unroll
-                for (int pl = 0; pl < 3; ++pl)
-                    if (pl < planes_last)
-                        *reinterpret_cast<uint32_t*>(p + pl * ps) = (uint32_t)a[pl] | ((uint32_t)b[pl] << 16);
+                *reinterpret_cast<uint32_t*>(p) = (uint32_t)a.p[0] | ((uint32_t)b2.p[0] << 16);
+                if (planes_last > 1)
+                    *reinterpret_cast<uint32_t*>(p + ps) = (uint32_t)a.p[1] | ((uint32_t)b2.p[1] << 16);
+                if (planes_last > 2)
+                    *reinterpret_cast<uint32_t*>(p + 2 * ps) = (uint32_t)a.p[2] | ((uint32_t)b2.p[2] << 16);
             }
         }
     }
@@ -416,14 +439,18 @@ cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream
         k_contract_f64<<<we.total, 256, smem, s>>>(in, we, sh.k, sh.m, sh.n_tslots);
         return cudaGetLastError();
     }
-    const size_t smem = (size_t)sh.k * sh.m * sizeof(float);
     const int planes_last = sh.m > 1 ? sh.planes : 0;
-    if (sh.m <= 32)
-        k_contract_f32<32><<<we.total, 256, smem, s>>>(in, we, sh.k, sh.m, sh.n_tslots, planes_last, sh.fp16,
-                                                        sh.pscale_r, dbg);
+    auto go = [&](auto kern, int maxm, int l0) {
+        const size_t smem = (size_t)sh.k * maxm * sizeof(float);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<we.total, 256, smem, s>>>(in, we, sh.k, sh.m, l0, sh.n_tslots, planes_last, sh.fp16, sh.pscale_r,
+                                        dbg);
+    };
+    if (sh.m <= 8) go(k_contract_f32<8>, 8, 0);
+    else if (sh.m <= 16) go(k_contract_f32<16>, 16, 0);
+    else if (sh.m <= 24) go(k_contract_f32<24>, 24, 0);
     else
-        k_contract_f32<64><<<we.total, 256, smem, s>>>(in, we, sh.k, sh.m, sh.n_tslots, planes_last, sh.fp16,
-                                                        sh.pscale_r, dbg);
+        for (int l0 = 0; l0 < sh.m; l0 += 32) go(k_contract_f32<32>, 32, l0);
     return cudaGetLastError();
 }
 

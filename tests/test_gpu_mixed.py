@@ -110,3 +110,17 @@ def test_profiler_counts_products(solver):
     assert prof["call"]["launches"] == res["n_launches"]
     assert prof["products"]["flops"] == pytest.approx(res["n_gemm"] * 6 * n * n * (n + 1))
     assert 0 < prof["products"]["ms"] <= prof["call"]["ms"]
+
+
+def test_more_than_32_giant_coefficients(solver):
+    """1100 terms: k = 34, m = 33 -> the contraction covers R_0..R_32 in two launches."""
+    n = 200
+    h = synth.tight_binding(n, 9)
+    ea, eb = O.gershgorin_bounds(h)
+    prm = solver.params(1100, 0.1, precision="bf16x3", mu_mode="fixed", mu=-6.0)
+    p, res = solver.density_matrix(to_dev(h), 0.0, prm)
+    assert (res["k"], res["m"]) == (34, 33)
+    c = O.chebyshev_coeffs(0.1, -6.0, res["emin"], res["emax"], 1100)
+    ref = O.poly_eig(h, c, res["emin"], res["emax"])
+    err = np.linalg.norm(p.cpu().numpy() - ref) / math.sqrt(n)
+    assert err <= 1e-6, err
