@@ -69,6 +69,14 @@ typedef enum {
 #define FO_FLAG_NO_RESULT_SYNC   0x2u  /* density-matrix calls: never block, leave fo_result untouched */
 #define FO_FLAG_GRAPH            0x4u  /* capture the call's kernels into a CUDA graph kept with its
                                           plan and replay it on later calls with the same plan */
+#define FO_FLAG_STAGED           0x8u  /* baby and giant steps in the staged form of Algorithm 1
+                                          (Sec. "Speed up with multiple GPU streams"): the
+                                          independent products of a stage in one launch, about
+                                          log2 k launches instead of k - 1. Each doubling stage
+                                          can amplify the error of its inputs by up to 4, so in
+                                          the split forms the result is ~30x less accurate than
+                                          with the default three-term recurrence (FP64 is
+                                          unaffected at its 1e-10 bar) */
 
 typedef struct {
     int32_t n_terms;          /* number of coefficients c_0..c_{n_terms-1}, >= 1 */

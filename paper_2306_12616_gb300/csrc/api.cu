@@ -33,13 +33,13 @@ enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUND
 struct PlanKey {
     std::vector<int64_t> n;
     int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
-    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0, max_newton = 0;
+    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0;
     double tr_tol = 0.0;
     bool operator==(const PlanKey& o) const {
         return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
                mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
                tile_req == o.tile_req && ctas_req == o.ctas_req && sym == o.sym && max_bisect == o.max_bisect &&
-               max_newton == o.max_newton && tr_tol == o.tr_tol;
+               max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged;
     }
 };
 
@@ -513,61 +513,101 @@ Step make_step(const Plan& p, int a, int b, int c, int d, int out, double alpha,
     return st;
 }
 
+// Independent products of the whole batch (one stage), at most kMaxSteps per launch.
+fo_status run_products(fo_ctx* ctx, Plan& p, const Step* steps, int nsteps, cudaStream_t s, const char* tag,
+                       int index, Run* run) {
+    for (int q0 = 0; q0 < nsteps; q0 += kMaxSteps) {
+        const int nq = std::min(kMaxSteps, nsteps - q0);
+        const int h = prof_begin(ctx, s, FO_STAGE_PRODUCTS);
+        int launches = 0;
+        if (p.sh.is64) {
+            FO_CUDA(launch_gemm_f64(steps + q0, nq, p.d_inst, p.d_io, p.wf64.dev, s), "gemm_f64");
+            launches = 1;
+        } else {
+            const HostWork& w = p.wtc[p.tile_n == 128 ? 1 : 0];
+            for (const Group& g : p.groups) {
+                std::string err;
+                const int tile0 = w.pre[g.i0];
+                cudaError_t e = tc_gemm(p.key.prec, p.tile_n, p.tile_ctas, steps + q0, nq, p.d_inst, p.d_io,
+                                        w.dev.pre, g.i0, g.i1, tile0, w.pre[g.i1] - tile0,
+                                        p.maps.data() + 128 * (size_t)g.b0, g.b0, g.nb, ctx->flag, s, &err,
+                                        p.key.sym);
+                if (e == cudaSuccess && debug_sync() && !ctx->capturing) e = cudaDeviceSynchronize();
+                if (e != cudaSuccess) {
+                    const std::string where = std::string("tc_gemm ") + tag + " " + std::to_string(index);
+                    if (!err.empty()) return fail(ctx, FO_ERR_CUDA, where + ": " + err);
+                    return cuda_fail(ctx, e, where.c_str());
+                }
+                ++launches;
+            }
+        }
+        prof_end(ctx, s, h, p.flops_product * nq, launches);
+        run->launches += launches;
+        run->n_gemm += nq;
+    }
+    return FO_OK;
+}
+
 fo_status run_product(fo_ctx* ctx, Plan& p, const Step& st, cudaStream_t s, const char* tag, int index,
                       Run* run) {
-    const int h = prof_begin(ctx, s, FO_STAGE_PRODUCTS);
-    int launches = 0;
-    if (p.sh.is64) {
-        FO_CUDA(launch_gemm_f64(st, p.d_inst, p.d_io, p.wf64.dev, s), "gemm_f64");
-        launches = 1;
-    } else {
-        const HostWork& w = p.wtc[p.tile_n == 128 ? 1 : 0];
-        for (const Group& g : p.groups) {
-            std::string err;
-            const int tile0 = w.pre[g.i0];
-            cudaError_t e = tc_gemm(p.key.prec, p.tile_n, p.tile_ctas, st, p.d_inst, p.d_io, w.dev.pre, g.i0, g.i1, tile0,
-                                    w.pre[g.i1] - tile0, p.maps.data() + 128 * (size_t)g.b0, g.b0, g.nb,
-                                    ctx->flag, s, &err, p.key.sym);
-            if (e == cudaSuccess && debug_sync() && !ctx->capturing) e = cudaDeviceSynchronize();
-            if (e != cudaSuccess) {
-                const std::string where = std::string("tc_gemm ") + tag + " " + std::to_string(index);
-                if (!err.empty()) return fail(ctx, FO_ERR_CUDA, where + ": " + err);
-                return cuda_fail(ctx, e, where.c_str());
-            }
-            ++launches;
-        }
-    }
-    prof_end(ctx, s, h, p.flops_product, launches);
-    run->launches += launches;
-    return FO_OK;
+    return run_products(ctx, p, &st, 1, s, tag, index, run);
 }
 
 // Slot of T_{j k} for j >= 1: T_k is baby slot k-1, giants T_{2k}.. follow.
 int giant_slot(const Plan& p, int j) { return j == 1 ? p.sh.k - 1 : p.sh.k + j - 2; }
 int r_slot(const Plan& p, int l) { return p.sh.n_tslots + l; }
 
-// Baby steps T_2..T_kmax: T_{i+1} = 2 T_1 T_i - T_{i-1} (T_0 = I as a diagonal shift).
-fo_status baby_steps(fo_ctx* ctx, Plan& p, int kmax, cudaStream_t s, Run* run) {
-    for (int i = 1; i < kmax; ++i) {
-        const Step st = i == 1 ? make_step(p, 0, 0, -1, -1, 1, 2.0, 0.0, -1.0, false, false, false, false, ctx)
-                               : make_step(p, 0, i - 1, i - 2, -1, i, 2.0, -1.0, 0.0, false, false, false, false, ctx);
-        FO_TRY(run_product(ctx, p, st, s, "baby", i + 1, run));
-        ++run->n_gemm;
+// The members U_1..U_jmax of a Chebyshev chain (U_j = T_j for the baby steps, U_j = T_{jk}
+// for the giant steps; U_0 = I is a diagonal shift), given U_1, by
+//  - the three-term recurrence U_{j+1} = 2 U_1 U_j - U_{j-1}, one product per launch
+//    (sequential), or
+//  - Algorithm 1 (staged): stage 1 computes U_2 = 2 U_1 U_1 - I; stage s >= 2, with
+//    u = 2^{s-2}, v = 2^{s-1}, computes U_{i+u} = 2 U_i U_u - U_{i-u} and
+//    U_{i+v} = 2 U_v U_i - U_{v-i} for u < i <= v, i.e. U_{v+1}..U_{2v} from U_1..U_v: the
+//    products of a stage are independent and run as one launch.
+// Either way jmax - 1 products; slot(j) gives the slot of U_j (j >= 1).
+template <class SlotOf>
+fo_status chebyshev_chain(fo_ctx* ctx, Plan& p, int jmax, SlotOf slot, bool staged, cudaStream_t s,
+                          const char* tag, Run* run) {
+    auto prod = [&](int a, int b, int c, int out) {
+        // 2 U_a U_b - U_c, U_0 = I
+        return c == 0 ? make_step(p, slot(a), slot(b), -1, -1, slot(out), 2.0, 0.0, -1.0, false, false, false,
+                                  false, ctx)
+                      : make_step(p, slot(a), slot(b), slot(c), -1, slot(out), 2.0, -1.0, 0.0, false, false,
+                                  false, false, ctx);
+    };
+    if (jmax < 2) return FO_OK;
+    if (!staged) {
+        for (int j = 1; j < jmax; ++j) {
+            const Step st = prod(1, j, j - 1, j + 1);
+            FO_TRY(run_product(ctx, p, st, s, tag, j + 1, run));
+        }
+        return FO_OK;
+    }
+    {
+        const Step st = prod(1, 1, 0, 2);
+        FO_TRY(run_product(ctx, p, st, s, tag, 2, run));
+    }
+    for (int v = 2, u = 1; v < jmax; u = v, v *= 2) {
+        std::vector<Step> stage;
+        for (int i = u + 1; i <= v; ++i)
+            if (i + u <= jmax) stage.push_back(prod(i, u, i - u, i + u));
+        for (int i = u + 1; i <= v; ++i)
+            if (i + v <= jmax) stage.push_back(prod(v, i, v - i, i + v));
+        FO_TRY(run_products(ctx, p, stage.data(), (int)stage.size(), s, tag, 2 * v, run));
     }
     return FO_OK;
 }
 
-// Giant steps T_{2k}..T_{(m-1)k}: T_{(j+1)k} = 2 T_k T_{jk} - T_{(j-1)k}.
+// Baby steps T_2..T_kmax.
+fo_status baby_steps(fo_ctx* ctx, Plan& p, int kmax, cudaStream_t s, Run* run) {
+    return chebyshev_chain(ctx, p, kmax, [](int j) { return j - 1; }, p.key.staged != 0, s, "baby", run);
+}
+
+// Giant steps T_{2k}..T_{(m-1)k}: the chain U_j = T_{jk} = T_j(T_k).
 fo_status giant_steps(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
-    for (int j = 1; j + 1 <= p.sh.m - 1; ++j) {
-        const int a = giant_slot(p, 1), b = giant_slot(p, j), out = giant_slot(p, j + 1);
-        const Step st = j == 1 ? make_step(p, a, b, -1, -1, out, 2.0, 0.0, -1.0, false, false, false, false, ctx)
-                               : make_step(p, a, b, giant_slot(p, j - 1), -1, out, 2.0, -1.0, 0.0, false, false,
-                                           false, false, ctx);
-        FO_TRY(run_product(ctx, p, st, s, "giant", j + 1, run));
-        ++run->n_gemm;
-    }
-    return FO_OK;
+    return chebyshev_chain(ctx, p, p.sh.m - 1, [&p](int j) { return giant_slot(p, j); }, p.key.staged != 0, s,
+                           "giant", run);
 }
 
 // Exact moments tau_0..tau_{n_terms-1} (needs the giant steps).
@@ -595,13 +635,11 @@ fo_status clenshaw(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
         const Step st = make_step(p, y, r_slot(p, l + 1), has_c ? r_slot(p, l + 2) : -1, r_slot(p, l), r_slot(p, l),
                                   2.0, has_c ? -1.0 : 0.0, 0.0, false, true, true, false, ctx);
         FO_TRY(run_product(ctx, p, st, s, "clenshaw", l, run));
-        ++run->n_gemm;
     }
     const bool has_c = m >= 3;
     const Step st = make_step(p, y, r_slot(p, 1), has_c ? r_slot(p, 2) : -1, r_slot(p, 0), -1, 1.0,
                               has_c ? -1.0 : 0.0, 0.0, false, true, false, true, ctx);
     FO_TRY(run_product(ctx, p, st, s, "final", 0, run));
-    ++run->n_gemm;
     return FO_OK;
 }
 
@@ -880,6 +918,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
     key.tile_req = prm->tile_n;
     key.ctas_req = prm->tile_ctas;
     key.max_bisect = prm->max_bisect;
+    key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
     if (prm->mu_mode == FO_MU_LEARNED) {
         key.max_newton = prm->max_newton;
         key.tr_tol = prm->tr_tol;
@@ -1097,6 +1136,7 @@ fo_status features_batch(fo_ctx* ctx, int batch, const double* const* dH, const 
     key.tile_req = q.tile_n;
     key.ctas_req = q.tile_ctas;
     key.max_bisect = q.max_bisect;
+    key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
     Plan* p = nullptr;
     FO_TRY(get_plan(ctx, key, &p));
     std::vector<InstIO> io(batch);

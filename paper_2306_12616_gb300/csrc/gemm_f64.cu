@@ -14,12 +14,17 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
-// Grouped over the batch: block b covers symmetric tile b - pre[i] of instance i.
-__global__ void __launch_bounds__(256) k_gemm_f64(const Step st, const Inst* __restrict__ insts,
+// Grouped over the batch and over the steps of a stage: block b covers symmetric tile
+// (b mod tiles) - pre[i] of instance i for step b / tiles.
+__global__ void __launch_bounds__(256) k_gemm_f64(const __grid_constant__ StepList steps,
+                                                  const Inst* __restrict__ insts,
                                                   const InstIO* __restrict__ io, Work wt) {
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN];
-    const int inst = find_inst(wt.pre, 0, wt.count, blockIdx.x);
+    const int sidx = blockIdx.x / wt.total;
+    const int bt = blockIdx.x - sidx * wt.total;
+    const Step& st = steps.s[sidx];
+    const int inst = find_inst(wt.pre, 0, wt.count, bt);
     const Inst& in = insts[inst];
     if (!in.res->active) return;
     const int64_t np = in.np;
@@ -34,7 +39,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const Step st, const Inst* __r
     const int64_t ldo = io[inst].ldp;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int t = (int)(np / BM);
-    int I = 0, b = blockIdx.x - wt.pre[inst];
+    int I = 0, b = bt - wt.pre[inst];
     while (b >= t - I) { b -= t - I; ++I; }
     const int J = I + b;
     const int64_t m0 = (int64_t)I * BM, n0 = (int64_t)J * BN;
@@ -100,8 +105,13 @@ int64_t f64_tiles(int64_t np) {
     return t * (t + 1) / 2;
 }
 
-cudaError_t launch_gemm_f64(const Step& st, const Inst* in, const InstIO* io, Work wt, cudaStream_t s) {
-    k_gemm_f64<<<wt.total, 256, 0, s>>>(st, in, io, wt);
+cudaError_t launch_gemm_f64(const Step* steps, int nsteps, const Inst* in, const InstIO* io, Work wt,
+                            cudaStream_t s) {
+    if (nsteps < 1 || nsteps > kMaxSteps) return cudaErrorInvalidValue;
+    StepList sl;
+    for (int q = 0; q < nsteps; ++q) sl.s[q] = steps[q];
+    sl.count = nsteps;
+    k_gemm_f64<<<(unsigned)wt.total * nsteps, 256, 0, s>>>(sl, in, io, wt);
     return cudaGetLastError();
 }
 

@@ -284,9 +284,9 @@ __device__ __forceinline__ void tile_of(int t, int tm, int tn, int tbn, int sym,
 
 template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
-    k_tc_gemm(const __grid_constant__ TcMaps maps, const Step st, const Inst* __restrict__ insts,
-              const InstIO* __restrict__ io, const int* __restrict__ pre, int i0, int i1, int tile0,
-              int b0, int sym, int* err_flag) {
+    k_tc_gemm(const __grid_constant__ TcMaps maps, const __grid_constant__ StepList steps,
+              const Inst* __restrict__ insts, const InstIO* __restrict__ io, const int* __restrict__ pre,
+              int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag) {
     using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB>;
     constexpr int S = Cfg::kStages;
     extern __shared__ unsigned char smem_raw[];
@@ -300,8 +300,10 @@ __global__ void __launch_bounds__(kThreads, MINB)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
     __shared__ int abort_flag;
 
-    // ---------------- instance and tile of this CTA (uniform across the CTA)
-    const int gtile = tile0 + (int)blockIdx.x;
+    // ---------------- step, instance and tile of this CTA (uniform across the CTA)
+    const int sidx = (int)blockIdx.x / tiles;
+    const Step& st = steps.s[sidx];
+    const int gtile = tile0 + (int)blockIdx.x - sidx * tiles;
     const int inst = find_inst(pre, i0, i1, gtile);
     const Inst& in = insts[inst];
     if (!in.res->active) return;
@@ -628,18 +630,19 @@ EncodeFn get_encode(std::string* err) {
 }
 
 template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB>
-cudaError_t launch_tc(const TcMaps& maps, const Step& st, const Inst* in, const InstIO* io, const int* pre,
+cudaError_t launch_tc(const TcMaps& maps, const StepList& st, const Inst* in, const InstIO* io, const int* pre,
                       int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag, cudaStream_t s) {
     using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB>;
     auto kern = k_tc_gemm<PA, PB, NPROD, F16, TBN, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)tiles, kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, b0, sym, err_flag);
+    kern<<<(unsigned)(tiles * st.count), kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0,
+                                                                    sym, err_flag);
     return cudaGetLastError();
 }
 
 template <int PA, int PB, int NPROD, bool F16>
-cudaError_t dispatch_tbn(int tile_n, int ctas, const TcMaps& maps, const Step& st, const Inst* in,
+cudaError_t dispatch_tbn(int tile_n, int ctas, const TcMaps& maps, const StepList& st, const Inst* in,
                          const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles, int b0, int sym,
                          int* err_flag, cudaStream_t s) {
     if (tile_n == 256)
@@ -689,11 +692,12 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
     return true;
 }
 
-cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step& st, const Inst* in, const InstIO* io,
+cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step* steps, int nsteps, const Inst* in, const InstIO* io,
                     const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0, int nb,
                     int* err_flag, cudaStream_t s, std::string* err, int sym) {
     if (tc_planes(prec) == 0 || (tile_n != 128 && tile_n != 256) || (ctas != 1 && ctas != 2) ||
-        (ctas == 2 && tile_n != 128) || nb < 1 || nb > kMaxBuckets || !err_flag) {
+        (ctas == 2 && tile_n != 128) || nb < 1 || nb > kMaxBuckets || !err_flag || nsteps < 1 ||
+        nsteps > kMaxSteps) {
         if (err) *err = "tc_gemm: unsupported precision, tile or bucket count";
         return cudaErrorInvalidValue;
     }
@@ -701,6 +705,9 @@ cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step& st, const Inst* 
     static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
     TcMaps tm;
     std::memcpy(&tm.m[0], maps, sizeof(CUtensorMap) * nb);
+    StepList st;
+    for (int q = 0; q < nsteps; ++q) st.s[q] = steps[q];
+    st.count = nsteps;
     switch (prec) {
         case FO_PREC_BF16X3:
             return dispatch_tbn<3, 3, 6, false>(tile_n, ctas, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);

@@ -96,6 +96,14 @@ struct Step {
     int* dbg;                  // self-check record (null unless built with FO_SELF_CHECK)
 };
 
+// Up to kMaxSteps independent products of the whole batch in one launch (a stage of the
+// staged recurrences): CTA b computes step b / tiles, tile b % tiles of the step.
+constexpr int kMaxSteps = 16;
+struct StepList {
+    Step s[kMaxSteps];
+    int32_t count;
+};
+
 // The block-to-instance map of a grouped launch: pre[j] = blocks of instances < j.
 struct Work {
     const int* pre;   // device, count + 1 entries
@@ -228,7 +236,8 @@ cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream
 
 // ----------------------------------------------------------- gemm_f64.cu / gemm_tc.cu
 int64_t f64_tiles(int64_t np);
-cudaError_t launch_gemm_f64(const Step& st, const Inst* in, const InstIO* io, Work wt, cudaStream_t s);
+cudaError_t launch_gemm_f64(const Step* steps, int nsteps, const Inst* in, const InstIO* io, Work wt,
+                            cudaStream_t s);
 
 constexpr int kMaxBuckets = 16;   // tensor maps per grouped launch
 int64_t tc_tiles(int64_t np, int tile_n);
@@ -241,7 +250,7 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
 // [b0, b0 + nb) with maps[0..nb)), tile_n = 256 or 128 output columns per tile.
 // ctas = CTAs per SM (2 only with tile_n = 128). sym = 0 computes every tile of the full
 // product (fo_recurrence_product only).
-cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step& st, const Inst* in, const InstIO* io,
+cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step* steps, int nsteps, const Inst* in, const InstIO* io,
                     const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
                     int nb, int* err_flag, cudaStream_t s, std::string* err, int sym = 1);
 // Tiles of the full (non-symmetric) product.
