@@ -161,6 +161,30 @@ def traffic_record(kernel: str, source: str):
     return rec
 
 
+# ------------------------------------------------- the paper's comparison, re-timed
+def eigh_baseline(hs: dict, results: dict, kT: float, reps: int = 2) -> dict:
+    """Density matrices by diagonalisation, the comparison the paper times against its
+    expansion (cuSolver / MAGMA dsyevd): torch.linalg.eigh in float64 (cuSolver syevd) and
+    P = U f(Lambda) U^T (cuBLAS), at the mu the solver found. Library calls; context only."""
+    import torch
+    out = {}
+    for n, h in hs.items():
+        mu = results[n]["mu"]
+        times = []
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lam, u = torch.linalg.eigh(h)
+            occ = 0.5 - 0.5 * torch.tanh((lam - mu) / (2.0 * kT))
+            p = (u * occ) @ u.T
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            del lam, u, p
+        out[str(n)] = {"ms": statistics.median(times[1:])}
+    return out
+
+
 # ------------------------------------------------------------- 512-instance batch
 def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300):
     """Density matrices per second of the batch of `count` tight-binding instances with N
@@ -373,6 +397,7 @@ def main():
             "traffic_note": (trec["note"] if trec else "no ncu capture of the current kernel source")}
     batch = None if args.no_batch else bench_batch(solver, stream, flush, max(3, args.steps // 2),
                                                     args.precision, count=args.batch_count)
+    eigh = None if args.no_fp64_check else eigh_baseline(hs, results, KT)
     cb = cpu_baseline(ns) if (rank == 0 and world == 1) else None
     per_n = {}
     for n in ns:
@@ -406,6 +431,7 @@ def main():
         "stages": stages,
         "fp64_gpu_dm_per_s": (len(fp64_ms) / (sum(fp64_ms.values()) * 1e-3)) if fp64_ms else None,
         "batch_512": batch,
+        "eigh_fp64_cusolver": eigh,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
