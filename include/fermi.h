@@ -97,7 +97,12 @@ typedef struct {
     int32_t tile_n;           /* tensor-core tile width: 0 = autotune per plan, or 128 / 256 */
     int32_t tile_ctas;        /* CTAs per SM of the product kernel: 0 = autotune, 1, or 2
                                  (2 only with 128-wide tiles); set together with tile_n */
-    int32_t reserved;
+    int32_t lanczos_steps;    /* 0: Gershgorin bounds. 1..64: tighter bounds from that many
+                                 float64 Lanczos steps on H (start vector: splitmix64 draws),
+                                 the extreme Ritz values widened by their residuals
+                                 beta_{K+1} |y_K| and by 1% of the width, clamped to the
+                                 Gershgorin interval. Not a guaranteed enclosure; ignored with
+                                 use_given_bounds */
 } fo_params;
 
 typedef struct {

@@ -33,13 +33,13 @@ enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUND
 struct PlanKey {
     std::vector<int64_t> n;
     int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
-    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0;
+    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0;
     double tr_tol = 0.0;
     bool operator==(const PlanKey& o) const {
         return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
                mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
                tile_req == o.tile_req && ctas_req == o.ctas_req && sym == o.sym && max_bisect == o.max_bisect &&
-               max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged;
+               max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged && lanczos == o.lanczos;
     }
 };
 
@@ -359,6 +359,7 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
         o += align256(8 * (size_t)ndiag);             // diag
         o += align256(8 * (size_t)p->npairs);         // gram
         o += align256(8 * (size_t)p->npairs * in.gram_blocks);   // gram partials
+        o += align256(8 * (3 * (size_t)in.np + 2 * kLzMax + 3));  // Lanczos state
         small[j] = off;
         off = o;
     }
@@ -434,6 +435,7 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
         in.diag = next(8 * (size_t)ndiag);
         in.gram = next(8 * (size_t)p->npairs);
         in.gpart = next(8 * (size_t)p->npairs * in.gram_blocks);
+        in.lz = next(8 * (3 * (size_t)in.np + 2 * kLzMax + 3));
         in.res = p->d_res + j;
     }
     // device tables: Inst[batch], InstIO[batch], then the prefix arrays
@@ -647,8 +649,10 @@ fo_status clenshaw(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
 fo_status front(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     const int h = prof_begin(ctx, s, FO_STAGE_BOUNDS);
     FO_CUDA(launch_bounds(p.d_inst, p.d_io, p.batch, p.wg.dev, p.part_g, p.key.use_given, s), "bounds");
+    int l = (p.key.use_given ? 1 : 2) + 1;
+    if (p.key.lanczos > 0 && !p.key.use_given)
+        FO_CUDA(launch_lanczos(p.d_inst, p.d_io, p.batch, p.wg.dev, p.part_g, p.key.lanczos, s, &l), "lanczos");
     FO_CUDA(launch_scale(p.d_inst, p.d_io, p.wsc.dev, p.sh, s, ctx->flag + 1), "scale");
-    const int l = (p.key.use_given ? 1 : 2) + 1;
     prof_end(ctx, s, h, 0.0, l);
     run->launches += l;
     return baby_steps(ctx, p, p.sh.k, s, run);
@@ -871,6 +875,8 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
     if (prm->mu_mode == FO_MU_LEARNED && !(prm->tr_tol >= 0.0)) return fail(ctx, FO_ERR_ARG, "tr_tol must be >= 0");
     if (prm->tile_n != 0 && prm->tile_n != 128 && prm->tile_n != 256)
         return fail(ctx, FO_ERR_ARG, "tile_n must be 0, 128 or 256");
+    if (prm->lanczos_steps < 0 || prm->lanczos_steps > kLzMax)
+        return fail(ctx, FO_ERR_ARG, "lanczos_steps must be in [0, 64]");
     if (prm->tile_ctas < 0 || prm->tile_ctas > 2 || (prm->tile_ctas == 2 && prm->tile_n != 128) ||
         (prm->tile_ctas != 0 && prm->tile_n == 0))
         return fail(ctx, FO_ERR_ARG, "tile_ctas must be 0, 1 or 2 (2 with tile_n = 128), set with tile_n");
@@ -919,6 +925,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
     key.ctas_req = prm->tile_ctas;
     key.max_bisect = prm->max_bisect;
     key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
+    key.lanczos = prm->lanczos_steps;
     if (prm->mu_mode == FO_MU_LEARNED) {
         key.max_newton = prm->max_newton;
         key.tr_tol = prm->tr_tol;
@@ -1137,6 +1144,7 @@ fo_status features_batch(fo_ctx* ctx, int batch, const double* const* dH, const 
     key.ctas_req = q.tile_ctas;
     key.max_bisect = q.max_bisect;
     key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
+    key.lanczos = q.lanczos_steps;
     Plan* p = nullptr;
     FO_TRY(get_plan(ctx, key, &p));
     std::vector<InstIO> io(batch);

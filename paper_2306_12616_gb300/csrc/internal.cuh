@@ -59,6 +59,7 @@ struct Inst {
     double* gram;         // Frobenius products, giant-major
     double* gpart;        // gram partials, gram_blocks x npairs
     DevResult* res;
+    double* lz;           // Lanczos state: 3 np + 2 kLzMax + 3 doubles
     int32_t bucket;       // tensor-map bucket (instances of equal np)
     int32_t in_bucket;    // index within the bucket
     int32_t gram_blocks;  // blocks of the Frobenius-product kernel for this instance
@@ -140,6 +141,7 @@ __host__ __device__ inline int red_blocks(int64_t np) {
     return (int)((np + r - 1) / r);
 }
 constexpr int kGershRows = 8;   // rows per block of the bounds kernel (a warp per row)
+constexpr int kLzMax = 64;      // Lanczos steps at most
 
 // Self-check build (-DFO_SELF_CHECK): kernels verify the index range and the alignment of
 // their global accesses, record the first violation in dbg[0..3] and skip the access.
@@ -161,6 +163,10 @@ cudaError_t launch_set_io(const InstIO* ios, int count, InstIO* d_io, const Inst
 // Gershgorin bounds (use_given = 0) or the given / copied bounds (use_given = 1).
 cudaError_t launch_bounds(const Inst* in, const InstIO* io, int batch, Work wg, double* part,
                           int use_given, cudaStream_t s);
+// Lanczos bounds (after the Gershgorin bounds): `steps` float64 Lanczos steps on H, extreme
+// Ritz values widened by their residuals and 1% of the width, clamped to Gershgorin.
+cudaError_t launch_lanczos(const Inst* in, const InstIO* io, int batch, Work wg, double* part, int steps,
+                           cudaStream_t s, int* launches);
 // d_bounds[0..2] = emin, emax, non-finite flag of one instance.
 cudaError_t launch_export_bounds(const DevResult* res, double* out3, cudaStream_t s);
 // X = (2H - (emin+emax) I)/(emax - emin) into slot 0 of every instance.
