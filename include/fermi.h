@@ -69,6 +69,13 @@ typedef enum {
 #define FO_FLAG_NO_RESULT_SYNC   0x2u  /* density-matrix calls: never block, leave fo_result untouched */
 #define FO_FLAG_GRAPH            0x4u  /* capture the call's kernels into a CUDA graph kept with its
                                           plan and replay it on later calls with the same plan */
+#define FO_FLAG_POWER_BASIS      0x10u /* evaluate the paper's literal form: power-basis
+                                          coefficients d_{i,j} (Eq. (formula for d0), (formula
+                                          for d)) and the nested Horner scheme Y = S_j + T_k Y of
+                                          Eq. (ansatz), instead of the Chebyshev-basis
+                                          coefficients and the Clenshaw recurrence. The d_{i,j}
+                                          grow like 2^j, so the result loses accuracy with m;
+                                          FP16X2 is rejected (overflow) */
 #define FO_FLAG_STAGED           0x8u  /* baby and giant steps in the staged form of Algorithm 1
                                           (Sec. "Speed up with multiple GPU streams"): the
                                           independent products of a stage in one launch, about

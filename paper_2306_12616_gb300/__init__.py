@@ -17,7 +17,7 @@ from dataclasses import dataclass
 __all__ = [
     "FO_OK", "FO_PREC_FP64", "FO_PREC_BF16X3", "FO_PREC_FP16X2", "FO_PREC_BF16X1",
     "FO_MU_FIXED", "FO_MU_BISECT", "FO_MU_LEARNED", "FO_FLAG_NO_RESULT_SYNC", "FO_FLAG_GRAPH",
-    "FO_FLAG_STAGED",
+    "FO_FLAG_STAGED", "FO_FLAG_POWER_BASIS",
     "FoParams", "FoResult", "FermiError", "lib", "library_path", "EXPORTED_SYMBOLS",
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
@@ -36,6 +36,7 @@ FO_MU_FIXED, FO_MU_BISECT, FO_MU_LEARNED = 0, 1, 2
 FO_FLAG_NO_RESULT_SYNC = 0x2
 FO_FLAG_GRAPH = 0x4
 FO_FLAG_STAGED = 0x8
+FO_FLAG_POWER_BASIS = 0x10
 
 PRECISIONS = {"fp64": FO_PREC_FP64, "bf16x3": FO_PREC_BF16X3, "fp16x2": FO_PREC_FP16X2,
               "bf16x1": FO_PREC_BF16X1}

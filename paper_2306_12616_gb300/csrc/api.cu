@@ -33,13 +33,13 @@ enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUND
 struct PlanKey {
     std::vector<int64_t> n;
     int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
-    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0;
+    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0, power = 0;
     double tr_tol = 0.0;
     bool operator==(const PlanKey& o) const {
         return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
                mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
                tile_req == o.tile_req && ctas_req == o.ctas_req && sym == o.sym && max_bisect == o.max_bisect &&
-               max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged && lanczos == o.lanczos;
+               max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged && lanczos == o.lanczos && power == o.power;
     }
 };
 
@@ -675,12 +675,32 @@ fo_status exact_mu(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int start_mu0
     return FO_OK;
 }
 
-// P of every active instance at its current mu: coefficients, R_l, Clenshaw, tr P, ||P||^2.
+// The paper's nested Horner form in the power basis of Y = T_k: Y_{m-1} = S_{m-1},
+// Y_j = S_j + T_k Y_{j+1}, P = Y_0 (float64 into the instance's P); Y_j overwrites S_j.
+fo_status horner(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    const int m = p.sh.m;
+    if (m == 1) return FO_OK;
+    const int y = giant_slot(p, 1);
+    for (int j = m - 2; j >= 1; --j) {
+        const Step st = make_step(p, y, r_slot(p, j + 1), -1, r_slot(p, j), r_slot(p, j), 1.0, 0.0, 0.0, false,
+                                  true, true, false, ctx);
+        FO_TRY(run_product(ctx, p, st, s, "horner", j, run));
+    }
+    const Step st = make_step(p, y, r_slot(p, 1), -1, r_slot(p, 0), -1, 1.0, 0.0, 0.0, false, true, false, true, ctx);
+    return run_product(ctx, p, st, s, "horner", 0, run);
+}
+
+// P of every active instance at its current mu: coefficients, R_l, Clenshaw, tr P, ||P||^2
+// (or, with the power basis, d_{i,j}, S_j and Horner).
 fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trace) {
     const Shape& sh = p.sh;
     int h = prof_begin(ctx, s, FO_STAGE_COEFFS);
     int lstage = 0;
     FO_CUDA(launch_coefficients(p.d_inst, p.d_io, p.batch, sh, p.ct, poly_trace, s, &lstage), "coeffs");
+    if (p.key.power) {
+        FO_CUDA(launch_g_to_d(p.d_inst, p.batch, sh, s), "power-basis coefficients");
+        lstage += 1;
+    }
     prof_end(ctx, s, h, 0.0, lstage);
     run->launches += lstage;
     h = prof_begin(ctx, s, FO_STAGE_CONTRACT);
@@ -692,7 +712,7 @@ fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trac
     }
     prof_end(ctx, s, h, 0.0, lstage);
     run->launches += lstage;
-    FO_TRY(clenshaw(ctx, p, s, run));
+    FO_TRY(p.key.power ? horner(ctx, p, s, run) : clenshaw(ctx, p, s, run));
     h = prof_begin(ctx, s, FO_STAGE_TRACE);
     FO_CUDA(launch_trace_frob(p.d_inst, p.d_io, p.wr.dev, p.part_t, s), "trace");
     prof_end(ctx, s, h, 0.0, 2);
@@ -875,6 +895,8 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
     if (prm->mu_mode == FO_MU_LEARNED && !(prm->tr_tol >= 0.0)) return fail(ctx, FO_ERR_ARG, "tr_tol must be >= 0");
     if (prm->tile_n != 0 && prm->tile_n != 128 && prm->tile_n != 256)
         return fail(ctx, FO_ERR_ARG, "tile_n must be 0, 128 or 256");
+    if ((prm->flags & FO_FLAG_POWER_BASIS) && prm->precision == FO_PREC_FP16X2)
+        return fail(ctx, FO_ERR_UNSUPPORTED, "the power basis overflows the fp16 range");
     if (prm->lanczos_steps < 0 || prm->lanczos_steps > kLzMax)
         return fail(ctx, FO_ERR_ARG, "lanczos_steps must be in [0, 64]");
     if (prm->tile_ctas < 0 || prm->tile_ctas > 2 || (prm->tile_ctas == 2 && prm->tile_n != 128) ||
@@ -926,6 +948,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
     key.max_bisect = prm->max_bisect;
     key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
     key.lanczos = prm->lanczos_steps;
+    key.power = (prm->flags & FO_FLAG_POWER_BASIS) ? 1 : 0;
     if (prm->mu_mode == FO_MU_LEARNED) {
         key.max_newton = prm->max_newton;
         key.tr_tol = prm->tr_tol;

@@ -219,6 +219,36 @@ __global__ void k_g_convert(const Inst* __restrict__ insts, int k, int m) {
     }
 }
 
+// The paper's power-basis coefficients d_{i,j} of P = sum_j T_k^j S_j, S_j = sum_i d_{i,j} T_i
+// (Eq. ansatz), from the giant-step coefficients: T_{lk} = T_l(T_k) = sum_j t_{l,j} T_k^j with
+// t_{l,j} the monomial coefficients of the Chebyshev polynomial T_l (t_{l+1,j} = 2 t_{l,j-1} -
+// t_{l-1,j}), so d_{i,j} = sum_l g_{i,l} t_{l,j}, i.e. D = G A^{-1} for the A of Eq. (coeff
+// recursion). Written over g in place; one block per instance, the table in shared memory.
+__global__ void k_g_to_d(const Inst* __restrict__ insts, int k, int m) {
+    extern __shared__ double sm_t[];   // t[l * m + j], m x m, then g[k x m]
+    const Inst& in = insts[blockIdx.x];
+    if (!in.res->active) return;
+    double* t = sm_t;
+    double* gs = sm_t + m * m;
+    for (int q = threadIdx.x; q < m * m; q += blockDim.x) t[q] = 0.0;
+    for (int q = threadIdx.x; q < k * m; q += blockDim.x) gs[q] = in.g[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        t[0] = 1.0;
+        if (m > 1) t[m + 1] = 1.0;
+        for (int l = 1; l + 1 < m; ++l)
+            for (int j = 0; j <= l + 1; ++j)
+                t[(l + 1) * m + j] = (j > 0 ? 2.0 * t[l * m + j - 1] : 0.0) - t[(l - 1) * m + j];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < k * m; q += blockDim.x) {
+        const int j = q / k, i = q - j * k;   // g and d stored l-major: [l * k + i]
+        double s = 0.0;
+        for (int l = j; l < m; ++l) s = fma(gs[l * k + i], t[l * m + j], s);
+        in.g[j * k + i] = s;
+    }
+}
+
 __global__ void k_poly_trace(const Inst* __restrict__ insts, int n_terms) {
     const Inst& in = insts[blockIdx.x];
     if (!in.res->active) return;
@@ -428,6 +458,13 @@ cudaError_t launch_coefficients(const Inst* in, const InstIO* io, int batch, con
         ++l;
     }
     if (launches) *launches += l;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g_to_d(const Inst* in, int batch, const Shape& sh, cudaStream_t s) {
+    const size_t smem = sizeof(double) * ((size_t)sh.m * sh.m + (size_t)sh.k * sh.m);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_g_to_d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_g_to_d<<<batch, 256, smem, s>>>(in, sh.k, sh.m);
     return cudaGetLastError();
 }
 

@@ -239,6 +239,8 @@ cudaError_t launch_set_mu(const Inst* in, const InstIO* io, int batch, cudaStrea
 cudaError_t launch_coefficients(const Inst* in, const InstIO* io, int batch, const Shape& sh,
                                 const double* ct, int with_poly_trace, cudaStream_t s, int* launches);
 cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream_t s, int* dbg);
+// g -> the paper's power-basis coefficients d (in place), for the Horner evaluation.
+cudaError_t launch_g_to_d(const Inst* in, int batch, const Shape& sh, cudaStream_t s);
 
 // ----------------------------------------------------------- gemm_f64.cu / gemm_tc.cu
 int64_t f64_tiles(int64_t np);
