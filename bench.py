@@ -359,16 +359,16 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * len(ns) / (ms_per_step * 1e-3)
 
-    # end to end through the host-buffer C ABI call (H2D + solve + D2H inside the region)
-    hout = {n: torch.empty((n, n), dtype=torch.float64).pin_memory() for n in ns}
-    for n in ns:
-        solver.density_matrix_host(hcpu[n], n / 2, prm, hout[n])
+    # end to end through the host-buffer C ABI call (H2D + solve + D2H inside the region):
+    # one batched host call per step, pinned buffers
+    hout = [torch.empty((n, n), dtype=torch.float64).pin_memory() for n in ns]
+    hin = [hcpu[n] for n in ns]
+    solver.density_matrix_batched_host(hin, nel, prm, hout)
     e2e_steps = max(2, args.steps // 2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for n in ns:
-            solver.density_matrix_host(hcpu[n], n / 2, prm, hout[n])
+        solver.density_matrix_batched_host(hin, nel, prm, hout)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     e2e_bytes = sum(8 * n * n for n in ns)
 

@@ -256,6 +256,18 @@ fo_status fo_density_matrix_host(fo_ctx *ctx, const double *hH, int64_t n, int64
                                  int64_t ldp, fo_result *res, void *stream);
 
 /*
+ * fo_density_matrix_batched with host buffers: copies every hH[b] to the device, runs the
+ * batch, copies every P back to hP[b] (hP[b][n[b] x n[b], ldp[b]]), then synchronises.
+ * Rows of one instance that are contiguous (ld[b] == n[b]) move as one linear copy; pinned
+ * host memory makes the copies asynchronous. Arguments as in fo_density_matrix_batched.
+ */
+fo_status fo_density_matrix_batched_host(fo_ctx *ctx, int32_t batch, const double *const *hH,
+                                         const int64_t *n, const int64_t *ld, const double *n_e,
+                                         const double *kT, const fo_params *params,
+                                         double *const *hP, const int64_t *ldp, fo_result *res,
+                                         void *stream);
+
+/*
  * Chebyshev moments tau_j = tr T_j(X), j < n_moments, of the scaled Hamiltonian on the
  * given bounds (d_bounds as written by fo_spectral_bounds), float64 into d_tau. Used as
  * features of the learned mu and exposed for spectral analysis. Moments up to 2k come

@@ -21,7 +21,7 @@ __all__ = [
     "FoParams", "FoResult", "FermiError", "lib", "library_path", "EXPORTED_SYMBOLS",
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
-    "fo_density_matrix_batched", "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
+    "fo_density_matrix_batched", "fo_density_matrix_batched_host", "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
     "fo_spectral_bounds_noalloc", "FO_NOALLOC_MAX_N", "fo_learned_features", "fo_mlp_init",
     "fo_mlp_set_params", "fo_mlp_get_params", "fo_mlp_forward", "fo_mlp_gradients", "fo_mlp_train",
     "fo_mlp_save", "fo_mlp_load", "FO_MLP_INPUTS", "FO_MLP_OUTPUTS", "FO_MLP_PARAMS", "FO_MLP_NORM",
@@ -45,10 +45,11 @@ MU_MODES = {"fixed": FO_MU_FIXED, "bisect": FO_MU_BISECT, "learned": FO_MU_LEARN
 # Every symbol the header declares (checked by the CPU test suite against the .so).
 EXPORTED_SYMBOLS = (
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
-    "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
-    "fo_density_matrix_batched", "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read",
-    "fo_spectral_bounds_noalloc", "fo_learned_features", "fo_mlp_init", "fo_mlp_set_params",
-    "fo_mlp_get_params", "fo_mlp_forward", "fo_mlp_gradients", "fo_mlp_train", "fo_mlp_save", "fo_mlp_load",
+    "fo_spectral_bounds", "fo_spectral_bounds_noalloc", "fo_chebyshev_coeffs", "fo_density_matrix",
+    "fo_density_matrix_host", "fo_density_matrix_batched", "fo_density_matrix_batched_host", "fo_moments",
+    "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "fo_learned_features", "fo_mlp_init",
+    "fo_mlp_set_params", "fo_mlp_get_params", "fo_mlp_forward", "fo_mlp_gradients", "fo_mlp_train",
+    "fo_mlp_save", "fo_mlp_load",
 )
 FO_NOALLOC_MAX_N = 32768
 FO_MLP_INPUTS, FO_MLP_OUTPUTS, FO_MLP_PARAMS, FO_MLP_NORM = 68, 2, 83970, 140
@@ -138,6 +139,9 @@ def lib() -> ctypes.CDLL:
             "fo_density_matrix_batched": (ctypes.c_int, [_c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                                          _c_ptr, ctypes.POINTER(FoParams), _c_ptr, _c_ptr,
                                                          _c_ptr, _c_ptr]),
+            "fo_density_matrix_batched_host": (ctypes.c_int, [_c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                                              _c_ptr, ctypes.POINTER(FoParams), _c_ptr,
+                                                              _c_ptr, _c_ptr, _c_ptr]),
             "fo_learned_features": (ctypes.c_int, [_c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                                    ctypes.POINTER(FoParams), _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
             "fo_mlp_init": (ctypes.c_int, [_c_ptr, ctypes.c_uint64]),
@@ -224,6 +228,12 @@ def fo_density_matrix_batched(ctx, batch, d_h_ptrs, n, ld, n_e, kT, params: FoPa
     array of FoResult of length batch, or None."""
     return lib().fo_density_matrix_batched(ctx, batch, d_h_ptrs, n, ld, n_e, kT, ctypes.byref(params),
                                            d_p_ptrs, ldp, results, stream)
+
+
+def fo_density_matrix_batched_host(ctx, batch, h_h_ptrs, n, ld, n_e, kT, params: FoParams, h_p_ptrs,
+                                   ldp, results, stream=0) -> int:
+    return lib().fo_density_matrix_batched_host(ctx, batch, h_h_ptrs, n, ld, n_e, kT, ctypes.byref(params),
+                                                h_p_ptrs, ldp, results, stream)
 
 
 def fo_learned_features(ctx, batch, d_h_ptrs, n, ld, n_e, kT, params: FoParams, d_feat, d_target,
@@ -381,6 +391,18 @@ class Solver:
         self._check(fo_density_matrix_batched(self.ctx, B, d_h, n, ld, ne, kt, params, d_p, ldp, res,
                                               _stream_handle(stream)))
         return ps, ([r.as_dict() for r in res] if res is not None else None)
+
+    def density_matrix_batched_host(self, hs, n_e, params: FoParams, outs, kT=None, stream=None):
+        """hs, outs: CPU float64 tensors (pinned for asynchronous copies). Returns result dicts."""
+        B = len(hs)
+        ptr, i64, dbl = ctypes.c_void_p * B, ctypes.c_int64 * B, ctypes.c_double * B
+        res = (FoResult * B)()
+        self._check(fo_density_matrix_batched_host(
+            self.ctx, B, ptr(*[h.data_ptr() for h in hs]), i64(*[h.shape[0] for h in hs]),
+            i64(*[h.stride(0) for h in hs]), dbl(*[float(x) for x in n_e]),
+            dbl(*[float(x) for x in kT]) if kT is not None else None, params,
+            ptr(*[o.data_ptr() for o in outs]), i64(*[o.stride(0) for o in outs]), res, _stream_handle(stream)))
+        return [r.as_dict() for r in res]
 
     # ------------------------------------------------------------ learned mu
     def learned_features(self, hs, n_e, params: FoParams, kT=None, stream=None):

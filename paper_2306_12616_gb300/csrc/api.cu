@@ -1361,40 +1361,77 @@ fo_status fo_density_matrix_batched(fo_ctx* ctx, int32_t batch, const double* co
                          reinterpret_cast<cudaStream_t>(stream));
 }
 
-fo_status fo_density_matrix_host(fo_ctx* ctx, const double* hH, int64_t n, int64_t ld, double n_e,
-                                 const fo_params* params, double* hP, int64_t ldp, fo_result* res,
-                                 void* stream) {
+fo_status fo_density_matrix_batched_host(fo_ctx* ctx, int32_t batch, const double* const* hH, const int64_t* n,
+                                         const int64_t* ld, const double* n_e, const double* kT,
+                                         const fo_params* params, double* const* hP, const int64_t* ldp,
+                                         fo_result* res, void* stream) {
     if (!ctx) return FO_ERR_ARG;
-    if (!hH || !hP || n < 1 || ld < n || ldp < n || !params) return fail(ctx, FO_ERR_ARG, "bad arguments");
+    if (batch < 1 || !hH || !hP || !n || !n_e || !params) return fail(ctx, FO_ERR_ARG, "bad arguments");
+    for (int b = 0; b < batch; ++b)
+        if (!hH[b] || !hP[b] || n[b] < 1 || (ld && ld[b] < n[b]) || (ldp && ldp[b] < n[b]))
+            return fail(ctx, FO_ERR_ARG, "bad instance arguments");
     DeviceGuard g(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t mat = align256((size_t)n * n * 8);
-    if (ctx->stage_bytes < 2 * mat) {
+    // device staging: H and P of every instance, densely packed
+    std::vector<size_t> off(batch);
+    size_t total = 0;
+    for (int b = 0; b < batch; ++b) {
+        off[b] = total;
+        total += 2 * align256((size_t)n[b] * n[b] * 8);
+    }
+    if (ctx->stage_bytes < total) {
         if (ctx->stage) {
             cudaDeviceSynchronize();
             cudaFree(ctx->stage);
             ctx->stage = nullptr;
             ctx->stage_bytes = 0;
         }
-        if (cudaMalloc(&ctx->stage, 2 * mat) != cudaSuccess) {
+        if (cudaMalloc(&ctx->stage, total) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, FO_ERR_NOMEM, "staging allocation failed");
         }
-        ctx->stage_bytes = 2 * mat;
+        ctx->stage_bytes = total;
     }
-    double* dH = reinterpret_cast<double*>(ctx->stage);
-    double* dP = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->stage) + mat);
-    FO_CUDA(cudaMemcpy2DAsync(dH, n * 8, hH, ld * 8, n * 8, n, cudaMemcpyHostToDevice, st), "H2D");
+    std::vector<const double*> dH(batch);
+    std::vector<double*> dP(batch);
+    std::vector<int64_t> ldn(n, n + batch);
+    char* base = reinterpret_cast<char*>(ctx->stage);
+    for (int b = 0; b < batch; ++b) {
+        double* h = reinterpret_cast<double*>(base + off[b]);
+        dH[b] = h;
+        dP[b] = reinterpret_cast<double*>(base + off[b] + align256((size_t)n[b] * n[b] * 8));
+        const int64_t l = ld ? ld[b] : n[b];
+        if (l == n[b])   // contiguous rows: one linear copy
+            FO_CUDA(cudaMemcpyAsync(h, hH[b], (size_t)n[b] * n[b] * 8, cudaMemcpyHostToDevice, st), "H2D");
+        else
+            FO_CUDA(cudaMemcpy2DAsync(h, n[b] * 8, hH[b], l * 8, n[b] * 8, n[b], cudaMemcpyHostToDevice, st),
+                    "H2D");
+    }
     fo_params prm = *params;
     prm.flags &= ~FO_FLAG_NO_RESULT_SYNC;
-    fo_result local;
-    const double* cH = dH;
-    const int64_t ldn = n;
-    fo_status s = density_batch(ctx, 1, &cH, &n, &ldn, &n_e, nullptr, &prm, &dP, &ldn, res ? res : &local, st);
+    std::vector<fo_result> local(batch);
+    fo_status s = density_batch(ctx, batch, dH.data(), n, ldn.data(), n_e, kT, &prm, dP.data(), ldn.data(),
+                                res ? res : local.data(), st);
     if (s != FO_OK && s != FO_ERR_NOT_CONVERGED) return s;
-    FO_CUDA(cudaMemcpy2DAsync(hP, ldp * 8, dP, n * 8, n * 8, n, cudaMemcpyDeviceToHost, st), "D2H");
+    for (int b = 0; b < batch; ++b) {
+        const int64_t l = ldp ? ldp[b] : n[b];
+        if (l == n[b])
+            FO_CUDA(cudaMemcpyAsync(hP[b], dP[b], (size_t)n[b] * n[b] * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        else
+            FO_CUDA(cudaMemcpy2DAsync(hP[b], l * 8, dP[b], n[b] * 8, n[b] * 8, n[b], cudaMemcpyDeviceToHost, st),
+                    "D2H");
+    }
     FO_CUDA(cudaStreamSynchronize(st), "sync");
     return s;
+}
+
+fo_status fo_density_matrix_host(fo_ctx* ctx, const double* hH, int64_t n, int64_t ld, double n_e,
+                                 const fo_params* params, double* hP, int64_t ldp, fo_result* res,
+                                 void* stream) {
+    if (!ctx) return FO_ERR_ARG;
+    if (!hH || !hP || n < 1 || ld < n || ldp < n || !params) return fail(ctx, FO_ERR_ARG, "bad arguments");
+    double* P = hP;
+    return fo_density_matrix_batched_host(ctx, 1, &hH, &n, &ld, &n_e, nullptr, params, &P, &ldp, res, stream);
 }
 
 fo_status fo_moments(fo_ctx* ctx, const double* dH, int64_t n, int64_t ld, const double* d_bounds,

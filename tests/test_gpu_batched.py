@@ -147,3 +147,18 @@ def test_batch_argument_errors(solver):
         solver.density_matrix_batched([h], [32.0], solver.params(64, 0.1, tile_n=64))
     with pytest.raises(Exception):
         solver.density_matrix_batched([h], [32.0], solver.params(64, 0.1, tile_n=256, tile_ctas=2))
+
+
+def test_batched_host_buffers_equal_device_buffers(solver):
+    ns, kts, hs = batch(4, 6, 64, 500)
+    prm = solver.params(300, 0.1, precision="bf16x3", mu_mode="bisect")
+    pd, rd = solver.density_matrix_batched([to_dev(h) for h in hs], [n / 2 for n in ns], prm, kT=kts)
+    hin = [torch.from_numpy(h).pin_memory() for h in hs]
+    # one instance with a row pitch larger than n (a 2-D copy)
+    wide = torch.zeros((ns[0], ns[0] + 3), dtype=torch.float64).pin_memory()
+    wide[:, :ns[0]] = hin[0]
+    hin[0] = wide[:, :ns[0]]
+    outs = [torch.empty((n, n), dtype=torch.float64).pin_memory() for n in ns]
+    rh = solver.density_matrix_batched_host(hin, [n / 2 for n in ns], prm, outs, kT=kts)
+    for a, b, x, y in zip(pd, outs, rd, rh):
+        assert torch.equal(a.cpu(), b) and x["mu"] == y["mu"]
