@@ -110,6 +110,9 @@ typedef struct {
                                  beta_{K+1} |y_K| and by 1% of the width, clamped to the
                                  Gershgorin interval. Not a guaranteed enclosure; ignored with
                                  use_given_bounds */
+    int32_t tile_drain;       /* warps draining the tensor-memory accumulators: 0 = autotune,
+                                 8, or 16 (with tile_n = 256); set together with tile_n */
+    int32_t reserved;
 } fo_params;
 
 typedef struct {
@@ -128,7 +131,7 @@ typedef struct {
     int32_t tile_ctas;        /* CTAs per SM of the product kernel used (0 for FP64) */
     int32_t evals;            /* evaluations of P (1 unless FO_MU_LEARNED corrected mu) */
     int32_t order;            /* expansion order proposed by the learned model (0 if none) */
-    int32_t reserved;
+    int32_t tile_drain;       /* accumulator drain warps of the product kernel (0 for FP64) */
 } fo_result;
 
 /* Stages of a density-matrix call, as recorded by the profiler. */

@@ -33,12 +33,12 @@ enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUND
 struct PlanKey {
     std::vector<int64_t> n;
     int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
-    int use_given = 0, tile_req = 0, ctas_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0, power = 0;
+    int use_given = 0, tile_req = 0, ctas_req = 0, drain_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0, power = 0;
     double tr_tol = 0.0;
     bool operator==(const PlanKey& o) const {
         return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
                mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
-               tile_req == o.tile_req && ctas_req == o.ctas_req && sym == o.sym && max_bisect == o.max_bisect &&
+               tile_req == o.tile_req && ctas_req == o.ctas_req && drain_req == o.drain_req && sym == o.sym && max_bisect == o.max_bisect &&
                max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged && lanczos == o.lanczos && power == o.power;
     }
 };
@@ -74,6 +74,7 @@ struct Plan {
     HostWork wg, wsc, we, wr, wgr, wtc[2], wf64;   // wtc[0]: 256-wide tiles, wtc[1]: 128-wide
     int tile_n = 0;
     int tile_ctas = 0;
+    int tile_drain = 0;
     int npairs = 0;
     void* dtab = nullptr;     // device tables: Inst[], InstIO[], prefixes
     Inst* d_inst = nullptr;
@@ -530,7 +531,7 @@ fo_status run_products(fo_ctx* ctx, Plan& p, const Step* steps, int nsteps, cuda
             for (const Group& g : p.groups) {
                 std::string err;
                 const int tile0 = w.pre[g.i0];
-                cudaError_t e = tc_gemm(p.key.prec, p.tile_n, p.tile_ctas, steps + q0, nq, p.d_inst, p.d_io,
+                cudaError_t e = tc_gemm(p.key.prec, p.tile_n, p.tile_ctas, p.tile_drain, steps + q0, nq, p.d_inst, p.d_io,
                                         w.dev.pre, g.i0, g.i1, tile0, w.pre[g.i1] - tile0,
                                         p.maps.data() + 128 * (size_t)g.b0, g.b0, g.nb, ctx->flag, s, &err,
                                         p.key.sym);
@@ -789,23 +790,24 @@ fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
 }
 
 // Tile configuration of the tensor-core products: the requested one, or the fastest of
-// (256 wide, 1 CTA/SM), (128 wide, 1 CTA/SM) and (128 wide, 2 CTAs/SM) on this plan's first
-// baby step, timed with CUDA events on the plan's own layout (the data are whatever the
-// workspace holds; the work does not depend on them).
+// (256 wide, 1 CTA/SM, 8 or 16 drain warps), (128 wide, 1 CTA/SM) and (128 wide, 2 CTAs/SM)
+// on this plan's first baby step, timed with CUDA events on the plan's own layout (the data
+// are whatever the workspace holds; the work does not depend on them).
 fo_status autotune(fo_ctx* ctx, Plan& p) {
     if (p.sh.is64 || p.n_slots == 0) {
-        p.tile_n = 0;
-        p.tile_ctas = 0;
+        p.tile_n = p.tile_ctas = p.tile_drain = 0;
         return FO_OK;
     }
     if (p.key.tile_req) {
         p.tile_n = p.key.tile_req;
         p.tile_ctas = p.key.ctas_req ? p.key.ctas_req : 1;
+        p.tile_drain = p.key.drain_req ? p.key.drain_req : 8;
         return FO_OK;
     }
     if (p.key.mode == MODE_PRODUCT || p.sh.k < 2) {
         p.tile_n = 256;
         p.tile_ctas = 1;
+        p.tile_drain = 8;
         return FO_OK;
     }
     // make every instance active (the per-call inputs are not needed by a product)
@@ -816,13 +818,14 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
     const Step st = make_step(p, 0, 0, -1, -1, 1, 2.0, 0.0, -1.0, false, false, false, false, ctx);
     cudaEvent_t e0 = ev_get(ctx), e1 = ev_get(ctx);
     float best = 0.0f;
-    int best_n = 256, best_c = 1;
+    int bn = 256, bc = 1, bd = 8;
     const bool prof = ctx->prof;
     ctx->prof = false;
-    const int cands[3][2] = {{256, 1}, {128, 1}, {128, 2}};
-    for (int ci = 0; ci < 3; ++ci) {
+    const int cands[4][3] = {{256, 1, 8}, {256, 1, 16}, {128, 1, 8}, {128, 2, 8}};
+    for (int ci = 0; ci < 4; ++ci) {
         p.tile_n = cands[ci][0];
         p.tile_ctas = cands[ci][1];
+        p.tile_drain = cands[ci][2];
         Run r;
         fo_status rs = run_product(ctx, p, st, s, "autotune", ci, &r);   // warm-up
         if (rs != FO_OK) { ctx->prof = prof; return rs; }
@@ -839,8 +842,9 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
         }
         if (ci == 0 || ms < best) {
             best = ms;
-            best_n = cands[ci][0];
-            best_c = cands[ci][1];
+            bn = cands[ci][0];
+            bc = cands[ci][1];
+            bd = cands[ci][2];
         }
     }
     ctx->prof = prof;
@@ -849,8 +853,9 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
     int flag = 0;
     FO_CUDA(cudaMemcpy(&flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost), "autotune flag");
     if (flag) return fail(ctx, FO_ERR_DEVICE_TIMEOUT, "tensor-core wait timed out during autotuning");
-    p.tile_n = best_n;
-    p.tile_ctas = best_c;
+    p.tile_n = bn;
+    p.tile_ctas = bc;
+    p.tile_drain = bd;
     return FO_OK;
 }
 
@@ -895,6 +900,10 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
     if (prm->mu_mode == FO_MU_LEARNED && !(prm->tr_tol >= 0.0)) return fail(ctx, FO_ERR_ARG, "tr_tol must be >= 0");
     if (prm->tile_n != 0 && prm->tile_n != 128 && prm->tile_n != 256)
         return fail(ctx, FO_ERR_ARG, "tile_n must be 0, 128 or 256");
+    if (prm->tile_drain != 0 && (prm->tile_drain != 8 && prm->tile_drain != 16))
+        return fail(ctx, FO_ERR_ARG, "tile_drain must be 0, 8 or 16");
+    if (prm->tile_drain == 16 && prm->tile_n != 256)
+        return fail(ctx, FO_ERR_ARG, "16 drain warps need tile_n = 256");
     if ((prm->flags & FO_FLAG_POWER_BASIS) && prm->precision == FO_PREC_FP16X2)
         return fail(ctx, FO_ERR_UNSUPPORTED, "the power basis overflows the fp16 range");
     if (prm->lanczos_steps < 0 || prm->lanczos_steps > kLzMax)
@@ -945,6 +954,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
     key.use_given = prm->use_given_bounds ? 1 : 0;
     key.tile_req = prm->tile_n;
     key.ctas_req = prm->tile_ctas;
+    key.drain_req = prm->tile_drain;
     key.max_bisect = prm->max_bisect;
     key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
     key.lanczos = prm->lanczos_steps;
@@ -1038,6 +1048,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
             r.n_launches = run.launches;
             r.tile_n = p->tile_n;
             r.tile_ctas = p->tile_ctas;
+            r.tile_drain = p->tile_drain;
             r.evals = 1;
             r.order = 0;
             if (prm->mu_mode == FO_MU_LEARNED) {
@@ -1165,6 +1176,7 @@ fo_status features_batch(fo_ctx* ctx, int batch, const double* const* dH, const 
     key.use_given = q.use_given_bounds ? 1 : 0;
     key.tile_req = q.tile_n;
     key.ctas_req = q.tile_ctas;
+    key.drain_req = q.tile_drain;
     key.max_bisect = q.max_bisect;
     key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
     key.lanczos = q.lanczos_steps;

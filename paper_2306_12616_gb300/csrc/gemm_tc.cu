@@ -190,8 +190,6 @@ __device__ __forceinline__ uint16_t bits_bf16(float v) {
     return *reinterpret_cast<uint16_t*>(&h);
 }
 
-constexpr int kDrainWarps = 8;    // 2 per TMEM lane quadrant, one per column half
-constexpr int kThreads = 32 * (2 + kDrainWarps);
 constexpr int kBoxBytes = kBM * kRowBytes;   // one 128-row TMA box of one plane: 8 KB
 
 struct TcMaps {
@@ -200,8 +198,14 @@ struct TcMaps {
 
 // MINB CTAs share an SM (1, or 2 for 128-wide tiles: one CTA's epilogue then overlaps the
 // other's main loop); the shared-memory ring and the register budget are split accordingly.
-template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB>
+// DW drain warps (8 or 16) read the TMEM accumulators: warp w serves lane quadrant w & 3 and
+// column group (w - 2) / 4 of TBN / (DW / 4) columns; more drain warps keep more TMEM loads in
+// flight per k-block.
+template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB, int DW>
 struct TcCfg {
+    static constexpr int kThreads = 32 * (2 + DW);
+    static constexpr int kCols = TBN / (DW / 4);     // accumulator columns per drain warp
+    static constexpr bool kLoad32 = MINB == 1 && DW == 8;   // else 16-column TMEM loads
     static constexpr int kBBoxes = TBN / kBM;
     static constexpr int kStageBytes = PA * kBoxBytes + PB * kBBoxes * kBoxBytes;
     static constexpr int kStagesRaw = (216 * 1024 / MINB) / kStageBytes;
@@ -282,13 +286,14 @@ __device__ __forceinline__ void tile_of(int t, int tm, int tn, int tbn, int sym,
     J = t - I * tn;
 }
 
-template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB)
+template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB, int DW>
+__global__ void __launch_bounds__(32 * (2 + DW), MINB)
     k_tc_gemm(const __grid_constant__ TcMaps maps, const __grid_constant__ StepList steps,
               const Inst* __restrict__ insts, const InstIO* __restrict__ io, const int* __restrict__ pre,
               int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag) {
-    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB>;
+    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB, DW>;
     constexpr int S = Cfg::kStages;
+    constexpr int NC = Cfg::kCols;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -331,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&seg_full[b], 1);
-            mbar_init(&seg_empty[b], 32 * kDrainWarps);
+            mbar_init(&seg_empty[b], 32 * DW);
         }
         mbar_init(acc_full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -354,9 +359,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
         return smem + s * Cfg::kStageBytes + PA * kBoxBytes + p * Cfg::kBBoxes * kBoxBytes;
     };
 
-    float sum[TBN / 2];  // a drain thread's accumulated columns of its tile row
+    float sum[NC];  // a drain thread's accumulated columns of its tile row
 #pragma unroll
-    for (int j = 0; j < TBN / 2; ++j) sum[j] = 0.0f;
+    for (int j = 0; j < NC; ++j) sum[j] = 0.0f;
     bool ok = true;
 
     if (warp == 0) {
@@ -443,9 +448,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
         __syncwarp();
     } else {
         // ---------------- drain warps: add every finished k-block to registers
-        const int q = warp & 3, half = (warp - 2) >> 2;
-        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16) + half * (TBN / 2);
-        const bool live = half * (TBN / 2) < tile_n;   // columns this warp reads hold data
+        const int q = warp & 3, grp = (warp - 2) >> 2;
+        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16) + grp * NC;
+        const bool live = grp * NC < tile_n;   // columns this warp reads hold data
         for (int kb = 0; kb < nk; ++kb) {
             const int buf = kb & 1;
             if (!mbar_wait_warp(&seg_full[buf], (kb >> 1) & 1, kWaitNs, vabort)) {
@@ -455,9 +460,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
             __syncwarp();
             fence_after();
             if (live) {
-                if (MINB == 1) {
+                if (Cfg::kLoad32) {
 #pragma unroll
-                    for (int cb = 0; cb < TBN / 64; ++cb) {
+                    for (int cb = 0; cb < NC / 32; ++cb) {
                         uint32_t r[32];
                         tmem_ld32(t_row + buf * TBN + cb * 32, r);
 #pragma unroll
@@ -466,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 } else {
                     // half the registers per thread: 16-column loads
 #pragma unroll
-                    for (int cb = 0; cb < TBN / 32; ++cb) {
+                    for (int cb = 0; cb < NC / 16; ++cb) {
                         uint32_t r[16];
                         tmem_ld16(t_row + buf * TBN + cb * 16, r);
 #pragma unroll
@@ -502,12 +507,12 @@ __global__ void __launch_bounds__(kThreads, MINB)
     constexpr int LD = TBN + 1;
     float* tile = reinterpret_cast<float*>(smem);
     {
-        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int q = warp & 3, grp = (warp - 2) >> 2;
         const int rl = q * 32 + lane;
 #pragma unroll
-        for (int c = 0; c < TBN / 2; ++c) tile[rl * LD + half * (TBN / 2) + c] = st.alpha * sum[c];
+        for (int c = 0; c < NC; ++c) tile[rl * LD + grp * NC + c] = st.alpha * sum[c];
     }
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kDrainWarps) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * DW) : "memory");
 
     // instance fields of the epilogue, read here so that they are not live in the main loop
     const int64_t n_real = insts[inst].n;
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     double* out64 = st.out64 ? io[inst].P : nullptr;
     const int64_t ldo = io[inst].ldp;
     const int planes = st.planes;
-    const int ew = warp - 2;  // 0..7
+    const int ew = warp - 2;  // 0..DW-1
     // store of the pair (grow, gcol), (grow, gcol + 1) for the elements whose flag is set
     auto store_pair = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1) {
         if (!(w0 || w1)) return;
@@ -565,8 +570,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
 
     // row pass: each drain warp takes 16 tile rows, lanes on column pairs; applies
     // beta C + D + shift and stores the entries with col >= row (all of them when not sym)
-    for (int rr = 0; rr < kBM / kDrainWarps; ++rr) {
-        const int r = ew * (kBM / kDrainWarps) + rr;
+    for (int rr = 0; rr < kBM / DW; ++rr) {
+        const int r = ew * (kBM / DW) + rr;
         const int64_t grow = (int64_t)m0 + r;
 #pragma unroll
         for (int h = 0; h < TBN / 64; ++h) {
@@ -595,11 +600,11 @@ __global__ void __launch_bounds__(kThreads, MINB)
         }
     }
     if (!sym) return;
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kDrainWarps) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * DW) : "memory");
     // mirror pass: output row n0 + c holds tile column c for the entries with col > row;
     // each drain warp takes TBN / 8 tile columns, lanes on row pairs
-    for (int cc = 0; cc < TBN / kDrainWarps; ++cc) {
-        const int c = ew * (TBN / kDrainWarps) + cc;
+    for (int cc = 0; cc < TBN / DW; ++cc) {
+        const int c = ew * (TBN / DW) + cc;
         const int64_t grow = (int64_t)n0 + c;       // output row
         if (grow >= np) break;
 #pragma unroll
@@ -629,27 +634,31 @@ EncodeFn get_encode(std::string* err) {
     return fn;
 }
 
-template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB>
+template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB, int DW>
 cudaError_t launch_tc(const TcMaps& maps, const StepList& st, const Inst* in, const InstIO* io, const int* pre,
                       int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag, cudaStream_t s) {
-    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB>;
-    auto kern = k_tc_gemm<PA, PB, NPROD, F16, TBN, MINB>;
+    using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB, DW>;
+    auto kern = k_tc_gemm<PA, PB, NPROD, F16, TBN, MINB, DW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(tiles * st.count), kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0,
+    kern<<<(unsigned)(tiles * st.count), Cfg::kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0,
                                                                     sym, err_flag);
     return cudaGetLastError();
 }
 
 template <int PA, int PB, int NPROD, bool F16>
-cudaError_t dispatch_tbn(int tile_n, int ctas, const TcMaps& maps, const StepList& st, const Inst* in,
+cudaError_t dispatch_tbn(int tile_n, int ctas, int drain, const TcMaps& maps, const StepList& st, const Inst* in,
                          const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles, int b0, int sym,
                          int* err_flag, cudaStream_t s) {
     if (tile_n == 256)
-        return launch_tc<PA, PB, NPROD, F16, 256, 1>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+        return drain == 16
+                   ? launch_tc<PA, PB, NPROD, F16, 256, 1, 16>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym,
+                                                               err_flag, s)
+                   : launch_tc<PA, PB, NPROD, F16, 256, 1, 8>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym,
+                                                              err_flag, s);
     if (ctas == 2)
-        return launch_tc<PA, PB, NPROD, F16, 128, 2>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
-    return launch_tc<PA, PB, NPROD, F16, 128, 1>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+        return launch_tc<PA, PB, NPROD, F16, 128, 2, 8>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+    return launch_tc<PA, PB, NPROD, F16, 128, 1, 8>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
 }
 
 }  // namespace
@@ -692,12 +701,12 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
     return true;
 }
 
-cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step* steps, int nsteps, const Inst* in, const InstIO* io,
-                    const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0, int nb,
-                    int* err_flag, cudaStream_t s, std::string* err, int sym) {
+cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in,
+                    const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
+                    int nb, int* err_flag, cudaStream_t s, std::string* err, int sym) {
     if (tc_planes(prec) == 0 || (tile_n != 128 && tile_n != 256) || (ctas != 1 && ctas != 2) ||
-        (ctas == 2 && tile_n != 128) || nb < 1 || nb > kMaxBuckets || !err_flag || nsteps < 1 ||
-        nsteps > kMaxSteps) {
+        (ctas == 2 && tile_n != 128) || (drain != 8 && drain != 16) || (drain == 16 && tile_n != 256) || nb < 1 ||
+        nb > kMaxBuckets || !err_flag || nsteps < 1 || nsteps > kMaxSteps) {
         if (err) *err = "tc_gemm: unsupported precision, tile or bucket count";
         return cudaErrorInvalidValue;
     }
@@ -710,11 +719,11 @@ cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step* steps, int nstep
     st.count = nsteps;
     switch (prec) {
         case FO_PREC_BF16X3:
-            return dispatch_tbn<3, 3, 6, false>(tile_n, ctas, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            return dispatch_tbn<3, 3, 6, false>(tile_n, ctas, drain, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
         case FO_PREC_FP16X2:
-            return dispatch_tbn<2, 2, 3, true>(tile_n, ctas, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            return dispatch_tbn<2, 2, 3, true>(tile_n, ctas, drain, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
         case FO_PREC_BF16X1:
-            return dispatch_tbn<1, 1, 1, false>(tile_n, ctas, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            return dispatch_tbn<1, 1, 1, false>(tile_n, ctas, drain, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
         default: return cudaErrorInvalidValue;
     }
 }

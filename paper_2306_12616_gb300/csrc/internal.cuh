@@ -258,7 +258,8 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
 // [b0, b0 + nb) with maps[0..nb)), tile_n = 256 or 128 output columns per tile.
 // ctas = CTAs per SM (2 only with tile_n = 128). sym = 0 computes every tile of the full
 // product (fo_recurrence_product only).
-cudaError_t tc_gemm(int prec, int tile_n, int ctas, const Step* steps, int nsteps, const Inst* in, const InstIO* io,
+// drain = TMEM drain warps (8, or 16 with 256-wide tiles).
+cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in, const InstIO* io,
                     const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
                     int nb, int* err_flag, cudaStream_t s, std::string* err, int sym = 1);
 // Tiles of the full (non-symmetric) product.

@@ -72,13 +72,13 @@ def test_tile_configs_bit_identical(solver, prec):
     ns, kts, hs = batch(5, 3, 100, 700)
     hd = [to_dev(h) for h in hs]
     out = {}
-    for t, c in ((256, 1), (128, 1), (128, 2)):
-        prm = solver.params(300, 0.1, precision=prec, mu_mode="bisect", tile_n=t, tile_ctas=c)
+    for t, c, d in ((256, 1, 8), (256, 1, 16), (128, 1, 8), (128, 2, 8)):
+        prm = solver.params(300, 0.1, precision=prec, mu_mode="bisect", tile_n=t, tile_ctas=c, tile_drain=d)
         ps, res = solver.density_matrix_batched(hd, [n / 2 for n in ns], prm, kT=kts)
-        assert all(r["tile_n"] == t and r["tile_ctas"] == c for r in res)
-        out[(t, c)] = ps
-    for key in ((128, 1), (128, 2)):
-        for a, b in zip(out[(256, 1)], out[key]):
+        assert all(r["tile_n"] == t and r["tile_ctas"] == c and r["tile_drain"] == d for r in res)
+        out[(t, c, d)] = ps
+    for key in ((256, 1, 16), (128, 1, 8), (128, 2, 8)):
+        for a, b in zip(out[(256, 1, 8)], out[key]):
             assert torch.equal(a, b), key
 
 
