@@ -350,7 +350,7 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     const int ndiag = sh.n_tslots + 2;
     for (int j = 0; j < batch; ++j) {
         Inst& in = p->inst[j];
-        in.gram_blocks = gram_blocks_for(in.np, batch);
+        in.gram_blocks = gram_blocks_for(in.np, sh.is64);
         size_t o = off;
         o += align256(8 * (size_t)sh.km);             // c
         o += align256(8 * (size_t)sh.km);             // g

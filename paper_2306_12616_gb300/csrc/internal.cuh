@@ -183,7 +183,8 @@ cudaError_t launch_copy_out(const Inst* in, const InstIO* io, Work we, const Sha
 // Standalone packing of a float32 matrix into slot `slot` (fo_recurrence_product).
 cudaError_t launch_pack_f32(const float* A, int64_t n, int64_t lda, char* slot, int64_t np, int planes,
                             int fp16, float pscale, cudaStream_t s);
-int gram_blocks_for(int64_t np, int batch);
+// Blocks of the Frobenius-product kernel for one instance (upper-triangle chunks).
+int gram_blocks_for(int64_t np, int is64);
 
 // ------------------------------------------------------------------- mlp.cu
 // Learned chemical potential: 68 inputs (64 moments, N_e/N, kT_x, e_a/100, e_b/100),

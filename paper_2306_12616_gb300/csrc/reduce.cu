@@ -295,28 +295,35 @@ __global__ void k_diag_sums(const Inst* __restrict__ insts, int is64) {
 }
 
 // --------------------------------------------------------- Frobenius inner products
-// <S_{giant0+g}, S_{baby0+b}>_F over all np*np entries of one instance (the zero border
-// contributes nothing). A block covers kGChunks consecutive chunks of kChunk entries. Each
-// chunk of every matrix is staged in shared memory, matrix-major (row s holds the chunk of
-// matrix s, rows padded by 16 bytes), double-buffered: the next chunk is loaded into
-// registers before the current one is multiplied, and stored to the other buffer after, so
-// one barrier per chunk separates the phases and the global loads overlap the arithmetic.
-// Each warp owns up to kTPW 4 x 4 tiles of (giant, baby) pairs; a lane reads 16-byte
-// vectors of 8 rows and accumulates 4 x 4 x (16 / sizeof(T)) products per step. Every lane
-// sums at most kGChunks * kChunk / 32 products per pair in T; lanes are combined by float64
-// shuffles and blocks by the partial sums (instance-local block order, k_sum_partials).
-constexpr int kChunkBytes = 1024;   // one chunk of one matrix
-constexpr int kBlockBytes = 16384;  // entries of one matrix per block, in bytes of float32
+// <S_{giant0+g}, S_{baby0+b}>_F of one instance. Every matrix is symmetric, so the product is
+// the diagonal sum plus twice the strict upper triangle: only the chunks (kChunk consecutive
+// entries of one row) on or above the diagonal are read, and the baby entries are weighted
+// 2 above the diagonal, 1 on it and 0 below it when they are staged. A block covers
+// kGChunks consecutive upper chunks. Each chunk of every matrix is staged in shared memory,
+// matrix-major (row s holds the chunk of matrix s, rows padded by 16 bytes), double-buffered:
+// the next chunk is loaded into registers before the current one is multiplied, and stored
+// to the other buffer after, so one barrier per chunk separates the phases and the global
+// loads overlap the arithmetic. Each warp owns up to kTPW 4 x 4 tiles of (giant, baby) pairs;
+// a lane reads 16-byte vectors of 8 rows and accumulates 4 x 4 x (16 / sizeof(T)) products
+// per step. Every lane sums at most kGChunks * kChunk / 32 products per pair in T; lanes are
+// combined by float64 shuffles and blocks by the partial sums (k_sum_partials).
+constexpr int kChunkBytes = 512;    // one chunk of one matrix: 128 float32 / 64 float64
+constexpr int kGChunks = 32;        // chunks per block
 constexpr int kMaxQuads = 12;       // staged rows <= 48
 constexpr int kTPW = 2;
 constexpr int kGramThreads = 512;
+
+// Upper chunks of an np x np matrix: row r holds chunks floor(r / kc) .. np / kc - 1.
+__host__ __device__ inline int64_t upper_chunks(int64_t np, int kc) {
+    const int64_t cpr = np / kc;
+    return (int64_t)kc * cpr * (cpr + 1) / 2;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict__ insts, Work wgr, int giant0,
                                                           int ngiant, int baby0, int nbaby) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kChunk = kChunkBytes / (int)sizeof(T);      // entries per chunk
-    constexpr int kGChunks = kBlockBytes / 4 / kChunk;        // chunks per block
     constexpr int V = 16 / sizeof(T);          // elements per 16-byte vector
     constexpr int RS = kChunk + V;             // row stride (elements)
     constexpr int VPR = kChunk / V;            // vectors per row
@@ -326,7 +333,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     const int lb = blockIdx.x - wgr.pre[i];
     const char* base = in.slots;
     const int64_t slot_bytes = in.slot_bytes;
-    const int64_t nchunks = in.np * in.np / kChunk;   // np^2 is a multiple of 16384
+    const int64_t np = in.np;
+    const int64_t cpr = np / kChunk;                  // chunks per row
+    const int64_t nchunks = upper_chunks(np, kChunk);
     const int64_t c0 = (int64_t)lb * kGChunks;
     const int64_t c1 = c0 + kGChunks < nchunks ? c0 + kGChunks : nchunks;
     const int ng4 = (ngiant + 3) / 4, nb4 = (nbaby + 3) / 4;
@@ -336,32 +345,64 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     T* buf0 = reinterpret_cast<T*>(smem_raw);
     T* buf1 = buf0 + nrows * RS;
 
+    // (row, chunk of the row) of upper chunk c0; rows of band b (kChunk rows) hold cpr - b
+    int64_t row = 0, cc = 0;
+    if (c0 < c1) {
+        int64_t b = 0, cum = 0;
+        while (cum + (int64_t)kChunk * (cpr - b) <= c0) {
+            cum += (int64_t)kChunk * (cpr - b);
+            ++b;
+        }
+        const int64_t off = c0 - cum, per = cpr - b;
+        row = (int64_t)kChunk * b + off / per;
+        cc = b + off % per;
+    }
+    auto advance = [&](int64_t& r, int64_t& c) {
+        if (++c == cpr) {
+            ++r;
+            c = r / kChunk;
+        }
+    };
+
     // vectors this thread loads per chunk: q = threadIdx.x + j * blockDim.x < nrows * VPR
     constexpr int kMaxLoads = (4 * kMaxQuads * VPR + kGramThreads - 1) / kGramThreads;
     const int nq = nrows * VPR;
-    auto src_of = [&](int q, int64_t chunk) -> const float4* {
+    auto src_of = [&](int q, int64_t r, int64_t c) -> const float4* {
         const int srow = q / VPR, ev = (q % VPR) * V;
         int slot = -1;
         if (srow < 4 * ng4) { if (srow < ngiant) slot = giant0 + srow; }
         else { const int bb = srow - 4 * ng4; if (bb < nbaby) slot = baby0 + bb; }
         if (slot < 0) return nullptr;
-        return reinterpret_cast<const float4*>(reinterpret_cast<const T*>(base + slot_bytes * slot) +
-                                               chunk * kChunk + ev);
+        return reinterpret_cast<const float4*>(reinterpret_cast<const T*>(base + slot_bytes * slot) + r * np +
+                                               c * kChunk + ev);
     };
     float4 pre[kMaxLoads];
-    auto load = [&](int64_t chunk) {
+    auto load = [&](int64_t r, int64_t c) {
 #pragma unroll
         for (int j = 0; j < kMaxLoads; ++j) {
             const int q = threadIdx.x + j * kGramThreads;
-            const float4* src = q < nq ? src_of(q, chunk) : nullptr;
+            const float4* src = q < nq ? src_of(q, r, c) : nullptr;
             pre[j] = src ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
-    auto store = [&](T* buf) {
+    // stores the prefetched chunk (row r, chunk c), baby entries weighted 2 / 1 / 0 above /
+    // on / below the diagonal
+    auto store = [&](T* buf, int64_t r, int64_t c) {
 #pragma unroll
         for (int j = 0; j < kMaxLoads; ++j) {
             const int q = threadIdx.x + j * kGramThreads;
-            if (q < nq) *reinterpret_cast<float4*>(buf + (q / VPR) * RS + (q % VPR) * V) = pre[j];
+            if (q >= nq) continue;
+            const int srow = q / VPR, ev = (q % VPR) * V;
+            T v[V];
+            *reinterpret_cast<float4*>(v) = pre[j];
+            if (srow >= 4 * ng4) {
+#pragma unroll
+                for (int u = 0; u < V; ++u) {
+                    const int64_t col = c * kChunk + ev + u;
+                    v[u] *= col > r ? T(2) : (col == r ? T(1) : T(0));
+                }
+            }
+            *reinterpret_cast<float4*>(buf + srow * RS + ev) = *reinterpret_cast<const float4*>(v);
         }
     };
 
@@ -372,15 +413,17 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
         for (int q = 0; q < 16; ++q) acc[t][q] = T(0);
 
     if (c0 < c1) {
-        load(c0);
-        store(buf0);
+        load(row, cc);
+        store(buf0, row, cc);
     }
     __syncthreads();
     for (int64_t c = c0; c < c1; ++c) {
         T* cur = ((c - c0) & 1) ? buf1 : buf0;
         T* nxt = ((c - c0) & 1) ? buf0 : buf1;
         const bool more = c + 1 < c1;
-        if (more) load(c + 1);
+        int64_t nrow = row, ncc = cc;
+        advance(nrow, ncc);
+        if (more) load(nrow, ncc);
 #pragma unroll
         for (int t = 0; t < kTPW; ++t) {
             const int tile = warp + t * nwarps;
@@ -403,7 +446,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
                         for (int v = 0; v < V; ++v) acc[t][4 * a + b] = fma(gv[a][v], bv[b][v], acc[t][4 * a + b]);
             }
         }
-        if (more) store(nxt);
+        if (more) store(nxt, nrow, ncc);
+        row = nrow;
+        cc = ncc;
         __syncthreads();
     }
     const int npairs = ngiant * nbaby;
@@ -578,11 +623,9 @@ cudaError_t launch_diag_sums(const Inst* in, int batch, int count, const Shape& 
     return cudaGetLastError();
 }
 
-int gram_blocks_for(int64_t np, int batch) {
-    (void)batch;
-    // kBlockBytes / 4 entries per block (for float32 and float64 alike)
-    const int64_t per = kBlockBytes / 4;
-    return (int)((np * np + per - 1) / per);
+int gram_blocks_for(int64_t np, int is64) {
+    const int64_t u = upper_chunks(np, kChunkBytes / (is64 ? 8 : 4));
+    return (int)((u + kGChunks - 1) / kGChunks);
 }
 
 cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0, int nbaby,
