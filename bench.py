@@ -54,9 +54,19 @@ def parse():
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batch measurement")
     ap.add_argument("--batch-count", type=int, default=512, help="instances of the batch measurement")
+    ap.add_argument("--tile", default="",
+                    help="force the product kernel's tile as NxCTASxDRAIN (e.g. 256x1x16) instead of "
+                         "autotuning it; profiling runs use this so the captured kernel is the timed one")
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the batch (profiling runs); the JSON line then describes the batch")
     return ap.parse_args()
+
+
+def tile_args(spec: str) -> dict:
+    if not spec:
+        return {}
+    tn, ctas, drain = (int(x) for x in spec.lower().split("x"))
+    return {"tile_n": tn, "tile_ctas": ctas, "tile_drain": drain}
 
 
 def dist_env():
@@ -186,19 +196,26 @@ def eigh_baseline(hs: dict, results: dict, kT: float, reps: int = 2) -> dict:
 
 
 # ------------------------------------------------------------- 512-instance batch
-def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300):
+def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300, rank=0, world=1,
+                tile=None):
     """Density matrices per second of the batch of `count` tight-binding instances with N
     log-uniform in [64, 1024] and kT ~ U(0.05, 0.2) eV, replayed as one CUDA graph per batch
-    (L2 flushed before each), plus one profiled eager pass for the product roofline."""
+    (L2 flushed before each), plus one profiled eager pass for the product roofline. With
+    several ranks the instances are sharded by cost (no collective on the data path) and the
+    batch time is the maximum over ranks."""
     import torch
     import synth
     from paper_2306_12616_gb300 import FO_FLAG_GRAPH
-    ns = [int(n) for n in synth.batch_sizes(count, 4000)]
-    kts = [float(t) for t in synth.batch_temperatures(count, 4000)]
-    hs = [torch.from_numpy(synth.tight_binding(n, 4000 + i)).to(flush.device) for i, n in enumerate(ns)]
+    from paper_2306_12616_gb300.dist import rank_share, reduce_max
+    ns_all = [int(n) for n in synth.batch_sizes(count, 4000)]
+    kts_all = [float(t) for t in synth.batch_temperatures(count, 4000)]
+    mine = rank_share(ns_all, rank, world)
+    ns, kts = [ns_all[i] for i in mine], [kts_all[i] for i in mine]
+    hs = [torch.from_numpy(synth.tight_binding(ns_all[i], 4000 + i)).to(flush.device) for i in mine]
     ps = [torch.empty_like(h) for h in hs]
     ne = [n / 2 for n in ns]
-    prm = solver.params(n_terms, 0.1, precision=precision, mu_mode="bisect", flags=FO_FLAG_GRAPH)
+    prm = solver.params(n_terms, 0.1, precision=precision, mu_mode="bisect", flags=FO_FLAG_GRAPH,
+                        **(tile or {}))
     _, res = solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps)   # plan, autotune, capture
     ok = all(r["status"] == 0 for r in res)
     worst_tr = max(abs(r["trace"] - n / 2) / n for r, n in zip(res, ns))
@@ -213,9 +230,9 @@ def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-    ms = statistics.median(times)
+    ms = reduce_max(statistics.median(times))
     # profiled eager pass: stage times and the product kernel's achieved rate
-    prm_e = solver.params(n_terms, 0.1, precision=precision, mu_mode="bisect")
+    prm_e = solver.params(n_terms, 0.1, precision=precision, mu_mode="bisect", **(tile or {}))
     solver.density_matrix_batched(hs, ne, prm_e, kT=kts, outs=ps, sync=False)
     torch.cuda.synchronize()
     solver.profile_enable(True)
@@ -229,9 +246,11 @@ def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300)
     return {"workload": f"{count} tight-binding H, N log-uniform in [64, 1024] (multiples of 4), "
                         f"kT ~ U(0.05, 0.2) eV, N_e = N/2, {n_terms} terms, {precision}, mu by bisection",
             "dm_per_s": count / (ms * 1e-3), "ms_per_batch": ms, "steps": steps, "graph": True,
-            "sum_n3": float(sum(float(n) ** 3 for n in ns)), "all_status_ok": ok,
+            "ranks": world, "instances_this_rank": len(ns),
+            "scaling": "strong" if world > 1 else None,
+            "sum_n3": float(sum(float(n) ** 3 for n in ns_all)), "all_status_ok": ok,
             "worst_trace_err_over_N": worst_tr, "tile_n": res[0]["tile_n"],
-            "tile_ctas": res[0]["tile_ctas"],
+            "tile_ctas": res[0]["tile_ctas"], "tile_drain": res[0]["tile_drain"],
             "eager_ms_per_batch": prof["call"]["ms"],
             "products_achieved_tflops": pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] > 0 else None,
             "products_share": pr["ms"] / max(1e-9, prof["call"]["ms"]),
@@ -273,6 +292,7 @@ def main():
     import torch
     import synth
     from paper_2306_12616_gb300 import Solver
+    from paper_2306_12616_gb300.dist import reduce_max
 
     if world > 1:
         import torch.distributed as dist
@@ -283,7 +303,7 @@ def main():
         solver = Solver(local)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         b = bench_batch(solver, torch.cuda.current_stream(), flush, max(1, args.steps), args.precision,
-                        count=args.batch_count)
+                        count=args.batch_count, rank=rank, world=world, tile=tile_args(args.tile))
         if rank == 0:
             print(json.dumps({"metric": "density matrices/s (batch)", "value": b["dm_per_s"],
                               "unit": "density matrices/s", "n_gpus": world, "steps": args.steps,
@@ -295,7 +315,7 @@ def main():
     ns = [int(x) for x in args.ns.split(",")]
     solver = Solver(local)
     stream = torch.cuda.current_stream()
-    prm = solver.params(args.n_terms, KT, precision=args.precision, mu_mode="bisect")
+    prm = solver.params(args.n_terms, KT, precision=args.precision, mu_mode="bisect", **tile_args(args.tile))
 
     # inputs resident in HBM (a different replica per rank)
     hs, ps, hcpu = {}, {}, {}
@@ -351,11 +371,7 @@ def main():
     prof = solver.profile_read(reset=True)
     solver.profile_enable(False)
     clk = clocks.stop()
-    total_ms = sum(per_step)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(per_step))
     ms_per_step = total_ms / args.steps
     value = world * len(ns) / (ms_per_step * 1e-3)
 
@@ -369,7 +385,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         solver.density_matrix_batched_host(hin, nel, prm, hout)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e_ms = reduce_max((time.perf_counter() - t0) * 1e3 / e2e_steps)
     e2e_bytes = sum(8 * n * n for n in ns)
 
     pk, pk_kind = peaks()
@@ -396,7 +412,8 @@ def main():
             "traffic": (trec["bytes_per_launch"] if trec else None),
             "traffic_note": (trec["note"] if trec else "no ncu capture of the current kernel source")}
     batch = None if args.no_batch else bench_batch(solver, stream, flush, max(3, args.steps // 2),
-                                                    args.precision, count=args.batch_count)
+                                                    args.precision, count=args.batch_count,
+                                                    rank=rank, world=world, tile=tile_args(args.tile))
     eigh = None if args.no_fp64_check else eigh_baseline(hs, results, KT)
     cb = cpu_baseline(ns) if (rank == 0 and world == 1) else None
     per_n = {}
@@ -404,7 +421,7 @@ def main():
         per_n[str(n)] = {"n_gemm": results[n]["n_gemm"], "k": results[n]["k"], "m": results[n]["m"],
                          "bisect_iters": results[n]["bisect_iters"], "mu_eV": results[n]["mu"],
                          "status": results[n]["status"], "tile_n": results[n]["tile_n"],
-                         "tile_ctas": results[n]["tile_ctas"]}
+                         "tile_ctas": results[n]["tile_ctas"], "tile_drain": results[n]["tile_drain"]}
         if n in accuracy:
             per_n[str(n)].update(accuracy[n])
             per_n[str(n)]["fp64_gpu_ms"] = fp64_ms[n]

@@ -103,7 +103,8 @@ typedef struct {
                                  bisection fallback; 0 = 2, < 0 = none */
     int32_t tile_n;           /* tensor-core tile width: 0 = autotune per plan, or 128 / 256 */
     int32_t tile_ctas;        /* CTAs per SM of the product kernel: 0 = autotune, 1, or 2
-                                 (2 only with 128-wide tiles); set together with tile_n */
+                                 (2 only with 128-wide tiles); set together with tile_n;
+                                 other values fail with FO_ERR_ARG */
     int32_t lanczos_steps;    /* 0: Gershgorin bounds. 1..64: tighter bounds from that many
                                  float64 Lanczos steps on H (start vector: splitmix64 draws),
                                  the extreme Ritz values widened by their residuals
@@ -111,7 +112,8 @@ typedef struct {
                                  Gershgorin interval. Not a guaranteed enclosure; ignored with
                                  use_given_bounds */
     int32_t tile_drain;       /* warps draining the tensor-memory accumulators: 0 = autotune,
-                                 8, or 16 (with tile_n = 256); set together with tile_n */
+                                 8, or 16 (with tile_n = 256); set together with tile_n;
+                                 other values fail with FO_ERR_ARG */
     int32_t reserved;
 } fo_params;
 
