@@ -45,7 +45,7 @@ SPLIT = {"bf16x3": 6, "fp16x2": 3, "bf16x1": 1, "fp64": 1}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", default="bf16x3", choices=("bf16x3", "fp16x2", "bf16x1", "fp64"))
@@ -99,9 +99,15 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(gpu_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "100", "-i", str(gpu_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # start timing only once sampling has begun (nvidia-smi takes a moment to start)
+        t0 = time.monotonic()
+        while self.proc is not None and time.monotonic() - t0 < 1.5:
+            if os.path.getsize(self.path) > 0 or self.proc.poll() is not None:
+                break
+            time.sleep(0.02)
 
     def stop(self) -> dict:
         if self.proc is None:
