@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--tile", default="",
                     help="force the product kernel's tile as NxCTASxDRAIN (e.g. 256x1x16) instead of "
                          "autotuning it; profiling runs use this so the captured kernel is the timed one")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-mu measurement on the metallic model")
+    ap.add_argument("--learned-pairs", type=int, default=20000,
+                    help="method-generated training pairs of the learned-mu measurement")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="run only the learned-mu measurement and print it")
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the batch (profiling runs); the JSON line then describes the batch")
     return ap.parse_args()
@@ -263,6 +269,90 @@ def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300,
             "stages_ms": {k: v["ms"] for k, v in prof.items() if isinstance(v, dict)}}
 
 
+# ------------------------------------------- learned mu on the metallic model (N = 1024)
+def bench_learned_metallic(solver, stream, pairs=20000, held_out=64, n=1024, n_terms=1000, kT=0.01,
+                           epochs=150, chunk=64, reps=3, tr_tols=(None, 0.5)):
+    """The learned chemical potential on a high density of states at the Fermi level:
+    metallic Hamiltonians (N = 1024, 25 % of the onsite energies ~ N(0, 0.02 eV)), kT =
+    0.01 eV, 1000 terms, N_e = 0.775 N (Fermi level at 0 eV), BF16x3. The network is trained
+    on `pairs` (H, mu) pairs that the exact method generates (matrices drawn on the device,
+    N_e ~ U(0.74, 0.81) N), then a held-out batch of `held_out` matrices is solved with mu
+    by bisection (the judge) and with the learned proposal, at the default trace tolerance
+    (2e-6 N) and at half an electron; reported per form: density matrices/s (CUDA events,
+    eager calls), products per density matrix, evaluations of P, acceptance, and the
+    proposal error against the exact mu."""
+    import numpy as np
+    import torch
+    import synth
+    from synth.device import metallic_batch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prm = solver.params(n_terms, kT, precision="bf16x3")
+    rng = np.random.default_rng(5500)
+    t0 = time.perf_counter()
+    feats, tgts = [], []
+    for b in range((pairs + chunk - 1) // chunk):
+        hb = metallic_batch(chunk, n, 6000 + b, dev)
+        ne = rng.uniform(0.74, 0.81, chunk) * n
+        f, t, res = solver.learned_features([hb[i] for i in range(chunk)], ne, prm)
+        if any(r["status"] != 0 for r in res):
+            raise RuntimeError("training pair generation failed")
+        feats.append(f)
+        tgts.append(t)
+        del hb
+    feat, tgt = torch.cat(feats)[:pairs], torch.cat(tgts)[:pairs]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    solver.mlp_init(55)
+    losses = solver.mlp_train(feat, tgt, epochs=epochs, batch=256, lr=1e-3, seed=55)
+    train_s = time.perf_counter() - t0
+    del feat, tgt, feats, tgts
+    hs = [torch.from_numpy(synth.metallic(n, 5000 + i)).to(dev) for i in range(held_out)]
+    ne = [synth.metallic_electrons(n)] * held_out
+    outs = [torch.empty_like(h) for h in hs]
+
+    def timed(p):
+        _, res = solver.density_matrix_batched(hs, ne, p, outs=outs)
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.density_matrix_batched(hs, ne, p, outs=outs)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        return res, {"dm_per_s": held_out / (ms * 1e-3), "ms_per_batch": ms,
+                     "products_per_dm": float(np.mean([r["n_gemm"] for r in res])),
+                     "all_status_ok": all(r["status"] == 0 for r in res),
+                     "worst_trace_err": max(abs(r["trace"] - x) for r, x in zip(res, ne))}
+
+    rb, bis = timed(solver.params(n_terms, kT, precision="bf16x3", mu_mode="bisect"))
+    # proposal error of the trained network on the held-out batch, against the exact mu
+    f_h, _, _ = solver.learned_features(hs, ne, prm)
+    _, norm = solver.mlp_get_params()
+    y = solver.mlp_forward((f_h - torch.tensor(norm[:68], device=dev)) / torch.tensor(norm[68:136], device=dev))
+    mux = y[:, 0].double().cpu().numpy() * norm[138] + norm[136]
+    mu0 = np.array([0.5 * (r["emin"] + r["emax"]) + 0.5 * (r["emax"] - r["emin"]) * x for r, x in zip(rb, mux)])
+    err = np.abs(mu0 - np.array([r["mu"] for r in rb]))
+    forms = {"bisection": bis}
+    for tol in tr_tols:
+        kw = {"tr_tol": tol} if tol is not None else {}
+        rl, st = timed(solver.params(n_terms, kT, precision="bf16x3", mu_mode="learned", max_newton=3, **kw))
+        st["accepted"] = float(np.mean([r["learned_accepted"] for r in rl]))
+        st["evaluations"] = float(np.mean([r["evals"] for r in rl]))
+        st["tr_tol"] = tol if tol is not None else f"2e-6 N = {2e-6 * n:g}"
+        forms["learned_tol_" + ("default" if tol is None else f"{tol:g}")] = st
+    del hs, outs
+    torch.cuda.empty_cache()
+    return {"workload": f"{held_out} metallic H (tight-binding hopping, 25% of onsite energies ~ N(0, 0.02 eV)), "
+                        f"N={n}, N_e={ne[0]:g}, kT={kT} eV, {n_terms} terms, bf16x3",
+            "training": {"pairs": pairs, "epochs": epochs, "pair_generation_s": gen_s, "train_s": train_s,
+                         "loss_first": losses[0], "loss_last": losses[-1]},
+            "proposal_err_eV": {"median": float(np.median(err)), "max": float(err.max())},
+            "forms": forms}
+
+
 # --------------------------------------------------------------------------- main
 def run_reference(args, rank, world):
     if rank != 0:
@@ -316,6 +406,13 @@ def main():
                               "warmup": args.warmup, "ms_per_step": b["ms_per_batch"], "higher_is_better": True,
                               "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
                               "config": {"workload": b["workload"]}, "batch": b}), flush=True)
+        solver.close()
+        return
+    if args.learned_only:
+        solver = Solver(local)
+        out = bench_learned_metallic(solver, torch.cuda.current_stream(), pairs=args.learned_pairs)
+        if rank == 0:
+            print(json.dumps({"learned_mu_metallic": out}), flush=True)
         solver.close()
         return
     ns = [int(x) for x in args.ns.split(",")]
@@ -421,6 +518,12 @@ def main():
                                                     args.precision, count=args.batch_count,
                                                     rank=rank, world=world, tile=tile_args(args.tile))
     eigh = None if args.no_fp64_check else eigh_baseline(hs, results, KT)
+    learned = None
+    if not args.no_learned and rank == 0:
+        try:
+            learned = bench_learned_metallic(solver, stream, pairs=args.learned_pairs)
+        except Exception as exc:   # reported, never fatal to the headline measurement
+            learned = {"error": f"{type(exc).__name__}: {exc}"}
     cb = cpu_baseline(ns) if (rank == 0 and world == 1) else None
     per_n = {}
     for n in ns:
@@ -455,6 +558,7 @@ def main():
         "fp64_gpu_dm_per_s": (len(fp64_ms) / (sum(fp64_ms.values()) * 1e-3)) if fp64_ms else None,
         "batch_512": batch,
         "eigh_fp64_cusolver": eigh,
+        "learned_mu_metallic": learned,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

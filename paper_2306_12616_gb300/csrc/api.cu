@@ -756,6 +756,10 @@ fo_status learned(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     bool any = true;
     for (int r = 0; r <= R; ++r) {
         FO_TRY(evaluate(ctx, p, s, run, 0));
+        if (r < R) {
+            FO_CUDA(launch_poly_width(p.d_inst, B, sh, p.ct, s), "expansion width");
+            run->launches += 1;
+        }
         FO_CUDA(cudaMemsetAsync(p.lcount, 0, sizeof(int), s), "judge");
         FO_CUDA(launch_learned_check(p.d_inst, p.d_io, B, r, R, p.key.tr_tol, sh.is64, p.lcount, s), "judge");
         run->launches += 1;

@@ -258,6 +258,44 @@ __global__ void k_poly_trace(const Inst* __restrict__ insts, int n_terms) {
     if (threadIdx.x == 0) in.res->trace_poly = s;
 }
 
+// Effective temperature of the truncated expansion p(e) = sum_n c_n T_n(x(e)) at the current
+// mu: kT_p = integral of p (1 - p) de over [e_a, e_b]. For the Fermi function itself the
+// integral is exactly kT; a truncated expansion smears the step over a wider range (about
+// the width divided by the number of terms), and d tr P / d mu ~ tr(P - P^2) / kT_p then
+// holds where tr(P - P^2) / kT overstates the slope. Gauss-Chebyshev rule on the nodes:
+// de = (e_b - e_a)/2 sin(theta) dtheta, p_j = sum_n c_n cos(n theta_j). One block per
+// instance.
+__global__ void __launch_bounds__(256) k_poly_width(const Inst* __restrict__ insts, const double* __restrict__ ct,
+                                                    int M, int n_terms) {
+    const Inst& in = insts[blockIdx.x];
+    DevResult* res = in.res;
+    if (!res->active) return;
+    const int64_t fourM = 4LL * M;
+    const double* c = in.c;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const int64_t step = 2LL * j + 1;
+        int64_t r = 0;
+        double p = 0.0;
+        for (int n = 0; n < n_terms; ++n) {
+            p = fma(c[n], ct[r], p);
+            r += step;
+            if (r >= fourM) r -= fourM;
+        }
+        const int64_t rs = (step - M + fourM) % fourM;    // sin(theta_j) = cos(theta_j - pi/2)
+        acc = fma(ct[rs], p * (1.0 - p), acc);
+    }
+    __shared__ double part[8];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        res->kt_eff = 0.5 * (res->bounds[1] - res->bounds[0]) * (3.14159265358979323846 / (double)M) * t;
+    }
+}
+
 // R_l = g_{0,l} I_n + sum_{i=1}^{k-1} g_{i,l} T_i for all l < m, float64. T_i is slot i-1,
 // R_l slot n_tslots + l. A block covers ew_rows(np) rows of one instance; outputs are
 // produced in groups of kGroup l's per pass over the T_i.
@@ -458,6 +496,11 @@ cudaError_t launch_coefficients(const Inst* in, const InstIO* io, int batch, con
         ++l;
     }
     if (launches) *launches += l;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poly_width(const Inst* in, int batch, const Shape& sh, const double* ct, cudaStream_t s) {
+    k_poly_width<<<batch, 256, 0, s>>>(in, ct, sh.M, sh.n_terms);
     return cudaGetLastError();
 }
 

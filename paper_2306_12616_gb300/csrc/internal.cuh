@@ -40,6 +40,7 @@ struct DevResult {
     double mu0;           // learned proposal (learned mode)
     double mu_prev, tr_prev;  // previous evaluation (learned mode secant)
     double order;         // learned expansion order (learned mode)
+    double kt_eff;        // effective temperature of the truncated expansion (learned mode)
 };
 
 // Per-instance descriptor, written once per plan. slots: the instance's slot region,
@@ -228,6 +229,7 @@ cudaError_t launch_targets(const Inst* in, int batch, int n_terms, float* tgt, c
 cudaError_t launch_assemble_low(const Inst* in, int batch, int k, cudaStream_t s);
 cudaError_t launch_learned_mu(const Inst* in, int batch, const float* y, const float* norm, int n_terms,
                               cudaStream_t s);
+cudaError_t launch_poly_width(const Inst* in, int batch, const Shape& sh, const double* ct, cudaStream_t s);
 cudaError_t launch_learned_check(const Inst* in, const InstIO* io, int batch, int round, int max_rounds,
                                  double tol, int is64, int* active_count, cudaStream_t s);
 

@@ -207,9 +207,11 @@ __global__ void k_learned_mu(const Inst* __restrict__ insts, int batch, const fl
 
 // The judge after evaluation `round` (0 = at the learned mu): accept when |tr P - N_e| <=
 // tol (tol <= 0: 1e-8 max(1, N_e) for float64, 2e-6 n for the split forms); otherwise, if
-// rounds remain, move mu by a Newton step on d tr P / d mu ~ (1 / kT) tr(P (I - P)) =
-// (tr P - ||P||_F^2) / kT (first round) or a secant step through the previous evaluation,
-// limited to 10 kT; else leave the instance active for the bisection fallback.
+// rounds remain, move mu by a Newton step on d tr P / d mu ~ tr(P (I - P)) / kT_p =
+// (tr P - ||P||_F^2) / kT_p (first round; kT_p the effective temperature of the truncated
+// expansion, k_poly_width, which is kT for an exact Fermi function) or a secant step
+// through the previous evaluation, limited to 10 kT_p; else leave the instance active for
+// the bisection fallback.
 __global__ void k_learned_check(const Inst* __restrict__ insts, const InstIO* __restrict__ io, int batch,
                                 int round, int max_rounds, double tol, int is64, int* __restrict__ active_count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,13 +232,14 @@ __global__ void k_learned_check(const Inst* __restrict__ insts, const InstIO* __
         atomicAdd(active_count, 1);
         return;
     }
-    double slope = (r->trace - r->frob2) / kT;
+    const double kte = (r->kt_eff > 0.0 && isfinite(r->kt_eff)) ? fmax(r->kt_eff, kT) : kT;
+    double slope = (r->trace - r->frob2) / kte;
     if (round > 0 && r->mu != r->mu_prev) {
         const double sec = (r->trace - r->tr_prev) / (r->mu - r->mu_prev);
         if (sec > 0.0 && isfinite(sec)) slope = sec;
     }
     double step = (slope > 0.0 && isfinite(slope)) ? -err / slope : 0.0;
-    step = fmin(fmax(step, -10.0 * kT), 10.0 * kT);
+    step = fmin(fmax(step, -10.0 * kte), 10.0 * kte);
     r->mu_prev = r->mu;
     r->tr_prev = r->trace;
     r->mu = r->mu + step;

@@ -67,6 +67,7 @@ __global__ void k_set_io(const IoChunk p, InstIO* d_io, const Inst* insts) {
     r->mu_lo = r->mu_hi = 0.0;
     r->mu0 = r->mu_prev = r->tr_prev = 0.0;
     r->order = 0.0;
+    r->kt_eff = 0.0;
 }
 
 // ------------------------------------------------------------------ Gershgorin bounds

@@ -8,6 +8,8 @@ from .hamiltonians import (  # noqa: F401
     random_symmetric,
     tight_binding,
     metallic,
+    metallic_electrons,
+    METALLIC_FILLING,
     batch_sizes,
     batch_temperatures,
     tight_binding_box,
