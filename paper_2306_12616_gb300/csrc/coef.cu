@@ -7,6 +7,7 @@
 // pipeline needs is cos(n theta_j) = cos(pi r / (2M)) with r = n (2j+1) mod 4M, so one
 // table ct[r] = cospi(r / (2M)), r < 4M, serves the nodes, the DCT and the DOS weights.
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <cuda_fp16.h>
 
 #include "internal.cuh"
@@ -372,17 +373,18 @@ __device__ __forceinline__ Split3 split_value(float v, int fp16, float pscale) {
     return o;
 }
 
-// R_l for l0 <= l < min(l0 + MAXM, m) (MAXM a multiple of 4; m > 32 takes two launches).
-// The coefficients are staged transposed, gsh[t * MAXM + j] = g_{t,l0+j} (zero beyond m),
-// so that one 16-byte shared load serves four R_l (8 FMAs on two entries). Each thread takes
-// two consecutive entries and loads them from eight T_t at a time before using them, which
-// keeps enough bytes in flight for the HBM bandwidth at 2-3 blocks per SM.
-constexpr int kCtDepth = 8;
+// R_l for l0 <= l < min(l0 + MAXM, m) (MAXM = m rounded up to a multiple of 4, at most 32;
+// m > 32 takes several launches). The coefficients are staged transposed, gsh[t * MAXM + j] =
+// g_{t,l0+j} (zero beyond m), so that one 16-byte shared load serves four R_l. The block's
+// entries are taken 256 at a time (one per thread); the 256-entry segments of T_1..T_{k-1}
+// of the next S - 1 steps are copied into an S-stage shared-memory ring by cp.async, so the
+// loads in flight do not depend on registers (S = 4 stages of 19 KB at k = 20).
+constexpr int kCtEntries = 256;
 
-template <int MAXM>
-__global__ void __launch_bounds__(256) k_contract_f32(const Inst* __restrict__ insts, Work we, int k,
-                                                      int m, int l0, int n_tslots, int planes_last, int fp16,
-                                                      float pscale, int* dbg) {
+template <int MAXM, int S>
+__global__ void __launch_bounds__(kCtEntries, 2) k_contract_f32(const Inst* __restrict__ insts, Work we, int k,
+                                                                int m, int l0, int n_tslots, int planes_last,
+                                                                int fp16, float pscale, int* dbg) {
     extern __shared__ __align__(16) float fsh[];
     const int i = find_inst(we.pre, 0, we.count, blockIdx.x);
     const Inst& in = insts[i];
@@ -391,66 +393,86 @@ __global__ void __launch_bounds__(256) k_contract_f32(const Inst* __restrict__ i
         const int t = q / MAXM, l = l0 + q - t * MAXM;
         fsh[q] = l < m ? (float)in.g[l * k + t] : 0.0f;
     }
-    __syncthreads();
+    const int nt = k - 1;                                   // T_1 .. T_{k-1}
+    float* ring = fsh + ((k * MAXM + 3) & ~3);
+    const int stage = nt * kCtEntries;
     const int64_t np = in.np, n = in.n;
     const int rows = ew_rows(np);
     const int64_t r0 = (int64_t)(blockIdx.x - we.pre[i]) * rows;
     const int64_t r1 = r0 + rows < np ? r0 + rows : np;
+    const int64_t e0 = r0 * np, e1 = r1 * np;             // multiples of 128 entries
+    const int steps = (int)((e1 - e0 + kCtEntries - 1) / kCtEntries);
     const int64_t tstride = in.slot_bytes / 4;
     const int64_t ps = np * np;
     const float* tbase = reinterpret_cast<const float*>(in.slots);
     float* rbase = reinterpret_cast<float*>(in.slots + n_tslots * in.slot_bytes);
-    for (int64_t idx = r0 * np + 2 * threadIdx.x; idx < r1 * np; idx += 2 * blockDim.x) {
-        float2 acc[MAXM];
+    // copies of the segments of step j (entries e0 + 256 j ...) into stage j % S: 16 bytes each,
+    // none past the block's last entry
+    // thread tid copies vector v4 = 4 (tid % 64) of the segments t = tid / 64, tid / 64 + 4, ...
+    constexpr int kTPS = kCtEntries / (kCtEntries / 4);   // segments started per pass: 4
+    const int v4 = 4 * (threadIdx.x % (kCtEntries / 4)), tq = threadIdx.x / (kCtEntries / 4);
+    auto issue = [&](int j) {
+        const int64_t base = e0 + (int64_t)j * kCtEntries + v4;
+        if (base >= e1) return;
+        float* dst = ring + (j % S) * stage + v4;
+        const float* src = tbase + (int64_t)tq * tstride + base;
+#pragma unroll 1
+        for (int t = tq; t < nt; t += kTPS, src += kTPS * tstride) cp_async16(dst + t * kCtEntries, src);
+    };
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j) acc[j] = make_float2(0.f, 0.f);
-        for (int t0 = 1; t0 < k; t0 += kCtDepth) {
-            float2 v[kCtDepth];
+    for (int s = 0; s < S - 1; ++s) {
+        if (s < steps) issue(s);
+        cp_async_commit();
+    }
+    __syncthreads();   // the coefficient table
+    for (int j = 0; j < steps; ++j) {
+        cp_async_wait<S - 2>();
+        __syncthreads();   // step j's segments have landed; the stage of step j - 1 is free
+        if (j + S - 1 < steps) issue(j + S - 1);
+        cp_async_commit();
+        const int64_t idx = e0 + (int64_t)j * kCtEntries + threadIdx.x;
+        if (idx >= e1) continue;
+        const float* seg = ring + (j % S) * stage + threadIdx.x;
+        f32x2 acc[MAXM / 2];   // (R_{l0+2p}, R_{l0+2p+1}) at this entry
 #pragma unroll
-            for (int u = 0; u < kCtDepth; ++u)
-                v[u] = t0 + u < k ? __ldg(reinterpret_cast<const float2*>(tbase + (int64_t)(t0 + u - 1) * tstride + idx))
-                                  : make_float2(0.f, 0.f);
+        for (int q = 0; q < MAXM / 2; ++q) acc[q] = 0ull;
+#pragma unroll 2
+        for (int t = 0; t < nt; ++t) {
+            const float v = seg[t * kCtEntries];
+            const f32x2 vv = pack2(v, v);
+            const ulonglong2* gt = reinterpret_cast<const ulonglong2*>(fsh + (t + 1) * MAXM);
 #pragma unroll
-            for (int u = 0; u < kCtDepth; ++u) {
-                if (t0 + u >= k) break;
-                const float* gt = fsh + (t0 + u) * MAXM;
-#pragma unroll
-                for (int j4 = 0; j4 < MAXM; j4 += 4) {
-                    const float4 g4 = *reinterpret_cast<const float4*>(gt + j4);
-                    acc[j4].x = fmaf(g4.x, v[u].x, acc[j4].x);
-                    acc[j4].y = fmaf(g4.x, v[u].y, acc[j4].y);
-                    acc[j4 + 1].x = fmaf(g4.y, v[u].x, acc[j4 + 1].x);
-                    acc[j4 + 1].y = fmaf(g4.y, v[u].y, acc[j4 + 1].y);
-                    acc[j4 + 2].x = fmaf(g4.z, v[u].x, acc[j4 + 2].x);
-                    acc[j4 + 2].y = fmaf(g4.z, v[u].y, acc[j4 + 2].y);
-                    acc[j4 + 3].x = fmaf(g4.w, v[u].x, acc[j4 + 3].x);
-                    acc[j4 + 3].y = fmaf(g4.w, v[u].y, acc[j4 + 3].y);
-                }
+            for (int j4 = 0; j4 < MAXM / 4; ++j4) {
+                const ulonglong2 g = gt[j4];   // (g_{t,l}, g_{t,l+1}), (g_{t,l+2}, g_{t,l+3})
+                ffma2(acc[2 * j4], g.x, vv);
+                ffma2(acc[2 * j4 + 1], g.y, vv);
             }
         }
-        const int64_t r = idx / np, c0 = idx - r * np;
-        const bool d0 = (r < n) && (c0 == r), d1 = (r < n) && (c0 + 1 == r);
+        // row and column of the entry (32-bit: a block spans fewer than 2^31 entries)
+        const int off = (int)(idx - r0 * np);
+        const int64_t r = r0 + off / (int)np, c = off % (int)np;
+        const bool dg = (r < n) && (c == r);
+        float* dst = rbase + (int64_t)l0 * tstride + idx;
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-            const int l = l0 + j;
+        for (int q = 0; q < MAXM; ++q, dst += tstride) {
+            const int l = l0 + q;
             if (l >= m) break;
-            float2 v = acc[j];
-            if (d0) v.x += fsh[j];   // g_{0,l}: the t = 0 row
-            if (d1) v.y += fsh[j];
-            float* dst = rbase + (int64_t)l * tstride + idx;
-            if (!FO_CHK(dbg, (reinterpret_cast<uintptr_t>(dst) & 7) == 0, 302, l, idx)) continue;
-            *reinterpret_cast<float2*>(dst) = v;
+            const float2 pr = unpack2(acc[q / 2]);
+            float v = (q & 1) ? pr.y : pr.x;
+            if (dg) v += fsh[q];   // g_{0,l}: the t = 0 row
+            if (!FO_CHK(dbg, idx >= 0 && idx < ps, 302, l, idx)) continue;
+            *dst = v;
             if (l == m - 1 && planes_last > 0) {
-                const Split3 a = split_value(v.x, fp16, pscale), b2 = split_value(v.y, fp16, pscale);
-                uint16_t* p = reinterpret_cast<uint16_t*>(rbase + (int64_t)l * tstride + ps) + idx;
-                *reinterpret_cast<uint32_t*>(p) = (uint32_t)a.p[0] | ((uint32_t)b2.p[0] << 16);
-                if (planes_last > 1)
-                    *reinterpret_cast<uint32_t*>(p + ps) = (uint32_t)a.p[1] | ((uint32_t)b2.p[1] << 16);
-                if (planes_last > 2)
-                    *reinterpret_cast<uint32_t*>(p + 2 * ps) = (uint32_t)a.p[2] | ((uint32_t)b2.p[2] << 16);
+                const Split3 a = split_value(v, fp16, pscale);
+                // planes of R_l: 16-bit entries from float offset ps of the slot
+                uint16_t* p = reinterpret_cast<uint16_t*>(dst - idx + ps) + idx;
+                p[0] = a.p[0];
+                if (planes_last > 1) p[ps] = a.p[1];
+                if (planes_last > 2) p[2 * ps] = a.p[2];
             }
         }
     }
+    cp_async_wait<0>();
 }
 
 int grid_for(int64_t total, int threads) {
@@ -520,17 +542,34 @@ cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream
         return cudaGetLastError();
     }
     const int planes_last = sh.m > 1 ? sh.planes : 0;
+    // ring depth: 4 stages when they fit beside the coefficient table in ~200 KB, else 3 or 2
+    const size_t stage_bytes = (size_t)(sh.k - 1) * kCtEntries * sizeof(float);
+    const int S = stage_bytes * 4 <= 192 * 1024 ? 4 : (stage_bytes * 3 <= 200 * 1024 ? 3 : 2);
     auto go = [&](auto kern, int maxm, int l0) {
-        const size_t smem = (size_t)sh.k * maxm * sizeof(float);
+        const size_t smem = (size_t)((sh.k * maxm + 3) & ~3) * sizeof(float) + S * stage_bytes;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<we.total, 256, smem, s>>>(in, we, sh.k, sh.m, l0, sh.n_tslots, planes_last, sh.fp16, sh.pscale_r,
-                                        dbg);
+        kern<<<we.total, kCtEntries, smem, s>>>(in, we, sh.k, sh.m, l0, sh.n_tslots, planes_last, sh.fp16,
+                                               sh.pscale_r, dbg);
     };
-    if (sh.m <= 8) go(k_contract_f32<8>, 8, 0);
-    else if (sh.m <= 16) go(k_contract_f32<16>, 16, 0);
-    else if (sh.m <= 24) go(k_contract_f32<24>, 24, 0);
-    else
-        for (int l0 = 0; l0 < sh.m; l0 += 32) go(k_contract_f32<32>, 32, l0);
+    auto pick = [&](auto tag, int l0) {
+        constexpr int SS = decltype(tag)::value;
+        const int mm = sh.m - l0 < 32 ? sh.m - l0 : 32;   // R_l of this launch
+        switch ((mm + 3) / 4) {
+            case 1: go(k_contract_f32<4, SS>, 4, l0); break;
+            case 2: go(k_contract_f32<8, SS>, 8, l0); break;
+            case 3: go(k_contract_f32<12, SS>, 12, l0); break;
+            case 4: go(k_contract_f32<16, SS>, 16, l0); break;
+            case 5: go(k_contract_f32<20, SS>, 20, l0); break;
+            case 6: go(k_contract_f32<24, SS>, 24, l0); break;
+            case 7: go(k_contract_f32<28, SS>, 28, l0); break;
+            default: go(k_contract_f32<32, SS>, 32, l0); break;
+        }
+    };
+    for (int l0 = 0; l0 < sh.m; l0 += 32) {
+        if (S == 4) pick(std::integral_constant<int, 4>(), l0);
+        else if (S == 3) pick(std::integral_constant<int, 3>(), l0);
+        else pick(std::integral_constant<int, 2>(), l0);
+    }
     return cudaGetLastError();
 }
 

@@ -35,8 +35,10 @@
 //
 // Tiles are 128 x TBN (TBN = 256 or 128, chosen per batch by the autotuner). With TBN = 256
 // a column tile that reaches past the matrix edge by 128 columns runs as a 128-wide MMA and
-// loads half the B rows. A 256-wide tile moves half the B bytes per MMA cycle of a 128-wide
-// one, which matters because the split forms load 2 to 6 operand planes per k-block.
+// loads half the B rows; so does the diagonal tile of an odd 128-row block in symmetric mode,
+// whose first 128 columns lie below the diagonal. A 256-wide tile moves half the B bytes per
+// MMA cycle of a 128-wide one, which matters because the split forms load 2 to 6 operand
+// planes per k-block.
 //
 // Roles (320 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs (warp 1 owns the
 // TMEM allocation), warps 2-9 drain TMEM: warp w reads lane quadrant (w & 3) = 32 tile rows
@@ -320,10 +322,17 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     const int tm = np / kBM, tn = (np + TBN - 1) / TBN;
     int I, J;
     tile_of(gtile - __ldg(pre + inst), tm, tn, TBN, sym, I, J);
-    const int m0 = I * kBM, n0 = J * TBN;
+    const int m0 = I * kBM;
+    int n0 = J * TBN;
     const int nk = np / kBK;
     // 128-row B boxes inside the matrix: a 256-wide tile at the edge may hold only one
-    const int nbox = (np - n0) / kBM < Cfg::kBBoxes ? (np - n0) / kBM : Cfg::kBBoxes;
+    int nbox = (np - n0) / kBM < Cfg::kBBoxes ? (np - n0) / kBM : Cfg::kBBoxes;
+    if (sym && n0 < m0) {
+        // diagonal tile of an odd row block (256-wide tiles): its first 128 columns lie
+        // below the diagonal, so only the 128 columns from the diagonal on are computed
+        n0 = m0;
+        nbox = 1;
+    }
     const int tile_n = nbox * kBM;
     const uint32_t idesc = idesc_f16(tile_n, F16);
     const uint32_t stage_tx = (uint32_t)(PA * kBoxBytes + PB * nbox * kBoxBytes);
@@ -577,7 +586,7 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         for (int h = 0; h < TBN / 64; ++h) {
             const int c = h * 64 + 2 * lane;
             const int64_t gcol = (int64_t)n0 + c;
-            if (gcol >= np) continue;
+            if (c >= tile_n) continue;   // past the matrix edge or the narrowed diagonal tile
             const int64_t o = grow * ld + gcol;
             float v0 = tile[r * LD + c], v1 = tile[r * LD + c + 1];
             if (Cm) {
@@ -606,7 +615,7 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     for (int cc = 0; cc < TBN / DW; ++cc) {
         const int c = ew * (TBN / DW) + cc;
         const int64_t grow = (int64_t)n0 + c;       // output row
-        if (grow >= np) break;
+        if (c >= tile_n) break;
 #pragma unroll
         for (int h = 0; h < kBM / 64; ++h) {
             const int r = h * 64 + 2 * lane;

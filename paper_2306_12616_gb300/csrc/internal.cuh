@@ -123,6 +123,36 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ pre, int lo, in
     return lo;
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only) and their group waits.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Two float32 values in one 64-bit register (low lane = x) and d = a * b + c on both lanes
+// at once (fma.rn.f32x2, sm_100 and later): the same round-to-nearest result per lane as
+// fmaf, at half the instruction count. Operands stay packed across a loop (loaded from
+// shared memory as 64-bit pairs), so packing is paid once, not per FMA.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float x, float y) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(f32x2 v) {
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(v));
+    return o;
+}
+__device__ __forceinline__ void ffma2(f32x2& acc, f32x2 a, f32x2 b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
 // Elementwise row blocks: a block covers ew_rows(np) rows (about 8192 entries).
 __host__ __device__ inline int ew_rows(int64_t np) {
     const int64_t r = 8192 / np;

@@ -298,21 +298,28 @@ __global__ void k_diag_sums(const Inst* __restrict__ insts, int is64) {
 // --------------------------------------------------------- Frobenius inner products
 // <S_{giant0+g}, S_{baby0+b}>_F of one instance. Every matrix is symmetric, so the product is
 // the diagonal sum plus twice the strict upper triangle: only the chunks (kChunk consecutive
-// entries of one row) on or above the diagonal are read, and the baby entries are weighted
-// 2 above the diagonal, 1 on it and 0 below it when they are staged. A block covers
-// kGChunks consecutive upper chunks. Each chunk of every matrix is staged in shared memory,
-// matrix-major (row s holds the chunk of matrix s, rows padded by 16 bytes), double-buffered:
-// the next chunk is loaded into registers before the current one is multiplied, and stored
-// to the other buffer after, so one barrier per chunk separates the phases and the global
-// loads overlap the arithmetic. Each warp owns up to kTPW 4 x 4 tiles of (giant, baby) pairs;
-// a lane reads 16-byte vectors of 8 rows and accumulates 4 x 4 x (16 / sizeof(T)) products
-// per step. Every lane sums at most kGChunks * kChunk / 32 products per pair in T; lanes are
-// combined by float64 shuffles and blocks by the partial sums (k_sum_partials).
+// entries of one row) on or above the diagonal are read. A block covers kGChunks consecutive
+// upper chunks. They are copied kCPS chunks at a time into a kGStages-deep shared-memory ring
+// by cp.async (16 bytes per copy, no register staging; each thread's copy addresses are
+// fixed up front and only offset per chunk), matrix-major (row s of a chunk holds the chunk
+// of matrix s, rows padded by 16 bytes), so that kGStages - 1 stages are in flight while one
+// is multiplied; one barrier per stage separates its consumption from the refill of the
+// stage it frees. Each warp owns up to kTPW 4 x 4 tiles of (giant, baby) pairs; a lane reads
+// 16-byte vectors of 8 rows and accumulates 4 x 4 x (16 / sizeof(T)) products per step
+// (float32: packed FMAs, even and odd entries in the two lanes). Chunks right of the
+// diagonal weigh the baby entries by 1 (the factor 2 of the strict upper triangle is applied
+// once at the end); the diagonal chunk of a row weighs them by 1, 1/2 or 0 right of, on or
+// left of the diagonal. Every lane sums at most kGChunks * kChunk / 32 products per pair in
+// T; lanes are combined by float64 shuffles and blocks by the partial sums (k_sum_partials).
 constexpr int kChunkBytes = 512;    // one chunk of one matrix: 128 float32 / 64 float64
-constexpr int kGChunks = 32;        // chunks per block
+constexpr int kGChunks = 64;        // chunks per block
+constexpr int kCPS = 2;             // chunks per stage
+constexpr int kGStages = 4;         // shared-memory ring depth (stages)
 constexpr int kMaxQuads = 12;       // staged rows <= 48
 constexpr int kTPW = 2;
 constexpr int kGramThreads = 512;
+// 16-byte copies per thread and chunk: staged rows x (kChunkBytes / 16) vectors / threads
+constexpr int kGLoads = (4 * kMaxQuads * (kChunkBytes / 16) + kGramThreads - 1) / kGramThreads;
 
 // Upper chunks of an np x np matrix: row r holds chunks floor(r / kc) .. np / kc - 1.
 __host__ __device__ inline int64_t upper_chunks(int64_t np, int kc) {
@@ -343,8 +350,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     const int nrows = 4 * (ng4 + nb4);
     const int ntiles = ng4 * nb4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    T* buf0 = reinterpret_cast<T*>(smem_raw);
-    T* buf1 = buf0 + nrows * RS;
+    const int chunk_elems = nrows * RS;
+    const int stage_elems = kCPS * chunk_elems;
+    T* ring = reinterpret_cast<T*>(smem_raw);
 
     // (row, chunk of the row) of upper chunk c0; rows of band b (kChunk rows) hold cpr - b
     int64_t row = 0, cc = 0;
@@ -364,94 +372,127 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
             c = r / kChunk;
         }
     };
-
-    // vectors this thread loads per chunk: q = threadIdx.x + j * blockDim.x < nrows * VPR
-    constexpr int kMaxLoads = (4 * kMaxQuads * VPR + kGramThreads - 1) / kGramThreads;
-    const int nq = nrows * VPR;
-    auto src_of = [&](int q, int64_t r, int64_t c) -> const float4* {
-        const int srow = q / VPR, ev = (q % VPR) * V;
-        int slot = -1;
-        if (srow < 4 * ng4) { if (srow < ngiant) slot = giant0 + srow; }
-        else { const int bb = srow - 4 * ng4; if (bb < nbaby) slot = baby0 + bb; }
-        if (slot < 0) return nullptr;
-        return reinterpret_cast<const float4*>(reinterpret_cast<const T*>(base + slot_bytes * slot) + r * np +
-                                               c * kChunk + ev);
+    // slot of staged row srow, or -1 for the padding rows of a partial quad
+    auto slot_of = [&](int srow) -> int {
+        if (srow < 4 * ng4) return srow < ngiant ? giant0 + srow : -1;
+        const int bb = srow - 4 * ng4;
+        return bb < nbaby ? baby0 + bb : -1;
     };
-    float4 pre[kMaxLoads];
-    auto load = [&](int64_t r, int64_t c) {
+    // this thread's copies: source at chunk (0, 0) and shared-memory offset in a chunk
+    const char* gsrc[kGLoads];
+    int sdst[kGLoads];
 #pragma unroll
-        for (int j = 0; j < kMaxLoads; ++j) {
-            const int q = threadIdx.x + j * kGramThreads;
-            const float4* src = q < nq ? src_of(q, r, c) : nullptr;
-            pre[j] = src ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    // stores the prefetched chunk (row r, chunk c), baby entries weighted 2 / 1 / 0 above /
-    // on / below the diagonal
-    auto store = [&](T* buf, int64_t r, int64_t c) {
-#pragma unroll
-        for (int j = 0; j < kMaxLoads; ++j) {
-            const int q = threadIdx.x + j * kGramThreads;
-            if (q >= nq) continue;
+    for (int j = 0; j < kGLoads; ++j) {
+        const int q = threadIdx.x + j * kGramThreads;
+        gsrc[j] = nullptr;
+        sdst[j] = 0;
+        if (q < nrows * VPR) {
             const int srow = q / VPR, ev = (q % VPR) * V;
-            T v[V];
-            *reinterpret_cast<float4*>(v) = pre[j];
-            if (srow >= 4 * ng4) {
+            const int slot = slot_of(srow);
+            sdst[j] = srow * RS + ev;
+            if (slot >= 0) gsrc[j] = base + slot_bytes * slot + (int64_t)ev * (int64_t)sizeof(T);
+        }
+    }
+    // the padding rows hold zeros in every stage, written once
+    for (int q = threadIdx.x; q < kGStages * kCPS * nrows * VPR; q += blockDim.x) {
+        const int st = q / (nrows * VPR), w = q % (nrows * VPR);
+        const int srow = w / VPR, ev = (w % VPR) * V;
+        if (slot_of(srow) < 0)
+            *reinterpret_cast<float4*>(ring + st * chunk_elems + srow * RS + ev) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int64_t nch = c1 - c0;
+    const int nst = (int)((nch + kCPS - 1) / kCPS);
+    int64_t ir = row, ic = cc, issued = 0;   // next chunk to copy
+    auto issue_stage = [&](int st) {
+        T* dst = ring + (st % kGStages) * stage_elems;
 #pragma unroll
-                for (int u = 0; u < V; ++u) {
-                    const int64_t col = c * kChunk + ev + u;
-                    v[u] *= col > r ? T(2) : (col == r ? T(1) : T(0));
-                }
+        for (int u = 0; u < kCPS; ++u) {
+            if (issued < nch) {
+                const int64_t off = (ir * np + ic * kChunk) * (int64_t)sizeof(T);
+#pragma unroll
+                for (int j = 0; j < kGLoads; ++j)
+                    if (gsrc[j]) cp_async16(dst + u * chunk_elems + sdst[j], gsrc[j] + off);
+                advance(ir, ic);
+                ++issued;
             }
-            *reinterpret_cast<float4*>(buf + srow * RS + ev) = *reinterpret_cast<const float4*>(v);
         }
     };
 
-    T acc[kTPW][16];
+    T acc[kTPW][16];        // float64 sums
+    f32x2 acc2[kTPW][16];   // float32 sums of the even / odd entries
 #pragma unroll
     for (int t = 0; t < kTPW; ++t)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[t][q] = T(0);
+        for (int q = 0; q < 16; ++q) {
+            acc[t][q] = T(0);
+            acc2[t][q] = 0ull;
+        }
 
-    if (c0 < c1) {
-        load(row, cc);
-        store(buf0, row, cc);
+#pragma unroll
+    for (int s = 0; s < kGStages - 1; ++s) {
+        if (s < nst) issue_stage(s);
+        cp_async_commit();
     }
-    __syncthreads();
-    for (int64_t c = c0; c < c1; ++c) {
-        T* cur = ((c - c0) & 1) ? buf1 : buf0;
-        T* nxt = ((c - c0) & 1) ? buf0 : buf1;
-        const bool more = c + 1 < c1;
-        int64_t nrow = row, ncc = cc;
-        advance(nrow, ncc);
-        if (more) load(nrow, ncc);
+    int64_t done = 0;
+    for (int s = 0; s < nst; ++s) {
+        cp_async_wait<kGStages - 2>();   // this thread's copies of stage s have landed
+        __syncthreads();                 // everyone's have; the ring slot of stage s - 1 is free
+        if (s + kGStages - 1 < nst) issue_stage(s + kGStages - 1);
+        cp_async_commit();
 #pragma unroll
-        for (int t = 0; t < kTPW; ++t) {
-            const int tile = warp + t * nwarps;
-            if (tile >= ntiles) break;                   // uniform across the warp
-            const T* g0 = cur + 4 * (tile / nb4) * RS;
-            const T* b0 = cur + (4 * ng4 + 4 * (tile % nb4)) * RS;
-            for (int e = lane * V; e < kChunk; e += 32 * V) {
-                T gv[4][V], bv[4][V];
+        for (int u = 0; u < kCPS; ++u) {
+            if (done >= nch) break;
+            const T* cur = ring + (s % kGStages) * stage_elems + u * chunk_elems;
+            const bool dchunk = cc == row / kChunk;   // the chunk holding the diagonal entry
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
-                    *reinterpret_cast<float4*>(gv[a]) = *reinterpret_cast<const float4*>(g0 + a * RS + e);
+            for (int t = 0; t < kTPW; ++t) {
+                const int tile = warp + t * nwarps;
+                if (tile >= ntiles) break;                   // uniform across the warp
+                const T* g0 = cur + 4 * (tile / nb4) * RS;
+                const T* b0 = cur + (4 * ng4 + 4 * (tile % nb4)) * RS;
+                for (int e = lane * V; e < kChunk; e += 32 * V) {
+                    T gv[4][V], bv[4][V];
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    *reinterpret_cast<float4*>(bv[b]) = *reinterpret_cast<const float4*>(b0 + b * RS + e);
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < 4; ++a)
+                        *reinterpret_cast<float4*>(gv[a]) = *reinterpret_cast<const float4*>(g0 + a * RS + e);
 #pragma unroll
                     for (int b = 0; b < 4; ++b)
+                        *reinterpret_cast<float4*>(bv[b]) = *reinterpret_cast<const float4*>(b0 + b * RS + e);
+                    if (dchunk) {
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[t][4 * a + b] = fma(gv[a][v], bv[b][v], acc[t][4 * a + b]);
+                        for (int v = 0; v < V; ++v) {
+                            const int64_t col = cc * kChunk + e + v;
+                            const T w = col > row ? T(1) : (col == row ? T(0.5) : T(0));
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) bv[b][v] *= w;
+                        }
+                    }
+                    if constexpr (sizeof(T) == 4) {
+                        const ulonglong2* gp = reinterpret_cast<const ulonglong2*>(&gv[0][0]);
+                        const ulonglong2* bp = reinterpret_cast<const ulonglong2*>(&bv[0][0]);
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                ffma2(acc2[t][4 * a + b], gp[a].x, bp[b].x);
+                                ffma2(acc2[t][4 * a + b], gp[a].y, bp[b].y);
+                            }
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                                for (int v = 0; v < V; ++v)
+                                    acc[t][4 * a + b] = fma(gv[a][v], bv[b][v], acc[t][4 * a + b]);
+                    }
+                }
             }
+            advance(row, cc);
+            ++done;
         }
-        if (more) store(nxt, nrow, ncc);
-        row = nrow;
-        cc = ncc;
-        __syncthreads();
     }
+    cp_async_wait<0>();
     const int npairs = ngiant * nbaby;
     double* partials = in.gpart;
 #pragma unroll
@@ -461,7 +502,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
         const int tg = tile / nb4, tb = tile % nb4;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            double v = (double)acc[t][q];
+            const float2 pr = unpack2(acc2[t][q]);
+            double v = sizeof(T) == 4 ? 2.0 * ((double)pr.x + (double)pr.y) : 2.0 * (double)acc[t][q];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             const int g = 4 * tg + q / 4, b = 4 * tb + q % 4;
             if (lane == 0 && g < ngiant && b < nbaby) partials[(int64_t)lb * npairs + g * nbaby + b] = v;
@@ -643,7 +685,7 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
         const int ng = ngiant - g < gmax ? ngiant - g : gmax;
         const int ng4 = (ng + 3) / 4;
         const size_t elem = is64 ? 8 : 4;
-        const size_t smem = (size_t)2 * 4 * (ng4 + nb4) * (kChunkBytes / elem + 16 / elem) * elem;
+        const size_t smem = (size_t)kGStages * kCPS * 4 * (ng4 + nb4) * (kChunkBytes / elem + 16 / elem) * elem;
         if (is64) {
             cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_gram<double><<<wgr.total, kGramThreads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
