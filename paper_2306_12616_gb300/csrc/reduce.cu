@@ -86,12 +86,25 @@ __global__ void __launch_bounds__(32 * kGershRows) k_gershgorin_rows(const Inst*
     int bad = 0;
     if (row < n) {
         const double* r = H + row * ld;
-        double s = 0.0, d = 0.0;
-        for (int64_t j = lane; j < n; j += 32) {
+        double s4[4] = {0.0, 0.0, 0.0, 0.0}, d = 0.0;
+        // four independent sums, so that four loads per lane are in flight
+        int64_t j = lane;
+        for (; j + 96 < n; j += 128) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldg(r + j + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                bad |= !isfinite(v[u]);
+                if (j + 32 * u == row) d = v[u]; else s4[u] += fabs(v[u]);
+            }
+        }
+        for (; j < n; j += 32) {
             const double v = __ldg(r + j);
             bad |= !isfinite(v);
-            if (j == row) d = v; else s += fabs(v);
+            if (j == row) d = v; else s4[0] += fabs(v);
         }
+        double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         s = warp_sum(s);
         d = warp_sum(d);
         lo = d - s;
@@ -317,9 +330,17 @@ constexpr int kCPS = 2;             // chunks per stage
 constexpr int kGStages = 4;         // shared-memory ring depth (stages)
 constexpr int kMaxQuads = 12;       // staged rows <= 48
 constexpr int kTPW = 2;
-constexpr int kGramThreads = 512;
+constexpr int kGramThreads = 512;   // largest block: 16 warps, up to 32 tiles
+constexpr int kGramMinThreads = 256;
 // 16-byte copies per thread and chunk: staged rows x (kChunkBytes / 16) vectors / threads
-constexpr int kGLoads = (4 * kMaxQuads * (kChunkBytes / 16) + kGramThreads - 1) / kGramThreads;
+constexpr int kGLoads = (4 * kMaxQuads * (kChunkBytes / 16) + kGramMinThreads - 1) / kGramMinThreads;
+
+// Threads of a block for ntiles (giant, baby) tiles: kTPW tiles per warp, at least 8 warps.
+__host__ __device__ inline int gram_threads(int ntiles) {
+    int w = (ntiles + kTPW - 1) / kTPW;
+    if (w < kGramMinThreads / 32) w = kGramMinThreads / 32;
+    return 32 * w;
+}
 
 // Upper chunks of an np x np matrix: row r holds chunks floor(r / kc) .. np / kc - 1.
 __host__ __device__ inline int64_t upper_chunks(int64_t np, int kc) {
@@ -383,7 +404,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     int sdst[kGLoads];
 #pragma unroll
     for (int j = 0; j < kGLoads; ++j) {
-        const int q = threadIdx.x + j * kGramThreads;
+        const int q = threadIdx.x + j * (int)blockDim.x;
         gsrc[j] = nullptr;
         sdst[j] = 0;
         if (q < nrows * VPR) {
@@ -428,6 +449,14 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
             acc2[t][q] = 0ull;
         }
 
+    // shared-memory offsets of this warp's tiles (-1: none)
+    int toff_g[kTPW], toff_b[kTPW];
+#pragma unroll
+    for (int t = 0; t < kTPW; ++t) {
+        const int tile = warp + t * nwarps;
+        toff_g[t] = tile < ntiles ? 4 * (tile / nb4) * RS : -1;
+        toff_b[t] = tile < ntiles ? (4 * ng4 + 4 * (tile % nb4)) * RS : -1;
+    }
 #pragma unroll
     for (int s = 0; s < kGStages - 1; ++s) {
         if (s < nst) issue_stage(s);
@@ -439,17 +468,32 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
         __syncthreads();                 // everyone's have; the ring slot of stage s - 1 is free
         if (s + kGStages - 1 < nst) issue_stage(s + kGStages - 1);
         cp_async_commit();
+        const T* stage_base = ring + (s % kGStages) * stage_elems;
+        // chunks of this stage: how many, and which one holds a diagonal entry at (row, col)
+        int nu = 0;
+        int64_t drow[kCPS], dcol0[kCPS];
 #pragma unroll
         for (int u = 0; u < kCPS; ++u) {
-            if (done >= nch) break;
-            const T* cur = ring + (s % kGStages) * stage_elems + u * chunk_elems;
-            const bool dchunk = cc == row / kChunk;   // the chunk holding the diagonal entry
+            drow[u] = -1;
+            dcol0[u] = 0;
+            if (done < nch) {
+                if (cc == row / kChunk) {
+                    drow[u] = row;
+                    dcol0[u] = cc * kChunk;
+                }
+                advance(row, cc);
+                ++done;
+                ++nu;
+            }
+        }
 #pragma unroll
-            for (int t = 0; t < kTPW; ++t) {
-                const int tile = warp + t * nwarps;
-                if (tile >= ntiles) break;                   // uniform across the warp
-                const T* g0 = cur + 4 * (tile / nb4) * RS;
-                const T* b0 = cur + (4 * ng4 + 4 * (tile % nb4)) * RS;
+        for (int t = 0; t < kTPW; ++t) {
+            if (toff_g[t] < 0) break;                   // uniform across the warp
+#pragma unroll
+            for (int u = 0; u < kCPS; ++u) {
+                if (u >= nu) break;
+                const T* g0 = stage_base + u * chunk_elems + toff_g[t];
+                const T* b0 = stage_base + u * chunk_elems + toff_b[t];
                 for (int e = lane * V; e < kChunk; e += 32 * V) {
                     T gv[4][V], bv[4][V];
 #pragma unroll
@@ -458,11 +502,11 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
 #pragma unroll
                     for (int b = 0; b < 4; ++b)
                         *reinterpret_cast<float4*>(bv[b]) = *reinterpret_cast<const float4*>(b0 + b * RS + e);
-                    if (dchunk) {
+                    if (drow[u] >= 0) {
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
-                            const int64_t col = cc * kChunk + e + v;
-                            const T w = col > row ? T(1) : (col == row ? T(0.5) : T(0));
+                            const int64_t col = dcol0[u] + e + v;
+                            const T w = col > drow[u] ? T(1) : (col == drow[u] ? T(0.5) : T(0));
 #pragma unroll
                             for (int b = 0; b < 4; ++b) bv[b][v] *= w;
                         }
@@ -488,8 +532,6 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
                     }
                 }
             }
-            advance(row, cc);
-            ++done;
         }
     }
     cp_async_wait<0>();
@@ -686,12 +728,13 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
         const int ng4 = (ng + 3) / 4;
         const size_t elem = is64 ? 8 : 4;
         const size_t smem = (size_t)kGStages * kCPS * 4 * (ng4 + nb4) * (kChunkBytes / elem + 16 / elem) * elem;
+        const int threads = gram_threads(ng4 * nb4);
         if (is64) {
             cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_gram<double><<<wgr.total, kGramThreads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
+            k_gram<double><<<wgr.total, threads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
         } else {
             cudaFuncSetAttribute(k_gram<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_gram<float><<<wgr.total, kGramThreads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
+            k_gram<float><<<wgr.total, threads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
         }
         const int npairs = ng * nbaby;
         k_sum_partials<<<dim3(npairs, batch), 128, 0, s>>>(in, npairs, (out_g0 + g) * nbaby);
