@@ -577,27 +577,46 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         }
     };
 
-    // row pass: each drain warp takes 16 tile rows, lanes on column pairs; applies
-    // beta C + D + shift and stores the entries with col >= row (all of them when not sym)
-    for (int rr = 0; rr < kBM / DW; ++rr) {
-        const int r = ew * (kBM / DW) + rr;
-        const int64_t grow = (int64_t)m0 + r;
+    // row pass: each drain warp takes kBM / DW tile rows, lanes on column pairs; applies
+    // beta C + D + shift and stores the entries with col >= row (all of them when not sym).
+    // The C and D operands of G consecutive (row, column piece) iterations are loaded before
+    // any of them is used, so that G loads per lane are in flight instead of one: C (two
+    // products old) and D are DRAM reads, and one at a time they set the epilogue's pace.
+    // (D may be the output slot itself, R_l -> b_l: each entry is read and then written by
+    // the same thread, and the mirror pass below writes only entries that no row pass reads.)
+    constexpr int RPW = kBM / DW;          // tile rows per drain warp
+    constexpr int HPR = TBN / 64;          // 64-column pieces per row
+    constexpr int NIT = RPW * HPR;
+    constexpr int G = DW == 16 ? 4 : 8;    // 16 drain warps run at the 96-register cap
+    static_assert(NIT % G == 0, "row-pass groups");
+    for (int q0 = 0; q0 < NIT; q0 += G) {
+        float2 cv[G], dv[G];
 #pragma unroll
-        for (int h = 0; h < TBN / 64; ++h) {
-            const int c = h * 64 + 2 * lane;
-            const int64_t gcol = (int64_t)n0 + c;
+        for (int u = 0; u < G; ++u) {
+            const int q = q0 + u, rr = q / HPR, h = q % HPR;
+            const int r = ew * RPW + rr, c = h * 64 + 2 * lane;
+            const int64_t o = ((int64_t)m0 + r) * ld + n0 + c;
+            cv[u] = make_float2(0.f, 0.f);
+            dv[u] = make_float2(0.f, 0.f);
+            if (c < tile_n) {
+                if (Cm) cv[u] = *reinterpret_cast<const float2*>(Cm + o);
+                if (Dm) dv[u] = *reinterpret_cast<const float2*>(Dm + o);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int q = q0 + u, rr = q / HPR, h = q % HPR;
+            const int r = ew * RPW + rr, c = h * 64 + 2 * lane;
             if (c >= tile_n) continue;   // past the matrix edge or the narrowed diagonal tile
-            const int64_t o = grow * ld + gcol;
+            const int64_t grow = (int64_t)m0 + r, gcol = (int64_t)n0 + c;
             float v0 = tile[r * LD + c], v1 = tile[r * LD + c + 1];
             if (Cm) {
-                const float2 cc = *reinterpret_cast<const float2*>(Cm + o);
-                v0 = fmaf(st.beta, cc.x, v0);
-                v1 = fmaf(st.beta, cc.y, v1);
+                v0 = fmaf(st.beta, cv[u].x, v0);
+                v1 = fmaf(st.beta, cv[u].y, v1);
             }
             if (Dm) {
-                const float2 dd = *reinterpret_cast<const float2*>(Dm + o);
-                v0 += dd.x;
-                v1 += dd.y;
+                v0 += dv[u].x;
+                v1 += dv[u].y;
             }
             if (grow < n_real) {
                 if (gcol == grow) v0 += st.shift;
