@@ -115,6 +115,11 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
         "r"(c4)
         : "memory");
 }
+// Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -400,6 +405,20 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
                         tma_load_5d(stage_b(s, p) + j * kBoxBytes, map, &full[s], kb * kBK, n0 + j * kBM, p,
                                     st.b, ib);
                 issued = kb + 1;
+            }
+            // every operand is requested: bring the epilogue's C and D rows of this tile
+            // into L2 while the last k-blocks are multiplied (prefetch hints, in bounds)
+            if (!*vabort) {
+                const char* sbase = insts[inst].slots;
+                const int64_t sbytes = insts[inst].slot_bytes;
+                const int cd[2] = {st.c, st.d};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (cd[q] < 0) continue;
+                    const char* rows = sbase + sbytes * cd[q] + ((int64_t)m0 * np + n0) * 4;
+                    for (int r = 0; r < kBM; ++r)
+                        prefetch_l2(rows + (int64_t)r * np * 4, (uint32_t)tile_n * 4u);
+                }
             }
             if (*vabort) {
                 for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
