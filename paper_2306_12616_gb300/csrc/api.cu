@@ -705,8 +705,8 @@ fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trac
     prof_end(ctx, s, h, 0.0, lstage);
     run->launches += lstage;
     h = prof_begin(ctx, s, FO_STAGE_CONTRACT);
-    lstage = (!sh.is64 && sh.m > 24) ? (sh.m + 31) / 32 : 1;
-    FO_CUDA(launch_contract(p.d_inst, p.we.dev, sh, s, ctx->flag + 1), "contract");
+    lstage = sh.is64 ? 1 : (sh.m + 31) / 32 + (sh.m > 1 ? 1 : 0);   // + the plane mirror of R_{m-1}
+    FO_CUDA(launch_contract(p.d_inst, p.we.dev, p.wsc.dev, sh, s, ctx->flag + 1), "contract");
     if (sh.m == 1) {
         FO_CUDA(launch_copy_out(p.d_inst, p.d_io, p.we.dev, sh, s), "copy_out");
         lstage += 1;
@@ -1550,6 +1550,7 @@ fo_status fo_recurrence_product(fo_ctx* ctx, int32_t precision, int32_t symmetri
     if (dD) FO_CUDA(launch_pack_f32(dD, n, ld, in.slots + 3 * in.slot_bytes, in.np, 0, 0, 1.0f, st), "pack");
     Step stp = make_step(*p, 0, 1, dC ? 2 : -1, dD ? 3 : -1, 4, alpha, beta, shift, false, false, false, false, ctx);
     stp.planes = 0;
+    stp.lower_master = 1;   // the whole float32 result is copied out
     Run run;
     FO_TRY(run_product(ctx, *p, stp, st, "product", 0, &run));
     FO_CUDA(cudaMemcpy2DAsync(dOut, ld * 4, in.slots + 4 * in.slot_bytes, in.np * 4, n * 4, n,

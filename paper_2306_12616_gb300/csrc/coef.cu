@@ -374,11 +374,15 @@ __device__ __forceinline__ Split3 split_value(float v, int fp16, float pscale) {
 }
 
 // R_l for l0 <= l < min(l0 + MAXM, m) (MAXM = m rounded up to a multiple of 4, at most 32;
-// m > 32 takes several launches). The coefficients are staged transposed, gsh[t * MAXM + j] =
-// g_{t,l0+j} (zero beyond m), so that one 16-byte shared load serves four R_l. The block's
-// entries are taken 256 at a time (one per thread); the 256-entry segments of T_1..T_{k-1}
-// of the next S - 1 steps are copied into an S-stage shared-memory ring by cp.async, so the
-// loads in flight do not depend on registers (S = 4 stages of 19 KB at k = 20).
+// m > 32 takes several launches), on and above the diagonal only (the float32 masters of the
+// T_i are maintained there; R_l is symmetric): row r from column r rounded down to a multiple
+// of 4 (16-byte aligned copies) to the end. The coefficients are staged transposed,
+// gsh[t * MAXM + j] = g_{t,l0+j} (zero beyond m), so that one 16-byte shared load serves
+// four R_l. The block's rows are walked in steps of 256 entries of one row (one per
+// thread); the 256-entry segments of T_1..T_{k-1} of the next S - 1 steps are copied into an
+// S-stage shared-memory ring by cp.async, so the loads in flight do not depend on registers.
+// The planes of R_{m-1} (the first operand of the giant steps) are completed below the
+// diagonal by k_mirror_planes.
 constexpr int kCtEntries = 256;
 
 template <int MAXM, int S>
@@ -400,38 +404,52 @@ __global__ void __launch_bounds__(kCtEntries, 2) k_contract_f32(const Inst* __re
     const int rows = ew_rows(np);
     const int64_t r0 = (int64_t)(blockIdx.x - we.pre[i]) * rows;
     const int64_t r1 = r0 + rows < np ? r0 + rows : np;
-    const int64_t e0 = r0 * np, e1 = r1 * np;             // multiples of 128 entries
-    const int steps = (int)((e1 - e0 + kCtEntries - 1) / kCtEntries);
     const int64_t tstride = in.slot_bytes / 4;
     const int64_t ps = np * np;
     const float* tbase = reinterpret_cast<const float*>(in.slots);
     float* rbase = reinterpret_cast<float*>(in.slots + n_tslots * in.slot_bytes);
-    // copies of the segments of step j (entries e0 + 256 j ...) into stage j % S: 16 bytes each,
-    // none past the block's last entry
+    // step cursor: (row, first column) of a 256-entry step; a row starts at its diagonal
+    // rounded down to a multiple of 4 and ends at np
+    auto advance = [&](int64_t& r, int64_t& c) {
+        c += kCtEntries;
+        if (c >= np) {
+            ++r;
+            c = r & ~int64_t(3);
+        }
+    };
     // thread tid copies vector v4 = 4 (tid % 64) of the segments t = tid / 64, tid / 64 + 4, ...
     constexpr int kTPS = kCtEntries / (kCtEntries / 4);   // segments started per pass: 4
     const int v4 = 4 * (threadIdx.x % (kCtEntries / 4)), tq = threadIdx.x / (kCtEntries / 4);
-    auto issue = [&](int j) {
-        const int64_t base = e0 + (int64_t)j * kCtEntries + v4;
-        if (base >= e1) return;
+    auto issue = [&](int j, int64_t r, int64_t c) {
+        if (c + v4 >= np) return;                          // past the end of the row
         float* dst = ring + (j % S) * stage + v4;
-        const float* src = tbase + (int64_t)tq * tstride + base;
+        const float* src = tbase + (int64_t)tq * tstride + r * np + c + v4;
 #pragma unroll 1
         for (int t = tq; t < nt; t += kTPS, src += kTPS * tstride) cp_async16(dst + t * kCtEntries, src);
     };
+    int64_t ir = r0, ic = r0 & ~int64_t(3);   // next step to copy
+    int64_t cr = ir, cc = ic;                 // next step to compute
 #pragma unroll
     for (int s = 0; s < S - 1; ++s) {
-        if (s < steps) issue(s);
+        if (ir < r1) {
+            issue(s, ir, ic);
+            advance(ir, ic);
+        }
         cp_async_commit();
     }
     __syncthreads();   // the coefficient table
-    for (int j = 0; j < steps; ++j) {
+    for (int j = 0; cr < r1; ++j) {
         cp_async_wait<S - 2>();
         __syncthreads();   // step j's segments have landed; the stage of step j - 1 is free
-        if (j + S - 1 < steps) issue(j + S - 1);
+        if (ir < r1) {
+            issue(j + S - 1, ir, ic);
+            advance(ir, ic);
+        }
         cp_async_commit();
-        const int64_t idx = e0 + (int64_t)j * kCtEntries + threadIdx.x;
-        if (idx >= e1) continue;
+        const int64_t r = cr, c = cc + threadIdx.x;
+        advance(cr, cc);
+        if (c >= np) continue;
+        const int64_t idx = r * np + c;
         const float* seg = ring + (j % S) * stage + threadIdx.x;
         f32x2 acc[MAXM / 2];   // (R_{l0+2p}, R_{l0+2p+1}) at this entry
 #pragma unroll
@@ -448,9 +466,6 @@ __global__ void __launch_bounds__(kCtEntries, 2) k_contract_f32(const Inst* __re
                 ffma2(acc[2 * j4 + 1], g.y, vv);
             }
         }
-        // row and column of the entry (32-bit: a block spans fewer than 2^31 entries)
-        const int off = (int)(idx - r0 * np);
-        const int64_t r = r0 + off / (int)np, c = off % (int)np;
         const bool dg = (r < n) && (c == r);
         float* dst = rbase + (int64_t)l0 * tstride + idx;
 #pragma unroll
@@ -473,6 +488,36 @@ __global__ void __launch_bounds__(kCtEntries, 2) k_contract_f32(const Inst* __re
         }
     }
     cp_async_wait<0>();
+}
+
+// The 16-bit planes of one slot below the diagonal from those above it: block (bi, bj),
+// bj >= bi, of 32 x 32 entries (the enumeration of k_scale_sym) is staged in shared memory
+// and written transposed at (bj, bi); a diagonal block fills its own lower half.
+__global__ void __launch_bounds__(256) k_mirror_planes(const Inst* __restrict__ insts, Work ws, int slot,
+                                                       int planes, int* dbg) {
+    __shared__ uint16_t tile[3][32][34];
+    const int i = find_inst(ws.pre, 0, ws.count, blockIdx.x);
+    if (!insts[i].res->active) return;
+    const int64_t np = insts[i].np;
+    const int tn = (int)(np / 32);
+    int bi = 0, b = blockIdx.x - ws.pre[i];
+    while (b >= tn - bi) { b -= tn - bi; ++bi; }
+    const int bj = bi + b;
+    const int64_t ps = np * np;
+    uint16_t* P16 = reinterpret_cast<uint16_t*>(insts[i].slots + insts[i].slot_bytes * slot + 4 * ps);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int pl = 0; pl < planes; ++pl)
+        for (int ry = ty; ry < 32; ry += 8)
+            tile[pl][ry][tx] = P16[pl * ps + ((int64_t)bi * 32 + ry) * np + (int64_t)bj * 32 + tx];
+    __syncthreads();
+    for (int pl = 0; pl < planes; ++pl)
+        for (int ry = ty; ry < 32; ry += 8) {
+            // output (bj*32 + ry, bi*32 + tx) = input (bi*32 + tx, bj*32 + ry), below the diagonal
+            const int64_t r = (int64_t)bj * 32 + ry, c = (int64_t)bi * 32 + tx;
+            if (r <= c) continue;
+            if (!FO_CHK(dbg, r < np && c < np, 303, r, c)) continue;
+            P16[pl * ps + r * np + c] = tile[pl][tx][ry];
+        }
 }
 
 int grid_for(int64_t total, int threads) {
@@ -533,7 +578,7 @@ cudaError_t launch_g_to_d(const Inst* in, int batch, const Shape& sh, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream_t s, int* dbg) {
+cudaError_t launch_contract(const Inst* in, Work we, Work wsym, const Shape& sh, cudaStream_t s, int* dbg) {
     if (sh.is64) {
         const size_t smem = (size_t)sh.k * sh.m * sizeof(double);
         if (smem > 48 * 1024)
@@ -570,6 +615,7 @@ cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream
         else if (S == 3) pick(std::integral_constant<int, 3>(), l0);
         else pick(std::integral_constant<int, 2>(), l0);
     }
+    if (planes_last > 0) k_mirror_planes<<<wsym.total, 256, 0, s>>>(in, wsym, sh.n_tslots + sh.m - 1, planes_last, dbg);
     return cudaGetLastError();
 }
 

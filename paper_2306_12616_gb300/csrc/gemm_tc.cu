@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     const int planes = st.planes;
     const int ew = warp - 2;  // 0..DW-1
     // store of the pair (grow, gcol), (grow, gcol + 1) for the elements whose flag is set
-    auto store_pair = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1) {
+    auto store_pair = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool master) {
         if (!(w0 || w1)) return;
         if (out64) {
             if (grow < n_real) {
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             split3(v1, F16, st.plane_scale, b0v, b1v, b2v);
         }
         if (w0 && w1) {
-            if (out_x) *reinterpret_cast<float2*>(out_x + o) = make_float2(v0, v1);
+            if (out_x && master) *reinterpret_cast<float2*>(out_x + o) = make_float2(v0, v1);
             if (planes > 0) {
                 uint16_t* pl = out_p + o;
                 *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0v << 16);
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         } else {
             const int e = w0 ? 0 : 1;
             const float v = w0 ? v0 : v1;
-            if (out_x) out_x[o + e] = v;
+            if (out_x && master) out_x[o + e] = v;
             if (planes > 0) {
                 uint16_t* pl = out_p + o + e;
                 pl[0] = w0 ? a0 : b0v;
@@ -643,10 +643,14 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             }
             tile[r * LD + c] = v0;
             tile[r * LD + c + 1] = v1;
-            store_pair(grow, gcol, v0, v1, !sym || gcol >= grow, !sym || gcol + 1 >= grow);
+            store_pair(grow, gcol, v0, v1, !sym || gcol >= grow, !sym || gcol + 1 >= grow, true);
         }
     }
     if (!sym) return;
+    // Below the diagonal the solver's slots need only the 16-bit planes (operands of later
+    // products, read by TMA as whole rows); every float32 master read (epilogue C and D,
+    // moments, contraction) stays on or above the diagonal.
+    const bool lower_master = st.lower_master != 0;
     asm volatile("bar.sync 1, %0;" ::"n"(32 * DW) : "memory");
     // mirror pass: output row n0 + c holds tile column c for the entries with col > row;
     // each drain warp takes TBN / 8 tile columns, lanes on row pairs
@@ -658,7 +662,8 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         for (int h = 0; h < kBM / 64; ++h) {
             const int r = h * 64 + 2 * lane;
             const int64_t gcol = (int64_t)m0 + r;   // output column
-            store_pair(grow, gcol, tile[r * LD + c], tile[(r + 1) * LD + c], grow > gcol, grow > gcol + 1);
+            store_pair(grow, gcol, tile[r * LD + c], tile[(r + 1) * LD + c], grow > gcol, grow > gcol + 1,
+                       lower_master);
         }
     }
 }

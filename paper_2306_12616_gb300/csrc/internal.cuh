@@ -92,6 +92,8 @@ struct Step {
     int32_t out64;             // 1: write the instance's float64 P (InstIO) instead of a slot
     int32_t planes;            // 16-bit planes to write for out
     int32_t fp16;
+    int32_t lower_master;      // symmetric mode: also write the float32 master below the
+                               // diagonal (the solver's slots keep it above the diagonal only)
     float alpha, beta, shift;  // float32 path; alpha includes the fp16 plane scales
     float plane_scale;
     double alpha64, beta64, shift64;
@@ -271,7 +273,7 @@ cudaError_t launch_bisect(const Inst* in, const InstIO* io, int batch, const Sha
 cudaError_t launch_set_mu(const Inst* in, const InstIO* io, int batch, cudaStream_t s);
 cudaError_t launch_coefficients(const Inst* in, const InstIO* io, int batch, const Shape& sh,
                                 const double* ct, int with_poly_trace, cudaStream_t s, int* launches);
-cudaError_t launch_contract(const Inst* in, Work we, const Shape& sh, cudaStream_t s, int* dbg);
+cudaError_t launch_contract(const Inst* in, Work we, Work wsym, const Shape& sh, cudaStream_t s, int* dbg);
 // g -> the paper's power-basis coefficients d (in place), for the Horner evaluation.
 cudaError_t launch_g_to_d(const Inst* in, int batch, const Shape& sh, cudaStream_t s);
 

@@ -503,12 +503,16 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
                     for (int b = 0; b < 4; ++b)
                         *reinterpret_cast<float4*>(bv[b]) = *reinterpret_cast<const float4*>(b0 + b * RS + e);
                     if (drow[u] >= 0) {
+                        // the entries left of the diagonal are not maintained (the float32
+                        // masters are kept on and above it only): select, never multiply
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             const int64_t col = dcol0[u] + e + v;
-                            const T w = col > drow[u] ? T(1) : (col == drow[u] ? T(0.5) : T(0));
 #pragma unroll
-                            for (int b = 0; b < 4; ++b) bv[b][v] *= w;
+                            for (int b = 0; b < 4; ++b)
+                                bv[b][v] = col > drow[u] ? bv[b][v] : (col == drow[u] ? T(0.5) * bv[b][v] : T(0));
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) gv[a][v] = col >= drow[u] ? gv[a][v] : T(0);
                         }
                     }
                     if constexpr (sizeof(T) == 4) {
@@ -645,9 +649,12 @@ __global__ void k_copy_out(const Inst* __restrict__ insts, const InstIO* __restr
     for (int rr = 0; rr < rows; ++rr) {
         const int64_t r = r0 + rr;
         if (r >= n) break;
-        for (int64_t c = threadIdx.x; c < n; c += blockDim.x)
-            P[r * ldp + c] = is64 ? reinterpret_cast<const double*>(src)[r * np + c]
-                                  : (double)reinterpret_cast<const float*>(src)[r * np + c];
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+            // float32 masters are kept on and above the diagonal only
+            const int64_t q = is64 || c >= r ? r * np + c : c * np + r;
+            P[r * ldp + c] = is64 ? reinterpret_cast<const double*>(src)[q]
+                                  : (double)reinterpret_cast<const float*>(src)[q];
+        }
     }
 }
 
