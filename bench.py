@@ -536,6 +536,24 @@ def main():
             per_n[str(n)]["fp64_gpu_ms"] = fp64_ms[n]
     stages = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
               for k, v in prof.items() if isinstance(v, dict)}
+    if args.precision != "fp64":
+        # algorithmic bytes per step of the HBM-bound stages (float32 masters kept on and above
+        # the diagonal, 16-bit planes in full; n_pad = N rounded up to 128) and the rate reached
+        hbm = pk.get("hbm_gbs")
+        byts = {"bounds": 0.0, "moments": 0.0, "contract": 0.0, "trace": 0.0}
+        for n in ns:
+            kk, mm = results[n]["k"], results[n]["m"]
+            npad = -(-n // 128) * 128
+            sp = {"bf16x3": 3, "fp16x2": 2, "bf16x1": 1}[args.precision]   # 16-bit planes
+            byts["bounds"] += 8 * n * n + 8 * n * (n + 1) / 2 + (4 + 2 * sp) * npad * npad
+            byts["moments"] += (kk - 1 + mm - 1) * 4 * npad * (npad + 128) / 2
+            byts["contract"] += (kk - 1 + mm) * 4 * npad * (npad + 4) / 2 + 3 * sp * npad * npad
+            byts["trace"] += 8 * n * n
+        for name, b in byts.items():
+            t = stages[name]["ms_per_step"] * 1e-3
+            stages[name]["algorithmic_bytes"] = b
+            stages[name]["achieved_gbs"] = b / t / 1e9 if t > 0 else None
+            stages[name]["frac_of_hbm"] = (b / t / 1e9) / hbm if (t > 0 and hbm) else None
     out = {
         "metric": METRIC, "value": value, "unit": "density matrices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
