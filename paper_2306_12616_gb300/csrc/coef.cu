@@ -21,9 +21,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Fermi-Dirac function f(e) = 1 / (1 + exp((e - mu)/kT)) (Eq. fermifunc) written as
-// (1 - tanh((e - mu)/(2 kT)))/2, which never overflows.
+// (1 - tanh((e - mu)/(2 kT)))/2, which never overflows. tanh(x) rounds to +-1 in float64 for
+// |x| >= 19.1, so beyond |x| = 20 f is 0 or 1 (the exact values differ by < 5e-18) and the
+// float64 tanh, slow on this GPU, is skipped: most Chebyshev nodes lie many kT away from mu.
 __device__ __forceinline__ double fermi(double e, double mu, double inv2kT) {
-    return 0.5 - 0.5 * tanh((e - mu) * inv2kT);
+    const double x = (e - mu) * inv2kT;
+    if (x >= 20.0) return 0.0;
+    if (x <= -20.0) return 1.0;
+    return 0.5 - 0.5 * tanh(x);
 }
 
 __global__ void k_cos_table(int M, double* ct) {
