@@ -164,9 +164,10 @@ __host__ __device__ inline int ew_blocks(int64_t np) {
     const int r = ew_rows(np);
     return (int)((np + r - 1) / r);
 }
-// Reduction row blocks (traces of P): about 64K entries per block.
+// Reduction row blocks (traces of P): about 16K entries per block, so that the loads of a
+// float64 P are spread over enough blocks to be in flight together.
 __host__ __device__ inline int red_rows(int64_t np) {
-    const int64_t r = 65536 / np;
+    const int64_t r = 16384 / np;
     return r < 1 ? 1 : (int)r;
 }
 __host__ __device__ inline int red_blocks(int64_t np) {

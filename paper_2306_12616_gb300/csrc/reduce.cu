@@ -273,7 +273,9 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
             const int64_t idx = r * np + c;
             if (!FO_CHK(dbg, r < np && c < np, 201, r, c)) continue;
             if (sh.is64) X64[idx] = v;
-            else store_split((float)v, X32 + idx, P16 + idx, np * np, sh.planes, sh.fp16, sh.pscale_t);
+            // below the diagonal only the planes are kept (float32 masters: on and above it)
+            else store_split((float)v, r <= c ? X32 + idx : nullptr, P16 + idx, np * np, sh.planes, sh.fp16,
+                             sh.pscale_t);
         }
     }
 }
@@ -623,17 +625,23 @@ __global__ void __launch_bounds__(256) k_trace_frob_part(const Inst* __restrict_
     }
 }
 
+// One warp per instance: lane l sums partials l, l + 32, ... in order, then a fixed shuffle
+// tree (deterministic for a given block count).
 __global__ void k_trace_frob_final(const Inst* __restrict__ insts, Work we, const double* partials) {
     const int i = blockIdx.x;
     DevResult* r = insts[i].res;
-    if (threadIdx.x != 0 || !r->active) return;
+    if (!r->active) return;
     double tr = 0.0, fr = 0.0;
-    for (int b = we.pre[i]; b < we.pre[i + 1]; ++b) {
+    for (int b = we.pre[i] + (int)threadIdx.x; b < we.pre[i + 1]; b += 32) {
         tr += partials[2 * (int64_t)b];
         fr += partials[2 * (int64_t)b + 1];
     }
-    r->trace = tr;
-    r->frob2 = fr;
+    tr = warp_sum(tr);
+    fr = warp_sum(fr);
+    if (threadIdx.x == 0) {
+        r->trace = tr;
+        r->frob2 = fr;
+    }
 }
 
 // P = R_0 (m = 1): slot n_tslots to the instance's float64 P.
