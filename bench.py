@@ -66,8 +66,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batch measurement")
     ap.add_argument("--batch-count", type=int, default=512, help="instances of the batch measurement")
     ap.add_argument("--tile", default="",
-                    help="force the product kernel's tile as NxCTASxDRAIN (e.g. 256x1x16) instead of "
-                         "autotuning it; profiling runs use this so the captured kernel is the timed one")
+                    help="force the product kernel's tile as NxCTASxDRAIN[xSTORE] (e.g. 256x1x16, or "
+                         "256x1x8x2 for upper-block plane storage) instead of autotuning it; profiling "
+                         "runs use this so the captured kernel is the timed one")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-mu measurement on the metallic model")
     ap.add_argument("--learned-pairs", type=int, default=20000,
@@ -82,8 +83,11 @@ def parse():
 def tile_args(spec: str) -> dict:
     if not spec:
         return {}
-    tn, ctas, drain = (int(x) for x in spec.lower().split("x"))
-    return {"tile_n": tn, "tile_ctas": ctas, "tile_drain": drain}
+    parts = [int(x) for x in spec.lower().split("x")]
+    out = {"tile_n": parts[0], "tile_ctas": parts[1], "tile_drain": parts[2]}
+    if len(parts) > 3:
+        out["tile_store"] = parts[3]
+    return out
 
 
 def dist_env():
@@ -274,6 +278,7 @@ def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300,
             "sum_n3": float(sum(float(n) ** 3 for n in ns_all)), "all_status_ok": ok,
             "worst_trace_err_over_N": worst_tr, "tile_n": res[0]["tile_n"],
             "tile_ctas": res[0]["tile_ctas"], "tile_drain": res[0]["tile_drain"],
+            "tile_store": res[0]["tile_store"],
             "eager_ms_per_batch": prof["call"]["ms"],
             "products_achieved_tflops": pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] > 0 else None,
             "products_share": pr["ms"] / max(1e-9, prof["call"]["ms"]),
@@ -541,7 +546,8 @@ def main():
         per_n[str(n)] = {"n_gemm": results[n]["n_gemm"], "k": results[n]["k"], "m": results[n]["m"],
                          "bisect_iters": results[n]["bisect_iters"], "mu_eV": results[n]["mu"],
                          "status": results[n]["status"], "tile_n": results[n]["tile_n"],
-                         "tile_ctas": results[n]["tile_ctas"], "tile_drain": results[n]["tile_drain"]}
+                         "tile_ctas": results[n]["tile_ctas"], "tile_drain": results[n]["tile_drain"],
+                         "tile_store": results[n]["tile_store"]}
         if n in accuracy:
             per_n[str(n)].update(accuracy[n])
             per_n[str(n)]["fp64_gpu_ms"] = fp64_ms[n]

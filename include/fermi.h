@@ -114,7 +114,13 @@ typedef struct {
     int32_t tile_drain;       /* warps draining the tensor-memory accumulators: 0 = autotune,
                                  8, or 16 (with tile_n = 256); set together with tile_n;
                                  other values fail with FO_ERR_ARG */
-    int32_t reserved;
+    int32_t tile_store;       /* storage of the 16-bit operand planes of the split forms' matrix
+                                 slots: 0 = chosen with the tile (autotuned with tile_n = 0,
+                                 else 1); 1 = the full square (the symmetric products mirror
+                                 each output tile); 2 = the 128 x 128 blocks on and above the
+                                 diagonal only, a block below read by the tensor cores as the
+                                 transpose of its counterpart above (MN-major operand tiles).
+                                 Results are bit-identical; other values fail with FO_ERR_ARG */
 } fo_params;
 
 typedef struct {
@@ -134,6 +140,7 @@ typedef struct {
     int32_t evals;            /* evaluations of P (1 unless FO_MU_LEARNED corrected mu) */
     int32_t order;            /* expansion order proposed by the learned model (0 if none) */
     int32_t tile_drain;       /* accumulator drain warps of the product kernel (0 for FP64) */
+    int32_t tile_store;       /* operand plane storage used (1 or 2 as in fo_params; 0 for FP64) */
 } fo_result;
 
 /* Stages of a density-matrix call, as recorded by the profiler. */

@@ -63,7 +63,7 @@ class FoParams(ctypes.Structure):
         ("emin", ctypes.c_double), ("emax", ctypes.c_double), ("max_bisect", ctypes.c_int32),
         ("flags", ctypes.c_uint32), ("tr_tol", ctypes.c_double), ("max_newton", ctypes.c_int32),
         ("tile_n", ctypes.c_int32), ("tile_ctas", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
-        ("tile_drain", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("tile_drain", ctypes.c_int32), ("tile_store", ctypes.c_int32),
     ]
 
 
@@ -75,7 +75,7 @@ class FoResult(ctypes.Structure):
         ("bisect_iters", ctypes.c_int32), ("learned_accepted", ctypes.c_int32),
         ("status", ctypes.c_int32), ("n_launches", ctypes.c_int32), ("tile_n", ctypes.c_int32),
         ("tile_ctas", ctypes.c_int32), ("evals", ctypes.c_int32), ("order", ctypes.c_int32),
-        ("tile_drain", ctypes.c_int32),
+        ("tile_drain", ctypes.c_int32), ("tile_store", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -332,7 +332,7 @@ class Solver:
                mu_mode: str | int = "bisect", k: int = 0, bounds=None, n_quad: int = 0,
                max_bisect: int = 0, flags: int = 0, tile_n: int = 0, tile_ctas: int = 0,
                tr_tol: float = 0.0, max_newton: int = 0, lanczos_steps: int = 0,
-               tile_drain: int = 0) -> FoParams:
+               tile_drain: int = 0, tile_store: int = 0) -> FoParams:
         p = FoParams()
         p.n_terms, p.k, p.kT, p.mu = n_terms, k, kT, mu
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
@@ -341,7 +341,7 @@ class Solver:
             p.use_given_bounds, p.emin, p.emax = 1, float(bounds[0]), float(bounds[1])
         p.n_quad, p.max_bisect, p.flags = n_quad, max_bisect, flags
         p.tile_n, p.tile_ctas, p.tr_tol, p.max_newton = tile_n, tile_ctas, tr_tol, max_newton
-        p.lanczos_steps, p.tile_drain = lanczos_steps, tile_drain
+        p.lanczos_steps, p.tile_drain, p.tile_store = lanczos_steps, tile_drain, tile_store
         return p
 
     def spectral_bounds(self, h, stream=None):

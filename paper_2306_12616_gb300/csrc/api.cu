@@ -33,12 +33,13 @@ enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUND
 struct PlanKey {
     std::vector<int64_t> n;
     int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
-    int use_given = 0, tile_req = 0, ctas_req = 0, drain_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0, power = 0;
+    int use_given = 0, tile_req = 0, ctas_req = 0, drain_req = 0, store_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0, power = 0;
     double tr_tol = 0.0;
     bool operator==(const PlanKey& o) const {
         return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
                mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
-               tile_req == o.tile_req && ctas_req == o.ctas_req && drain_req == o.drain_req && sym == o.sym && max_bisect == o.max_bisect &&
+               tile_req == o.tile_req && ctas_req == o.ctas_req && drain_req == o.drain_req &&
+               store_req == o.store_req && sym == o.sym && max_bisect == o.max_bisect &&
                max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged && lanczos == o.lanczos && power == o.power;
     }
 };
@@ -70,11 +71,12 @@ struct Plan {
     std::vector<Inst> inst;   // host copy, sorted
     std::vector<Bucket> buckets;
     std::vector<Group> groups;
-    std::vector<unsigned char> maps;   // 128 bytes per bucket
+    std::vector<unsigned char> maps;   // 256 bytes per bucket: K-major and MN-major tensor maps
     HostWork wg, wsc, we, wr, wgr, wtc[2], wf64;   // wtc[0]: 256-wide tiles, wtc[1]: 128-wide
     int tile_n = 0;
     int tile_ctas = 0;
     int tile_drain = 0;
+    int tile_store = 0;   // 1: full planes, 2: upper 128-blocks (sh.ublk); 0 for FP64
     int npairs = 0;
     void* dtab = nullptr;     // device tables: Inst[], InstIO[], prefixes
     Inst* d_inst = nullptr;
@@ -168,6 +170,16 @@ bool debug_sync() {
     static int v = -1;
     if (v < 0) {
         const char* e = getenv("FERMI_DEBUG_SYNC");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+// FERMI_AUTOTUNE_LOG=1: print every autotuned plan's candidate timings to stderr.
+bool autotune_log() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("FERMI_AUTOTUNE_LOG");
         v = (e && e[0] == '1') ? 1 : 0;
     }
     return v == 1;
@@ -466,14 +478,16 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
         return fail(ctx, FO_ERR_CUDA, "plan table upload failed");
     // tensor maps: one per bucket over (column, row, plane, slot, instance)
     if (!sh.is64 && p->n_slots > 0) {
-        p->maps.assign(128 * p->buckets.size(), 0);
+        p->maps.assign(256 * p->buckets.size(), 0);
         for (size_t b = 0; b < p->buckets.size(); ++b) {
             const Bucket& bk = p->buckets[b];
             const char* planes0 = W + bk.off + 4 * (size_t)bk.np * (size_t)bk.np;
             std::string err;
-            if (!tc_make_map(p->maps.data() + 128 * b, planes0, bk.np, sh.planes, p->n_slots, bk.count,
-                             p->inst[bk.first].slot_bytes, bk.inst_bytes, sh.fp16 != 0, &err))
-                return fail(ctx, FO_ERR_CUDA, "tensor map: " + err);
+            for (int q = 0; q < 2; ++q)   // K-major tiles, then MN-major tiles
+                if (!tc_make_map(p->maps.data() + 256 * b + 128 * q, planes0, bk.np, sh.planes, p->n_slots,
+                                 bk.count, p->inst[bk.first].slot_bytes, bk.inst_bytes, sh.fp16 != 0, &err,
+                                 q == 1))
+                    return fail(ctx, FO_ERR_CUDA, "tensor map: " + err);
         }
     }
     // the cosine table depends on M only
@@ -533,8 +547,8 @@ fo_status run_products(fo_ctx* ctx, Plan& p, const Step* steps, int nsteps, cuda
                 const int tile0 = w.pre[g.i0];
                 cudaError_t e = tc_gemm(p.key.prec, p.tile_n, p.tile_ctas, p.tile_drain, steps + q0, nq, p.d_inst, p.d_io,
                                         w.dev.pre, g.i0, g.i1, tile0, w.pre[g.i1] - tile0,
-                                        p.maps.data() + 128 * (size_t)g.b0, g.b0, g.nb, ctx->flag, s, &err,
-                                        p.key.sym);
+                                        p.maps.data() + 256 * (size_t)g.b0, g.b0, g.nb, ctx->flag, s, &err,
+                                        p.key.sym ? (p.sh.ublk ? 2 : 1) : 0);
                 if (e == cudaSuccess && debug_sync() && !ctx->capturing) e = cudaDeviceSynchronize();
                 if (e != cudaSuccess) {
                     const std::string where = std::string("tc_gemm ") + tag + " " + std::to_string(index);
@@ -798,20 +812,24 @@ fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
 // on this plan's first baby step, timed with CUDA events on the plan's own layout (the data
 // are whatever the workspace holds; the work does not depend on them).
 fo_status autotune(fo_ctx* ctx, Plan& p) {
+    p.sh.ublk = 0;
     if (p.sh.is64 || p.n_slots == 0) {
-        p.tile_n = p.tile_ctas = p.tile_drain = 0;
+        p.tile_n = p.tile_ctas = p.tile_drain = p.tile_store = 0;
         return FO_OK;
     }
     if (p.key.tile_req) {
         p.tile_n = p.key.tile_req;
         p.tile_ctas = p.key.ctas_req ? p.key.ctas_req : 1;
         p.tile_drain = p.key.drain_req ? p.key.drain_req : 8;
+        p.tile_store = (p.key.store_req == 2 && p.key.sym) ? 2 : 1;
+        p.sh.ublk = p.tile_store == 2;
         return FO_OK;
     }
     if (p.key.mode == MODE_PRODUCT || p.sh.k < 2) {
         p.tile_n = 256;
         p.tile_ctas = 1;
         p.tile_drain = 8;
+        p.tile_store = 1;
         return FO_OK;
     }
     // make every instance active (the per-call inputs are not needed by a product)
@@ -822,14 +840,19 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
     const Step st = make_step(p, 0, 0, -1, -1, 1, 2.0, 0.0, -1.0, false, false, false, false, ctx);
     cudaEvent_t e0 = ev_get(ctx), e1 = ev_get(ctx);
     float best = 0.0f;
-    int bn = 256, bc = 1, bd = 8;
+    int bn = 256, bc = 1, bd = 8, bs = 1;
     const bool prof = ctx->prof;
     ctx->prof = false;
-    const int cands[4][3] = {{256, 1, 8}, {256, 1, 16}, {128, 1, 8}, {128, 2, 8}};
-    for (int ci = 0; ci < 4; ++ci) {
+    // tile width, CTAs per SM, drain warps, plane storage (the upper-block storage trades the
+    // mirrored epilogue writes for transposed operand loads: it pays on short tiles)
+    const int cands[8][4] = {{256, 1, 8, 1}, {256, 1, 16, 1}, {128, 1, 8, 1}, {128, 2, 8, 1},
+                             {256, 1, 8, 2}, {256, 1, 16, 2}, {128, 1, 8, 2}, {128, 2, 8, 2}};
+    const int ncand = p.key.sym ? 8 : 4;
+    for (int ci = 0; ci < ncand; ++ci) {
         p.tile_n = cands[ci][0];
         p.tile_ctas = cands[ci][1];
         p.tile_drain = cands[ci][2];
+        p.sh.ublk = cands[ci][3] == 2;
         Run r;
         fo_status rs = run_product(ctx, p, st, s, "autotune", ci, &r);   // warm-up
         if (rs != FO_OK) { ctx->prof = prof; return rs; }
@@ -844,11 +867,16 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
             ctx->prof = prof;
             return fail(ctx, FO_ERR_CUDA, "autotune timing failed");
         }
+        if (autotune_log())
+            std::fprintf(stderr, "autotune n0=%lld batch=%d tile %dx%dx%d store %d: %.4f ms per product\n",
+                         (long long)p.key.n[0], p.batch, cands[ci][0], cands[ci][1], cands[ci][2], cands[ci][3],
+                         ms / 3.0);
         if (ci == 0 || ms < best) {
             best = ms;
             bn = cands[ci][0];
             bc = cands[ci][1];
             bd = cands[ci][2];
+            bs = cands[ci][3];
         }
     }
     ctx->prof = prof;
@@ -860,6 +888,8 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
     p.tile_n = bn;
     p.tile_ctas = bc;
     p.tile_drain = bd;
+    p.tile_store = bs;
+    p.sh.ublk = bs == 2;
     return FO_OK;
 }
 
@@ -915,6 +945,8 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
     if (prm->tile_ctas < 0 || prm->tile_ctas > 2 || (prm->tile_ctas == 2 && prm->tile_n != 128) ||
         (prm->tile_ctas != 0 && prm->tile_n == 0))
         return fail(ctx, FO_ERR_ARG, "tile_ctas must be 0, 1 or 2 (2 with tile_n = 128), set with tile_n");
+    if (prm->tile_store < 0 || prm->tile_store > 2 || (prm->tile_store != 0 && prm->tile_n == 0))
+        return fail(ctx, FO_ERR_ARG, "tile_store must be 0, 1 or 2, set with tile_n");
     return FO_OK;
 }
 
@@ -959,6 +991,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
     key.tile_req = prm->tile_n;
     key.ctas_req = prm->tile_ctas;
     key.drain_req = prm->tile_drain;
+    key.store_req = prm->tile_store;
     key.max_bisect = prm->max_bisect;
     key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
     key.lanczos = prm->lanczos_steps;
@@ -1053,6 +1086,7 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
             r.tile_n = p->tile_n;
             r.tile_ctas = p->tile_ctas;
             r.tile_drain = p->tile_drain;
+            r.tile_store = p->tile_store;
             r.evals = 1;
             r.order = 0;
             if (prm->mu_mode == FO_MU_LEARNED) {
@@ -1181,6 +1215,7 @@ fo_status features_batch(fo_ctx* ctx, int batch, const double* const* dH, const 
     key.tile_req = q.tile_n;
     key.ctas_req = q.tile_ctas;
     key.drain_req = q.tile_drain;
+    key.store_req = q.tile_store;
     key.max_bisect = q.max_bisect;
     key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
     key.lanczos = q.lanczos_steps;

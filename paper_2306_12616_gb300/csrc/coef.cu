@@ -497,9 +497,11 @@ __global__ void __launch_bounds__(kCtEntries, 2) k_contract_f32(const Inst* __re
 
 // The 16-bit planes of one slot below the diagonal from those above it: block (bi, bj),
 // bj >= bi, of 32 x 32 entries (the enumeration of k_scale_sym) is staged in shared memory
-// and written transposed at (bj, bi); a diagonal block fills its own lower half.
+// and written transposed at (bj, bi); a diagonal block fills its own lower half. With ublk
+// only the diagonal 128-blocks are completed (a lower 128-block is then read as the
+// transpose of its upper counterpart).
 __global__ void __launch_bounds__(256) k_mirror_planes(const Inst* __restrict__ insts, Work ws, int slot,
-                                                       int planes, int* dbg) {
+                                                       int planes, int ublk, int* dbg) {
     __shared__ uint16_t tile[3][32][34];
     const int i = find_inst(ws.pre, 0, ws.count, blockIdx.x);
     if (!insts[i].res->active) return;
@@ -508,6 +510,7 @@ __global__ void __launch_bounds__(256) k_mirror_planes(const Inst* __restrict__ 
     int bi = 0, b = blockIdx.x - ws.pre[i];
     while (b >= tn - bi) { b -= tn - bi; ++bi; }
     const int bj = bi + b;
+    if (ublk && bi * 32 / kPad != bj * 32 / kPad) return;
     const int64_t ps = np * np;
     uint16_t* P16 = reinterpret_cast<uint16_t*>(insts[i].slots + insts[i].slot_bytes * slot + 4 * ps);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -620,7 +623,8 @@ cudaError_t launch_contract(const Inst* in, Work we, Work wsym, const Shape& sh,
         else if (S == 3) pick(std::integral_constant<int, 3>(), l0);
         else pick(std::integral_constant<int, 2>(), l0);
     }
-    if (planes_last > 0) k_mirror_planes<<<wsym.total, 256, 0, s>>>(in, wsym, sh.n_tslots + sh.m - 1, planes_last, dbg);
+    if (planes_last > 0) k_mirror_planes<<<wsym.total, 256, 0, s>>>(in, wsym, sh.n_tslots + sh.m - 1, planes_last,
+                                                         sh.ublk, dbg);
     return cudaGetLastError();
 }
 

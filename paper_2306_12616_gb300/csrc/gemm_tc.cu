@@ -25,6 +25,16 @@
 // unstable: in the eigenbasis of X the pair (T_ab, T_ba) is multiplied by a matrix with
 // eigenvalues +-2 sqrt(l_a l_b), which grows geometrically whenever l_a l_b < 0.)
 //
+// Plane storage (per plan). Full: every output tile is also written transposed, so each
+// operand block is loaded K-major. Upper blocks: only the 128 x 128 blocks on and above the
+// diagonal hold planes (the diagonal blocks whole); an operand block left of the diagonal
+// is the transpose of a stored block and is loaded from it as an MN-major tile (boxes of 64
+// columns x 32 rows, 128-byte swizzle), which saves the mirrored plane writes of the
+// epilogue and about a quarter of the DRAM traffic but makes the tiles of the lower row
+// blocks load more boxes. The autotuner picks whichever is faster for the batch (short
+// tiles favour the upper blocks, long tiles the full storage); the products are the same
+// sums in the same order, so the results are bit-identical.
+//
 // Accumulation. The tensor core rounds its float32 accumulator once per instruction, so a
 // long chain of MMAs into one accumulator loses accuracy linearly in K. Each k-block (32 k)
 // is therefore accumulated afresh into one of two TMEM accumulators (ping-pong) and drained
@@ -52,6 +62,7 @@
 
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -185,6 +196,25 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory descriptor of an MN-major operand tile staged by TMA as boxes of 64 MN
+// entries (128 bytes, 128-byte swizzle) x 32 k rows: 8-row core groups 1 KB apart along k
+// (stride byte offset), 64-entry MN groups one 4 KB box apart (leading byte offset). The k16
+// slices of a 32-wide k-block start 16 rows (2 KB) apart.
+constexpr int kMnBoxCols = 64;
+constexpr int kMnBoxBytes = kMnBoxCols * 2 * kBK;   // 4 KB
+constexpr int kMnKStep = 16 * kMnBoxCols * 2;       // bytes per k16 slice
+__device__ __forceinline__ uint64_t sdesc_mn128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(kMnBoxBytes >> 4) << 16;   // leading byte offset: next 64-entry MN group
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8 k rows
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // SWIZZLE_128B
+    return d;
+}
+constexpr uint32_t kIdescMnA = 1u << 15;   // instruction descriptor: A is MN-major
+constexpr uint32_t kIdescMnB = 1u << 16;   // instruction descriptor: B is MN-major
+
 // Instruction descriptor, kind::f16: float32 accumulator, A/B bf16 (1) or fp16 (0), both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_f16(int tile_n, bool fp16) {
@@ -200,7 +230,8 @@ __device__ __forceinline__ uint16_t bits_bf16(float v) {
 constexpr int kBoxBytes = kBM * kRowBytes;   // one 128-row TMA box of one plane: 8 KB
 
 struct TcMaps {
-    CUtensorMap m[kMaxBuckets];
+    CUtensorMap m[kMaxBuckets];    // boxes of 32 columns x 128 rows (K-major operand tiles)
+    CUtensorMap mn[kMaxBuckets];   // boxes of 64 columns x 32 rows, 128-byte swizzle (MN-major tiles)
 };
 
 // MINB CTAs share an SM (1, or 2 for 128-wide tiles: one CTA's epilogue then overlaps the
@@ -321,6 +352,8 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     if (!in.res->active) return;
     const int np = (int)in.np;
     const CUtensorMap* map = &maps.m[in.bucket - b0];
+    const CUtensorMap* map_mn = &maps.mn[in.bucket - b0];
+    const bool ub = sym == 2;   // upper-block storage: lower operand blocks read transposed
     const int ib = in.in_bucket;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -355,6 +388,7 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         mbar_init(acc_full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+        if (sym == 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map_mn)) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -396,14 +430,45 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
                     break;
                 }
                 mbar_expect_tx(&full[s], stage_tx);
+                // upper-block storage: a 128-row operand block left of the diagonal block is
+                // not stored; its transpose (above the diagonal) is loaded as an MN-major tile
+                const int KB = kb * kBK / kBM;
+                const bool a_mn = ub && KB < m0 / kBM;
+                if (!ub || (!a_mn && KB >= n0 / kBM + nbox - 1)) {
 #pragma unroll
-                for (int p = 0; p < PA; ++p)
-                    tma_load_5d(stage_a(s, p), map, &full[s], kb * kBK, m0, p, st.a, ib);
+                    for (int p = 0; p < PA; ++p)
+                        tma_load_5d(stage_a(s, p), map, &full[s], kb * kBK, m0, p, st.a, ib);
 #pragma unroll
-                for (int p = 0; p < PB; ++p)
-                    for (int j = 0; j < nbox; ++j)
-                        tma_load_5d(stage_b(s, p) + j * kBoxBytes, map, &full[s], kb * kBK, n0 + j * kBM, p,
-                                    st.b, ib);
+                    for (int p = 0; p < PB; ++p)
+                        for (int j = 0; j < nbox; ++j)
+                            tma_load_5d(stage_b(s, p) + j * kBoxBytes, map, &full[s], kb * kBK, n0 + j * kBM, p,
+                                        st.b, ib);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < PA; ++p) {
+                        if (!a_mn) {
+                            tma_load_5d(stage_a(s, p), map, &full[s], kb * kBK, m0, p, st.a, ib);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < kBM / kMnBoxCols; ++q)
+                                tma_load_5d(stage_a(s, p) + q * kMnBoxBytes, map_mn, &full[s],
+                                            m0 + kMnBoxCols * q, kb * kBK, p, st.a, ib);
+                        }
+                    }
+#pragma unroll
+                    for (int p = 0; p < PB; ++p)
+                        for (int j = 0; j < nbox; ++j) {
+                            if (KB >= n0 / kBM + j) {
+                                tma_load_5d(stage_b(s, p) + j * kBoxBytes, map, &full[s], kb * kBK, n0 + j * kBM,
+                                            p, st.b, ib);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < kBM / kMnBoxCols; ++q)
+                                    tma_load_5d(stage_b(s, p) + j * kBoxBytes + q * kMnBoxBytes, map_mn, &full[s],
+                                                n0 + j * kBM + kMnBoxCols * q, kb * kBK, p, st.b, ib);
+                            }
+                        }
+                }
                 issued = kb + 1;
             }
             // every operand is requested: bring the epilogue's C and D rows of this tile
@@ -436,40 +501,65 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer: one k-block per accumulator, corrections first
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % S, buf = kb & 1;
-                if (kb >= 2) {
-                    if (!mbar_wait(&seg_empty[buf], ((kb >> 1) - 1) & 1, kWaitNs, vabort)) {
+            // ---------------- MMA issuer: one k-block per accumulator, corrections first.
+            // The loop is instantiated once per plane storage, so the K-major one carries no
+            // trace of the MN-major layouts (a runtime layout branch in it cost 5%).
+            auto issue = [&](auto ub_tag) {
+                constexpr bool U = decltype(ub_tag)::value;
+                for (int kb = 0; kb < nk; ++kb) {
+                    const int s = kb % S, buf = kb & 1;
+                    if (kb >= 2) {
+                        if (!mbar_wait(&seg_empty[buf], ((kb >> 1) - 1) & 1, kWaitNs, vabort)) {
+                            atomicExch(&abort_flag, 1);
+                            atomicExch(err_flag, 1);
+                            break;
+                        }
+                    }
+                    if (!mbar_wait(&full[s], (kb / S) & 1, kWaitNs, vabort)) {
                         atomicExch(&abort_flag, 1);
                         atomicExch(err_flag, 1);
                         break;
                     }
-                }
-                if (!mbar_wait(&full[s], (kb / S) & 1, kWaitNs, vabort)) {
-                    atomicExch(&abort_flag, 1);
-                    atomicExch(err_flag, 1);
-                    break;
-                }
-                fence_after();
-                const uint32_t d = tmem + buf * TBN;
+                    fence_after();
+                    const uint32_t d = tmem + buf * TBN;
+                    // operand layouts of this k-block (see the producer): K-major tiles advance
+                    // 32 bytes per k16 slice, MN-major tiles 16 rows (2 KB)
+                    const int KB = kb * kBK / kBM;
+                    const bool a_mn = U && KB < m0 / kBM;
+                    const bool b0_mn = U && KB < n0 / kBM;
+                    const bool b1_mn = U && KB < n0 / kBM + 1;
+                    auto adesc = [&](int p, int kk) {
+                        const uint32_t base = smem_u32(stage_a(s, p));
+                        return a_mn ? sdesc_mn128(base + kk * kMnKStep) : sdesc_sw64(base + kk * 32);
+                    };
+                    auto bdesc = [&](int p, int kk, int j, bool mn) {
+                        const uint32_t base = smem_u32(stage_b(s, p)) + j * kBoxBytes;
+                        return mn ? sdesc_mn128(base + kk * kMnKStep) : sdesc_sw64(base + kk * 32);
+                    };
+                    // the two 128-column halves of B may differ in layout (the k-block of the
+                    // diagonal block of the first half): one MMA per half when they do
+                    const int halves = (!U || nbox == 1 || b0_mn == b1_mn) ? 1 : 2;
+                    const uint32_t idh = (halves == 1 ? idesc : idesc_f16(kBM, F16)) | (a_mn ? kIdescMnA : 0u);
+                    for (int j = 0; j < halves; ++j) {
+                        const bool mn = j ? b1_mn : b0_mn;
+                        const uint32_t id = idh | (mn ? kIdescMnB : 0u);
 #pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk) {
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
 #pragma unroll
-                    for (int pr = 1; pr < NPROD; ++pr) {
-                        umma_f16(d, sdesc_sw64(smem_u32(stage_a(s, prod_a(pr))) + kk * 32),
-                                 sdesc_sw64(smem_u32(stage_b(s, prod_b(pr))) + kk * 32), idesc,
-                                 !(kk == 0 && pr == 1));
+                            for (int pr = 1; pr < NPROD; ++pr)
+                                umma_f16(d + j * kBM, adesc(prod_a(pr), kk), bdesc(prod_b(pr), kk, j, mn), id,
+                                         !(kk == 0 && pr == 1));
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk)
+                            umma_f16(d + j * kBM, adesc(0, kk), bdesc(0, kk, j, mn), id, (NPROD > 1) || kk > 0);
                     }
+                    umma_commit(&empty[s]);
+                    umma_commit(&seg_full[buf]);
                 }
-#pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk) {
-                    umma_f16(d, sdesc_sw64(smem_u32(stage_a(s, 0)) + kk * 32),
-                             sdesc_sw64(smem_u32(stage_b(s, 0)) + kk * 32), idesc, (NPROD > 1) || kk > 0);
-                }
-                umma_commit(&empty[s]);
-                umma_commit(&seg_full[buf]);
-            }
+            };
+            if (ub) issue(std::true_type{});
+            else issue(std::false_type{});
             // arrives once every issued MMA has completed (also after an abort)
             umma_commit(acc_full);
         }
@@ -658,6 +748,11 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         const int c = ew * (TBN / DW) + cc;
         const int64_t grow = (int64_t)n0 + c;       // output row
         if (c >= tile_n) break;
+        // upper-block storage keeps planes for the 128-row blocks on and above the diagonal
+        // block only (a lower block is read as the transpose of its upper counterpart):
+        // outside the tile's diagonal block nothing below the diagonal is written, except
+        // into the caller's float64 P, which is returned whole
+        if (ub && !lower_master && !out64 && grow >= (int64_t)m0 + kBM) break;
 #pragma unroll
         for (int h = 0; h < kBM / 64; ++h) {
             const int r = h * 64 + 2 * lane;
@@ -732,19 +827,19 @@ int64_t tc_tiles(int64_t np, int tile_n) {
 }
 
 bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int nslots, int count,
-                 int64_t slot_bytes, int64_t inst_bytes, bool fp16, std::string* err) {
+                 int64_t slot_bytes, int64_t inst_bytes, bool fp16, std::string* err, bool mn) {
     EncodeFn enc = get_encode(err);
     if (!enc) return false;
     cuuint64_t dims[5] = {(cuuint64_t)np, (cuuint64_t)np, (cuuint64_t)nplanes, (cuuint64_t)nslots,
                           (cuuint64_t)count};
     cuuint64_t strides[4] = {(cuuint64_t)np * 2, (cuuint64_t)np * np * 2, (cuuint64_t)slot_bytes,
                              (cuuint64_t)inst_bytes};
-    cuuint32_t box[5] = {(cuuint32_t)kBK, (cuuint32_t)kBM, 1, 1, 1};
+    cuuint32_t box[5] = {(cuuint32_t)(mn ? kMnBoxCols : kBK), (cuuint32_t)(mn ? kBK : kBM), 1, 1, 1};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = enc(reinterpret_cast<CUtensorMap*>(map128),
                      fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
                      const_cast<void*>(planes0), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     mn ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         if (err) *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
@@ -765,7 +860,10 @@ cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps
     if (tiles <= 0) return cudaSuccess;
     static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
     TcMaps tm;
-    std::memcpy(&tm.m[0], maps, sizeof(CUtensorMap) * nb);
+    for (int b = 0; b < nb; ++b) {
+        std::memcpy(&tm.m[b], static_cast<const char*>(maps) + 256 * (size_t)b, sizeof(CUtensorMap));
+        std::memcpy(&tm.mn[b], static_cast<const char*>(maps) + 256 * (size_t)b + 128, sizeof(CUtensorMap));
+    }
     StepList st;
     for (int q = 0; q < nsteps; ++q) st.s[q] = steps[q];
     st.count = nsteps;

@@ -81,7 +81,9 @@ struct InstIO {
 struct Shape {
     int32_t k, m, km, n_terms, M;
     int32_t n_tslots;     // T slots per instance (R slot l is n_tslots + l)
-    int32_t planes, fp16, is64, pad_;
+    int32_t planes, fp16, is64;
+    int32_t ublk;         // 1: the slots' 16-bit planes hold the 128-blocks on and above the
+                          // diagonal only (a lower block is read transposed by the products)
     float pscale_t, pscale_r;
 };
 
@@ -287,13 +289,17 @@ constexpr int kMaxBuckets = 16;   // tensor maps per grouped launch
 int64_t tc_tiles(int64_t np, int tile_n);
 int tc_planes(int prec);
 // 5-D tensor map over the planes of every slot of every instance of one bucket:
-// (column, row, plane, slot, instance), 16-bit elements, box 32 x 128 x 1 x 1 x 1.
+// (column, row, plane, slot, instance), 16-bit elements: boxes of 32 columns x 128 rows with
+// 64-byte swizzle (K-major operand tiles) or, with mn, 64 columns x 32 rows with 128-byte
+// swizzle (MN-major operand tiles).
 bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int nslots, int count,
-                 int64_t slot_bytes, int64_t inst_bytes, bool fp16, std::string* err);
+                 int64_t slot_bytes, int64_t inst_bytes, bool fp16, std::string* err, bool mn);
 // Grouped split-precision product over instances [i0, i1) (sorted by tile count, buckets
-// [b0, b0 + nb) with maps[0..nb)), tile_n = 256 or 128 output columns per tile.
+// [b0, b0 + nb) with maps: 256 bytes per bucket, its K-major then its MN-major tensor map),
+// tile_n = 256 or 128 output columns per tile.
 // ctas = CTAs per SM (2 only with tile_n = 128). sym = 0 computes every tile of the full
-// product (fo_recurrence_product only).
+// product (fo_recurrence_product only), 1 the tiles on and above the diagonal of a symmetric
+// product over fully stored planes, 2 the same over planes stored as upper 128-blocks.
 // drain = TMEM drain warps (8, or 16 with 256-wide tiles).
 cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in, const InstIO* io,
                     const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,

@@ -252,7 +252,10 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
     uint16_t* P16 = reinterpret_cast<uint16_t*>(slot + 4 * np * np);
     for (int ry = ty; ry < 32; ry += 8) {
         // (bi*32 + ry, bj*32 + tx); in a diagonal tile the lower half mirrors the upper
-        for (int pass = 0; pass < (bi == bj ? 1 : 2); ++pass) {
+        // upper-block storage keeps the transposed tile below the diagonal inside the diagonal
+        // 128-block only (a lower 128-block is read as the transpose of its upper counterpart)
+        const bool lower = bi != bj && (!sh.ublk || bi * 32 / kPad == bj * 32 / kPad);
+        for (int pass = 0; pass < (lower ? 2 : 1); ++pass) {
             int64_t r, c;
             double h;
             if (pass == 0) {

@@ -68,18 +68,25 @@ def test_batch_equals_single_calls(solver):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp16x2", "bf16x1"])
 def test_tile_configs_bit_identical(solver, prec):
-    """Every tile configuration the autotuner may pick gives the same bits."""
+    """Every tile configuration and plane storage the autotuner may pick gives the same bits."""
     ns, kts, hs = batch(5, 3, 100, 700)
     hd = [to_dev(h) for h in hs]
     out = {}
     for t, c, d in ((256, 1, 8), (256, 1, 16), (128, 1, 8), (128, 2, 8)):
-        prm = solver.params(300, 0.1, precision=prec, mu_mode="bisect", tile_n=t, tile_ctas=c, tile_drain=d)
-        ps, res = solver.density_matrix_batched(hd, [n / 2 for n in ns], prm, kT=kts)
-        assert all(r["tile_n"] == t and r["tile_ctas"] == c and r["tile_drain"] == d for r in res)
-        out[(t, c, d)] = ps
-    for key in ((256, 1, 16), (128, 1, 8), (128, 2, 8)):
-        for a, b in zip(out[(256, 1, 8)], out[key]):
+        for st in (1, 2):
+            prm = solver.params(300, 0.1, precision=prec, mu_mode="bisect", tile_n=t, tile_ctas=c, tile_drain=d,
+                                tile_store=st)
+            ps, res = solver.density_matrix_batched(hd, [n / 2 for n in ns], prm, kT=kts)
+            assert all(r["tile_n"] == t and r["tile_ctas"] == c and r["tile_drain"] == d and r["tile_store"] == st
+                       for r in res)
+            out[(t, c, d, st)] = ps
+    for key in out:
+        for a, b in zip(out[(256, 1, 8, 1)], out[key]):
             assert torch.equal(a, b), key
+    # the autotuner's pick is one of them
+    _, res = solver.density_matrix_batched(hd, [n / 2 for n in ns],
+                                           solver.params(300, 0.1, precision=prec, mu_mode="bisect"), kT=kts)
+    assert all(r["tile_store"] in (1, 2) for r in res)
 
 
 def test_graph_replay_equals_eager(solver):
