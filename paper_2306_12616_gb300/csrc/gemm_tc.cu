@@ -414,36 +414,28 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer
+            // ---------------- TMA producer (instantiated per plane storage, as the MMA issuer)
             int issued = 0;
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % S;
-                if (kb >= S) {
-                    if (!mbar_wait(&empty[s], ((kb / S) - 1) & 1, kWaitNs, vabort)) {
+            auto produce = [&](auto ub_tag) {
+                constexpr bool U = decltype(ub_tag)::value;
+                for (int kb = 0; kb < nk; ++kb) {
+                    const int s = kb % S;
+                    if (kb >= S) {
+                        if (!mbar_wait(&empty[s], ((kb / S) - 1) & 1, kWaitNs, vabort)) {
+                            atomicExch(&abort_flag, 1);
+                            atomicExch(err_flag, 1);
+                            break;
+                        }
+                    }
+                    if (!FO_CHK(st.dbg, kb * kBK < np && m0 + kBM <= np && n0 + tile_n <= np, 108, m0, n0)) {
                         atomicExch(&abort_flag, 1);
-                        atomicExch(err_flag, 1);
                         break;
                     }
-                }
-                if (!FO_CHK(st.dbg, kb * kBK < np && m0 + kBM <= np && n0 + tile_n <= np, 108, m0, n0)) {
-                    atomicExch(&abort_flag, 1);
-                    break;
-                }
-                mbar_expect_tx(&full[s], stage_tx);
-                // upper-block storage: a 128-row operand block left of the diagonal block is
-                // not stored; its transpose (above the diagonal) is loaded as an MN-major tile
-                const int KB = kb * kBK / kBM;
-                const bool a_mn = ub && KB < m0 / kBM;
-                if (!ub || (!a_mn && KB >= n0 / kBM + nbox - 1)) {
-#pragma unroll
-                    for (int p = 0; p < PA; ++p)
-                        tma_load_5d(stage_a(s, p), map, &full[s], kb * kBK, m0, p, st.a, ib);
-#pragma unroll
-                    for (int p = 0; p < PB; ++p)
-                        for (int j = 0; j < nbox; ++j)
-                            tma_load_5d(stage_b(s, p) + j * kBoxBytes, map, &full[s], kb * kBK, n0 + j * kBM, p,
-                                        st.b, ib);
-                } else {
+                    mbar_expect_tx(&full[s], stage_tx);
+                    // upper-block storage: a 128-row operand block left of the diagonal block is
+                    // not stored; its transpose (above the diagonal) is loaded as an MN-major tile
+                    const int KB = kb * kBK / kBM;
+                    const bool a_mn = U && KB < m0 / kBM;
 #pragma unroll
                     for (int p = 0; p < PA; ++p) {
                         if (!a_mn) {
@@ -458,7 +450,7 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
 #pragma unroll
                     for (int p = 0; p < PB; ++p)
                         for (int j = 0; j < nbox; ++j) {
-                            if (KB >= n0 / kBM + j) {
+                            if (!(U && KB < n0 / kBM + j)) {
                                 tma_load_5d(stage_b(s, p) + j * kBoxBytes, map, &full[s], kb * kBK, n0 + j * kBM,
                                             p, st.b, ib);
                             } else {
@@ -468,9 +460,11 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
                                                 n0 + j * kBM + kMnBoxCols * q, kb * kBK, p, st.b, ib);
                             }
                         }
+                    issued = kb + 1;
                 }
-                issued = kb + 1;
-            }
+            };
+            if (ub) produce(std::true_type{});
+            else produce(std::false_type{});
             // every operand is requested: bring the epilogue's C and D rows of this tile
             // into L2 while the last k-blocks are multiplied (prefetch hints, in bounds)
             if (!*vabort) {
@@ -504,10 +498,29 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             // ---------------- MMA issuer: one k-block per accumulator, corrections first.
             // The loop is instantiated once per plane storage, so the K-major one carries no
             // trace of the MN-major layouts (a runtime layout branch in it cost 5%).
+            // Descriptors: the address field (bits 0-13, address / 16) of a stage's operand is
+            // the ring base's plus a compile-time offset, so each MMA's descriptor is one add.
+            const uint64_t d_k = sdesc_sw64(smem_u32(smem)), d_mn = sdesc_mn128(smem_u32(smem));
             auto issue = [&](auto ub_tag) {
                 constexpr bool U = decltype(ub_tag)::value;
                 for (int kb = 0; kb < nk; ++kb) {
                     const int s = kb % S, buf = kb & 1;
+                    // operand layouts of this k-block (see the producer): K-major tiles advance
+                    // 32 bytes per k16 slice, MN-major tiles 16 rows (2 KB)
+                    const int KB = kb * kBK / kBM;
+                    const bool a_mn = U && KB < m0 / kBM;
+                    const bool b0_mn = U && KB < n0 / kBM;
+                    const bool b1_mn = U && KB < n0 / kBM + 1;
+                    const uint64_t so = (uint64_t)s * (uint64_t)(Cfg::kStageBytes >> 4);
+                    auto adesc = [&](int p, int kk) {
+                        return a_mn ? d_mn + so + (uint64_t)((p * kBoxBytes + kk * kMnKStep) >> 4)
+                                    : d_k + so + (uint64_t)((p * kBoxBytes + kk * 32) >> 4);
+                    };
+                    auto bdesc = [&](int p, int kk, int j, bool mn) {
+                        const int off = PA * kBoxBytes + (p * Cfg::kBBoxes + j) * kBoxBytes;
+                        return mn ? d_mn + so + (uint64_t)((off + kk * kMnKStep) >> 4)
+                                  : d_k + so + (uint64_t)((off + kk * 32) >> 4);
+                    };
                     if (kb >= 2) {
                         if (!mbar_wait(&seg_empty[buf], ((kb >> 1) - 1) & 1, kWaitNs, vabort)) {
                             atomicExch(&abort_flag, 1);
@@ -522,20 +535,6 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
                     }
                     fence_after();
                     const uint32_t d = tmem + buf * TBN;
-                    // operand layouts of this k-block (see the producer): K-major tiles advance
-                    // 32 bytes per k16 slice, MN-major tiles 16 rows (2 KB)
-                    const int KB = kb * kBK / kBM;
-                    const bool a_mn = U && KB < m0 / kBM;
-                    const bool b0_mn = U && KB < n0 / kBM;
-                    const bool b1_mn = U && KB < n0 / kBM + 1;
-                    auto adesc = [&](int p, int kk) {
-                        const uint32_t base = smem_u32(stage_a(s, p));
-                        return a_mn ? sdesc_mn128(base + kk * kMnKStep) : sdesc_sw64(base + kk * 32);
-                    };
-                    auto bdesc = [&](int p, int kk, int j, bool mn) {
-                        const uint32_t base = smem_u32(stage_b(s, p)) + j * kBoxBytes;
-                        return mn ? sdesc_mn128(base + kk * kMnKStep) : sdesc_sw64(base + kk * 32);
-                    };
                     // the two 128-column halves of B may differ in layout (the k-block of the
                     // diagonal block of the first half): one MMA per half when they do
                     const int halves = (!U || nbox == 1 || b0_mn == b1_mn) ? 1 : 2;

@@ -322,9 +322,13 @@ __global__ void k_diag_sums(const Inst* __restrict__ insts, int is64) {
 // fixed up front and only offset per chunk), matrix-major (row s of a chunk holds the chunk
 // of matrix s, rows padded by 16 bytes), so that kGStages - 1 stages are in flight while one
 // is multiplied; one barrier per stage separates its consumption from the refill of the
-// stage it frees. Each warp owns up to kTPW 4 x 4 tiles of (giant, baby) pairs; a lane reads
-// 16-byte vectors of 8 rows and accumulates 4 x 4 x (16 / sizeof(T)) products per step
-// (float32: packed FMAs, even and odd entries in the two lanes). Chunks right of the
+// stage it frees. Each warp owns up to TPW tiles of TG x TB (giant, baby) pairs; a lane reads
+// 16-byte vectors of TG + TB rows and accumulates TG x TB x (16 / sizeof(T)) products per
+// step (float32: packed FMAs, even and odd entries in the two lanes). One 5 x 5, 4 x 5 or
+// 5 x 4 tile per warp where the pairs fit 16 warps, else two 4 x 4 tiles per warp (see
+// gram_shape): a larger tile reads each staged vector from shared memory fewer times per
+// product and leaves each warp more independent loads in flight, which is what bounds this
+// kernel (shared-load latency). Chunks right of the
 // diagonal weigh the baby entries by 1 (the factor 2 of the strict upper triangle is applied
 // once at the end); the diagonal chunk of a row weighs them by 1, 1/2 or 0 right of, on or
 // left of the diagonal. Every lane sums at most kGChunks * kChunk / 32 products per pair in
@@ -333,16 +337,15 @@ constexpr int kChunkBytes = 512;    // one chunk of one matrix: 128 float32 / 64
 constexpr int kGChunks = 64;        // chunks per block
 constexpr int kCPS = 2;             // chunks per stage
 constexpr int kGStages = 4;         // shared-memory ring depth (stages)
-constexpr int kMaxQuads = 12;       // staged rows <= 48
-constexpr int kTPW = 2;
-constexpr int kGramThreads = 512;   // largest block: 16 warps, up to 32 tiles
+constexpr int kMaxRows = 48;        // staged rows (giant and baby groups, padded)
+constexpr int kGramThreads = 512;   // largest block: 16 warps
 constexpr int kGramMinThreads = 256;
 // 16-byte copies per thread and chunk: staged rows x (kChunkBytes / 16) vectors / threads
-constexpr int kGLoads = (4 * kMaxQuads * (kChunkBytes / 16) + kGramMinThreads - 1) / kGramMinThreads;
+constexpr int kGLoads = (kMaxRows * (kChunkBytes / 16) + kGramMinThreads - 1) / kGramMinThreads;
 
-// Threads of a block for ntiles (giant, baby) tiles: kTPW tiles per warp, at least 8 warps.
-__host__ __device__ inline int gram_threads(int ntiles) {
-    int w = (ntiles + kTPW - 1) / kTPW;
+// Threads of a block for ntiles (giant, baby) tiles: tpw tiles per warp, at least 8 warps.
+__host__ __device__ inline int gram_threads(int ntiles, int tpw) {
+    int w = (ntiles + tpw - 1) / tpw;
     if (w < kGramMinThreads / 32) w = kGramMinThreads / 32;
     return 32 * w;
 }
@@ -353,9 +356,10 @@ __host__ __device__ inline int64_t upper_chunks(int64_t np, int kc) {
     return (int64_t)kc * cpr * (cpr + 1) / 2;
 }
 
-template <typename T>
+template <typename T, int TG, int TB, int TPW>
 __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict__ insts, Work wgr, int giant0,
                                                           int ngiant, int baby0, int nbaby) {
+    constexpr int NP = TG * TB;                // pairs per tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kChunk = kChunkBytes / (int)sizeof(T);      // entries per chunk
     constexpr int V = 16 / sizeof(T);          // elements per 16-byte vector
@@ -372,9 +376,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     const int64_t nchunks = upper_chunks(np, kChunk);
     const int64_t c0 = (int64_t)lb * kGChunks;
     const int64_t c1 = c0 + kGChunks < nchunks ? c0 + kGChunks : nchunks;
-    const int ng4 = (ngiant + 3) / 4, nb4 = (nbaby + 3) / 4;
-    const int nrows = 4 * (ng4 + nb4);
-    const int ntiles = ng4 * nb4;
+    const int ngq = (ngiant + TG - 1) / TG, nbq = (nbaby + TB - 1) / TB;
+    const int nrows = TG * ngq + TB * nbq;
+    const int ntiles = ngq * nbq;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int chunk_elems = nrows * RS;
     const int stage_elems = kCPS * chunk_elems;
@@ -400,8 +404,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     };
     // slot of staged row srow, or -1 for the padding rows of a partial quad
     auto slot_of = [&](int srow) -> int {
-        if (srow < 4 * ng4) return srow < ngiant ? giant0 + srow : -1;
-        const int bb = srow - 4 * ng4;
+        if (srow < TG * ngq) return srow < ngiant ? giant0 + srow : -1;
+        const int bb = srow - TG * ngq;
         return bb < nbaby ? baby0 + bb : -1;
     };
     // this thread's copies: source at chunk (0, 0) and shared-memory offset in a chunk
@@ -444,23 +448,23 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
         }
     };
 
-    T acc[kTPW][16];        // float64 sums
-    f32x2 acc2[kTPW][16];   // float32 sums of the even / odd entries
+    T acc[TPW][NP];        // float64 sums
+    f32x2 acc2[TPW][NP];   // float32 sums of the even / odd entries
 #pragma unroll
-    for (int t = 0; t < kTPW; ++t)
+    for (int t = 0; t < TPW; ++t)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < NP; ++q) {
             acc[t][q] = T(0);
             acc2[t][q] = 0ull;
         }
 
     // shared-memory offsets of this warp's tiles (-1: none)
-    int toff_g[kTPW], toff_b[kTPW];
+    int toff_g[TPW], toff_b[TPW];
 #pragma unroll
-    for (int t = 0; t < kTPW; ++t) {
+    for (int t = 0; t < TPW; ++t) {
         const int tile = warp + t * nwarps;
-        toff_g[t] = tile < ntiles ? 4 * (tile / nb4) * RS : -1;
-        toff_b[t] = tile < ntiles ? (4 * ng4 + 4 * (tile % nb4)) * RS : -1;
+        toff_g[t] = tile < ntiles ? TG * (tile / nbq) * RS : -1;
+        toff_b[t] = tile < ntiles ? (TG * ngq + TB * (tile % nbq)) * RS : -1;
     }
 #pragma unroll
     for (int s = 0; s < kGStages - 1; ++s) {
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
             }
         }
 #pragma unroll
-        for (int t = 0; t < kTPW; ++t) {
+        for (int t = 0; t < TPW; ++t) {
             if (toff_g[t] < 0) break;                   // uniform across the warp
 #pragma unroll
             for (int u = 0; u < kCPS; ++u) {
@@ -500,12 +504,12 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
                 const T* g0 = stage_base + u * chunk_elems + toff_g[t];
                 const T* b0 = stage_base + u * chunk_elems + toff_b[t];
                 for (int e = lane * V; e < kChunk; e += 32 * V) {
-                    T gv[4][V], bv[4][V];
+                    T gv[TG][V], bv[TB][V];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < TG; ++a)
                         *reinterpret_cast<float4*>(gv[a]) = *reinterpret_cast<const float4*>(g0 + a * RS + e);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b)
+                    for (int b = 0; b < TB; ++b)
                         *reinterpret_cast<float4*>(bv[b]) = *reinterpret_cast<const float4*>(b0 + b * RS + e);
                     if (drow[u] >= 0) {
                         // the entries left of the diagonal are not maintained (the float32
@@ -514,30 +518,30 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
                         for (int v = 0; v < V; ++v) {
                             const int64_t col = dcol0[u] + e + v;
 #pragma unroll
-                            for (int b = 0; b < 4; ++b)
+                            for (int b = 0; b < TB; ++b)
                                 bv[b][v] = col > drow[u] ? bv[b][v] : (col == drow[u] ? T(0.5) * bv[b][v] : T(0));
 #pragma unroll
-                            for (int a = 0; a < 4; ++a) gv[a][v] = col >= drow[u] ? gv[a][v] : T(0);
+                            for (int a = 0; a < TG; ++a) gv[a][v] = col >= drow[u] ? gv[a][v] : T(0);
                         }
                     }
                     if constexpr (sizeof(T) == 4) {
                         const ulonglong2* gp = reinterpret_cast<const ulonglong2*>(&gv[0][0]);
                         const ulonglong2* bp = reinterpret_cast<const ulonglong2*>(&bv[0][0]);
 #pragma unroll
-                        for (int a = 0; a < 4; ++a)
+                        for (int a = 0; a < TG; ++a)
 #pragma unroll
-                            for (int b = 0; b < 4; ++b) {
-                                ffma2(acc2[t][4 * a + b], gp[a].x, bp[b].x);
-                                ffma2(acc2[t][4 * a + b], gp[a].y, bp[b].y);
+                            for (int b = 0; b < TB; ++b) {
+                                ffma2(acc2[t][TB * a + b], gp[a].x, bp[b].x);
+                                ffma2(acc2[t][TB * a + b], gp[a].y, bp[b].y);
                             }
                     } else {
 #pragma unroll
-                        for (int a = 0; a < 4; ++a)
+                        for (int a = 0; a < TG; ++a)
 #pragma unroll
-                            for (int b = 0; b < 4; ++b)
+                            for (int b = 0; b < TB; ++b)
 #pragma unroll
                                 for (int v = 0; v < V; ++v)
-                                    acc[t][4 * a + b] = fma(gv[a][v], bv[b][v], acc[t][4 * a + b]);
+                                    acc[t][TB * a + b] = fma(gv[a][v], bv[b][v], acc[t][TB * a + b]);
                     }
                 }
             }
@@ -547,16 +551,16 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     const int npairs = ngiant * nbaby;
     double* partials = in.gpart;
 #pragma unroll
-    for (int t = 0; t < kTPW; ++t) {
+    for (int t = 0; t < TPW; ++t) {
         const int tile = warp + t * nwarps;
         if (tile >= ntiles) break;
-        const int tg = tile / nb4, tb = tile % nb4;
+        const int tg = tile / nbq, tb = tile % nbq;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < NP; ++q) {
             const float2 pr = unpack2(acc2[t][q]);
             double v = sizeof(T) == 4 ? 2.0 * ((double)pr.x + (double)pr.y) : 2.0 * (double)acc[t][q];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            const int g = 4 * tg + q / 4, b = 4 * tb + q % 4;
+            const int g = TG * tg + q / TB, b = TB * tb + q % TB;
             if (lane == 0 && g < ngiant && b < nbaby) partials[(int64_t)lb * npairs + g * nbaby + b] = v;
         }
     }
@@ -731,28 +735,27 @@ int gram_blocks_for(int64_t np, int is64) {
     return (int)((u + kGChunks - 1) / kGChunks);
 }
 
-cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0, int nbaby,
-                        int out_g0, int is64, cudaStream_t s, int* launches) {
-    if (ngiant <= 0 || nbaby <= 0) return cudaSuccess;
-    if (nbaby > 32) return cudaErrorInvalidValue;
-    const int max_tiles = (kGramThreads / 32) * kTPW;
-    const int nb4 = (nbaby + 3) / 4;
-    // giants per launch: the tiles fit the warps, and the staged rows stay <= 64
-    int gmax = 4 * (max_tiles / nb4);
-    if (gmax > 4 * (kMaxQuads - nb4)) gmax = 4 * (kMaxQuads - nb4);
-    if (gmax < 4) return cudaErrorInvalidValue;
+template <int TG, int TB, int TPW>
+cudaError_t launch_gram_shape(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0, int nbaby,
+                              int out_g0, int is64, cudaStream_t s, int* launches) {
+    const int max_tiles = (kGramThreads / 32) * TPW;
+    const int nbq = (nbaby + TB - 1) / TB;
+    // giants per launch: the tiles fit the warps, and the staged rows stay <= kMaxRows
+    int gmax = TG * (max_tiles / nbq);
+    if (gmax > TG * ((kMaxRows - TB * nbq) / TG)) gmax = TG * ((kMaxRows - TB * nbq) / TG);
+    if (gmax < TG) return cudaErrorInvalidValue;
     for (int g = 0; g < ngiant; g += gmax) {
         const int ng = ngiant - g < gmax ? ngiant - g : gmax;
-        const int ng4 = (ng + 3) / 4;
+        const int ngq = (ng + TG - 1) / TG;
         const size_t elem = is64 ? 8 : 4;
-        const size_t smem = (size_t)kGStages * kCPS * 4 * (ng4 + nb4) * (kChunkBytes / elem + 16 / elem) * elem;
-        const int threads = gram_threads(ng4 * nb4);
+        const size_t smem = (size_t)kGStages * kCPS * (TG * ngq + TB * nbq) * (kChunkBytes / elem + 16 / elem) * elem;
+        const int threads = gram_threads(ngq * nbq, TPW);
         if (is64) {
-            cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_gram<double><<<wgr.total, threads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
+            cudaFuncSetAttribute(k_gram<double, TG, TB, TPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_gram<double, TG, TB, TPW><<<wgr.total, threads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
         } else {
-            cudaFuncSetAttribute(k_gram<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_gram<float><<<wgr.total, threads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
+            cudaFuncSetAttribute(k_gram<float, TG, TB, TPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_gram<float, TG, TB, TPW><<<wgr.total, threads, smem, s>>>(in, wgr, giant0 + g, ng, baby0, nbaby);
         }
         const int npairs = ng * nbaby;
         k_sum_partials<<<dim3(npairs, batch), 128, 0, s>>>(in, npairs, (out_g0 + g) * nbaby);
@@ -761,6 +764,40 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Tile shape of the Frobenius products for ngiant x nbaby pairs: 0 = two 4 x 4 tiles per warp
+// (any size, several launches if needed); 1, 2, 3 = one 5 x 5, 4 x 5 or 5 x 4 tile per warp,
+// taken when all pairs fit one launch of at most 16 warps. Among those the fewest staged-row
+// reads per vector (tiles x (TG + TB)) wins, ties to the smaller tile.
+int gram_shape(int ngiant, int nbaby) {
+    const int shapes[4][3] = {{4, 4, 2}, {5, 5, 1}, {4, 5, 1}, {5, 4, 1}};
+    int best = 0;
+    long cost = 0;
+    for (int i = 0; i < 4; ++i) {
+        const int tg = shapes[i][0], tb = shapes[i][1], tpw = shapes[i][2];
+        const int ngq = (ngiant + tg - 1) / tg, nbq = (nbaby + tb - 1) / tb;
+        const bool fits = ngq * nbq <= (kGramThreads / 32) * tpw && tg * ngq + tb * nbq <= kMaxRows;
+        if (i > 0 && !fits) continue;
+        const long c = (long)ngq * nbq * (tg + tb);
+        if (i == 0 || c < cost) {
+            best = i;
+            cost = c;
+        }
+    }
+    return best;
+}
+
+cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0, int nbaby,
+                        int out_g0, int is64, cudaStream_t s, int* launches) {
+    if (ngiant <= 0 || nbaby <= 0) return cudaSuccess;
+    if (nbaby > 32) return cudaErrorInvalidValue;
+    switch (gram_shape(ngiant, nbaby)) {
+        case 1: return launch_gram_shape<5, 5, 1>(in, batch, wgr, giant0, ngiant, baby0, nbaby, out_g0, is64, s, launches);
+        case 2: return launch_gram_shape<4, 5, 1>(in, batch, wgr, giant0, ngiant, baby0, nbaby, out_g0, is64, s, launches);
+        case 3: return launch_gram_shape<5, 4, 1>(in, batch, wgr, giant0, ngiant, baby0, nbaby, out_g0, is64, s, launches);
+        default: return launch_gram_shape<4, 4, 2>(in, batch, wgr, giant0, ngiant, baby0, nbaby, out_g0, is64, s, launches);
+    }
 }
 
 cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, cudaStream_t s) {
