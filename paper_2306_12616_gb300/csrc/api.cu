@@ -72,7 +72,7 @@ struct Plan {
     std::vector<Bucket> buckets;
     std::vector<Group> groups;
     std::vector<unsigned char> maps;   // 256 bytes per bucket: K-major and MN-major tensor maps
-    HostWork wg, wsc, we, wr, wgr, wtc[2], wf64;   // wtc[0]: 256-wide tiles, wtc[1]: 128-wide
+    HostWork wg, wsc, we, wr, wgr, wct, wtc[2], wf64;   // wtc[0]: 256-wide tiles, wtc[1]: 128-wide
     int tile_n = 0;
     int tile_ctas = 0;
     int tile_drain = 0;
@@ -388,6 +388,7 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     fill(p->we, [](const Inst& in) { return (int64_t)ew_blocks(in.np); });
     fill(p->wr, [](const Inst& in) { return (int64_t)red_blocks(in.np); });
     fill(p->wgr, [](const Inst& in) { return (int64_t)in.gram_blocks; });
+    fill(p->wct, [&](const Inst& in) { return (int64_t)ct_blocks(in.np, sh.k); });
     const bool full = key.mode == MODE_PRODUCT && !key.sym;
     fill(p->wtc[0], [&](const Inst& in) { return full ? tc_tiles_full(in.np, 256) : tc_tiles(in.np, 256); });
     fill(p->wtc[1], [&](const Inst& in) { return full ? tc_tiles_full(in.np, 128) : tc_tiles(in.np, 128); });
@@ -452,7 +453,7 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
         in.res = p->d_res + j;
     }
     // device tables: Inst[batch], InstIO[batch], then the prefix arrays
-    HostWork* lists[] = {&p->wg, &p->wsc, &p->we, &p->wr, &p->wgr, &p->wtc[0], &p->wtc[1], &p->wf64};
+    HostWork* lists[] = {&p->wg, &p->wsc, &p->we, &p->wr, &p->wgr, &p->wct, &p->wtc[0], &p->wtc[1], &p->wf64};
     size_t bytes = align256(sizeof(Inst) * batch) + align256(sizeof(InstIO) * batch);
     for (HostWork* w : lists) bytes += align256(sizeof(int) * w->pre.size());
     if (cudaMalloc(&p->dtab, bytes) != cudaSuccess) {
@@ -720,7 +721,7 @@ fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trac
     run->launches += lstage;
     h = prof_begin(ctx, s, FO_STAGE_CONTRACT);
     lstage = sh.is64 ? 1 : (sh.m + 31) / 32 + (sh.m > 1 ? 1 : 0);   // + the plane mirror of R_{m-1}
-    FO_CUDA(launch_contract(p.d_inst, p.we.dev, p.wsc.dev, sh, s, ctx->flag + 1), "contract");
+    FO_CUDA(launch_contract(p.d_inst, p.we.dev, p.wct.dev, p.wsc.dev, sh, s, ctx->flag + 1), "contract");
     if (sh.m == 1) {
         FO_CUDA(launch_copy_out(p.d_inst, p.d_io, p.we.dev, sh, s), "copy_out");
         lstage += 1;

@@ -380,115 +380,129 @@ __device__ __forceinline__ Split3 split_value(float v, int fp16, float pscale) {
 
 // R_l for l0 <= l < min(l0 + MAXM, m) (MAXM = m rounded up to a multiple of 4, at most 32;
 // m > 32 takes several launches), on and above the diagonal only (the float32 masters of the
-// T_i are maintained there; R_l is symmetric): row r from column r rounded down to a multiple
-// of 4 (16-byte aligned copies) to the end. The coefficients are staged transposed,
-// gsh[t * MAXM + j] = g_{t,l0+j} (zero beyond m), so that one 16-byte shared load serves
-// four R_l. The block's rows are walked in steps of 256 entries of one row (one per
-// thread); the 256-entry segments of T_1..T_{k-1} of the next S - 1 steps are copied into an
-// S-stage shared-memory ring by cp.async, so the loads in flight do not depend on registers.
-// The planes of R_{m-1} (the first operand of the giant steps) are completed below the
-// diagonal by k_mirror_planes.
-constexpr int kCtEntries = 256;
-
-template <int MAXM, int S>
-__global__ void __launch_bounds__(kCtEntries, 2) k_contract_f32(const Inst* __restrict__ insts, Work we, int k,
-                                                                int m, int l0, int n_tslots, int planes_last,
-                                                                int fp16, float pscale, int* dbg) {
+// T_i are maintained there; R_l is symmetric). The upper triangle is walked as 16-byte quads
+// (row r from column 4 floor(r / 4) to the end; ct_quads), one quad per thread and step,
+// consecutive threads on consecutive quads; quad q of the flattened order lies in the row
+// group b = floor(r / 4) with C(b) <= q < C(b + 1), C(b) = b np - 2 b (b - 1), found by a
+// square root and corrected exactly. Each thread stages the quads of T_1..T_{k-1} it will
+// use into its own slots of an S-stage shared-memory ring by cp.async (no block barrier:
+// a thread only reads what it copied) and multiplies them by the coefficients, staged as
+// duplicated pairs gsh[t][l] = (g_{t,l0+l}, g_{t,l0+l}) (zero beyond m): one 16-byte
+// broadcast load serves two R_l, each packed FMA two entries of the quad, and each R_l leaves
+// as one 16-byte store. The planes of R_{m-1} (the first operand of the giant steps) are
+// completed below the diagonal by k_mirror_planes.
+template <int MAXM>
+__global__ void __launch_bounds__(256, 1) k_contract_f32(const Inst* __restrict__ insts, Work wct, int k, int m,
+                                                          int l0, int n_tslots, int planes_last, int fp16,
+                                                          float pscale, int S, int* dbg) {
     extern __shared__ __align__(16) float fsh[];
-    const int i = find_inst(we.pre, 0, we.count, blockIdx.x);
+    const int i = find_inst(wct.pre, 0, wct.count, blockIdx.x);
     const Inst& in = insts[i];
     if (!in.res->active) return;
-    for (int q = threadIdx.x; q < k * MAXM; q += blockDim.x) {
+    const int tpb = blockDim.x, tid = threadIdx.x;
+    for (int q = tid; q < k * MAXM; q += tpb) {
         const int t = q / MAXM, l = l0 + q - t * MAXM;
-        fsh[q] = l < m ? (float)in.g[l * k + t] : 0.0f;
+        const float g = l < m ? (float)in.g[l * k + t] : 0.0f;
+        fsh[2 * q] = g;
+        fsh[2 * q + 1] = g;
     }
     const int nt = k - 1;                                   // T_1 .. T_{k-1}
-    float* ring = fsh + ((k * MAXM + 3) & ~3);
-    const int stage = nt * kCtEntries;
+    float4* ring = reinterpret_cast<float4*>(fsh + 2 * k * MAXM);   // [stage][t][thread]
     const int64_t np = in.np, n = in.n;
-    const int rows = ew_rows(np);
-    const int64_t r0 = (int64_t)(blockIdx.x - we.pre[i]) * rows;
-    const int64_t r1 = r0 + rows < np ? r0 + rows : np;
+    const int64_t q_all = ct_quads(np);
+    const int64_t per = (int64_t)tpb * kCtSteps;
+    const int64_t q0 = (int64_t)(blockIdx.x - wct.pre[i]) * per;
+    const int64_t q1 = q0 + per < q_all ? q0 + per : q_all;
+    const int nsteps = (int)((q1 - q0 + tpb - 1) / tpb);
     const int64_t tstride = in.slot_bytes / 4;
     const int64_t ps = np * np;
     const float* tbase = reinterpret_cast<const float*>(in.slots);
     float* rbase = reinterpret_cast<float*>(in.slots + n_tslots * in.slot_bytes);
-    // step cursor: (row, first column) of a 256-entry step; a row starts at its diagonal
-    // rounded down to a multiple of 4 and ends at np
-    auto advance = [&](int64_t& r, int64_t& c) {
-        c += kCtEntries;
-        if (c >= np) {
-            ++r;
-            c = r & ~int64_t(3);
-        }
+    const int64_t G = np / 4;                               // row groups
+    // (row, column) of this thread's quad of step j, or row -1 past the block's range
+    auto locate = [&](int j, int64_t& r, int64_t& c) {
+        const int64_t q = q0 + (int64_t)j * tpb + tid;
+        r = -1;
+        c = 0;
+        if (q >= q1) return;
+        const float d = (float)(np + 2) * (float)(np + 2) - 8.0f * (float)q;
+        int64_t b = (int64_t)(((float)(np + 2) - sqrtf(d > 0.0f ? d : 0.0f)) * 0.25f);
+        if (b < 0) b = 0;
+        if (b > G - 1) b = G - 1;
+        auto C = [&](int64_t x) { return x * np - 2 * x * (x - 1); };
+        while (b > 0 && C(b) > q) --b;
+        while (b + 1 < G && C(b + 1) <= q) ++b;
+        const int64_t len = G - b;                          // quads per row of the group
+        const int64_t off = q - C(b);
+        r = 4 * b + off / len;
+        c = 4 * b + 4 * (off % len);
     };
-    // thread tid copies vector v4 = 4 (tid % 64) of the segments t = tid / 64, tid / 64 + 4, ...
-    constexpr int kTPS = kCtEntries / (kCtEntries / 4);   // segments started per pass: 4
-    const int v4 = 4 * (threadIdx.x % (kCtEntries / 4)), tq = threadIdx.x / (kCtEntries / 4);
-    auto issue = [&](int j, int64_t r, int64_t c) {
-        if (c + v4 >= np) return;                          // past the end of the row
-        float* dst = ring + (j % S) * stage + v4;
-        const float* src = tbase + (int64_t)tq * tstride + r * np + c + v4;
+    auto issue = [&](int j) {
+        int64_t r, c;
+        locate(j, r, c);
+        if (r >= 0 && nt > 0) {
+            float4* dst = ring + (int64_t)(j % S) * nt * tpb + tid;
+            const float* src = tbase + r * np + c;   // slot t holds T_{t+1}
 #pragma unroll 1
-        for (int t = tq; t < nt; t += kTPS, src += kTPS * tstride) cp_async16(dst + t * kCtEntries, src);
+            for (int t = 0; t < nt; ++t, dst += tpb, src += tstride) cp_async16(dst, src);
+        }
+        cp_async_commit();
     };
-    int64_t ir = r0, ic = r0 & ~int64_t(3);   // next step to copy
-    int64_t cr = ir, cc = ic;                 // next step to compute
-#pragma unroll
-    for (int s = 0; s < S - 1; ++s) {
-        if (ir < r1) {
-            issue(s, ir, ic);
-            advance(ir, ic);
-        }
-        cp_async_commit();
-    }
+    for (int j = 0; j < S - 1; ++j) issue(j);
     __syncthreads();   // the coefficient table
-    for (int j = 0; cr < r1; ++j) {
-        cp_async_wait<S - 2>();
-        __syncthreads();   // step j's segments have landed; the stage of step j - 1 is free
-        if (ir < r1) {
-            issue(j + S - 1, ir, ic);
-            advance(ir, ic);
-        }
-        cp_async_commit();
-        const int64_t r = cr, c = cc + threadIdx.x;
-        advance(cr, cc);
-        if (c >= np) continue;
-        const int64_t idx = r * np + c;
-        const float* seg = ring + (j % S) * stage + threadIdx.x;
-        f32x2 acc[MAXM / 2];   // (R_{l0+2p}, R_{l0+2p+1}) at this entry
+    const ulonglong2* gtab = reinterpret_cast<const ulonglong2*>(fsh);   // [t][l / 2]
+    for (int j = 0; j < nsteps; ++j) {
+        issue(j + S - 1);
+        cp_async_wait_dyn(S - 1);   // this thread's copies of step j have landed
+        int64_t r, c;
+        locate(j, r, c);
+        if (r < 0) continue;
+        const float4* seg = ring + (int64_t)(j % S) * nt * tpb + tid;
+        f32x2 acc[MAXM][2];   // R_{l0+l} at entries (0, 1) and (2, 3) of the quad
 #pragma unroll
-        for (int q = 0; q < MAXM / 2; ++q) acc[q] = 0ull;
+        for (int l = 0; l < MAXM; ++l) acc[l][0] = acc[l][1] = 0ull;
 #pragma unroll 2
         for (int t = 0; t < nt; ++t) {
-            const float v = seg[t * kCtEntries];
-            const f32x2 vv = pack2(v, v);
-            const ulonglong2* gt = reinterpret_cast<const ulonglong2*>(fsh + (t + 1) * MAXM);
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(seg + (int64_t)t * tpb);
+            const ulonglong2* gt = gtab + (t + 1) * (MAXM / 2);
 #pragma unroll
-            for (int j4 = 0; j4 < MAXM / 4; ++j4) {
-                const ulonglong2 g = gt[j4];   // (g_{t,l}, g_{t,l+1}), (g_{t,l+2}, g_{t,l+3})
-                ffma2(acc[2 * j4], g.x, vv);
-                ffma2(acc[2 * j4 + 1], g.y, vv);
+            for (int l2 = 0; l2 < MAXM / 2; ++l2) {
+                const ulonglong2 g = gt[l2];   // (g_l, g_l), (g_{l+1}, g_{l+1})
+                ffma2(acc[2 * l2][0], v.x, g.x);
+                ffma2(acc[2 * l2][1], v.y, g.x);
+                ffma2(acc[2 * l2 + 1][0], v.x, g.y);
+                ffma2(acc[2 * l2 + 1][1], v.y, g.y);
             }
         }
-        const bool dg = (r < n) && (c == r);
+        const int64_t idx = r * np + c;
+        if (!FO_CHK(dbg, idx >= 0 && idx + 3 < ps && (idx & 3) == 0, 302, (int)r, idx)) continue;
+        const int dg = (r < n && c == (r & ~int64_t(3))) ? (int)(r & 3) : -1;   // diagonal entry
         float* dst = rbase + (int64_t)l0 * tstride + idx;
 #pragma unroll
-        for (int q = 0; q < MAXM; ++q, dst += tstride) {
-            const int l = l0 + q;
-            if (l >= m) break;
-            const float2 pr = unpack2(acc[q / 2]);
-            float v = (q & 1) ? pr.y : pr.x;
-            if (dg) v += fsh[q];   // g_{0,l}: the t = 0 row
-            if (!FO_CHK(dbg, idx >= 0 && idx < ps, 302, l, idx)) continue;
-            *dst = v;
-            if (l == m - 1 && planes_last > 0) {
-                const Split3 a = split_value(v, fp16, pscale);
+        for (int l = 0; l < MAXM; ++l, dst += tstride) {
+            if (l0 + l >= m) break;
+            float2 a = unpack2(acc[l][0]), b = unpack2(acc[l][1]);
+            float4 v = make_float4(a.x, a.y, b.x, b.y);
+            if (dg >= 0) {   // g_{0,l}: the t = 0 row (T_0 = I)
+                const float g0 = fsh[2 * l];
+                if (dg == 0) v.x += g0;
+                else if (dg == 1) v.y += g0;
+                else if (dg == 2) v.z += g0;
+                else v.w += g0;
+            }
+            *reinterpret_cast<float4*>(dst) = v;
+            if (l0 + l == m - 1 && planes_last > 0) {
+                const Split3 s0 = split_value(v.x, fp16, pscale), s1 = split_value(v.y, fp16, pscale);
+                const Split3 s2 = split_value(v.z, fp16, pscale), s3 = split_value(v.w, fp16, pscale);
                 // planes of R_l: 16-bit entries from float offset ps of the slot
-                uint16_t* p = reinterpret_cast<uint16_t*>(dst - idx + ps) + idx;
-                p[0] = a.p[0];
-                if (planes_last > 1) p[ps] = a.p[1];
-                if (planes_last > 2) p[2 * ps] = a.p[2];
+                uint16_t* pl = reinterpret_cast<uint16_t*>(dst - idx + ps) + idx;
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    if (p >= planes_last) break;
+                    const uint2 w = make_uint2((uint32_t)s0.p[p] | ((uint32_t)s1.p[p] << 16),
+                                               (uint32_t)s2.p[p] | ((uint32_t)s3.p[p] << 16));
+                    *reinterpret_cast<uint2*>(pl + p * ps) = w;
+                }
             }
         }
     }
@@ -586,7 +600,7 @@ cudaError_t launch_g_to_d(const Inst* in, int batch, const Shape& sh, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_contract(const Inst* in, Work we, Work wsym, const Shape& sh, cudaStream_t s, int* dbg) {
+cudaError_t launch_contract(const Inst* in, Work we, Work wct, Work wsym, const Shape& sh, cudaStream_t s, int* dbg) {
     if (sh.is64) {
         const size_t smem = (size_t)sh.k * sh.m * sizeof(double);
         if (smem > 48 * 1024)
@@ -595,33 +609,29 @@ cudaError_t launch_contract(const Inst* in, Work we, Work wsym, const Shape& sh,
         return cudaGetLastError();
     }
     const int planes_last = sh.m > 1 ? sh.planes : 0;
-    // ring depth: 4 stages when they fit beside the coefficient table in ~200 KB, else 3 or 2
-    const size_t stage_bytes = (size_t)(sh.k - 1) * kCtEntries * sizeof(float);
-    const int S = stage_bytes * 4 <= 192 * 1024 ? 4 : (stage_bytes * 3 <= 200 * 1024 ? 3 : 2);
+    // ring depth: as many stages (2 to 4) of every thread's k - 1 quads as fit ~200 KB
+    const int tpb = ct_threads(sh.k);
+    const size_t stage_bytes = (size_t)(sh.k - 1) * tpb * 16;
+    int S = 4;
+    while (S > 2 && stage_bytes * S > 200 * 1024) --S;
     auto go = [&](auto kern, int maxm, int l0) {
-        const size_t smem = (size_t)((sh.k * maxm + 3) & ~3) * sizeof(float) + S * stage_bytes;
+        const size_t smem = (size_t)2 * sh.k * maxm * sizeof(float) + S * stage_bytes;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<we.total, kCtEntries, smem, s>>>(in, we, sh.k, sh.m, l0, sh.n_tslots, planes_last, sh.fp16,
-                                               sh.pscale_r, dbg);
-    };
-    auto pick = [&](auto tag, int l0) {
-        constexpr int SS = decltype(tag)::value;
-        const int mm = sh.m - l0 < 32 ? sh.m - l0 : 32;   // R_l of this launch
-        switch ((mm + 3) / 4) {
-            case 1: go(k_contract_f32<4, SS>, 4, l0); break;
-            case 2: go(k_contract_f32<8, SS>, 8, l0); break;
-            case 3: go(k_contract_f32<12, SS>, 12, l0); break;
-            case 4: go(k_contract_f32<16, SS>, 16, l0); break;
-            case 5: go(k_contract_f32<20, SS>, 20, l0); break;
-            case 6: go(k_contract_f32<24, SS>, 24, l0); break;
-            case 7: go(k_contract_f32<28, SS>, 28, l0); break;
-            default: go(k_contract_f32<32, SS>, 32, l0); break;
-        }
+        kern<<<wct.total, tpb, smem, s>>>(in, wct, sh.k, sh.m, l0, sh.n_tslots, planes_last, sh.fp16, sh.pscale_r,
+                                          S, dbg);
     };
     for (int l0 = 0; l0 < sh.m; l0 += 32) {
-        if (S == 4) pick(std::integral_constant<int, 4>(), l0);
-        else if (S == 3) pick(std::integral_constant<int, 3>(), l0);
-        else pick(std::integral_constant<int, 2>(), l0);
+        const int mm = sh.m - l0 < 32 ? sh.m - l0 : 32;   // R_l of this launch
+        switch ((mm + 3) / 4) {
+            case 1: go(k_contract_f32<4>, 4, l0); break;
+            case 2: go(k_contract_f32<8>, 8, l0); break;
+            case 3: go(k_contract_f32<12>, 12, l0); break;
+            case 4: go(k_contract_f32<16>, 16, l0); break;
+            case 5: go(k_contract_f32<20>, 20, l0); break;
+            case 6: go(k_contract_f32<24>, 24, l0); break;
+            case 7: go(k_contract_f32<28>, 28, l0); break;
+            default: go(k_contract_f32<32>, 32, l0); break;
+        }
     }
     if (planes_last > 0) k_mirror_planes<<<wsym.total, 256, 0, s>>>(in, wsym, sh.n_tslots + sh.m - 1, planes_last,
                                                          sh.ublk, dbg);

@@ -137,6 +137,13 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// cp.async.wait_group for a run-time count (0 to 3)
+__device__ __forceinline__ void cp_async_wait_dyn(int n) {
+    if (n <= 0) cp_async_wait<0>();
+    else if (n == 1) cp_async_wait<1>();
+    else if (n == 2) cp_async_wait<2>();
+    else cp_async_wait<3>();
+}
 
 // Two float32 values in one 64-bit register (low lane = x) and d = a * b + c on both lanes
 // at once (fma.rn.f32x2, sm_100 and later): the same round-to-nearest result per lane as
@@ -165,6 +172,21 @@ __host__ __device__ inline int ew_rows(int64_t np) {
 __host__ __device__ inline int ew_blocks(int64_t np) {
     const int r = ew_rows(np);
     return (int)((np + r - 1) / r);
+}
+// Contraction of the float32 forms: the upper triangle is walked as 16-byte quads (row r
+// holds the quads from column 4 floor(r / 4) to np - 4), ct_threads(k) per block, one quad
+// per thread and step, kCtSteps steps per block.
+constexpr int kCtSteps = 16;
+__host__ __device__ inline int ct_threads(int k) {
+    // two stages of the k - 1 staged quads of every thread within ~200 KB of shared memory
+    int t = 256;
+    while (t > 64 && 2 * (int64_t)t * (k - 1) * 16 > 200 * 1024) t /= 2;
+    return t;
+}
+__host__ __device__ inline int64_t ct_quads(int64_t np) { return np * (np + 4) / 8; }
+__host__ __device__ inline int ct_blocks(int64_t np, int k) {
+    const int64_t per = (int64_t)ct_threads(k) * kCtSteps;
+    return (int)((ct_quads(np) + per - 1) / per);
 }
 // Reduction row blocks (traces of P): about 16K entries per block, so that the loads of a
 // float64 P are spread over enough blocks to be in flight together.
@@ -276,7 +298,7 @@ cudaError_t launch_bisect(const Inst* in, const InstIO* io, int batch, const Sha
 cudaError_t launch_set_mu(const Inst* in, const InstIO* io, int batch, cudaStream_t s);
 cudaError_t launch_coefficients(const Inst* in, const InstIO* io, int batch, const Shape& sh,
                                 const double* ct, int with_poly_trace, cudaStream_t s, int* launches);
-cudaError_t launch_contract(const Inst* in, Work we, Work wsym, const Shape& sh, cudaStream_t s, int* dbg);
+cudaError_t launch_contract(const Inst* in, Work we, Work wct, Work wsym, const Shape& sh, cudaStream_t s, int* dbg);
 // g -> the paper's power-basis coefficients d (in place), for the Horner evaluation.
 cudaError_t launch_g_to_d(const Inst* in, int batch, const Shape& sh, cudaStream_t s);
 
