@@ -362,7 +362,11 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     tile_of(gtile - __ldg(pre + inst), tm, tn, TBN, sym, I, J);
     const int m0 = I * kBM;
     int n0 = J * TBN;
-    const int nk = np / kBK;
+    // k-blocks. The zero border past column n contributes exact zeros, so 128-wide tiles stop
+    // at the k-block holding column n - 1 (short-K tiles of small matrices gain most); the
+    // 256-wide kernels keep n_pad / 32, which they derive without another live register
+    // (they run at their register cap, and the trimmed count made them spill)
+    const int nk = TBN == 128 ? (int)((in.n + kBK - 1) / kBK) : np / kBK;
     // 128-row B boxes inside the matrix: a 256-wide tile at the edge may hold only one
     int nbox = (np - n0) / kBM < Cfg::kBBoxes ? (np - n0) / kBM : Cfg::kBBoxes;
     if (sym && n0 < m0) {
