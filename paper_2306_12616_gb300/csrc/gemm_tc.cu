@@ -376,7 +376,12 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         nbox = 1;
     }
     const int tile_n = nbox * kBM;
-    const uint32_t idesc = idesc_f16(tile_n, F16);
+    // columns the MMAs compute: up to the 32-column group holding column n - 1 (the zero border
+    // past it contributes nothing; the epilogue writes the remaining columns as zeros), so the
+    // edge tiles of a matrix whose n is not a multiple of the tile width issue narrower MMAs
+    const int64_t nrem = in.n - n0;
+    const int tile_k = nrem >= tile_n ? tile_n : (int)(((nrem + 31) / 32) * 32);
+    const uint32_t idesc = idesc_f16(tile_k, F16);
     const uint32_t stage_tx = (uint32_t)(PA * kBoxBytes + PB * nbox * kBoxBytes);
 
     if (threadIdx.x == 0) {
@@ -541,11 +546,11 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
                     const uint32_t d = tmem + buf * TBN;
                     // the two 128-column halves of B may differ in layout (the k-block of the
                     // diagonal block of the first half): one MMA per half when they do
-                    const int halves = (!U || nbox == 1 || b0_mn == b1_mn) ? 1 : 2;
-                    const uint32_t idh = (halves == 1 ? idesc : idesc_f16(kBM, F16)) | (a_mn ? kIdescMnA : 0u);
+                    const int halves = (!U || nbox == 1 || tile_k <= kBM || b0_mn == b1_mn) ? 1 : 2;
                     for (int j = 0; j < halves; ++j) {
                         const bool mn = j ? b1_mn : b0_mn;
-                        const uint32_t id = idh | (mn ? kIdescMnB : 0u);
+                        const uint32_t id = (halves == 1 ? idesc : idesc_f16(j ? tile_k - kBM : kBM, F16)) |
+                                            (a_mn ? kIdescMnA : 0u) | (mn ? kIdescMnB : 0u);
 #pragma unroll
                         for (int kk = 0; kk < kBK / 16; ++kk) {
 #pragma unroll
@@ -571,7 +576,9 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         // ---------------- drain warps: add every finished k-block to registers
         const int q = warp & 3, grp = (warp - 2) >> 2;
         const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16) + grp * NC;
-        const bool live = grp * NC < tile_n;   // columns this warp reads hold data
+        // columns of this warp that the MMAs write (a multiple of 32): the others are never
+        // read, so their sums stay zero, the value of the zero border there
+        const int wcols = tile_k - grp * NC < 0 ? 0 : (tile_k - grp * NC > NC ? NC : tile_k - grp * NC);
         for (int kb = 0; kb < nk; ++kb) {
             const int buf = kb & 1;
             if (!mbar_wait_warp(&seg_full[buf], (kb >> 1) & 1, kWaitNs, vabort)) {
@@ -580,24 +587,24 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             }
             __syncwarp();
             fence_after();
-            if (live) {
-                if (Cfg::kLoad32) {
+            if (Cfg::kLoad32) {
 #pragma unroll
-                    for (int cb = 0; cb < NC / 32; ++cb) {
-                        uint32_t r[32];
-                        tmem_ld32(t_row + buf * TBN + cb * 32, r);
+                for (int cb = 0; cb < NC / 32; ++cb) {
+                    if (cb * 32 >= wcols) break;
+                    uint32_t r[32];
+                    tmem_ld32(t_row + buf * TBN + cb * 32, r);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
-                    }
-                } else {
-                    // half the registers per thread: 16-column loads
+                    for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
+                }
+            } else {
+                // half the registers per thread: 16-column loads
 #pragma unroll
-                    for (int cb = 0; cb < NC / 16; ++cb) {
-                        uint32_t r[16];
-                        tmem_ld16(t_row + buf * TBN + cb * 16, r);
+                for (int cb = 0; cb < NC / 16; ++cb) {
+                    if (cb * 16 >= wcols) break;
+                    uint32_t r[16];
+                    tmem_ld16(t_row + buf * TBN + cb * 16, r);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) sum[cb * 16 + j] += __uint_as_float(r[j]);
-                    }
+                    for (int j = 0; j < 16; ++j) sum[cb * 16 + j] += __uint_as_float(r[j]);
                 }
             }
             fence_before();
