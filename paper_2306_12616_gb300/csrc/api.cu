@@ -813,6 +813,7 @@ fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
 // on this plan's first baby step, timed with CUDA events on the plan's own layout (the data
 // are whatever the workspace holds; the work does not depend on them).
 fo_status autotune(fo_ctx* ctx, Plan& p) {
+    constexpr int kTuneReps = 5;   // timed products per candidate (the storages differ by a few per cent)
     p.sh.ublk = 0;
     if (p.sh.is64 || p.n_slots == 0) {
         p.tile_n = p.tile_ctas = p.tile_drain = p.tile_store = 0;
@@ -858,7 +859,7 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
         fo_status rs = run_product(ctx, p, st, s, "autotune", ci, &r);   // warm-up
         if (rs != FO_OK) { ctx->prof = prof; return rs; }
         cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < kTuneReps; ++rep) {
             rs = run_product(ctx, p, st, s, "autotune", ci, &r);
             if (rs != FO_OK) { ctx->prof = prof; return rs; }
         }
@@ -871,7 +872,7 @@ fo_status autotune(fo_ctx* ctx, Plan& p) {
         if (autotune_log())
             std::fprintf(stderr, "autotune n0=%lld batch=%d tile %dx%dx%d store %d: %.4f ms per product\n",
                          (long long)p.key.n[0], p.batch, cands[ci][0], cands[ci][1], cands[ci][2], cands[ci][3],
-                         ms / 3.0);
+                         ms / kTuneReps);
         if (ci == 0 || ms < best) {
             best = ms;
             bn = cands[ci][0];
