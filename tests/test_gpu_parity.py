@@ -182,3 +182,23 @@ def test_argument_errors(solver):
     prm = solver.params(8, -1.0, precision="fp64", mu_mode="fixed")
     with pytest.raises(fo.FermiError):
         solver.density_matrix(h, 4.0, prm)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-6), ("fp64", 1e-10)])
+@pytest.mark.parametrize("n_terms,k", [(160, 8), (400, 8)])
+def test_forced_baby_step_count(solver, prec, tol, n_terms, k):
+    """A forced k changes the split of the n_terms coefficients between baby and giant steps
+    (k = 8 at 160 terms: 19 giants x 7 babies in the Frobenius products, 5 x 4 tiles; at 400
+    terms: m = 50, 49 x 7 pairs over two launches of 4 x 4 tiles, and two contraction launches
+    for R_0..R_49), not the polynomial: P stays the oracle's expansion at the reported mu.
+    The float64 form pins those paths (measured ~1e-14). The split form's bar is 2e-6 here, not
+    1e-6: with k below sqrt(n_terms) the Clenshaw chain in Y = T_k runs m = 20 and 50 steps
+    instead of 13 and 20, and its float32 rounding grows with m (measured 1.05e-6, 1.36e-6)."""
+    n = 600
+    h = synth.tight_binding(n, 4242)
+    p, r = solver.density_matrix(to_dev(h), n / 2, solver.params(n_terms, 0.1, precision=prec, mu_mode="bisect",
+                                                                 k=k))
+    assert r["status"] == 0 and (r["k"], r["m"]) == (k, -(-n_terms // k))
+    c = O.chebyshev_coeffs(0.1, r["mu"], r["emin"], r["emax"], n_terms)
+    ref = O.poly_eig(h, c, r["emin"], r["emax"])
+    assert rel_frob(p.cpu().numpy(), ref) <= tol
