@@ -472,24 +472,35 @@ def main():
     torch.cuda.synchronize()
 
     # timed region: K steps, events on the launching stream, L2 flushed before each step
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    solver.profile_enable(True)
-    per_step = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        per_step.append(e0.elapsed_time(e1))
-    torch.cuda.synchronize()
-    prof = solver.profile_read(reset=True)
-    solver.profile_enable(False)
-    clk = clocks.stop()
+    def timed_region():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        solver.profile_enable(True)
+        per_step = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            per_step.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        prof = solver.profile_read(reset=True)
+        solver.profile_enable(False)
+        return per_step, prof, clocks.stop()
+
+    # a region that saw a hardware or thermal slowdown on any rank is measured once more by
+    # every rank (sw_power_cap is the normal state of a dense tensor-core load and is only
+    # reported); the decision is reduced over the ranks so that their barriers stay paired
+    throttled = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    per_step, prof, clk = timed_region()
+    first = sorted(throttled & set(clk.get("reasons", [])))
+    if reduce_max(1.0 if first else 0.0) > 0.0:
+        per_step, prof, clk = timed_region()
+        clk["remeasured_after"] = first or ["another rank"]
     total_ms = reduce_max(sum(per_step))
     ms_per_step = total_ms / args.steps
     value = world * len(ns) / (ms_per_step * 1e-3)
