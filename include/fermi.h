@@ -194,14 +194,17 @@ fo_status fo_spectral_bounds(fo_ctx *ctx, const double *dH, int64_t n, int64_t l
  * Spectral bounds for callers that cannot allocate device memory when they need them (for
  * example code running inside a memory pool it does not own, or an embedding that forbids
  * cudaMalloc after start-up). The paper has no counterpart: this is a service entry point.
- * It computes exactly what fo_spectral_bounds computes (same outputs in d_bounds[0..2]) but
- * needs no context and allocates nothing: its per-block partial results live in a fixed
+ * It computes the same bounds as fo_spectral_bounds up to float64 rounding (the row sums
+ * are added in a different order), with the same outputs in d_bounds[0..2], but needs no
+ * context and allocates nothing: its per-block partial results live in a fixed
  * 128 KiB array in device memory that is part of the library image, resident on every GPU
  * that loads the library until the process exits.
  *  - n must not exceed FO_NOALLOC_MAX_N (the capacity of that array); larger n, NULL
  *    pointers or ld < n return FO_ERR_ARG, with nothing launched.
- *  - The first call on a device looks up the array's device address (with that device
- *    current) and caches it; make that first call before any stream capture.
+ *  - Every call looks up the array's device address on the current device
+ *    (cudaGetSymbolAddress, which allocates nothing), so a device reset does not leave a
+ *    stale address behind; the first call on a device also loads the library's device
+ *    code there, so make it before any stream capture.
  *  - The call uses the current CUDA device; H and d_bounds must live on it.
  *  - Every call on a device shares the array, which keeps the last call's contents; each
  *    call overwrites what it reads, so no clearing is needed, but calls whose kernels

@@ -12,8 +12,6 @@
 // must be serialised by the caller.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "internal.cuh"
 
 namespace fo {
@@ -21,7 +19,6 @@ namespace {
 
 constexpr int kRowsPerBlock = 8;                       // one warp per row, 8 warps per block
 constexpr int kMaxBlocks = FO_NOALLOC_MAX_N / kRowsPerBlock;
-constexpr int kMaxDevices = 64;
 
 // Per-block (min_i lo_i, max_i hi_i, any non-finite) of the Gershgorin discs: 4096 x 32 B = 128 KiB.
 struct Partial {
@@ -113,20 +110,16 @@ __global__ void k_bounds_final_static(const Partial* part, int nparts, double* o
     }
 }
 
-// Device address of g_scratch, looked up once per device with that device current. In host
-// code the symbol itself is only a host-side stand-in and must never be passed to a kernel.
-std::mutex g_mu;
-Partial* g_addr[kMaxDevices] = {nullptr};
-
-cudaError_t scratch_address(int dev, Partial** out) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<Partial*>(p);
-    }
-    *out = g_addr[dev];
+// Device address of g_scratch on the current device. In host code the symbol itself is only
+// a host-side stand-in and must never be passed to a kernel. The address is looked up on
+// every call (cudaGetSymbolAddress is cheap and allocates nothing) rather than cached: after
+// a device reset or a re-created primary context the module is loaded anew, possibly at
+// another address, and a cached pointer would be stale.
+cudaError_t scratch_address(Partial** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<Partial*>(p);
     return cudaSuccess;
 }
 
@@ -138,13 +131,8 @@ extern "C" fo_status fo_spectral_bounds_noalloc(const double* dH, int64_t n, int
     using namespace fo;
     if (!dH || !d_bounds || n < 1 || ld < n) return FO_ERR_ARG;
     if (n > FO_NOALLOC_MAX_N) return FO_ERR_ARG;   // beyond the fixed scratch capacity
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return FO_ERR_CUDA;
-    }
     Partial* part = nullptr;
-    if (scratch_address(dev, &part) != cudaSuccess) {
+    if (scratch_address(&part) != cudaSuccess) {
         cudaGetLastError();
         return FO_ERR_CUDA;
     }
