@@ -76,6 +76,15 @@ typedef enum {
                                           coefficients and the Clenshaw recurrence. The d_{i,j}
                                           grow like 2^j, so the result loses accuracy with m;
                                           FP16X2 is rejected (overflow) */
+#define FO_FLAG_NO_TRACE_FIX     0x20u /* split forms with mu searched: return P as the expansion
+                                          produced it, without the trace correction (see
+                                          fo_density_matrix); for measuring what it changes */
+#define FO_FLAG_ALLOW_LOOSE      0x40u /* split precisions: run the combinations whose error is
+                                          measured above the 1e-6 bar of the split forms
+                                          (FO_FLAG_STAGED, FO_FLAG_POWER_BASIS, and a forced k
+                                          with m > k: the longer Clenshaw chain, ~1.4e-6 at
+                                          m = 50); without this flag they fail with
+                                          FO_ERR_UNSUPPORTED */
 #define FO_FLAG_STAGED           0x8u  /* baby and giant steps in the staged form of Algorithm 1
                                           (Sec. "Speed up with multiple GPU streams"): the
                                           independent products of a stage in one launch, about
@@ -97,8 +106,10 @@ typedef struct {
     double  emin, emax;       /* spectral bounds when use_given_bounds (emax > emin) */
     int32_t max_bisect;       /* bisection cap; 0 = 200 */
     uint32_t flags;           /* FO_FLAG_* */
-    double  tr_tol;           /* FO_MU_LEARNED: accept P when |tr P - N_e| <= tr_tol; 0 = default
-                                 (1e-8 max(1, N_e) for FP64, 2e-6 n for the split forms) */
+    double  tr_tol;           /* FO_MU_LEARNED: accept the P evaluated at a proposed mu when its
+                                 trace before the trace correction meets |tr P - N_e| <= tr_tol;
+                                 0 = default: 1e-8 max(1, N_e) for FP64, 1e-7 n for the split
+                                 forms (the band their float32 rounding of tr P lies in) */
     int32_t max_newton;       /* FO_MU_LEARNED: trace-corrected re-evaluations of P before the
                                  bisection fallback; 0 = 2, < 0 = none */
     int32_t tile_n;           /* tensor-core tile width: 0 = autotune per plan, or 128 / 256 */
@@ -121,6 +132,14 @@ typedef struct {
                                  diagonal only, a block below read by the tensor cores as the
                                  transpose of its counterpart above (MN-major operand tiles).
                                  Results are bit-identical; other values fail with FO_ERR_ARG */
+    int32_t chain;            /* split forms: 0 = default (1), 1 = one launch per matrix product,
+                                 2 = each chain of dependent products (the baby steps, the giant
+                                 steps, the Clenshaw recurrence) as one launch whose tiles wait,
+                                 per instance, for the previous step's tiles (bounded waits; a
+                                 timeout fails the call with FO_ERR_DEVICE_TIMEOUT). Same bits */
+    int32_t chain_window;     /* chain launches: tiles run window by window, a window being
+                                 consecutive instances (largest first) with at least this many
+                                 tiles per step; 0 = one window (step by step over the batch) */
 } fo_params;
 
 typedef struct {
@@ -141,6 +160,11 @@ typedef struct {
     int32_t order;            /* expansion order proposed by the learned model (0 if none) */
     int32_t tile_drain;       /* accumulator drain warps of the product kernel (0 for FP64) */
     int32_t tile_store;       /* operand plane storage used (1 or 2 as in fo_params; 0 for FP64) */
+    double  trace_raw;        /* tr(P) as the expansion produced it, before the trace correction
+                                 (equal to trace when none was applied) */
+    double  trace_gamma;      /* gamma of the trace correction P + gamma (P - P^2) (0: none) */
+    double  trace_proj;       /* float64 residual removed per diagonal entry by the trace
+                                 projection after the correction (0: none) */
 } fo_result;
 
 /* Stages of a density-matrix call, as recorded by the profiler. */
@@ -232,7 +256,21 @@ fo_status fo_chebyshev_coeffs(fo_ctx *ctx, double kT, double mu, double emin, do
  * is regrouped as sum_l T_l(T_k) R_l, R_l = sum_i g_{i,l} T_i (the bracket d_i^T a_l of
  * Eq. (formula for d)), and the giant steps run as a Clenshaw recurrence in T_k whose
  * product epilogue accumulates R_l. mu per params.mu_mode; n_e is the electron count
- * (tr P = n_e, spinless occupations in [0,1]). If res != NULL the call synchronises the
+ * (tr P = n_e, spinless occupations in [0,1]).
+ * Trace correction (split precisions with mu searched, m > 1, unless FO_FLAG_NO_TRACE_FIX):
+ * the float32 masters of the split forms leave tr P off n_e by their rounding (~1e-8 n). With
+ * gamma = (n_e - tr P)/(tr P - ||P||_F^2) the call applies P <- P + gamma (P - P^2), the
+ * first-order shift of mu by gamma kT for the Fermi function (df/dmu = f(1-f)/kT), as one
+ * more symmetric product P P with a float64 epilogue, and then adds r/n to the diagonal,
+ * r = n_e - tr P the float64 residual that this product's own rounding leaves (the
+ * Frobenius-nearest matrix with trace n_e; skipped when |r| > 1e-4 max(1, n_e)). It is a
+ * correction of rounding, not a search for mu: it is applied only when it moves P by at most
+ * 1e-6 in ||.||_F/sqrt(n) (bound |n_e - tr P| / (2 sqrt(n tr(P - P^2)))) and |gamma| <= 1/4,
+ * which holds for the rounding of every split form measured with mu by bisection; otherwise
+ * (e.g. a learned mu accepted at a loose tr_tol) P keeps its trace and trace_gamma is 0. The
+ * reported mu is that of the expansion; res->trace_raw keeps the trace before the
+ * correction. If res != NULL
+ * the call synchronises the
  * stream and fills *res; with res == NULL (or FO_FLAG_NO_RESULT_SYNC) it never blocks.
  * Returns the host-side status; device-side failures (non-finite H, no bracket) are
  * reported through res->status and the return value when res != NULL.

@@ -17,7 +17,7 @@ from dataclasses import dataclass
 __all__ = [
     "FO_OK", "FO_PREC_FP64", "FO_PREC_BF16X3", "FO_PREC_FP16X2", "FO_PREC_BF16X1",
     "FO_MU_FIXED", "FO_MU_BISECT", "FO_MU_LEARNED", "FO_FLAG_NO_RESULT_SYNC", "FO_FLAG_GRAPH",
-    "FO_FLAG_STAGED", "FO_FLAG_POWER_BASIS",
+    "FO_FLAG_STAGED", "FO_FLAG_POWER_BASIS", "FO_FLAG_NO_TRACE_FIX", "FO_FLAG_ALLOW_LOOSE",
     "FoParams", "FoResult", "FermiError", "lib", "library_path", "EXPORTED_SYMBOLS",
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
@@ -37,6 +37,8 @@ FO_FLAG_NO_RESULT_SYNC = 0x2
 FO_FLAG_GRAPH = 0x4
 FO_FLAG_STAGED = 0x8
 FO_FLAG_POWER_BASIS = 0x10
+FO_FLAG_NO_TRACE_FIX = 0x20
+FO_FLAG_ALLOW_LOOSE = 0x40
 
 PRECISIONS = {"fp64": FO_PREC_FP64, "bf16x3": FO_PREC_BF16X3, "fp16x2": FO_PREC_FP16X2,
               "bf16x1": FO_PREC_BF16X1}
@@ -63,7 +65,8 @@ class FoParams(ctypes.Structure):
         ("emin", ctypes.c_double), ("emax", ctypes.c_double), ("max_bisect", ctypes.c_int32),
         ("flags", ctypes.c_uint32), ("tr_tol", ctypes.c_double), ("max_newton", ctypes.c_int32),
         ("tile_n", ctypes.c_int32), ("tile_ctas", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
-        ("tile_drain", ctypes.c_int32), ("tile_store", ctypes.c_int32),
+        ("tile_drain", ctypes.c_int32), ("tile_store", ctypes.c_int32), ("chain", ctypes.c_int32),
+        ("chain_window", ctypes.c_int32),
     ]
 
 
@@ -76,6 +79,7 @@ class FoResult(ctypes.Structure):
         ("status", ctypes.c_int32), ("n_launches", ctypes.c_int32), ("tile_n", ctypes.c_int32),
         ("tile_ctas", ctypes.c_int32), ("evals", ctypes.c_int32), ("order", ctypes.c_int32),
         ("tile_drain", ctypes.c_int32), ("tile_store", ctypes.c_int32),
+        ("trace_raw", ctypes.c_double), ("trace_gamma", ctypes.c_double), ("trace_proj", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -332,7 +336,7 @@ class Solver:
                mu_mode: str | int = "bisect", k: int = 0, bounds=None, n_quad: int = 0,
                max_bisect: int = 0, flags: int = 0, tile_n: int = 0, tile_ctas: int = 0,
                tr_tol: float = 0.0, max_newton: int = 0, lanczos_steps: int = 0,
-               tile_drain: int = 0, tile_store: int = 0) -> FoParams:
+               tile_drain: int = 0, tile_store: int = 0, chain: int = 0, chain_window: int = 0) -> FoParams:
         p = FoParams()
         p.n_terms, p.k, p.kT, p.mu = n_terms, k, kT, mu
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
@@ -342,6 +346,7 @@ class Solver:
         p.n_quad, p.max_bisect, p.flags = n_quad, max_bisect, flags
         p.tile_n, p.tile_ctas, p.tr_tol, p.max_newton = tile_n, tile_ctas, tr_tol, max_newton
         p.lanczos_steps, p.tile_drain, p.tile_store = lanczos_steps, tile_drain, tile_store
+        p.chain, p.chain_window = chain, chain_window
         return p
 
     def spectral_bounds(self, h, stream=None):

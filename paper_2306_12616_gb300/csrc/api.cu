@@ -33,14 +33,16 @@ enum PlanMode { MODE_DENSITY = 0, MODE_MOMENTS = 1, MODE_PRODUCT = 2, MODE_BOUND
 struct PlanKey {
     std::vector<int64_t> n;
     int mode = MODE_DENSITY, n_terms = 1, k_req = 0, prec = 0, mu_mode = 0, n_quad = 0;
-    int use_given = 0, tile_req = 0, ctas_req = 0, drain_req = 0, store_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0, power = 0;
+    int use_given = 0, tile_req = 0, ctas_req = 0, drain_req = 0, store_req = 0, sym = 1, max_bisect = 0, max_newton = 0, staged = 0, lanczos = 0, power = 0, nofix = 0;
+    int chain = 0, chain_win = 0;
     double tr_tol = 0.0;
     bool operator==(const PlanKey& o) const {
         return n == o.n && mode == o.mode && n_terms == o.n_terms && k_req == o.k_req && prec == o.prec &&
                mu_mode == o.mu_mode && n_quad == o.n_quad && use_given == o.use_given &&
                tile_req == o.tile_req && ctas_req == o.ctas_req && drain_req == o.drain_req &&
                store_req == o.store_req && sym == o.sym && max_bisect == o.max_bisect &&
-               max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged && lanczos == o.lanczos && power == o.power;
+               max_newton == o.max_newton && tr_tol == o.tr_tol && staged == o.staged && lanczos == o.lanczos && power == o.power &&
+               nofix == o.nofix && chain == o.chain && chain_win == o.chain_win;
     }
 };
 
@@ -66,6 +68,10 @@ struct Plan {
     int batch = 0;
     Shape sh{};
     bool giants = false, moments = false;
+    bool fix = false;         // split forms with mu searched: trace correction after the expansion
+    int chain = 0;            // split forms: each chain of products (baby, giant, Clenshaw) in one launch
+    int chain_win = 0;        // tiles per step of a chain launch's instance windows (0: one window)
+    int* counters = nullptr;  // chain launches: ticket and per-instance tile counters (workspace)
     int n_slots = 0;
     std::vector<int> order;   // sorted position -> caller index
     std::vector<Inst> inst;   // host copy, sorted
@@ -85,6 +91,7 @@ struct Plan {
     double* ct = nullptr;
     double* part_g = nullptr;
     double* part_t = nullptr;
+    double* part_tc = nullptr;    // per-tile (tr, ||.||^2) partials of the float64-output products
     float* lscratch = nullptr;    // learned mu: features, normalised features, activations, outputs
     int* lcount = nullptr;        // learned mu: instances still active after a judge
     size_t total = 0;
@@ -310,6 +317,9 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     const bool learned = key.mode == MODE_DENSITY && key.mu_mode == FO_MU_LEARNED;
     p->giants = (bisect || learned) && sh.m > 2;   // the learned mode falls back to exact moments
     p->moments = bisect || learned || key.mode == MODE_MOMENTS;
+    p->fix = (bisect || learned) && !sh.is64 && sh.m > 1 && !key.nofix;
+    p->chain = !sh.is64 && key.mode == MODE_DENSITY && key.chain == 2 ? 1 : 0;
+    p->chain_win = key.chain_win;
     if (p->moments && sh.k > 33) return fail(ctx, FO_ERR_UNSUPPORTED, "exact moments support k <= 33");
     if (learned && sh.k > 32) return fail(ctx, FO_ERR_UNSUPPORTED, "learned mu supports k <= 32");
     switch (key.mode) {
@@ -377,7 +387,6 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
         off = o;
     }
     const size_t off_res = take(sizeof(DevResult) * batch);
-    const size_t off_ct = take(8 * 4 * (size_t)sh.M);
     // work lists
     auto fill = [&](HostWork& w, auto count) {
         w.pre.assign(batch + 1, 0);
@@ -395,15 +404,18 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     fill(p->wf64, [](const Inst& in) { return f64_tiles(in.np); });
     const size_t off_pg = take(8 * 3 * (size_t)std::max(1, p->wg.pre[batch]));
     const size_t off_pt = take(8 * 2 * (size_t)std::max(1, p->wr.pre[batch]));
+    const size_t off_ptc = take(8 * 2 * (size_t)std::max(1, p->wtc[1].pre[batch]));   // 128-blocks
+    const size_t off_cnt = take(4 * ((size_t)batch + 8));
     const size_t off_ls = take(4 * (size_t)batch * (2 * kMlpIn + 4 * kMlpHidden + kMlpOut));
     const size_t off_lc = take(sizeof(int));
     p->total = off;
     // remember the offsets in the (not yet placed) pointers
     for (int j = 0; j < batch; ++j) p->inst[j].c = reinterpret_cast<double*>(small[j]);
     p->d_res = reinterpret_cast<DevResult*>(off_res);
-    p->ct = reinterpret_cast<double*>(off_ct);
     p->part_g = reinterpret_cast<double*>(off_pg);
     p->part_t = reinterpret_cast<double*>(off_pt);
+    p->part_tc = reinterpret_cast<double*>(off_ptc);
+    p->counters = reinterpret_cast<int*>(off_cnt);
     p->lscratch = reinterpret_cast<float*>(off_ls);
     p->lcount = reinterpret_cast<int*>(off_lc);
     // launch groups: at most kMaxBuckets tensor maps per launch
@@ -430,9 +442,10 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
     const int batch = p->batch;
     const int ndiag = sh.n_tslots + 2;
     p->d_res = reinterpret_cast<DevResult*>(W + reinterpret_cast<size_t>(p->d_res));
-    p->ct = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->ct));
     p->part_g = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->part_g));
     p->part_t = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->part_t));
+    p->part_tc = reinterpret_cast<double*>(W + reinterpret_cast<size_t>(p->part_tc));
+    p->counters = reinterpret_cast<int*>(W + reinterpret_cast<size_t>(p->counters));
     p->lscratch = reinterpret_cast<float*>(W + reinterpret_cast<size_t>(p->lscratch));
     p->lcount = reinterpret_cast<int*>(W + reinterpret_cast<size_t>(p->lcount));
     for (int j = 0; j < batch; ++j) {
@@ -452,10 +465,14 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
         in.lz = next(8 * (3 * (size_t)in.np + 2 * kLzMax + 3));
         in.res = p->d_res + j;
     }
-    // device tables: Inst[batch], InstIO[batch], then the prefix arrays
+    // device tables: Inst[batch], InstIO[batch], the prefix arrays, then the cosine table of
+    // the coefficient nodes. These stay valid for the plan's life: the workspace is shared
+    // by every cached plan of the context, and another plan's call overwrites it.
     HostWork* lists[] = {&p->wg, &p->wsc, &p->we, &p->wr, &p->wgr, &p->wct, &p->wtc[0], &p->wtc[1], &p->wf64};
     size_t bytes = align256(sizeof(Inst) * batch) + align256(sizeof(InstIO) * batch);
     for (HostWork* w : lists) bytes += align256(sizeof(int) * w->pre.size());
+    const size_t off_ct = bytes;
+    bytes += align256(8 * 4 * (size_t)sh.M);
     if (cudaMalloc(&p->dtab, bytes) != cudaSuccess) {
         cudaGetLastError();
         p->dtab = nullptr;
@@ -477,6 +494,7 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
     }
     if (cudaMemcpy(p->dtab, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(ctx, FO_ERR_CUDA, "plan table upload failed");
+    p->ct = reinterpret_cast<double*>(reinterpret_cast<char*>(p->dtab) + off_ct);
     // tensor maps: one per bucket over (column, row, plane, slot, instance)
     if (!sh.is64 && p->n_slots > 0) {
         p->maps.assign(256 * p->buckets.size(), 0);
@@ -491,7 +509,7 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
                     return fail(ctx, FO_ERR_CUDA, "tensor map: " + err);
         }
     }
-    // the cosine table depends on M only
+    // the cosine table depends on M only (kept in the plan's own device tables)
     cudaError_t e = launch_cos_table(sh.M, p->ct, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cos_table");
@@ -571,6 +589,56 @@ fo_status run_product(fo_ctx* ctx, Plan& p, const Step& st, cudaStream_t s, cons
     return run_products(ctx, p, &st, 1, s, tag, index, run);
 }
 
+// A chain of dependent products (step q reads what step q - 1 wrote) of the whole batch: one
+// launch per group of instances and per kMaxChain steps when the plan runs chains
+// (tc_chain), else one launch per step.
+fo_status run_chain(fo_ctx* ctx, Plan& p, const std::vector<Step>& steps, cudaStream_t s, const char* tag,
+                    Run* run) {
+    if (steps.empty()) return FO_OK;
+    if (!p.chain || p.sh.is64) {
+        for (size_t q = 0; q < steps.size(); ++q) FO_TRY(run_product(ctx, p, steps[q], s, tag, (int)q, run));
+        return FO_OK;
+    }
+    const HostWork& w = p.wtc[p.tile_n == 128 ? 1 : 0];
+    for (size_t q0 = 0; q0 < steps.size(); q0 += kMaxChain) {
+        const int nq = (int)std::min<size_t>(kMaxChain, steps.size() - q0);
+        const int h = prof_begin(ctx, s, FO_STAGE_PRODUCTS);
+        int launches = 0;
+        for (const Group& g : p.groups) {
+            std::string err;
+            cudaError_t e = tc_chain(p.key.prec, p.tile_n, p.tile_ctas, p.tile_drain, steps.data() + q0, nq, p.d_inst,
+                                     p.d_io, w.dev.pre, w.pre.data(), g.i0, g.i1, p.maps.data() + 256 * (size_t)g.b0,
+                                     g.b0, g.nb, ctx->flag, p.counters, p.chain_win, s, &err,
+                                     p.key.sym ? (p.sh.ublk ? 2 : 1) : 0);
+            if (e == cudaSuccess && debug_sync() && !ctx->capturing) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) {
+                const std::string where = std::string("tc_chain ") + tag;
+                if (!err.empty()) return fail(ctx, FO_ERR_CUDA, where + ": " + err);
+                return cuda_fail(ctx, e, where.c_str());
+            }
+            ++launches;
+        }
+        prof_end(ctx, s, h, p.flops_product * nq, launches);
+        run->launches += launches;
+        run->n_gemm += nq;
+    }
+    return FO_OK;
+}
+
+// The product that writes the caller's float64 P (last Clenshaw or Horner step). In the split
+// forms its epilogue also leaves per-tile partials of tr P and ||P||_F^2, and, when the trace
+// correction follows, the planes of P in slot `pslot` (R_0's, read and then overwritten
+// entry by entry, like every Clenshaw step's R_l -> b_l) as the operands of P P.
+void final_step_extras(const Plan& p, Step& st, int pslot) {
+    if (p.sh.is64) return;
+    st.part = p.part_tc;
+    st.part_pre = p.wtc[1].dev.pre;
+    if (p.fix) {
+        st.out = pslot;
+        st.planes = p.sh.planes;
+    }
+}
+
 // Slot of T_{j k} for j >= 1: T_k is baby slot k-1, giants T_{2k}.. follow.
 int giant_slot(const Plan& p, int j) { return j == 1 ? p.sh.k - 1 : p.sh.k + j - 2; }
 int r_slot(const Plan& p, int l) { return p.sh.n_tslots + l; }
@@ -596,11 +664,9 @@ fo_status chebyshev_chain(fo_ctx* ctx, Plan& p, int jmax, SlotOf slot, bool stag
     };
     if (jmax < 2) return FO_OK;
     if (!staged) {
-        for (int j = 1; j < jmax; ++j) {
-            const Step st = prod(1, j, j - 1, j + 1);
-            FO_TRY(run_product(ctx, p, st, s, tag, j + 1, run));
-        }
-        return FO_OK;
+        std::vector<Step> chain;
+        for (int j = 1; j < jmax; ++j) chain.push_back(prod(1, j, j - 1, j + 1));
+        return run_chain(ctx, p, chain, s, tag, run);
     }
     {
         const Step st = prod(1, 1, 0, 2);
@@ -648,17 +714,18 @@ fo_status clenshaw(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     const int m = p.sh.m;
     if (m == 1) return FO_OK;
     const int y = giant_slot(p, 1);
+    std::vector<Step> chain;
     for (int l = m - 2; l >= 1; --l) {
         const bool has_c = l + 2 <= m - 1;
-        const Step st = make_step(p, y, r_slot(p, l + 1), has_c ? r_slot(p, l + 2) : -1, r_slot(p, l), r_slot(p, l),
-                                  2.0, has_c ? -1.0 : 0.0, 0.0, false, true, true, false, ctx);
-        FO_TRY(run_product(ctx, p, st, s, "clenshaw", l, run));
+        chain.push_back(make_step(p, y, r_slot(p, l + 1), has_c ? r_slot(p, l + 2) : -1, r_slot(p, l), r_slot(p, l),
+                                  2.0, has_c ? -1.0 : 0.0, 0.0, false, true, true, false, ctx));
     }
     const bool has_c = m >= 3;
-    const Step st = make_step(p, y, r_slot(p, 1), has_c ? r_slot(p, 2) : -1, r_slot(p, 0), -1, 1.0,
-                              has_c ? -1.0 : 0.0, 0.0, false, true, false, true, ctx);
-    FO_TRY(run_product(ctx, p, st, s, "final", 0, run));
-    return FO_OK;
+    Step st = make_step(p, y, r_slot(p, 1), has_c ? r_slot(p, 2) : -1, r_slot(p, 0), -1, 1.0,
+                        has_c ? -1.0 : 0.0, 0.0, false, true, false, true, ctx);
+    final_step_extras(p, st, r_slot(p, 0));
+    chain.push_back(st);
+    return run_chain(ctx, p, chain, s, "clenshaw", run);
 }
 
 // Spectral bounds, X and the baby steps T_2..T_k of every instance.
@@ -702,13 +769,45 @@ fo_status horner(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
                                   true, true, false, ctx);
         FO_TRY(run_product(ctx, p, st, s, "horner", j, run));
     }
-    const Step st = make_step(p, y, r_slot(p, 1), -1, r_slot(p, 0), -1, 1.0, 0.0, 0.0, false, true, false, true, ctx);
+    Step st = make_step(p, y, r_slot(p, 1), -1, r_slot(p, 0), -1, 1.0, 0.0, 0.0, false, true, false, true, ctx);
+    final_step_extras(p, st, r_slot(p, 0));
     return run_product(ctx, p, st, s, "horner", 0, run);
 }
 
+// tr P and ||P||_F^2 of every active instance after the float64-output product: from the
+// product's partials per 128 x 128 block (split forms, m > 1), else by a pass over P. tmode 1
+// also computes the trace correction's gamma (see trace_fix).
+fo_status trace_stage(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int tmode) {
+    const int h = prof_begin(ctx, s, FO_STAGE_TRACE);
+    if (!p.sh.is64 && p.sh.m > 1) {
+        FO_CUDA(launch_tile_trace(p.d_inst, p.d_io, p.batch, p.wtc[1].dev.pre, p.part_tc, tmode, s), "trace");
+        prof_end(ctx, s, h, 0.0, 1);
+        run->launches += 1;
+    } else {
+        FO_CUDA(launch_trace_frob(p.d_inst, p.d_io, p.wr.dev, p.part_t, s), "trace");
+        prof_end(ctx, s, h, 0.0, 2);
+        run->launches += 2;
+    }
+    return FO_OK;
+}
+
+// Trace correction of the split forms (after trace_stage with tmode 1 set gamma): the product
+// P P with the float64 epilogue P <- P + gamma (P - P P), the first-order shift of mu that
+// restores tr P = N_e, then the per-instance sum of the new trace and the removal of the
+// product's own float64 residual by the trace projection (k_tile_trace, mode 2).
+fo_status trace_fix(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    const int pslot = r_slot(p, 0);
+    Step st = make_step(p, pslot, pslot, -1, -1, -1, 1.0, 0.0, 0.0, false, false, false, true, ctx);
+    st.fix64 = 1;
+    st.part = p.part_tc;
+    st.part_pre = p.wtc[1].dev.pre;
+    FO_TRY(run_product(ctx, p, st, s, "trace fix", 0, run));
+    return trace_stage(ctx, p, s, run, 2);
+}
+
 // P of every active instance at its current mu: coefficients, R_l, Clenshaw, tr P, ||P||^2
-// (or, with the power basis, d_{i,j}, S_j and Horner).
-fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trace) {
+// (or, with the power basis, d_{i,j}, S_j and Horner). tmode as in trace_stage.
+fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trace, int tmode) {
     const Shape& sh = p.sh;
     int h = prof_begin(ctx, s, FO_STAGE_COEFFS);
     int lstage = 0;
@@ -729,11 +828,7 @@ fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trac
     prof_end(ctx, s, h, 0.0, lstage);
     run->launches += lstage;
     FO_TRY(p.key.power ? horner(ctx, p, s, run) : clenshaw(ctx, p, s, run));
-    h = prof_begin(ctx, s, FO_STAGE_TRACE);
-    FO_CUDA(launch_trace_frob(p.d_inst, p.d_io, p.wr.dev, p.part_t, s), "trace");
-    prof_end(ctx, s, h, 0.0, 2);
-    run->launches += 2;
-    return FO_OK;
+    return trace_stage(ctx, p, s, run, tmode);
 }
 
 // Learned mu: moments up to 2k from the baby steps, the network's proposal, evaluation of P
@@ -770,7 +865,7 @@ fo_status learned(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     const int R = p.key.max_newton == 0 ? 2 : (p.key.max_newton < 0 ? 0 : p.key.max_newton);
     bool any = true;
     for (int r = 0; r <= R; ++r) {
-        FO_TRY(evaluate(ctx, p, s, run, 0));
+        FO_TRY(evaluate(ctx, p, s, run, 0, 0));
         if (r < R) {
             FO_CUDA(launch_poly_width(p.d_inst, B, sh, p.ct, s), "expansion width");
             run->launches += 1;
@@ -787,7 +882,13 @@ fo_status learned(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     }
     if (any) {
         FO_TRY(exact_mu(ctx, p, s, run, 1));
-        FO_TRY(evaluate(ctx, p, s, run, 1));
+        FO_TRY(evaluate(ctx, p, s, run, 1, 0));
+    }
+    if (p.fix) {
+        // every instance's partials are those of its last evaluation (accepted instances are
+        // skipped by later ones): gamma for all of them, then the correcting product
+        FO_TRY(trace_stage(ctx, p, s, run, 1));
+        FO_TRY(trace_fix(ctx, p, s, run));
     }
     return FO_OK;
 }
@@ -798,13 +899,14 @@ fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     switch (p.key.mu_mode) {
         case FO_MU_BISECT:
             FO_TRY(exact_mu(ctx, p, s, run, 0));
-            return evaluate(ctx, p, s, run, 1);
+            FO_TRY(evaluate(ctx, p, s, run, 1, p.fix ? 1 : 0));
+            return p.fix ? trace_fix(ctx, p, s, run) : FO_OK;
         case FO_MU_LEARNED:
             return learned(ctx, p, s, run);
         default:
             FO_CUDA(launch_set_mu(p.d_inst, p.d_io, p.batch, s), "mu");
             run->launches += 1;
-            return evaluate(ctx, p, s, run, 0);
+            return evaluate(ctx, p, s, run, 0, 0);
     }
 }
 
@@ -942,6 +1044,20 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
         return fail(ctx, FO_ERR_ARG, "16 drain warps need tile_n = 256");
     if ((prm->flags & FO_FLAG_POWER_BASIS) && prm->precision == FO_PREC_FP16X2)
         return fail(ctx, FO_ERR_UNSUPPORTED, "the power basis overflows the fp16 range");
+    if (prm->precision != FO_PREC_FP64 && !(prm->flags & FO_FLAG_ALLOW_LOOSE)) {
+        // combinations measured beyond the split forms' 1e-6 bar run only on request
+        if (prm->flags & FO_FLAG_STAGED)
+            return fail(ctx, FO_ERR_UNSUPPORTED,
+                        "staged chains in a split precision exceed the 1e-6 bar (set FO_FLAG_ALLOW_LOOSE)");
+        if (prm->flags & FO_FLAG_POWER_BASIS)
+            return fail(ctx, FO_ERR_UNSUPPORTED,
+                        "the power basis in a split precision exceeds the 1e-6 bar (set FO_FLAG_ALLOW_LOOSE)");
+        int k = 0, m = 0;
+        if (prm->k > 0 && plan_km(prm->n_terms, prm->k, &k, &m) && m > k)
+            return fail(ctx, FO_ERR_UNSUPPORTED,
+                        "k below ceil(sqrt(n_terms)) lengthens the Clenshaw chain beyond the split forms' "
+                        "1e-6 bar (set FO_FLAG_ALLOW_LOOSE)");
+    }
     if (prm->lanczos_steps < 0 || prm->lanczos_steps > kLzMax)
         return fail(ctx, FO_ERR_ARG, "lanczos_steps must be in [0, 64]");
     if (prm->tile_ctas < 0 || prm->tile_ctas > 2 || (prm->tile_ctas == 2 && prm->tile_n != 128) ||
@@ -949,6 +1065,8 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
         return fail(ctx, FO_ERR_ARG, "tile_ctas must be 0, 1 or 2 (2 with tile_n = 128), set with tile_n");
     if (prm->tile_store < 0 || prm->tile_store > 2 || (prm->tile_store != 0 && prm->tile_n == 0))
         return fail(ctx, FO_ERR_ARG, "tile_store must be 0, 1 or 2, set with tile_n");
+    if (prm->chain < 0 || prm->chain > 2 || prm->chain_window < 0)
+        return fail(ctx, FO_ERR_ARG, "chain must be 0, 1 or 2 and chain_window >= 0");
     return FO_OK;
 }
 
@@ -981,6 +1099,8 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
             return fail(ctx, FO_ERR_ARG, "n_e must be in [0, n]");
         if (kT && (!(kT[b] > 0.0) || !std::isfinite(kT[b]))) return fail(ctx, FO_ERR_ARG, "kT must be > 0");
     }
+    // a device timeout of an earlier call is reported by that call: clear it for this one
+    FO_CUDA(cudaMemsetAsync(ctx->flag, 0, sizeof(int), st), "reset the timeout flag");
     PlanKey key;
     key.n.assign(n, n + batch);
     key.mode = MODE_DENSITY;
@@ -998,6 +1118,9 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
     key.staged = (prm->flags & FO_FLAG_STAGED) ? 1 : 0;
     key.lanczos = prm->lanczos_steps;
     key.power = (prm->flags & FO_FLAG_POWER_BASIS) ? 1 : 0;
+    key.nofix = (prm->flags & FO_FLAG_NO_TRACE_FIX) ? 1 : 0;
+    key.chain = prm->chain;
+    key.chain_win = prm->chain_window;
     if (prm->mu_mode == FO_MU_LEARNED) {
         key.max_newton = prm->max_newton;
         key.tr_tol = prm->tr_tol;
@@ -1050,7 +1173,8 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
         }
         FO_CUDA(cudaGraphLaunch(p->graph, st), "graph launch");
         // the graph holds the same launches as an eager call
-        run.n_gemm = (p->sh.k - 1) + (p->giants ? p->sh.m - 2 : 0) + (p->sh.m > 1 ? p->sh.m - 1 : 0);
+        run.n_gemm = (p->sh.k - 1) + (p->giants ? p->sh.m - 2 : 0) + (p->sh.m > 1 ? p->sh.m - 1 : 0) +
+                     (p->fix ? 1 : 0);
         run.launches += p->graph_launches;
     } else {
         FO_TRY(run_density(ctx, *p, st, &run));
@@ -1075,6 +1199,9 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
             std::memset(&r, 0, sizeof(r));
             r.mu = hr.mu;
             r.trace = hr.trace;
+            r.trace_raw = hr.trace_raw;
+            r.trace_gamma = hr.gamma;
+            r.trace_proj = hr.proj;
             r.trace_poly = hr.trace_poly;
             r.frob2 = hr.frob2;
             r.emin = hr.bounds[0];
@@ -1097,7 +1224,8 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
                 const int ev = hr.evals + (hr.learned_ok ? 0 : 1);
                 const int km1 = p->sh.m > 1 ? p->sh.m - 1 : 0;
                 r.evals = ev;
-                r.n_gemm = (p->sh.k - 1) + ev * km1 + (hr.learned_ok ? 0 : (p->giants ? p->sh.m - 2 : 0));
+                r.n_gemm = (p->sh.k - 1) + ev * km1 + (hr.learned_ok ? 0 : (p->giants ? p->sh.m - 2 : 0)) +
+                           (p->fix ? 1 : 0);
                 r.order = (int)std::lround(hr.order);
                 if (!hr.learned_ok) r.bisect_iters = hr.iters;
                 else r.bisect_iters = 0;

@@ -60,6 +60,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -253,7 +254,9 @@ struct TcCfg {
     static_assert(kSmem <= 232448 - 64, "shared memory budget of one CTA exceeded");
     static_assert(MINB * kTmemCols <= 512, "tensor memory of the co-resident CTAs exceeded");
     static_assert(MINB * (kSmem + 1024) <= 233472, "shared memory of the co-resident CTAs exceeded");
-    static_assert(kStages * kStageBytes >= kBM * (TBN + 1) * 4, "result tile must fit the stage ring");
+    static constexpr int kRowPartOff = ((kBM * (TBN + 1) * 4 + 15) / 16) * 16;   // after the result tile
+    static_assert(kStages * kStageBytes >= kRowPartOff + kBM * 2 * 2 * 8,
+                  "result tile and trace partials must fit the stage ring");
 };
 
 // (a-plane, b-plane) of each product, largest first:
@@ -282,6 +285,24 @@ __device__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint64_t limit_ns
                 else if (t - t0 > limit_ns) stop = 1;
             }
             if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+        }
+    }
+}
+
+// Chain launches: bounded wait until *ctr >= need, with acquire semantics at GPU scope (the
+// CTAs that counted released their stores). Gives up, returning false, when another CTA
+// raised the device error flag or after the 2 s deadline.
+__device__ bool wait_count(const int* ctr, int need, const int* err_flag) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= need) return true;
+        if ((it & 63u) == 63u) {
+            if (*reinterpret_cast<const volatile int*>(err_flag)) return false;
+            const uint64_t t = gtimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitNs) return false;
         }
     }
 }
@@ -324,9 +345,12 @@ __device__ __forceinline__ void tile_of(int t, int tm, int tn, int tbn, int sym,
     J = t - I * tn;
 }
 
-template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB, int DW>
+// CHAIN: one launch runs a chain of dependent steps (ChainList): tiles are taken by ticket, a
+// tile waits for its instance's previous step and signals its own completion.
+template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB, int DW, bool CHAIN>
 __global__ void __launch_bounds__(32 * (2 + DW), MINB)
-    k_tc_gemm(const __grid_constant__ TcMaps maps, const __grid_constant__ StepList steps,
+    k_tc_gemm(const __grid_constant__ TcMaps maps,
+              const __grid_constant__ std::conditional_t<CHAIN, ChainList, StepList> steps,
               const Inst* __restrict__ insts, const InstIO* __restrict__ io, const int* __restrict__ pre,
               int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag) {
     using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB, DW>;
@@ -344,12 +368,48 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     __shared__ int abort_flag;
 
     // ---------------- step, instance and tile of this CTA (uniform across the CTA)
-    const int sidx = (int)blockIdx.x / tiles;
+    int sidx, gtile, inst;
+    // chain launches: the ticket's step and the tile count its instance must reach first,
+    // kept in shared memory (re-read after the main loop instead of held in registers)
+    __shared__ int s_chain[4];   // ticket, step, count needed, stop
+    if constexpr (CHAIN) {
+        // the ticket decides the work: window, step within it, tile within the step. Whether
+        // another CTA already gave up is read once, by thread 0, so that the whole CTA leaves
+        // (or stays) together
+        if (threadIdx.x == 0) {
+            s_chain[0] = atomicAdd(steps.ticket, 1);
+            s_chain[3] = *reinterpret_cast<const volatile int*>(err_flag);
+        }
+        __syncthreads();
+        const int t = s_chain[0];
+        int w = 0;
+        while (w + 1 < steps.nwin && steps.win_base[w + 1] <= t) ++w;
+        const int wi0 = steps.win_i0[w], wi1 = steps.win_i0[w + 1];
+        const int w0 = __ldg(pre + wi0);
+        const int tw = __ldg(pre + wi1) - w0;
+        const int local = t - steps.win_base[w];
+        sidx = local / tw;
+        gtile = w0 + (local - sidx * tw);
+        inst = find_inst(pre, wi0, wi1, gtile);
+        if (s_chain[3]) return;   // a CTA gave up: the chain stops
+        if (threadIdx.x == 0) {
+            s_chain[1] = sidx;
+            s_chain[2] = sidx * (__ldg(pre + inst + 1) - __ldg(pre + inst));
+        }
+    } else {
+        sidx = (int)blockIdx.x / tiles;
+        gtile = tile0 + (int)blockIdx.x - sidx * tiles;
+        inst = find_inst(pre, i0, i1, gtile);
+    }
     const Step& st = steps.s[sidx];
-    const int gtile = tile0 + (int)blockIdx.x - sidx * tiles;
-    const int inst = find_inst(pre, i0, i1, gtile);
     const Inst& in = insts[inst];
-    if (!in.res->active) return;
+    if (!in.res->active) {
+        // an instance parked by the learned judge: its tiles count as done
+        if constexpr (CHAIN) {
+            if (threadIdx.x == 0) atomicAdd(steps.done + (inst - i0), 1);
+        }
+        return;
+    }
     const int np = (int)in.np;
     const CUtensorMap* map = &maps.m[in.bucket - b0];
     const CUtensorMap* map_mn = &maps.mn[in.bucket - b0];
@@ -425,9 +485,20 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         if (lane == 0) {
             // ---------------- TMA producer (instantiated per plane storage, as the MMA issuer)
             int issued = 0;
+            if constexpr (CHAIN) {
+                // the previous step's tiles of this instance (its stores are read by TMA, an
+                // async-proxy read, after the generic-proxy acquire: the proxy fence orders them)
+                const int need = *reinterpret_cast<volatile int*>(&s_chain[2]);
+                if (need > 0 && !wait_count(steps.done + (inst - i0), need, err_flag)) {
+                    atomicExch(&abort_flag, 1);
+                    atomicExch(err_flag, 1);
+                }
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
             auto produce = [&](auto ub_tag) {
                 constexpr bool U = decltype(ub_tag)::value;
                 for (int kb = 0; kb < nk; ++kb) {
+                    if (CHAIN && kb == 0 && *vabort) break;
                     const int s = kb % S;
                     if (kb >= S) {
                         if (!mbar_wait(&empty[s], ((kb / S) - 1) & 1, kWaitNs, vabort)) {
@@ -628,6 +699,9 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     }
     if (warp < 2 || *vabort) return;  // uniform across the drain warps
 
+    // the step's record again for the epilogue (derived anew, not held through the main loop)
+    {
+    const Step& st = steps.s[CHAIN ? *reinterpret_cast<volatile int*>(&s_chain[1]) : (int)blockIdx.x / tiles];
     // ---------------- drain warps: update and store through shared memory. The stage ring
     // is idle (every TMA load was consumed, every MMA completed), so it holds the 128 x TBN
     // float32 result tile; all global traffic below is coalesced across the warp.
@@ -641,6 +715,15 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         for (int c = 0; c < NC; ++c) tile[rl * LD + grp * NC + c] = st.alpha * sum[c];
     }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * DW) : "memory");
+    if constexpr (CHAIN) {
+        // every drain thread acquires the previous step's stores itself before its generic
+        // loads of C and D (satisfied already: the producer waited before the first TMA);
+        // after the accumulators went to shared memory, so none of them is live here. A wait
+        // that gives up raises the error flag and goes on (the drain warps must all reach
+        // their named barriers)
+        const int need = *reinterpret_cast<volatile int*>(&s_chain[2]);
+        if (need > 0 && !wait_count(steps.done + (inst - i0), need, err_flag)) atomicExch(err_flag, 1);
+    }
 
     // instance fields of the epilogue, read here so that they are not live in the main loop
     const int64_t n_real = insts[inst].n;
@@ -654,19 +737,50 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     const float* Dm = st.d >= 0 ? reinterpret_cast<const float*>(base + sb * st.d) : nullptr;
     double* out64 = st.out64 ? io[inst].P : nullptr;
     const int64_t ldo = io[inst].ldp;
+    const bool fix = out64 && st.fix64;
+    const double gam = fix ? insts[inst].res->gamma : 0.0;
     const int planes = st.planes;
     const int ew = warp - 2;  // 0..DW-1
-    // store of the pair (grow, gcol), (grow, gcol + 1) for the elements whose flag is set
-    auto store_pair = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool master) {
-        if (!(w0 || w1)) return;
-        if (out64) {
-            if (grow < n_real) {
-                double* dst = out64 + grow * ldo + gcol;
-                if (w0 && gcol < n_real) dst[0] = (double)v0;
-                if (w1 && gcol + 1 < n_real) dst[1] = (double)v1;
-            }
-            return;
+    // float64 result (the caller's P) of the pair (grow, gcol), (grow, gcol + 1) for the
+    // elements whose flag is set: the float32 value itself, or with fix the correction
+    // P + gamma (P - v) of the P already stored there (each element is read and rewritten by
+    // one thread; an element and its mirror hold the same bits, so both get the same result).
+    // Returns in (ta, fa) the written entries' contributions to the trace and to ||P||_F^2
+    // (those on or above the diagonal; strictly above counts twice).
+    // Trace and Frobenius partials per (tile row, 128-column block): each (row, 64-column
+    // piece) is reduced by a fixed shuffle tree over the lanes and the two pieces of a block
+    // are added in column order, so the partials, and the sums over their rows, do not depend
+    // on the tile width or on which warp handled the row (every tiling gives the same bits);
+    // kept in the idle stage ring after the result tile
+    double (*rowpart)[2][2] = reinterpret_cast<double (*)[2][2]>(smem + Cfg::kRowPartOff);
+    auto store64 = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool upper, double& ta,
+                       double& fa) {
+        ta = 0.0;
+        fa = 0.0;
+        if (grow >= n_real) return;
+        double* dst = out64 + grow * ldo + gcol;
+        const bool e0 = w0 && gcol < n_real, e1 = w1 && gcol + 1 < n_real;
+        double x0 = (double)v0, x1 = (double)v1;
+        if (fix) {
+            if (e0) { const double p = dst[0]; x0 = fma(gam, p - x0, p); }
+            if (e1) { const double p = dst[1]; x1 = fma(gam, p - x1, p); }
         }
+        if (e0) dst[0] = x0;
+        if (e1) dst[1] = x1;
+        if (upper) {
+            if (e0) {
+                if (gcol == grow) { ta += x0; fa = fma(x0, x0, fa); }
+                else fa = fma(2.0 * x0, x0, fa);
+            }
+            if (e1) {
+                if (gcol + 1 == grow) { ta += x1; fa = fma(x1, x1, fa); }
+                else fa = fma(2.0 * x1, x1, fa);
+            }
+        }
+    };
+    // slot store (float32 master and 16-bit planes) of the same pair
+    auto store_slot = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool master) {
+        if (!(w0 || w1) || (!out_x && planes == 0)) return;
         const int64_t o = grow * ld + gcol;
         if (!FO_CHK(st.dbg, o >= 0 && o + 2 <= ld * ld, 111, grow, gcol)) return;
         uint16_t a0 = 0, a1 = 0, a2 = 0, b0v = 0, b1v = 0, b2v = 0;
@@ -696,6 +810,11 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         }
     };
 
+    // The passes are instantiated twice: the products that write the caller's float64 P (with
+    // their trace partials) and all others, whose loops then carry none of that code (a shared
+    // loop with run-time checks made every product ~13 % slower).
+    auto passes = [&](auto f64_tag) {
+    constexpr bool F64 = decltype(f64_tag)::value;
     // row pass: each drain warp takes kBM / DW tile rows, lanes on column pairs; applies
     // beta C + D + shift and stores the entries with col >= row (all of them when not sym).
     // The C and D operands of G consecutive (row, column piece) iterations are loaded before
@@ -718,8 +837,11 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             cv[u] = make_float2(0.f, 0.f);
             dv[u] = make_float2(0.f, 0.f);
             if (c < tile_n) {
-                if (Cm) cv[u] = *reinterpret_cast<const float2*>(Cm + o);
-                if (Dm) dv[u] = *reinterpret_cast<const float2*>(Dm + o);
+                // within a chain launch other SMs wrote C and D during this launch: L2 loads
+                if (Cm) cv[u] = CHAIN ? __ldcg(reinterpret_cast<const float2*>(Cm + o))
+                                      : *reinterpret_cast<const float2*>(Cm + o);
+                if (Dm) dv[u] = CHAIN ? __ldcg(reinterpret_cast<const float2*>(Dm + o))
+                                      : *reinterpret_cast<const float2*>(Dm + o);
             }
         }
 #pragma unroll
@@ -743,7 +865,43 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             }
             tile[r * LD + c] = v0;
             tile[r * LD + c + 1] = v1;
-            store_pair(grow, gcol, v0, v1, !sym || gcol >= grow, !sym || gcol + 1 >= grow, true);
+            const bool w0 = !sym || gcol >= grow, w1 = !sym || gcol + 1 >= grow;
+            double ta = 0.0, fa = 0.0;
+            if constexpr (F64) store64(grow, gcol, v0, v1, w0, w1, true, ta, fa);
+            store_slot(grow, gcol, v0, v1, w0, w1, true);
+            if (F64 && st.part) {
+                // this (row, piece)'s sums (the `continue` above is uniform across the warp:
+                // tile widths are multiples of 128); pieces 2b, 2b + 1 form the tile's
+                // 128-column block b, added in that order by the warp that owns the row
+                for (int o = 16; o > 0; o >>= 1) {
+                    ta += __shfl_xor_sync(0xffffffffu, ta, o);
+                    fa += __shfl_xor_sync(0xffffffffu, fa, o);
+                }
+                if (lane == 0) {
+                    double* rp = rowpart[r][h >> 1];
+                    if (h & 1) {
+                        rp[0] += ta;
+                        rp[1] += fa;
+                    } else {
+                        rp[0] = ta;
+                        rp[1] = fa;
+                    }
+                }
+            }
+        }
+    }
+    if (F64 && st.part) {
+        // the tile's 128 x 128 blocks: rows added in order; block (I, J) of the instance's
+        // upper-block enumeration (row blocks in order, J >= I within a row)
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * DW) : "memory");
+        const int nblk = tile_n / kBM;
+        if (ew == 0 && lane < 2 * nblk) {
+            const int b = lane >> 1, qty = lane & 1;
+            double sacc = 0.0;
+            for (int r = 0; r < kBM; ++r) sacc += rowpart[r][b][qty];
+            const int64_t nb = np / kBM, I = m0 / kBM, J = n0 / kBM + b;
+            const int64_t blk = (int64_t)st.part_pre[inst] + I * nb - I * (I - 1) / 2 + (J - I);
+            st.part[2 * blk + qty] = sacc;
         }
     }
     if (!sym) return;
@@ -762,14 +920,31 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         // block only (a lower block is read as the transpose of its upper counterpart):
         // outside the tile's diagonal block nothing below the diagonal is written, except
         // into the caller's float64 P, which is returned whole
-        if (ub && !lower_master && !out64 && grow >= (int64_t)m0 + kBM) break;
+        const bool slot_rows = !(ub && !lower_master && grow >= (int64_t)m0 + kBM);
+        if (!slot_rows && !F64) break;
 #pragma unroll
         for (int h = 0; h < kBM / 64; ++h) {
             const int r = h * 64 + 2 * lane;
             const int64_t gcol = (int64_t)m0 + r;   // output column
-            store_pair(grow, gcol, tile[r * LD + c], tile[(r + 1) * LD + c], grow > gcol, grow > gcol + 1,
-                       lower_master);
+            const float v0 = tile[r * LD + c], v1 = tile[(r + 1) * LD + c];
+            if constexpr (F64) {
+                double ta, fa;   // entries below the diagonal: counted twice by their mirrors above
+                store64(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, false, ta, fa);
+            }
+            if (slot_rows) store_slot(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, lower_master);
         }
+    }
+    };
+    if (out64) passes(std::true_type{});
+    else passes(std::false_type{});
+    if constexpr (CHAIN) {
+        // this tile's stores are complete: release them to the next step's tiles (generic
+        // stores read later through TMA: a proxy fence as well), then count the tile
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __threadfence();
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * DW) : "memory");
+        if (ew == 0 && lane == 0 && s_chain[0] != steps.drop) atomicAdd(steps.done + (inst - i0), 1);
+    }
     }
 }
 
@@ -791,31 +966,63 @@ EncodeFn get_encode(std::string* err) {
     return fn;
 }
 
-template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB, int DW>
-cudaError_t launch_tc(const TcMaps& maps, const StepList& st, const Inst* in, const InstIO* io, const int* pre,
-                      int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag, cudaStream_t s) {
+template <int PA, int PB, int NPROD, bool F16, int TBN, int MINB, int DW, bool CHAIN, class SL>
+cudaError_t launch_tc(const TcMaps& maps, const SL& st, unsigned grid, const Inst* in, const InstIO* io,
+                      const int* pre, int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag,
+                      cudaStream_t s) {
     using Cfg = TcCfg<PA, PB, NPROD, F16, TBN, MINB, DW>;
-    auto kern = k_tc_gemm<PA, PB, NPROD, F16, TBN, MINB, DW>;
+    auto kern = k_tc_gemm<PA, PB, NPROD, F16, TBN, MINB, DW, CHAIN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(tiles * st.count), Cfg::kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0,
-                                                                    sym, err_flag);
+    kern<<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag);
     return cudaGetLastError();
 }
 
-template <int PA, int PB, int NPROD, bool F16>
-cudaError_t dispatch_tbn(int tile_n, int ctas, int drain, const TcMaps& maps, const StepList& st, const Inst* in,
-                         const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles, int b0, int sym,
-                         int* err_flag, cudaStream_t s) {
+template <int PA, int PB, int NPROD, bool F16, bool CHAIN, class SL>
+cudaError_t dispatch_tbn(int tile_n, int ctas, int drain, const TcMaps& maps, const SL& st, unsigned grid,
+                         const Inst* in, const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles,
+                         int b0, int sym, int* err_flag, cudaStream_t s) {
     if (tile_n == 256)
-        return drain == 16
-                   ? launch_tc<PA, PB, NPROD, F16, 256, 1, 16>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym,
-                                                               err_flag, s)
-                   : launch_tc<PA, PB, NPROD, F16, 256, 1, 8>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym,
-                                                              err_flag, s);
+        return drain == 16 ? launch_tc<PA, PB, NPROD, F16, 256, 1, 16, CHAIN>(maps, st, grid, in, io, pre, i0, i1,
+                                                                               tile0, tiles, b0, sym, err_flag, s)
+                           : launch_tc<PA, PB, NPROD, F16, 256, 1, 8, CHAIN>(maps, st, grid, in, io, pre, i0, i1,
+                                                                              tile0, tiles, b0, sym, err_flag, s);
     if (ctas == 2)
-        return launch_tc<PA, PB, NPROD, F16, 128, 2, 8>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
-    return launch_tc<PA, PB, NPROD, F16, 128, 1, 8>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+        return launch_tc<PA, PB, NPROD, F16, 128, 2, 8, CHAIN>(maps, st, grid, in, io, pre, i0, i1, tile0, tiles, b0,
+                                                               sym, err_flag, s);
+    return launch_tc<PA, PB, NPROD, F16, 128, 1, 8, CHAIN>(maps, st, grid, in, io, pre, i0, i1, tile0, tiles, b0, sym,
+                                                           err_flag, s);
+}
+
+template <bool CHAIN, class SL>
+cudaError_t dispatch_prec(int prec, int tile_n, int ctas, int drain, const TcMaps& maps, const SL& st, unsigned grid,
+                          const Inst* in, const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles,
+                          int b0, int sym, int* err_flag, cudaStream_t s) {
+    switch (prec) {
+        case FO_PREC_BF16X3:
+            return dispatch_tbn<3, 3, 6, false, CHAIN>(tile_n, ctas, drain, maps, st, grid, in, io, pre, i0, i1,
+                                                       tile0, tiles, b0, sym, err_flag, s);
+        case FO_PREC_FP16X2:
+            return dispatch_tbn<2, 2, 3, true, CHAIN>(tile_n, ctas, drain, maps, st, grid, in, io, pre, i0, i1,
+                                                      tile0, tiles, b0, sym, err_flag, s);
+        case FO_PREC_BF16X1:
+            return dispatch_tbn<1, 1, 1, false, CHAIN>(tile_n, ctas, drain, maps, st, grid, in, io, pre, i0, i1,
+                                                       tile0, tiles, b0, sym, err_flag, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool tile_config_ok(int prec, int tile_n, int ctas, int drain) {
+    return tc_planes(prec) != 0 && (tile_n == 128 || tile_n == 256) && (ctas == 1 || ctas == 2) &&
+           !(ctas == 2 && tile_n != 128) && (drain == 8 || drain == 16) && !(drain == 16 && tile_n != 256);
+}
+
+void copy_maps(TcMaps& tm, const void* maps, int nb) {
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+    for (int b = 0; b < nb; ++b) {
+        std::memcpy(&tm.m[b], static_cast<const char*>(maps) + 256 * (size_t)b, sizeof(CUtensorMap));
+        std::memcpy(&tm.mn[b], static_cast<const char*>(maps) + 256 * (size_t)b + 128, sizeof(CUtensorMap));
+    }
 }
 
 }  // namespace
@@ -861,31 +1068,67 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
 cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in,
                     const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
                     int nb, int* err_flag, cudaStream_t s, std::string* err, int sym) {
-    if (tc_planes(prec) == 0 || (tile_n != 128 && tile_n != 256) || (ctas != 1 && ctas != 2) ||
-        (ctas == 2 && tile_n != 128) || (drain != 8 && drain != 16) || (drain == 16 && tile_n != 256) || nb < 1 ||
-        nb > kMaxBuckets || !err_flag || nsteps < 1 || nsteps > kMaxSteps) {
+    if (!tile_config_ok(prec, tile_n, ctas, drain) || nb < 1 || nb > kMaxBuckets || !err_flag || nsteps < 1 ||
+        nsteps > kMaxSteps) {
         if (err) *err = "tc_gemm: unsupported precision, tile or bucket count";
         return cudaErrorInvalidValue;
     }
     if (tiles <= 0) return cudaSuccess;
-    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
     TcMaps tm;
-    for (int b = 0; b < nb; ++b) {
-        std::memcpy(&tm.m[b], static_cast<const char*>(maps) + 256 * (size_t)b, sizeof(CUtensorMap));
-        std::memcpy(&tm.mn[b], static_cast<const char*>(maps) + 256 * (size_t)b + 128, sizeof(CUtensorMap));
-    }
+    copy_maps(tm, maps, nb);
     StepList st;
     for (int q = 0; q < nsteps; ++q) st.s[q] = steps[q];
     st.count = nsteps;
-    switch (prec) {
-        case FO_PREC_BF16X3:
-            return dispatch_tbn<3, 3, 6, false>(tile_n, ctas, drain, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
-        case FO_PREC_FP16X2:
-            return dispatch_tbn<2, 2, 3, true>(tile_n, ctas, drain, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
-        case FO_PREC_BF16X1:
-            return dispatch_tbn<1, 1, 1, false>(tile_n, ctas, drain, tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
-        default: return cudaErrorInvalidValue;
+    return dispatch_prec<false>(prec, tile_n, ctas, drain, tm, st, (unsigned)(tiles * nsteps), in, io, pre, i0, i1,
+                                tile0, tiles, b0, sym, err_flag, s);
+}
+
+cudaError_t tc_chain(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in,
+                     const InstIO* io, const int* pre_dev, const int* pre_host, int i0, int i1, const void* maps,
+                     int b0, int nb, int* err_flag, int* counters, int win_tiles, cudaStream_t s, std::string* err,
+                     int sym) {
+    if (!tile_config_ok(prec, tile_n, ctas, drain) || nb < 1 || nb > kMaxBuckets || !err_flag || !counters ||
+        nsteps < 1 || nsteps > kMaxChain || sym == 0 || i1 <= i0) {
+        if (err) *err = "tc_chain: unsupported precision, tile, bucket or step count";
+        return cudaErrorInvalidValue;
     }
+    const int total = pre_host[i1] - pre_host[i0];
+    if (total <= 0) return cudaSuccess;
+    // the chain's tickets: windows of consecutive instances holding at least win_tiles tiles
+    // per step (the last window takes the rest), each window step-major
+    thread_local ChainList cl;   // large (steps, windows): the launch copies it
+    std::memset(&cl, 0, sizeof(cl));
+    for (int q = 0; q < nsteps; ++q) cl.s[q] = steps[q];
+    cl.count = nsteps;
+    int nw = 0, base = 0, j = i0;
+    while (j < i1) {
+        int k = j + 1;
+        if (win_tiles > 0)
+            while (k < i1 && pre_host[k] - pre_host[j] < win_tiles) ++k;
+        else
+            k = i1;
+        if (nw == kMaxWin - 1) k = i1;   // the window table is full: the rest in one window
+        cl.win_base[nw] = base;
+        cl.win_i0[nw] = j;
+        base += nsteps * (pre_host[k] - pre_host[j]);
+        ++nw;
+        j = k;
+    }
+    cl.win_base[nw] = base;
+    cl.win_i0[nw] = i1;
+    cl.nwin = nw;
+    cl.ticket = counters;
+    cl.done = counters + 1;
+    // FERMI_CHAIN_DROP_SIGNAL=t: the tile of ticket t does not count itself done, so the tiles
+    // waiting on it run out their bounded wait (tests of the timeout path; no fault involved)
+    const char* drop = getenv("FERMI_CHAIN_DROP_SIGNAL");
+    cl.drop = drop ? atoi(drop) : -1;
+    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(int) * (size_t)(1 + i1 - i0), s);
+    if (e != cudaSuccess) return e;
+    TcMaps tm;
+    copy_maps(tm, maps, nb);
+    return dispatch_prec<true>(prec, tile_n, ctas, drain, tm, cl, (unsigned)base, in, io, pre_dev, i0, i1, 0, 0, b0,
+                               sym, err_flag, s);
 }
 
 }  // namespace fo

@@ -36,11 +36,15 @@ struct DevResult {
     int32_t learned_ok;   // learned mu accepted
     int32_t active;       // 0: every kernel skips this instance
     int32_t evals;        // evaluations of P (learned mode)
+    int32_t fixed;        // the trace correction was applied
     double mu_lo, mu_hi;  // final bracket of the mu search
     double mu0;           // learned proposal (learned mode)
     double mu_prev, tr_prev;  // previous evaluation (learned mode secant)
     double order;         // learned expansion order (learned mode)
     double kt_eff;        // effective temperature of the truncated expansion (learned mode)
+    double trace_raw;     // tr P as the expansion produced it, before the trace correction
+    double gamma;         // trace correction P += gamma (P - P^2) (0 unless fixed)
+    double proj;          // residual removed by the trace projection, per diagonal entry
 };
 
 // Per-instance descriptor, written once per plan. slots: the instance's slot region,
@@ -96,9 +100,14 @@ struct Step {
     int32_t fp16;
     int32_t lower_master;      // symmetric mode: also write the float32 master below the
                                // diagonal (the solver's slots keep it above the diagonal only)
+    int32_t fix64;             // with out64: P <- P + gamma (P - alpha A B^T) in float64, P the
+                               // instance's float64 P (read and rewritten), gamma = res->gamma
     float alpha, beta, shift;  // float32 path; alpha includes the fp16 plane scales
     float plane_scale;
     double alpha64, beta64, shift64;
+    double* part;              // with out64: (tr, ||.||_F^2) partials of the float64 result per
+                               // 128 x 128 block on and above the diagonal, 2 doubles per block
+    const int* part_pre;       // block prefix per instance (the 128-wide tile work list)
     int* dbg;                  // self-check record (null unless built with FO_SELF_CHECK)
 };
 
@@ -108,6 +117,26 @@ constexpr int kMaxSteps = 16;
 struct StepList {
     Step s[kMaxSteps];
     int32_t count;
+};
+
+// A chain of dependent products of the whole batch in one launch (the baby steps, the giant
+// steps or the Clenshaw recurrence: step s reads what step s - 1 wrote). Every CTA takes a
+// ticket from `ticket` when it starts; tickets run window by window (consecutive instances),
+// within a window step by step, within a step tile by tile, so a tile's dependencies always
+// hold smaller tickets, taken by CTAs that are already running. A tile of step s waits until
+// `done[instance]` counts s x (tiles per step of that instance), and adds one when its stores
+// are complete. Both counters are zeroed before the launch.
+constexpr int kMaxChain = 128;
+constexpr int kMaxWin = 64;
+struct ChainList {
+    Step s[kMaxChain];
+    int32_t count;                 // steps
+    int32_t nwin;                  // windows
+    int32_t win_base[kMaxWin + 1]; // first ticket of window w; win_base[nwin] = all tickets
+    int32_t win_i0[kMaxWin + 1];   // first instance of window w; win_i0[nwin] = end instance
+    int* ticket;
+    int* done;
+    int32_t drop;                  // a ticket whose tile does not signal (timeout tests); -1: none
 };
 
 // The block-to-instance map of a grouped launch: pre[j] = blocks of instances < j.
@@ -237,6 +266,13 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
 // tau_0 .. tau_{n_terms-1} from the traces and the Frobenius products.
 cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, cudaStream_t s);
 cudaError_t launch_trace_frob(const Inst* in, const InstIO* io, Work wr, double* part, cudaStream_t s);
+// tr P and ||P||_F^2 of every instance from the per-block partials of its float64-output
+// product (prefix `pre` of the 128 x 128 blocks on and above the diagonal, batch + 1 entries). mode 0: the result's trace; mode 1: the
+// trace before the correction and the correction's gamma = (N_e - tr P)/(tr P - ||P||_F^2)
+// (every instance without a failed stage is made active again); mode 2: the trace after the
+// correction, whose float64 residual is then removed by the trace projection of P's diagonal.
+cudaError_t launch_tile_trace(const Inst* in, const InstIO* io, int batch, const int* pre, const double* part,
+                              int mode, cudaStream_t s);
 cudaError_t launch_copy_out(const Inst* in, const InstIO* io, Work we, const Shape& sh, cudaStream_t s);
 // Standalone packing of a float32 matrix into slot `slot` (fo_recurrence_product).
 cudaError_t launch_pack_f32(const float* A, int64_t n, int64_t lda, char* slot, int64_t np, int planes,
@@ -326,6 +362,13 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
 cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in, const InstIO* io,
                     const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
                     int nb, int* err_flag, cudaStream_t s, std::string* err, int sym = 1);
+// A chain of dependent symmetric products (ChainList) over instances [i0, i1) in one launch,
+// windows of consecutive instances holding at least `win_tiles` tiles per step each (0: one
+// window). counters: 1 + (i1 - i0) ints of device scratch, zeroed here on `s`.
+cudaError_t tc_chain(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in,
+                     const InstIO* io, const int* pre_dev, const int* pre_host, int i0, int i1, const void* maps,
+                     int b0, int nb, int* err_flag, int* counters, int win_tiles, cudaStream_t s, std::string* err,
+                     int sym);
 // Tiles of the full (non-symmetric) product.
 inline int64_t tc_tiles_full(int64_t np, int tile_n) { return (np / 128) * ((np + tile_n - 1) / tile_n); }
 

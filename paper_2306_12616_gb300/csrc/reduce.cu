@@ -68,6 +68,8 @@ __global__ void k_set_io(const IoChunk p, InstIO* d_io, const Inst* insts) {
     r->mu0 = r->mu_prev = r->tr_prev = 0.0;
     r->order = 0.0;
     r->kt_eff = 0.0;
+    r->trace_raw = r->gamma = r->proj = 0.0;
+    r->fixed = 0;
 }
 
 // ------------------------------------------------------------------ Gershgorin bounds
@@ -648,6 +650,91 @@ __global__ void k_trace_frob_final(const Inst* __restrict__ insts, Work we, cons
     if (threadIdx.x == 0) {
         r->trace = tr;
         r->frob2 = fr;
+        r->trace_raw = tr;
+        r->gamma = 0.0;
+        r->proj = 0.0;
+    }
+}
+
+// Trace of P from the partials of its float64-output product, one per 128 x 128 block on and
+// above the diagonal; one warp per instance, lane l sums blocks l, l + 32, ... in order, then a
+// fixed shuffle tree (the same bits for every tile configuration of the product).
+//  mode 0: tr P and ||P||_F^2 of the result (no correction).
+//  mode 1: before the trace correction. The split products leave tr P off N_e by their
+//    rounding (float32 masters: ~1e-8 N). The correction is the first-order shift of mu
+//    that restores tr P = N_e: d f / d mu = f (1 - f) / kT for the Fermi function, so
+//    P(mu + dmu) ~ P + gamma (P - P^2) with gamma = dmu / kT, and tr(P - P^2) = tr P -
+//    ||P||_F^2 for symmetric P gives gamma = (N_e - tr P) / (tr P - ||P||_F^2). The
+//    correction is a rounding correction, not a search for mu: it is applied only where it
+//    moves P by less than the split forms' 1e-6 bar. With the eigenvalues of P in [0, 1],
+//    ||P - P^2||_F <= sqrt(t) / 2 for t = tr(P - P^2), so ||gamma (P - P^2)||_F / sqrt(n) <=
+//    |N_e - tr P| / (2 sqrt(t n)); where that bound exceeds 1e-6 (a learned mu accepted at a
+//    loose trace tolerance), or |gamma| > 1/4, gamma = 0 and P keeps its trace. Every
+//    instance without a failed stage is made active again (learned mu parks the accepted
+//    ones) for the correcting product.
+//  mode 2: after the correcting product, whose own split-product rounding leaves a float64
+//    residual r = N_e - tr P (|gamma| times the rounding of tr P^2). The matrix nearest to P
+//    in the Frobenius norm with trace N_e is P + (r / n) I: the warp adds r / n to the n
+//    diagonal entries when the correction was applied and |r| <= 1e-4 max(1, N_e) (a larger
+//    residual is left in place for the caller to see) and sums the new diagonal for the
+//    reported trace.
+__global__ void k_tile_trace(const Inst* __restrict__ insts, const InstIO* __restrict__ io, const int* pre,
+                             const double* part, int mode) {
+    const int i = blockIdx.x;
+    DevResult* r = insts[i].res;
+    if (mode == 1 ? r->status != FO_OK : !r->active) return;
+    double tr = 0.0, fr = 0.0;
+    for (int b = pre[i] + (int)threadIdx.x; b < pre[i + 1]; b += 32) {
+        tr += part[2 * (int64_t)b];
+        fr += part[2 * (int64_t)b + 1];
+    }
+    tr = warp_sum(tr);
+    fr = warp_sum(fr);
+    if (mode == 0) {
+        if (threadIdx.x == 0) {
+            r->trace = tr;
+            r->frob2 = fr;
+            r->trace_raw = tr;
+            r->gamma = 0.0;
+            r->proj = 0.0;
+        }
+        return;
+    }
+    const double n_e = io[i].n_e;
+    if (mode == 1) {
+        if (threadIdx.x == 0) {
+            const double t = tr - fr;
+            double g = (n_e - tr) / t;
+            const double move = fabs(n_e - tr) / (2.0 * sqrt(t * (double)insts[i].n));
+            const bool ok = t > 0.0 && isfinite(g) && fabs(g) <= 0.25 && move <= 1e-6;
+            if (!ok) g = 0.0;
+            r->trace_raw = tr;
+            r->trace = tr;
+            r->frob2 = fr;
+            r->gamma = g;
+            r->fixed = ok ? 1 : 0;
+            r->proj = 0.0;
+            r->active = 1;
+        }
+        return;
+    }
+    const int64_t n = insts[i].n, ldp = io[i].ldp;
+    double* P = io[i].P;
+    const double res = n_e - tr;
+    double d = 0.0;
+    if (r->fixed && fabs(res) <= 1e-4 * fmax(1.0, n_e) && isfinite(res)) d = res / (double)n;
+    double t2 = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += 32) {
+        const double v = P[j * ldp + j] + d;
+        if (d != 0.0) P[j * ldp + j] = v;
+        t2 += v;
+    }
+    t2 = warp_sum(t2);
+    if (threadIdx.x == 0) {
+        // ||P + d I||^2 = ||P||^2 + 2 d tr P + n d^2
+        r->frob2 = fr + 2.0 * d * tr + (double)n * d * d;
+        r->trace = t2;
+        r->proj = d;
     }
 }
 
@@ -802,6 +889,12 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
 
 cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, cudaStream_t s) {
     k_assemble_moments<<<batch, 32, 0, s>>>(in, sh.k, sh.m, sh.n_terms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_trace(const Inst* in, const InstIO* io, int batch, const int* pre, const double* part,
+                              int mode, cudaStream_t s) {
+    k_tile_trace<<<batch, 32, 0, s>>>(in, io, pre, part, mode);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,31 @@ def load_golden(name):
     return np.loadtxt(os.path.join(GOLDEN, name), comments="#", ndmin=2)
 
 
+_TB_EIG = {}
+
+
+def tb_eig(n):
+    """The tight-binding H of the bench sizes (seed 2000 + N) with its float64
+    eigendecomposition (numpy/LAPACK), computed once per process and shared by the tests."""
+    import numpy as np
+    import synth
+    if n not in _TB_EIG:
+        h = synth.tight_binding(n, 2000 + n)
+        w, u = np.linalg.eigh(h)
+        _TB_EIG[n] = (h, w, u)
+    return _TB_EIG[n]
+
+
+def poly_columns(n, cols, c, ea, eb):
+    """Columns `cols` of the oracle polynomial sum_j c_j T_j(X) of tb_eig(n)'s H on [ea, eb],
+    from the eigendecomposition: U p(x(Lambda)) U^T e_j."""
+    import numpy as np
+    import oracle as O
+    _, w, u = tb_eig(n)
+    pw = np.polynomial.chebyshev.chebval(O.spectrum_scaled(w, ea, eb), c)
+    return u @ (pw[:, None] * u[cols].T)
+
+
 def header_symbols():
     """Function names declared in include/fermi.h."""
     import re

@@ -47,7 +47,7 @@ def test_density_matrix_at_lanczos_bounds(solver, prec, tol):
     c = O.chebyshev_coeffs(0.1, r["mu"], r["emin"], r["emax"], 400)
     ref = O.poly_eig(h, c, r["emin"], r["emax"])
     assert np.linalg.norm(p.cpu().numpy() - ref) / math.sqrt(n) <= tol
-    assert abs(r["trace"] - n / 2) <= (2e-6 * n if prec != "fp64" else 1e-8)
+    assert abs(r["trace"] - n / 2) <= 1e-8
 
 
 def test_tighter_bounds_resolve_the_fermi_function(solver):

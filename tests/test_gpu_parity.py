@@ -137,7 +137,7 @@ def test_fp64_random_config_bisection(solver):
     assert res["n_gemm"] == 15 + 14 + 15
 
 
-@pytest.mark.parametrize("n", [100, 1000])
+@pytest.mark.parametrize("n", [100, 1000, 2000])
 def test_fp64_tight_binding_bisection(solver, n):
     h = synth.tight_binding(n, 2000 + n)
     prm = solver.params(400, 0.1, precision="fp64", mu_mode="bisect")
@@ -150,6 +150,27 @@ def test_fp64_tight_binding_bisection(solver, n):
                            route="eig").p
     assert rel_frob(p, ref) <= 1e-10
     assert abs(np.trace(p) - n / 2) <= 1e-8
+
+
+def test_fp64_full_size_sampled_columns(solver):
+    """The float64 path at the largest bench size (N = 5000, 400 terms): sampled columns of P
+    against the oracle polynomial at the GPU's bounds and mu (from the oracle's
+    eigendecomposition), mu against the oracle's bisection on the eigenvalues, the trace."""
+    from conftest import poly_columns, tb_eig
+    n = 5000
+    h, w, _ = tb_eig(n)
+    p, res = solver.density_matrix(to_dev(h), n / 2, solver.params(400, 0.1, precision="fp64", mu_mode="bisect"))
+    assert res["status"] == 0 and (res["k"], res["m"]) == (20, 20)
+    cols = np.arange(7, n, n // 8)
+    c = O.chebyshev_coeffs(0.1, res["mu"], res["emin"], res["emax"], 400)
+    ref = poly_columns(n, cols, c, res["emin"], res["emax"])
+    err = math.sqrt(np.mean(np.sum((p[:, cols].cpu().numpy() - ref) ** 2, axis=0)))
+    assert err <= 1e-10, err
+    assert abs(res["trace"] - n / 2) <= 1e-8
+    ga, gb = O.gershgorin_bounds(h)
+    taus = O.moments_eig(O.spectrum_scaled(w, ga, gb), 400)
+    br = O.bisect_mu(lambda mu: O.poly_trace(mu, taus, 0.1, ga, gb, 400), n / 2, ga, gb, 0.1)
+    assert br.status == "ok" and abs(res["mu"] - br.mu) <= 1e-9
 
 
 def test_fp64_host_buffers(solver):
@@ -191,13 +212,20 @@ def test_forced_baby_step_count(solver, prec, tol, n_terms, k):
     (k = 8 at 160 terms: 19 giants x 7 babies in the Frobenius products, 5 x 4 tiles; at 400
     terms: m = 50, 49 x 7 pairs over two launches of 4 x 4 tiles, and two contraction launches
     for R_0..R_49), not the polynomial: P stays the oracle's expansion at the reported mu.
-    The float64 form pins those paths (measured ~1e-14). The split form's bar is 2e-6 here, not
-    1e-6: with k below sqrt(n_terms) the Clenshaw chain in Y = T_k runs m = 20 and 50 steps
-    instead of 13 and 20, and its float32 rounding grows with m (measured 1.05e-6, 1.36e-6)."""
+    The float64 form pins those paths (measured ~1e-14). In a split form, k below sqrt(n_terms)
+    makes the Clenshaw chain in Y = T_k run m = 20 and 50 steps instead of 13 and 20, and its
+    float32 rounding grows with m (measured 1.05e-6, 1.36e-6): beyond the 1e-6 bar, so the
+    library refuses it unless FO_FLAG_ALLOW_LOOSE asks for it; then it is checked at 2e-6."""
     n = 600
     h = synth.tight_binding(n, 4242)
+    flags = 0
+    if prec != "fp64":
+        with pytest.raises(fo.FermiError) as e:
+            solver.density_matrix(to_dev(h), n / 2, solver.params(n_terms, 0.1, precision=prec, k=k))
+        assert e.value.status == fo.FO_ERR_UNSUPPORTED
+        flags = fo.FO_FLAG_ALLOW_LOOSE
     p, r = solver.density_matrix(to_dev(h), n / 2, solver.params(n_terms, 0.1, precision=prec, mu_mode="bisect",
-                                                                 k=k))
+                                                                 k=k, flags=flags))
     assert r["status"] == 0 and (r["k"], r["m"]) == (k, -(-n_terms // k))
     c = O.chebyshev_coeffs(0.1, r["mu"], r["emin"], r["emax"], n_terms)
     ref = O.poly_eig(h, c, r["emin"], r["emax"])

@@ -14,7 +14,7 @@ import torch
 
 import oracle as O
 import synth
-from paper_2306_12616_gb300 import FO_FLAG_POWER_BASIS
+from paper_2306_12616_gb300 import FO_FLAG_ALLOW_LOOSE, FO_FLAG_POWER_BASIS
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -25,6 +25,9 @@ def to_dev(h):
 
 
 def run(solver, h, n_terms, kT, prec, flags, mu=0.0):
+    # the split forms' power basis is beyond their 1e-6 bar: it runs on request only
+    if prec != "fp64" and flags:
+        flags |= FO_FLAG_ALLOW_LOOSE
     prm = solver.params(n_terms, kT, precision=prec, mu_mode="fixed", mu=mu, flags=flags)
     p, r = solver.density_matrix(to_dev(h), 0.0, prm)
     return p.cpu().numpy(), r
@@ -75,8 +78,13 @@ def test_power_basis_instability_grows_with_m(solver):
     assert p_bf16[2] > 100 * rows[2][1][("bf16x3", 0)]
 
 
-def test_power_basis_rejects_fp16x2(solver):
+def test_power_basis_rejects_fp16x2_and_needs_the_request(solver):
+    import paper_2306_12616_gb300 as fo
     h = to_dev(synth.random_symmetric(64, 1))
     with pytest.raises(Exception):
         solver.density_matrix(h, 0.0, solver.params(64, 0.1, precision="fp16x2", mu_mode="fixed",
+                                                     flags=FO_FLAG_POWER_BASIS | FO_FLAG_ALLOW_LOOSE))
+    with pytest.raises(fo.FermiError) as e:
+        solver.density_matrix(h, 0.0, solver.params(64, 0.1, precision="bf16x3", mu_mode="fixed",
                                                      flags=FO_FLAG_POWER_BASIS))
+    assert e.value.status == fo.FO_ERR_UNSUPPORTED

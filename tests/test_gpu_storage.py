@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import synth
-from paper_2306_12616_gb300 import FO_FLAG_POWER_BASIS, FO_FLAG_STAGED
+from paper_2306_12616_gb300 import FO_FLAG_ALLOW_LOOSE, FO_FLAG_POWER_BASIS, FO_FLAG_STAGED
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -20,8 +20,8 @@ DEV = "cuda:0"
 CASES = [
     ("fixed", dict(mu_mode="fixed", mu=-6.0)),
     ("bisect", dict(mu_mode="bisect")),
-    ("staged", dict(mu_mode="bisect", flags=FO_FLAG_STAGED)),
-    ("power", dict(mu_mode="bisect", flags=FO_FLAG_POWER_BASIS)),
+    ("staged", dict(mu_mode="bisect", flags=FO_FLAG_STAGED | FO_FLAG_ALLOW_LOOSE)),
+    ("power", dict(mu_mode="bisect", flags=FO_FLAG_POWER_BASIS | FO_FLAG_ALLOW_LOOSE)),
     ("lanczos", dict(mu_mode="bisect", lanczos_steps=16)),
     ("learned", dict(mu_mode="learned")),
 ]
