@@ -137,6 +137,11 @@ typedef struct {
                                  steps, the Clenshaw recurrence) as one launch whose tiles wait,
                                  per instance, for the previous step's tiles (bounded waits; a
                                  timeout fails the call with FO_ERR_DEVICE_TIMEOUT). Same bits */
+    int32_t tile_persist;     /* split forms: 0 or 1 = one CTA per tile (default), 2 = the
+                                 persistent product kernel (128-wide tiles, one CTA per SM walking
+                                 the tiles; separate epilogue warps finish a tile while the next
+                                 one's products run; with tile_n = 0 its two plane storages are
+                                 autotuned). Same bits; measured slower than the default */
     int32_t chain_window;     /* chain launches: tiles run window by window, a window being
                                  consecutive instances (largest first) with at least this many
                                  tiles per step; 0 = one window (step by step over the batch) */
@@ -165,6 +170,7 @@ typedef struct {
     double  trace_gamma;      /* gamma of the trace correction P + gamma (P - P^2) (0: none) */
     double  trace_proj;       /* float64 residual removed per diagonal entry by the trace
                                  projection after the correction (0: none) */
+    int32_t tile_persist;     /* product kernel used: 2 persistent, 1 one CTA per tile, 0 FP64 */
 } fo_result;
 
 /* Stages of a density-matrix call, as recorded by the profiler. */

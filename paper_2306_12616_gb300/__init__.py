@@ -66,7 +66,7 @@ class FoParams(ctypes.Structure):
         ("flags", ctypes.c_uint32), ("tr_tol", ctypes.c_double), ("max_newton", ctypes.c_int32),
         ("tile_n", ctypes.c_int32), ("tile_ctas", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
         ("tile_drain", ctypes.c_int32), ("tile_store", ctypes.c_int32), ("chain", ctypes.c_int32),
-        ("chain_window", ctypes.c_int32),
+        ("tile_persist", ctypes.c_int32), ("chain_window", ctypes.c_int32),
     ]
 
 
@@ -80,6 +80,7 @@ class FoResult(ctypes.Structure):
         ("tile_ctas", ctypes.c_int32), ("evals", ctypes.c_int32), ("order", ctypes.c_int32),
         ("tile_drain", ctypes.c_int32), ("tile_store", ctypes.c_int32),
         ("trace_raw", ctypes.c_double), ("trace_gamma", ctypes.c_double), ("trace_proj", ctypes.c_double),
+        ("tile_persist", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -336,7 +337,8 @@ class Solver:
                mu_mode: str | int = "bisect", k: int = 0, bounds=None, n_quad: int = 0,
                max_bisect: int = 0, flags: int = 0, tile_n: int = 0, tile_ctas: int = 0,
                tr_tol: float = 0.0, max_newton: int = 0, lanczos_steps: int = 0,
-               tile_drain: int = 0, tile_store: int = 0, chain: int = 0, chain_window: int = 0) -> FoParams:
+               tile_drain: int = 0, tile_store: int = 0, chain: int = 0, chain_window: int = 0,
+               tile_persist: int = 0) -> FoParams:
         p = FoParams()
         p.n_terms, p.k, p.kT, p.mu = n_terms, k, kT, mu
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
@@ -346,7 +348,7 @@ class Solver:
         p.n_quad, p.max_bisect, p.flags = n_quad, max_bisect, flags
         p.tile_n, p.tile_ctas, p.tr_tol, p.max_newton = tile_n, tile_ctas, tr_tol, max_newton
         p.lanczos_steps, p.tile_drain, p.tile_store = lanczos_steps, tile_drain, tile_store
-        p.chain, p.chain_window = chain, chain_window
+        p.chain, p.chain_window, p.tile_persist = chain, chain_window, tile_persist
         return p
 
     def spectral_bounds(self, h, stream=None):

@@ -948,6 +948,523 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     }
 }
 
+// ------------------------------------------------------------------ persistent kernel
+// One CTA per SM walks the launch's tiles (t = blockIdx.x, + gridDim.x, ...; the work list is
+// ordered largest first, so every CTA gets a similar mix and the last tiles are the
+// smallest). 128-wide tiles. Roles:
+//   warp 0 lane 0   TMA producer, k-blocks of successive tiles into one ring;
+//   warp 1 lane 0   MMA issuer into two TMEM accumulators (ping-pong per k-block);
+//   DW drain warps  add every finished k-block to float32 registers; at the end of a tile
+//                   they write alpha * sum into a result buffer in shared memory and move
+//                   on to the next tile's k-blocks;
+//   EW epilogue warps take the result buffer: the same row and mirror passes as k_tc_gemm
+//                   (C, D, shift, plane split, mirrored stores, float64 P, trace
+//                   partials), then hand the buffer back.
+// So the epilogue of tile i runs while the MMAs of tile i + 1 do (the one-tile-per-CTA
+// kernel leaves the tensor pipe idle during its epilogue), and barrier set-up, TMEM
+// allocation and the first TMA latency are paid once per CTA instead of once per tile.
+// Barrier phases follow the CTA's running counts of k-blocks and tiles. Every wait is
+// bounded as in k_tc_gemm; a CTA that gives up raises the error flag, lets every role leave
+// its loop, waits (bounded) for its copies in flight and frees its TMEM.
+template <int PA, int PB, int NPROD, bool F16, int DW, int EW>
+struct PcCfg {
+    static constexpr int TBN = 128;
+    static constexpr int kThreads = 32 * (2 + DW + EW);
+    static constexpr int kCols = TBN / (DW / 4);   // accumulator columns per drain warp
+    static constexpr int kStageBytes = PA * kBoxBytes + PB * kBoxBytes;
+    static constexpr int kLD = TBN + 1;
+    static constexpr int kTileBytes = kBM * kLD * 4;
+    static constexpr int kRowPartBytes = kBM * 2 * 8;
+    static constexpr int kBarBytes = 512;
+    static constexpr int kFixed = kTileBytes + kRowPartBytes + kBarBytes + 1024 /*align*/;
+    static constexpr int kStagesRaw = (232448 - 64 - kFixed) / kStageBytes;
+    static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
+    static constexpr int kSmem = kStages * kStageBytes + kFixed;
+    static constexpr int kTmemCols = 2 * TBN;
+    static_assert(kStages >= 2, "persistent kernel: too few ring stages");
+    static_assert(kSmem <= 232448 - 64, "persistent kernel: shared memory budget exceeded");
+    static_assert(kBM % EW == 0 && (kBM / EW) * (TBN / 64) % 8 == 0, "epilogue warp split");
+};
+
+// The tile of work item t of a launch (steps x tiles), as every role of the persistent
+// kernel derives it.
+struct PTile {
+    int sidx, inst, m0, n0, nk, tile_k;
+    bool active;
+};
+__device__ __forceinline__ void persist_tile(int t, int tiles, int tile0, const int* __restrict__ pre, int i0,
+                                             int i1, const Inst* __restrict__ insts, int sym, PTile& d) {
+    d.sidx = t / tiles;
+    const int gt = tile0 + t - d.sidx * tiles;
+    d.inst = find_inst(pre, i0, i1, gt);
+    const Inst& in = insts[d.inst];
+    d.active = in.res->active != 0;
+    const int np = (int)in.np;
+    int I, J;
+    tile_of(gt - __ldg(pre + d.inst), np / kBM, np / kBM, kBM, sym, I, J);
+    d.m0 = I * kBM;
+    d.n0 = J * kBM;
+    d.nk = (int)((in.n + kBK - 1) / kBK);
+    const int64_t nrem = in.n - d.n0;
+    d.tile_k = nrem >= kBM ? kBM : (int)(((nrem + 31) / 32) * 32);
+}
+
+// The epilogue of one 128 x 128 tile of the persistent kernel, run by its EW epilogue warps
+// (named barrier 1) from the result buffer `tile` (alpha A B^T, leading dimension LD): the
+// same row and mirror passes as k_tc_gemm -- beta C + D + shift, float32 master and 16-bit
+// planes on and above the diagonal, planes (and, with lower_master, masters) of the mirrored
+// half, the caller's float64 P (out64; with fix64 the trace correction), and the trace
+// partials of a float64-output product.
+template <bool F16, int EW, int TBN, int LD>
+__device__ __forceinline__ void persist_epilogue(const Step& st, const Inst* __restrict__ insts,
+                                                 const InstIO* __restrict__ io, int inst, int m0, int n0, int sym,
+                                                 bool ub, float* tile, double (*rowpart)[2], int ew, int lane) {
+    const Inst& in = insts[inst];
+    const int64_t n_real = in.n;
+    const int64_t np = in.np;
+    char* const base = in.slots;
+    const int64_t sb = in.slot_bytes;
+    const int64_t ld = np;
+    const int64_t pstride = np * np;
+    float* out_x = st.out >= 0 ? reinterpret_cast<float*>(base + sb * st.out) : nullptr;
+    uint16_t* out_p = st.out >= 0 ? reinterpret_cast<uint16_t*>(base + sb * st.out + 4 * pstride) : nullptr;
+    const float* Cm = st.c >= 0 ? reinterpret_cast<const float*>(base + sb * st.c) : nullptr;
+    const float* Dm = st.d >= 0 ? reinterpret_cast<const float*>(base + sb * st.d) : nullptr;
+    double* out64 = st.out64 ? io[inst].P : nullptr;
+    const int64_t ldo = io[inst].ldp;
+    const bool fix = out64 && st.fix64;
+    const double gam = fix ? in.res->gamma : 0.0;
+    const int planes = st.planes;
+    auto store64 = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool upper, double& ta,
+                       double& fa) {
+        ta = 0.0;
+        fa = 0.0;
+        if (grow >= n_real) return;
+        double* dst = out64 + grow * ldo + gcol;
+        const bool e0 = w0 && gcol < n_real, e1 = w1 && gcol + 1 < n_real;
+        double x0 = (double)v0, x1 = (double)v1;
+        if (fix) {
+            if (e0) { const double p = dst[0]; x0 = fma(gam, p - x0, p); }
+            if (e1) { const double p = dst[1]; x1 = fma(gam, p - x1, p); }
+        }
+        if (e0) dst[0] = x0;
+        if (e1) dst[1] = x1;
+        if (upper) {
+            if (e0) {
+                if (gcol == grow) { ta += x0; fa = fma(x0, x0, fa); }
+                else fa = fma(2.0 * x0, x0, fa);
+            }
+            if (e1) {
+                if (gcol + 1 == grow) { ta += x1; fa = fma(x1, x1, fa); }
+                else fa = fma(2.0 * x1, x1, fa);
+            }
+        }
+    };
+    auto store_slot = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool master) {
+        if (!(w0 || w1) || (!out_x && planes == 0)) return;
+        const int64_t o = grow * ld + gcol;
+        if (!FO_CHK(st.dbg, o >= 0 && o + 2 <= ld * ld, 111, grow, gcol)) return;
+        uint16_t a0 = 0, a1 = 0, a2 = 0, b0v = 0, b1v = 0, b2v = 0;
+        if (planes > 0) {
+            split3(v0, F16, st.plane_scale, a0, a1, a2);
+            split3(v1, F16, st.plane_scale, b0v, b1v, b2v);
+        }
+        if (w0 && w1) {
+            if (out_x && master) *reinterpret_cast<float2*>(out_x + o) = make_float2(v0, v1);
+            if (planes > 0) {
+                uint16_t* pl = out_p + o;
+                *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0v << 16);
+                if (planes > 1) *reinterpret_cast<uint32_t*>(pl + pstride) = (uint32_t)a1 | ((uint32_t)b1v << 16);
+                if (planes > 2)
+                    *reinterpret_cast<uint32_t*>(pl + 2 * pstride) = (uint32_t)a2 | ((uint32_t)b2v << 16);
+            }
+        } else {
+            const int e = w0 ? 0 : 1;
+            const float v = w0 ? v0 : v1;
+            if (out_x && master) out_x[o + e] = v;
+            if (planes > 0) {
+                uint16_t* pl = out_p + o + e;
+                pl[0] = w0 ? a0 : b0v;
+                if (planes > 1) pl[pstride] = w0 ? a1 : b1v;
+                if (planes > 2) pl[2 * pstride] = w0 ? a2 : b2v;
+            }
+        }
+    };
+    // instantiated for float64-output products and the others (see k_tc_gemm)
+    auto passes = [&](auto f64_tag) {
+        constexpr bool F64 = decltype(f64_tag)::value;
+        constexpr int RPW = kBM / EW;
+        constexpr int HPR = TBN / 64;
+        constexpr int NIT = RPW * HPR;
+        constexpr int G = 8;
+        static_assert(NIT % G == 0, "row-pass groups");
+        for (int q0 = 0; q0 < NIT; q0 += G) {
+            float2 cv[G], dv[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const int q = q0 + u, rr = q / HPR, h = q % HPR;
+                const int r = ew * RPW + rr, c = h * 64 + 2 * lane;
+                const int64_t o = ((int64_t)m0 + r) * ld + n0 + c;
+                cv[u] = Cm ? *reinterpret_cast<const float2*>(Cm + o) : make_float2(0.f, 0.f);
+                dv[u] = Dm ? *reinterpret_cast<const float2*>(Dm + o) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const int q = q0 + u, rr = q / HPR, h = q % HPR;
+                const int r = ew * RPW + rr, c = h * 64 + 2 * lane;
+                const int64_t grow = (int64_t)m0 + r, gcol = (int64_t)n0 + c;
+                float v0 = tile[r * LD + c], v1 = tile[r * LD + c + 1];
+                if (Cm) {
+                    v0 = fmaf(st.beta, cv[u].x, v0);
+                    v1 = fmaf(st.beta, cv[u].y, v1);
+                }
+                if (Dm) {
+                    v0 += dv[u].x;
+                    v1 += dv[u].y;
+                }
+                if (grow < n_real) {
+                    if (gcol == grow) v0 += st.shift;
+                    if (gcol + 1 == grow) v1 += st.shift;
+                }
+                tile[r * LD + c] = v0;
+                tile[r * LD + c + 1] = v1;
+                const bool w0 = !sym || gcol >= grow, w1 = !sym || gcol + 1 >= grow;
+                double ta = 0.0, fa = 0.0;
+                if constexpr (F64) store64(grow, gcol, v0, v1, w0, w1, true, ta, fa);
+                store_slot(grow, gcol, v0, v1, w0, w1, true);
+                if (F64 && st.part) {
+                    // (row, 64-column piece) sums by a fixed shuffle tree; the two pieces of
+                    // the row added in column order (the same bits as k_tc_gemm's partials)
+                    for (int o = 16; o > 0; o >>= 1) {
+                        ta += __shfl_xor_sync(0xffffffffu, ta, o);
+                        fa += __shfl_xor_sync(0xffffffffu, fa, o);
+                    }
+                    if (lane == 0) {
+                        if (h & 1) {
+                            rowpart[r][0] += ta;
+                            rowpart[r][1] += fa;
+                        } else {
+                            rowpart[r][0] = ta;
+                            rowpart[r][1] = fa;
+                        }
+                    }
+                }
+            }
+        }
+        if (F64 && st.part) {
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
+            if (ew == 0 && lane < 2) {
+                double sacc = 0.0;
+                for (int r = 0; r < kBM; ++r) sacc += rowpart[r][lane];
+                const int64_t nb = np / kBM, I = m0 / kBM, J = n0 / kBM;
+                const int64_t blk = (int64_t)st.part_pre[inst] + I * nb - I * (I - 1) / 2 + (J - I);
+                st.part[2 * blk + lane] = sacc;
+            }
+        }
+        if (!sym) return;
+        const bool lower_master = st.lower_master != 0;
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
+        // mirror pass: output row n0 + c holds tile column c for the entries with col > row
+        for (int cc = 0; cc < TBN / EW; ++cc) {
+            const int c = ew * (TBN / EW) + cc;
+            const int64_t grow = (int64_t)n0 + c;
+            const bool slot_rows = !(ub && !lower_master && grow >= (int64_t)m0 + kBM);
+            if (!slot_rows && !F64) break;
+#pragma unroll
+            for (int hh = 0; hh < kBM / 64; ++hh) {
+                const int r = hh * 64 + 2 * lane;
+                const int64_t gcol = (int64_t)m0 + r;
+                const float v0 = tile[r * LD + c], v1 = tile[(r + 1) * LD + c];
+                if constexpr (F64) {
+                    double ta, fa;
+                    store64(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, false, ta, fa);
+                }
+                if (slot_rows) store_slot(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, lower_master);
+            }
+        }
+        // (the buffer goes back through res_empty, which counts every epilogue thread)
+    };
+    if (out64) passes(std::true_type{});
+    else passes(std::false_type{});
+}
+
+template <int PA, int PB, int NPROD, bool F16, int DW, int EW>
+__global__ void __launch_bounds__(32 * (2 + DW + EW), 1)
+    k_tc_persist(const __grid_constant__ TcMaps maps, const __grid_constant__ StepList steps,
+                 const Inst* __restrict__ insts, const InstIO* __restrict__ io, const int* __restrict__ pre,
+                 int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag) {
+    using Cfg = PcCfg<PA, PB, NPROD, F16, DW, EW>;
+    constexpr int S = Cfg::kStages;
+    constexpr int NC = Cfg::kCols;
+    constexpr int TBN = Cfg::TBN;
+    constexpr int LD = Cfg::kLD;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* tile = reinterpret_cast<float*>(smem + S * Cfg::kStageBytes);
+    double (*rowpart)[2] = reinterpret_cast<double (*)[2]>(smem + S * Cfg::kStageBytes + Cfg::kTileBytes);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * Cfg::kStageBytes + Cfg::kTileBytes + Cfg::kRowPartBytes);
+    uint64_t* empty = full + S;
+    uint64_t* seg_full = empty + S;
+    uint64_t* seg_empty = seg_full + 2;
+    uint64_t* acc_full = seg_empty + 2;
+    uint64_t* res_full = acc_full + 1;
+    uint64_t* res_empty = res_full + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(res_empty + 1);
+    __shared__ int abort_flag;
+    __shared__ int s_go;   // the epilogue group's decision for its next tile
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int work = tiles * steps.count;
+    const bool ub = sym == 2;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&seg_full[b], 1);
+            mbar_init(&seg_empty[b], 32 * DW);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(res_full, 32 * DW);
+        mbar_init(res_empty, 32 * EW);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(Cfg::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    volatile int* vabort = &abort_flag;
+    auto give_up = [&]() {
+        atomicExch(&abort_flag, 1);
+        atomicExch(err_flag, 1);
+    };
+    auto stage_a = [&](int s, int p) { return smem + s * Cfg::kStageBytes + p * kBoxBytes; };
+    auto stage_b = [&](int s, int p) { return smem + s * Cfg::kStageBytes + PA * kBoxBytes + p * kBoxBytes; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            uint32_t g = 0;   // k-blocks issued by this CTA
+            auto produce = [&](auto ub_tag) {
+                constexpr bool U = decltype(ub_tag)::value;
+                for (int t = blockIdx.x; t < work; t += gridDim.x) {
+                    PTile d;
+                    persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, d);
+                    if (!d.active) continue;
+                    const Step& st = steps.s[d.sidx];
+                    const Inst& in = insts[d.inst];
+                    const CUtensorMap* map = &maps.m[in.bucket - b0];
+                    const CUtensorMap* map_mn = &maps.mn[in.bucket - b0];
+                    const int ib = in.in_bucket;
+                    for (int kb = 0; kb < d.nk; ++kb, ++g) {
+                        const int s = (int)(g % S);
+                        if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, kWaitNs, vabort)) {
+                            give_up();
+                            return;
+                        }
+                        mbar_expect_tx(&full[s], (uint32_t)((PA + PB) * kBoxBytes));
+                        const int KB = kb * kBK / kBM;
+                        const bool a_mn = U && KB < d.m0 / kBM;
+                        const bool b_mn = U && KB < d.n0 / kBM;
+#pragma unroll
+                        for (int p = 0; p < PA; ++p) {
+                            if (!a_mn) {
+                                tma_load_5d(stage_a(s, p), map, &full[s], kb * kBK, d.m0, p, st.a, ib);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < kBM / kMnBoxCols; ++q)
+                                    tma_load_5d(stage_a(s, p) + q * kMnBoxBytes, map_mn, &full[s],
+                                                d.m0 + kMnBoxCols * q, kb * kBK, p, st.a, ib);
+                            }
+                        }
+#pragma unroll
+                        for (int p = 0; p < PB; ++p) {
+                            if (!b_mn) {
+                                tma_load_5d(stage_b(s, p), map, &full[s], kb * kBK, d.n0, p, st.b, ib);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < kBM / kMnBoxCols; ++q)
+                                    tma_load_5d(stage_b(s, p) + q * kMnBoxBytes, map_mn, &full[s],
+                                                d.n0 + kMnBoxCols * q, kb * kBK, p, st.b, ib);
+                            }
+                        }
+                    }
+                    // the epilogue's C and D rows of this tile into L2 (hints, in bounds)
+                    const int np = (int)in.np;
+                    const int cd[2] = {st.c, st.d};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (cd[q] < 0) continue;
+                        const char* rows = in.slots + in.slot_bytes * cd[q] + ((int64_t)d.m0 * np + d.n0) * 4;
+                        for (int r = 0; r < kBM; ++r) prefetch_l2(rows + (int64_t)r * np * 4, (uint32_t)TBN * 4u);
+                    }
+                }
+            };
+            if (ub) produce(std::true_type{});
+            else produce(std::false_type{});
+            // before the CTA may exit: normally the MMA warp's release (commit arrivals) of the
+            // last S stages; after an abort at least the landing of the copies in flight
+            const uint32_t k0 = g > (uint32_t)S ? g - S : 0;
+            if (*vabort) {
+                for (uint32_t k = k0; k < g; ++k) mbar_wait(&full[k % S], (k / S) & 1, kDrainNs, nullptr);
+            } else {
+                for (uint32_t k = k0; k < g; ++k)
+                    if (!mbar_wait(&empty[k % S], (k / S) & 1, kWaitNs, vabort)) {
+                        give_up();
+                        break;
+                    }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: one k-block per accumulator, corrections first
+            uint32_t g = 0, h = 0;   // k-blocks consumed, accumulator uses
+            const uint64_t d_k = sdesc_sw64(smem_u32(smem)), d_mn = sdesc_mn128(smem_u32(smem));
+            auto issue = [&](auto ub_tag) {
+                constexpr bool U = decltype(ub_tag)::value;
+                for (int t = blockIdx.x; t < work; t += gridDim.x) {
+                    PTile d;
+                    persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, d);
+                    if (!d.active) continue;
+                    const uint32_t idesc0 = idesc_f16(d.tile_k, F16);
+                    for (int kb = 0; kb < d.nk; ++kb, ++g, ++h) {
+                        const int s = (int)(g % S), buf = (int)(h & 1);
+                        const int KB = kb * kBK / kBM;
+                        const bool a_mn = U && KB < d.m0 / kBM;
+                        const bool b_mn = U && KB < d.n0 / kBM;
+                        const uint64_t so = (uint64_t)s * (uint64_t)(Cfg::kStageBytes >> 4);
+                        auto adesc = [&](int p, int kk) {
+                            return a_mn ? d_mn + so + (uint64_t)((p * kBoxBytes + kk * kMnKStep) >> 4)
+                                        : d_k + so + (uint64_t)((p * kBoxBytes + kk * 32) >> 4);
+                        };
+                        auto bdesc = [&](int p, int kk) {
+                            const int off = PA * kBoxBytes + p * kBoxBytes;
+                            return b_mn ? d_mn + so + (uint64_t)((off + kk * kMnKStep) >> 4)
+                                        : d_k + so + (uint64_t)((off + kk * 32) >> 4);
+                        };
+                        if (h >= 2 && !mbar_wait(&seg_empty[buf], ((h >> 1) - 1) & 1, kWaitNs, vabort)) {
+                            give_up();
+                            return;
+                        }
+                        if (!mbar_wait(&full[s], (g / S) & 1, kWaitNs, vabort)) {
+                            give_up();
+                            return;
+                        }
+                        fence_after();
+                        const uint32_t dt = tmem + (uint32_t)(buf * TBN);
+                        const uint32_t id = idesc0 | (a_mn ? kIdescMnA : 0u) | (b_mn ? kIdescMnB : 0u);
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+#pragma unroll
+                            for (int pr = 1; pr < NPROD; ++pr)
+                                umma_f16(dt, adesc(prod_a(pr), kk), bdesc(prod_b(pr), kk), id, !(kk == 0 && pr == 1));
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk)
+                            umma_f16(dt, adesc(0, kk), bdesc(0, kk), id, (NPROD > 1) || kk > 0);
+                        umma_commit(&empty[s]);
+                        umma_commit(&seg_full[buf]);
+                    }
+                }
+            };
+            if (ub) issue(std::true_type{});
+            else issue(std::false_type{});
+            umma_commit(acc_full);   // every issued MMA has completed (also after an abort)
+        }
+        __syncwarp();
+    } else if (warp < 2 + DW) {
+        // ---------------- drain warps: k-blocks into registers, the tile into shared memory
+        const int q = warp & 3, grp = (warp - 2) >> 2;
+        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16) + grp * NC;
+        uint32_t h = 0, nt = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < work && ok; t += gridDim.x) {
+            PTile d;
+            persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, d);
+            if (!d.active) continue;
+            float sum[NC];
+#pragma unroll
+            for (int j = 0; j < NC; ++j) sum[j] = 0.0f;
+            // columns the MMAs write (the others keep the border's zero)
+            const int wcols = d.tile_k - grp * NC < 0 ? 0 : (d.tile_k - grp * NC > NC ? NC : d.tile_k - grp * NC);
+            for (int kb = 0; kb < d.nk; ++kb, ++h) {
+                const int buf = (int)(h & 1);
+                if (!mbar_wait_warp(&seg_full[buf], (h >> 1) & 1, kWaitNs, vabort)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                fence_after();
+#pragma unroll
+                for (int cb = 0; cb < NC / 16; ++cb) {
+                    if (cb * 16 >= wcols) break;
+                    uint32_t r[16];
+                    tmem_ld16(t_row + buf * TBN + cb * 16, r);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sum[cb * 16 + j] += __uint_as_float(r[j]);
+                }
+                fence_before();
+                mbar_arrive(&seg_empty[buf]);
+            }
+            if (!ok) break;
+            // the epilogue warps have released the result buffer of the previous tile
+            if (nt > 0 && !mbar_wait_warp(res_empty, (nt - 1) & 1, kWaitNs, vabort)) {
+                ok = false;
+                break;
+            }
+            const float alpha = steps.s[d.sidx].alpha;
+            const int rl = q * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) tile[rl * LD + grp * NC + c] = alpha * sum[c];
+            mbar_arrive(res_full);
+            ++nt;
+        }
+        // every MMA has completed before TMEM is freed
+        if (!mbar_wait_warp(acc_full, 0, kWaitNs, nullptr)) ok = false;
+        __syncwarp();
+        if (!ok && lane == 0) give_up();
+    } else {
+        // ---------------- epilogue warps
+        const int ew = warp - 2 - DW;   // 0..EW-1
+        uint32_t nt = 0;
+        for (int t = blockIdx.x; t < work; t += gridDim.x) {
+            PTile d;
+            persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, d);
+            if (!d.active) continue;
+            // the group decides together: after every warp's (bounded) wait, one thread samples
+            // the abort flag (which any role may raise at any time) into s_go between two group
+            // barriers, so that no warp can be left alone at the group's named barrier
+            if (!mbar_wait_warp(res_full, nt & 1, kWaitNs, vabort) && lane == 0) give_up();
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
+            if (ew == 0 && lane == 0) s_go = *vabort ? 0 : 1;
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
+            if (!s_go) break;
+            persist_epilogue<F16, EW, TBN, LD>(steps.s[d.sidx], insts, io, d.inst, d.m0, d.n0, sym, ub, tile,
+                                               rowpart, ew, lane);
+            mbar_arrive(res_empty);
+            ++nt;
+        }
+    }
+    // ---------------- every role is done: free TMEM
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(Cfg::kTmemCols));
+    }
+}
+
 // ------------------------------------------------------------------ host side
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
 
@@ -992,6 +1509,25 @@ cudaError_t dispatch_tbn(int tile_n, int ctas, int drain, const TcMaps& maps, co
                                                                sym, err_flag, s);
     return launch_tc<PA, PB, NPROD, F16, 128, 1, 8, CHAIN>(maps, st, grid, in, io, pre, i0, i1, tile0, tiles, b0, sym,
                                                            err_flag, s);
+}
+
+// The persistent kernel: one CTA per SM (its shared memory admits no second one).
+template <int PA, int PB, int NPROD, bool F16>
+cudaError_t launch_persist(const TcMaps& maps, const StepList& st, const Inst* in, const InstIO* io, const int* pre,
+                           int i0, int i1, int tile0, int tiles, int b0, int sym, int* err_flag, cudaStream_t s) {
+    constexpr int DW = 8, EW = 4;
+    using Cfg = PcCfg<PA, PB, NPROD, F16, DW, EW>;
+    auto kern = k_tc_persist<PA, PB, NPROD, F16, DW, EW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int work = tiles * st.count;
+    const unsigned grid = (unsigned)(work < sms ? work : sms);
+    kern<<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag);
+    return cudaGetLastError();
 }
 
 template <bool CHAIN, class SL>
@@ -1067,9 +1603,9 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
 
 cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in,
                     const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
-                    int nb, int* err_flag, cudaStream_t s, std::string* err, int sym) {
+                    int nb, int* err_flag, cudaStream_t s, std::string* err, int sym, int persist) {
     if (!tile_config_ok(prec, tile_n, ctas, drain) || nb < 1 || nb > kMaxBuckets || !err_flag || nsteps < 1 ||
-        nsteps > kMaxSteps) {
+        nsteps > kMaxSteps || (persist && tile_n != 128)) {
         if (err) *err = "tc_gemm: unsupported precision, tile or bucket count";
         return cudaErrorInvalidValue;
     }
@@ -1079,6 +1615,17 @@ cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps
     StepList st;
     for (int q = 0; q < nsteps; ++q) st.s[q] = steps[q];
     st.count = nsteps;
+    if (persist) {
+        switch (prec) {
+            case FO_PREC_BF16X3:
+                return launch_persist<3, 3, 6, false>(tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            case FO_PREC_FP16X2:
+                return launch_persist<2, 2, 3, true>(tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            case FO_PREC_BF16X1:
+                return launch_persist<1, 1, 1, false>(tm, st, in, io, pre, i0, i1, tile0, tiles, b0, sym, err_flag, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     return dispatch_prec<false>(prec, tile_n, ctas, drain, tm, st, (unsigned)(tiles * nsteps), in, io, pre, i0, i1,
                                 tile0, tiles, b0, sym, err_flag, s);
 }

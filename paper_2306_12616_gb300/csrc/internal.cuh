@@ -359,9 +359,11 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
 // product (fo_recurrence_product only), 1 the tiles on and above the diagonal of a symmetric
 // product over fully stored planes, 2 the same over planes stored as upper 128-blocks.
 // drain = TMEM drain warps (8, or 16 with 256-wide tiles).
+// persist = 1: the persistent kernel (tile_n = 128; one CTA per SM walks the tiles, with
+// separate epilogue warps overlapping each tile's epilogue with the next tile's products).
 cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in, const InstIO* io,
                     const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
-                    int nb, int* err_flag, cudaStream_t s, std::string* err, int sym = 1);
+                    int nb, int* err_flag, cudaStream_t s, std::string* err, int sym = 1, int persist = 0);
 // A chain of dependent symmetric products (ChainList) over instances [i0, i1) in one launch,
 // windows of consecutive instances holding at least `win_tiles` tiles per step each (0: one
 // window). counters: 1 + (i1 - i0) ints of device scratch, zeroed here on `s`.
