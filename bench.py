@@ -73,6 +73,8 @@ def parse():
                     help="product launches: 0 library default, 1 one per product, 2 one per chain")
     ap.add_argument("--chain-window", type=int, default=0,
                     help="chain launches: tiles per step of an instance window (0: one window)")
+    ap.add_argument("--no-order", action="store_true",
+                    help="skip the learned-order measurement on the batch family")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-mu measurement on the metallic model")
     ap.add_argument("--learned-pairs", type=int, default=20000,
@@ -360,6 +362,100 @@ def bench_batch(solver, stream, flush, steps, precision, count=512, n_terms=300,
             "products_achieved_tflops": pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] > 0 else None,
             "products_share": pr["ms"] / max(1e-9, prof["call"]["ms"]),
             "stages_ms": {k: v["ms"] for k, v in prof.items() if isinstance(v, dict)}}
+
+
+# ----------------------------- learned expansion order on the 512-instance batch family
+def bench_learned_order(solver, stream, flush, steps, count=512, n_terms=300, pairs=2048, lanczos=40,
+                        epochs=150):
+    """The learned expansion order (FO_MU_ORDER) on the batch family with Lanczos bounds: the
+    network is trained on `pairs` method-generated pairs of the family (matrices drawn on the
+    device, sizes log-uniform in [64, 1024]), then the 512-instance batch (the batch_512
+    matrices) is solved with mu by bisection at the configured 300 terms and with the
+    learned order (mu by bisection at that order), each replayed as one CUDA graph, the L2
+    flushed before each replay. Reported per form: density matrices/s, products per DM; for
+    the learned order the coefficients used, the extra truncation against the 300-term P
+    and the trace errors."""
+    import numpy as np
+    import torch
+    import synth
+    from synth.device import tight_binding_batch
+    from paper_2306_12616_gb300 import FO_FLAG_GRAPH
+    dev = flush.device
+    t0 = time.perf_counter()
+    ns_tr = [int(n) for n in synth.batch_sizes(pairs, 9100)]
+    kts_tr = [float(t) for t in synth.batch_temperatures(pairs, 9100)]
+    groups = {}
+    for i, n in enumerate(ns_tr):
+        groups.setdefault(n, []).append(i)
+    hs_tr = [None] * pairs
+    for n, idx in groups.items():
+        hb = tight_binding_batch(len(idx), n, 9200 + n, dev)
+        for j, i in enumerate(idx):
+            hs_tr[i] = hb[j]
+    prm_f = solver.params(n_terms, 0.1, precision="bf16x3", lanczos_steps=lanczos)
+    feats, tgts = [], []
+    for b0 in range(0, pairs, 512):
+        f, t, r = solver.learned_features(hs_tr[b0:b0 + 512], [n / 2 for n in ns_tr[b0:b0 + 512]], prm_f,
+                                          kT=kts_tr[b0:b0 + 512])
+        if any(x["status"] != 0 for x in r):
+            raise RuntimeError("training pair generation failed")
+        feats.append(f)
+        tgts.append(t)
+    del hs_tr, groups
+    feat, tgt = torch.cat(feats), torch.cat(tgts)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    solver.mlp_init(91)
+    losses = solver.mlp_train(feat, tgt, epochs=epochs, batch=256, lr=1e-3, seed=91)
+    train_s = time.perf_counter() - t0
+    del feat, tgt, feats, tgts
+    torch.cuda.empty_cache()
+    ns = [int(n) for n in synth.batch_sizes(count, 4000)]
+    kts = [float(t) for t in synth.batch_temperatures(count, 4000)]
+    hs = [torch.from_numpy(synth.tight_binding(ns[i], 4000 + i)).to(dev) for i in range(count)]
+    ne = [n / 2 for n in ns]
+    out = {}
+    results = {}
+    for label, mode in (("bisection", "bisect"), ("learned_order", "order")):
+        ps = [torch.empty_like(h) for h in hs]
+        prm = solver.params(n_terms, 0.1, precision="bf16x3", mu_mode=mode, lanczos_steps=lanczos,
+                            flags=FO_FLAG_GRAPH)
+        _, res = solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps)
+        for _ in range(3):
+            solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps, sync=False)
+        times = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.density_matrix_batched(hs, ne, prm, kT=kts, outs=ps, sync=False)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        results[label] = (ps, res)
+        out[label] = {"dm_per_s": count / (ms * 1e-3), "ms_per_batch": ms,
+                      "products_per_dm": float(np.mean([r["n_gemm"] for r in res])),
+                      "all_status_ok": all(r["status"] == 0 for r in res),
+                      "worst_trace_err": max(abs(r["trace"] - x) for r, x in zip(res, ne))}
+    po, ro = results["learned_order"]
+    pb, _ = results["bisection"]
+    extra = [float(torch.linalg.norm(a - b)) / math.sqrt(n) for a, b, n in zip(po, pb, ns)]
+    used = [r["order"] for r in ro]
+    out["learned_order"].update({
+        "coefficients_used": {"min": min(used), "median": float(np.median(used)), "max": max(used),
+                              "of": n_terms},
+        "extra_truncation_vs_full_order": {"median": float(np.median(extra)), "max": max(extra),
+                                           "metric": "||P_order - P_300||_F / sqrt(N)"}})
+    del hs, results, po, pb
+    torch.cuda.empty_cache()
+    return {"workload": f"{count} tight-binding H (the batch_512 matrices), N log-uniform in [64, 1024], "
+                        f"kT ~ U(0.05, 0.2) eV, N_e = N/2, {n_terms} terms, bf16x3, Lanczos bounds "
+                        f"({lanczos} steps), one CUDA graph per batch",
+            "training": {"pairs": pairs, "epochs": epochs, "pair_generation_s": gen_s, "train_s": train_s,
+                         "loss_first": losses[0], "loss_last": losses[-1]},
+            "forms": out}
 
 
 # ------------------------------------------- learned mu on the metallic model (N = 1024)
@@ -686,6 +782,12 @@ def main():
             learned = bench_learned_metallic(solver, stream, pairs=args.learned_pairs)
         except Exception as exc:   # reported, never fatal to the headline measurement
             learned = {"error": f"{type(exc).__name__}: {exc}"}
+    order = None
+    if not args.no_order and not args.no_batch and rank == 0 and args.precision == "bf16x3":
+        try:
+            order = bench_learned_order(solver, stream, flush, max(3, args.steps // 2), count=args.batch_count)
+        except Exception as exc:   # reported, never fatal to the headline measurement
+            order = {"error": f"{type(exc).__name__}: {exc}"}
     cb = cpu_baseline(ns) if (rank == 0 and world == 1) else None
     per_n = {}
     for n in ns:
@@ -752,6 +854,7 @@ def main():
         "batch_512": batch,
         "eigh_fp64_cusolver": eigh,
         "learned_mu_metallic": learned,
+        "learned_order_batch": order,
         "paper_context": PAPER_CONTEXT,
     }
     if rank == 0:

@@ -61,7 +61,13 @@ typedef enum {
 typedef enum {
     FO_MU_FIXED = 0,    /* use params.mu */
     FO_MU_BISECT = 1,   /* bisection on sum_n c_n(mu) tau_n = N_e with exact moments */
-    FO_MU_LEARNED = 2   /* MLP proposal, verified on the trace; bisection as fallback */
+    FO_MU_LEARNED = 2,  /* MLP proposal, verified on the trace; bisection as fallback */
+    FO_MU_ORDER = 3     /* MLP proposal of each instance's expansion order: the expansion is cut
+                           at the proposed order (x 1.25, rounded up to whole giant steps, at
+                           most n_terms), products it makes zero or unused are skipped, and mu
+                           is the bisection's on the exact moments of that expansion (started
+                           at the MLP's mu). fo_result.order = the coefficients used, m = the
+                           giant steps used, n_gemm = the instance's products */
 } fo_mu_mode;
 
 /* Flags (fo_params.flags). */
@@ -162,7 +168,8 @@ typedef struct {
     int32_t tile_n;           /* tensor-core tile width used (0 for FP64) */
     int32_t tile_ctas;        /* CTAs per SM of the product kernel used (0 for FP64) */
     int32_t evals;            /* evaluations of P (1 unless FO_MU_LEARNED corrected mu) */
-    int32_t order;            /* expansion order proposed by the learned model (0 if none) */
+    int32_t order;            /* expansion order proposed by the learned model (FO_MU_LEARNED) or
+                                 the coefficients used (FO_MU_ORDER); 0 otherwise */
     int32_t tile_drain;       /* accumulator drain warps of the product kernel (0 for FP64) */
     int32_t tile_store;       /* operand plane storage used (1 or 2 as in fo_params; 0 for FP64) */
     double  trace_raw;        /* tr(P) as the expansion produced it, before the trace correction
@@ -344,8 +351,10 @@ fo_status fo_moments(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld,
  *           Hamiltonian; only tau_j with j <= 2k are available from the k baby steps, the
  *           others are 0), N_e / N, kT_x = 2 kT / (emax - emin), emin / 100, emax / 100;
  *   outputs mu_x = (2 mu - (emin + emax)) / (emax - emin) and log2(L*) / log2(n_terms),
- *           L* the number of terms after which every trace tail |sum_{j>=L'} c_j tau_j|
- *           stays below 1e-4 N (the proposed expansion order, reported in fo_result.order).
+ *           L* the smallest number of terms whose coefficient tail sum_{j>=L*} |c_j| is at
+ *           most 2.5e-7 (the proposed expansion order: the expansion cut there is within
+ *           2.5e-7 of the full one in the 2-norm, since |T_j| <= 1 on the scaled spectrum;
+ *           reported in fo_result.order, used to cut the expansion by FO_MU_ORDER).
  * Inputs and outputs are standardised with the training set's mean and standard deviation
  * (the normalisation vector: feature mean[68], feature std[68], target mean[2], target
  * std[2]). Parameters are stored W1 (256 x 68), b1 (256), W2 (256 x 256), b2 (256),

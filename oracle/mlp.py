@@ -11,8 +11,9 @@ build-side addition whose every step this module writes out in float64:
   scaled axis kT_x = 2 kT / (e_b - e_a), and the bounds e_a / 100, e_b / 100;
 * the regression targets (``targets``): mu on the scaled axis,
   mu_x = (2 mu - (e_a + e_b)) / (e_b - e_a), and the order target log2(L*) / log2(n_terms),
-  L* the smallest number of terms whose trace tail stays below 1e-4 N
-  (``order_from_tail``);
+  L* the smallest number of terms whose coefficient tail sum_{j >= L*} |c_j| is at most
+  2.5e-7 (``order_from_coefficients``): since |T_j(x)| <= 1 on [-1, 1], cutting the
+  expansion there changes P by at most that much in the 2-norm, a quarter of the 1e-6 bar;
 * a fully connected network 68 -> 256 -> 256 -> 2 with SiLU activations,
   silu(z) = z / (1 + exp(-z)) (Elfwing, Uchibe and Doya 2018), y = W3 a2 + b3;
 * the weighted squared error L = (1/B) sum_b sum_j w_j (y_bj - t_bj)^2 and its gradients
@@ -29,14 +30,14 @@ import math
 import numpy as np
 
 __all__ = ["N_IN", "N_HID", "N_OUT", "N_MOM", "silu", "silu_grad", "forward", "loss",
-           "gradients", "adam_step", "features", "targets", "order_from_tail", "param_shapes",
+           "gradients", "adam_step", "features", "targets", "order_from_coefficients", "param_shapes",
            "flatten", "unflatten", "init_params"]
 
 N_MOM = 64
 N_IN = N_MOM + 4
 N_HID = 256
 N_OUT = 2
-ORDER_EPS = 1e-4
+ORDER_EPS = 2.5e-7
 
 
 def param_shapes() -> list[tuple[str, tuple[int, ...]]]:
@@ -140,23 +141,24 @@ def features(tau: np.ndarray, n: int, n_e: float, kT: float, ea: float, eb: floa
     return f
 
 
-def order_from_tail(c: np.ndarray, tau: np.ndarray, n: int, eps: float = ORDER_EPS) -> int:
-    """Smallest L >= 1 such that |sum_{j=L'}^{n_terms-1} c_j tau_j| <= eps n for every
-    L' >= L (the trace contributed by the terms from L' on)."""
+def order_from_coefficients(c: np.ndarray, eps: float = ORDER_EPS) -> int:
+    """Smallest L >= 1 such that sum_{j=L}^{n_terms-1} |c_j| <= eps: the expansion cut at L
+    terms differs from the full one by at most eps in the 2-norm (|T_j| <= 1 on the scaled
+    spectrum), whatever the Hamiltonian."""
     n_terms = len(c)
     tail = 0.0
     L = n_terms
     for j in range(n_terms - 1, 0, -1):
-        tail += c[j] * tau[j]
-        if abs(tail) > eps * n:
+        tail += abs(c[j])
+        if tail > eps:
             break
         L = j
     return L
 
 
-def targets(mu: float, ea: float, eb: float, c: np.ndarray, tau: np.ndarray, n: int) -> np.ndarray:
-    """(mu_x, log2(L*) / log2(n_terms))."""
+def targets(mu: float, ea: float, eb: float, c: np.ndarray) -> np.ndarray:
+    """(mu_x, log2(L*) / log2(n_terms)) for the coefficients c of the expansion at mu."""
     n_terms = len(c)
-    L = order_from_tail(c, tau, n)
+    L = order_from_coefficients(c)
     return np.array([(2.0 * mu - (ea + eb)) / (eb - ea),
                      math.log2(max(L, 1)) / math.log2(max(n_terms, 2))])

@@ -16,7 +16,7 @@ from dataclasses import dataclass
 
 __all__ = [
     "FO_OK", "FO_PREC_FP64", "FO_PREC_BF16X3", "FO_PREC_FP16X2", "FO_PREC_BF16X1",
-    "FO_MU_FIXED", "FO_MU_BISECT", "FO_MU_LEARNED", "FO_FLAG_NO_RESULT_SYNC", "FO_FLAG_GRAPH",
+    "FO_MU_FIXED", "FO_MU_BISECT", "FO_MU_LEARNED", "FO_MU_ORDER", "FO_FLAG_NO_RESULT_SYNC", "FO_FLAG_GRAPH",
     "FO_FLAG_STAGED", "FO_FLAG_POWER_BASIS", "FO_FLAG_NO_TRACE_FIX", "FO_FLAG_ALLOW_LOOSE",
     "FoParams", "FoResult", "FermiError", "lib", "library_path", "EXPORTED_SYMBOLS",
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
@@ -32,7 +32,7 @@ FO_OK = 0
 FO_ERR_ARG, FO_ERR_CUDA, FO_ERR_NOMEM, FO_ERR_NONFINITE = 1, 2, 3, 4
 FO_ERR_NO_BRACKET, FO_ERR_NOT_CONVERGED, FO_ERR_DEVICE_TIMEOUT, FO_ERR_UNSUPPORTED = 5, 6, 7, 8
 FO_PREC_FP64, FO_PREC_BF16X3, FO_PREC_FP16X2, FO_PREC_BF16X1 = 0, 1, 2, 3
-FO_MU_FIXED, FO_MU_BISECT, FO_MU_LEARNED = 0, 1, 2
+FO_MU_FIXED, FO_MU_BISECT, FO_MU_LEARNED, FO_MU_ORDER = 0, 1, 2, 3
 FO_FLAG_NO_RESULT_SYNC = 0x2
 FO_FLAG_GRAPH = 0x4
 FO_FLAG_STAGED = 0x8
@@ -42,7 +42,7 @@ FO_FLAG_ALLOW_LOOSE = 0x40
 
 PRECISIONS = {"fp64": FO_PREC_FP64, "bf16x3": FO_PREC_BF16X3, "fp16x2": FO_PREC_FP16X2,
               "bf16x1": FO_PREC_BF16X1}
-MU_MODES = {"fixed": FO_MU_FIXED, "bisect": FO_MU_BISECT, "learned": FO_MU_LEARNED}
+MU_MODES = {"fixed": FO_MU_FIXED, "bisect": FO_MU_BISECT, "learned": FO_MU_LEARNED, "order": FO_MU_ORDER}
 
 # Every symbol the header declares (checked by the CPU test suite against the .so).
 EXPORTED_SYMBOLS = (

@@ -150,6 +150,9 @@ struct fo_ctx {
 namespace {
 
 constexpr size_t kMaxPlans = 8;
+// Learned expansion order: the network's proposed order is enlarged by this factor (then
+// rounded up to whole giant steps) before it cuts the expansion.
+constexpr double kOrderMargin = 1.25;
 
 struct DeviceGuard {
     int prev = -1;
@@ -315,7 +318,7 @@ fo_status layout_plan(fo_ctx* ctx, const PlanKey& key, Plan* p) {
     sh.pscale_t = 256.0f;
     sh.pscale_r = 1.0f;
     const bool bisect = key.mode == MODE_DENSITY && key.mu_mode == FO_MU_BISECT;
-    const bool learned = key.mode == MODE_DENSITY && key.mu_mode == FO_MU_LEARNED;
+    const bool learned = key.mode == MODE_DENSITY && (key.mu_mode == FO_MU_LEARNED || key.mu_mode == FO_MU_ORDER);
     p->giants = (bisect || learned) && sh.m > 2;   // the learned mode falls back to exact moments
     p->moments = bisect || learned || key.mode == MODE_MOMENTS;
     p->fix = (bisect || learned) && !sh.is64 && sh.m > 1 && !key.nofix;
@@ -655,7 +658,7 @@ int r_slot(const Plan& p, int l) { return p.sh.n_tslots + l; }
 // Either way jmax - 1 products; slot(j) gives the slot of U_j (j >= 1).
 template <class SlotOf>
 fo_status chebyshev_chain(fo_ctx* ctx, Plan& p, int jmax, SlotOf slot, bool staged, cudaStream_t s,
-                          const char* tag, Run* run) {
+                          const char* tag, Run* run, bool giant = false) {
     auto prod = [&](int a, int b, int c, int out) {
         // 2 U_a U_b - U_c, U_0 = I
         return c == 0 ? make_step(p, slot(a), slot(b), -1, -1, slot(out), 2.0, 0.0, -1.0, false, false, false,
@@ -666,7 +669,11 @@ fo_status chebyshev_chain(fo_ctx* ctx, Plan& p, int jmax, SlotOf slot, bool stag
     if (jmax < 2) return FO_OK;
     if (!staged) {
         std::vector<Step> chain;
-        for (int j = 1; j < jmax; ++j) chain.push_back(prod(1, j, j - 1, j + 1));
+        for (int j = 1; j < jmax; ++j) {
+            chain.push_back(prod(1, j, j - 1, j + 1));
+            // the giant step T_{(j+1)k} feeds the moments of expansions with m_eff > j + 1 only
+            if (giant) chain.back().need_m = j + 1;
+        }
         return run_chain(ctx, p, chain, s, tag, run);
     }
     {
@@ -692,7 +699,7 @@ fo_status baby_steps(fo_ctx* ctx, Plan& p, int kmax, cudaStream_t s, Run* run) {
 // Giant steps T_{2k}..T_{(m-1)k}: the chain U_j = T_{jk} = T_j(T_k).
 fo_status giant_steps(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     return chebyshev_chain(ctx, p, p.sh.m - 1, [&p](int j) { return giant_slot(p, j); }, p.key.staged != 0, s,
-                           "giant", run);
+                           "giant", run, true);
 }
 
 // Exact moments tau_0..tau_{n_terms-1} (needs the giant steps).
@@ -720,6 +727,9 @@ fo_status clenshaw(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
         const bool has_c = l + 2 <= m - 1;
         chain.push_back(make_step(p, y, r_slot(p, l + 1), has_c ? r_slot(p, l + 2) : -1, r_slot(p, l), r_slot(p, l),
                                   2.0, has_c ? -1.0 : 0.0, 0.0, false, true, true, false, ctx));
+        // an expansion cut at m_eff giant steps has b_l = R_l = 0 for l >= m_eff and
+        // b_{m_eff - 1} = R_{m_eff - 1} (already in its slot): only l < m_eff - 1 is computed
+        chain.back().need_m = l + 1;
     }
     const bool has_c = m >= 3;
     Step st = make_step(p, y, r_slot(p, 1), has_c ? r_slot(p, 2) : -1, r_slot(p, 0), -1, 1.0,
@@ -836,7 +846,9 @@ fo_status evaluate(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int poly_trac
 // and the trace judge; corrected re-evaluations; exact moments and bisection for whatever
 // is still rejected. Eager calls stop as soon as every instance is accepted; a captured
 // graph runs every round (rejected-free instances skip the work of each kernel).
-fo_status learned(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+// Moments up to 2k from the baby steps, the network's features, forward pass and proposal
+// (mu, and with use_order the per-instance expansion order).
+fo_status propose(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int use_order) {
     const Shape& sh = p.sh;
     const int B = p.batch;
     const MlpOffsets mo = mlp_offsets();
@@ -860,9 +872,17 @@ fo_status learned(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     FO_CUDA(launch_features(p.d_inst, p.d_io, B, sh.k, 0, feat, s), "features");
     FO_CUDA(mlp_gather_norm(feat, nullptr, B, kMlpIn, norm, norm + kMlpIn, xn, s), "normalise");
     FO_CUDA(mlp_forward(params, xn, B, z1, a1, z2, a2, y, s), "network");
-    FO_CUDA(launch_learned_mu(p.d_inst, B, y, norm, sh.n_terms, s), "proposal");
+    FO_CUDA(launch_learned_mu(p.d_inst, B, y, norm, sh.n_terms, sh.k, sh.m, use_order, kOrderMargin, s),
+            "proposal");
     prof_end(ctx, s, h, 0.0, 6);
     run->launches += 6;
+    return FO_OK;
+}
+
+fo_status learned(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    const Shape& sh = p.sh;
+    const int B = p.batch;
+    FO_TRY(propose(ctx, p, s, run, 0));
     const int R = p.key.max_newton == 0 ? 2 : (p.key.max_newton < 0 ? 0 : p.key.max_newton);
     bool any = true;
     for (int r = 0; r <= R; ++r) {
@@ -894,6 +914,17 @@ fo_status learned(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     return FO_OK;
 }
 
+// Learned expansion order: the network proposes each instance's order, the expansion is cut
+// there (coefficients from n_eff on are zero, the giant and Clenshaw products it leaves zero
+// or unused are skipped), and mu is the bisection's on the exact moments of that expansion,
+// started from the network's mu; the trace correction follows as for bisection.
+fo_status learned_order(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
+    FO_TRY(propose(ctx, p, s, run, 1));
+    FO_TRY(exact_mu(ctx, p, s, run, 1));
+    FO_TRY(evaluate(ctx, p, s, run, 1, p.fix ? 1 : 0));
+    return p.fix ? trace_fix(ctx, p, s, run) : FO_OK;
+}
+
 // The whole method for every instance of a density plan (after the per-call inputs).
 fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     FO_TRY(front(ctx, p, s, run));
@@ -904,6 +935,8 @@ fo_status run_density(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
             return p.fix ? trace_fix(ctx, p, s, run) : FO_OK;
         case FO_MU_LEARNED:
             return learned(ctx, p, s, run);
+        case FO_MU_ORDER:
+            return learned_order(ctx, p, s, run);
         default:
             FO_CUDA(launch_set_mu(p.d_inst, p.d_io, p.batch, s), "mu");
             run->launches += 1;
@@ -1044,9 +1077,9 @@ fo_status check_params(fo_ctx* ctx, const fo_params* prm) {
     if (!(prm->kT > 0.0) || !std::isfinite(prm->kT)) return fail(ctx, FO_ERR_ARG, "kT must be > 0");
     if (prm->use_given_bounds && !(prm->emax > prm->emin))
         return fail(ctx, FO_ERR_ARG, "emax must exceed emin");
-    if (prm->mu_mode < FO_MU_FIXED || prm->mu_mode > FO_MU_LEARNED)
+    if (prm->mu_mode < FO_MU_FIXED || prm->mu_mode > FO_MU_ORDER)
         return fail(ctx, FO_ERR_ARG, "unknown mu_mode");
-    if (prm->mu_mode == FO_MU_LEARNED && !ctx->mlp_ready)
+    if ((prm->mu_mode == FO_MU_LEARNED || prm->mu_mode == FO_MU_ORDER) && !ctx->mlp_ready)
         return fail(ctx, FO_ERR_UNSUPPORTED, "learned mu needs a trained, loaded or set model");
     if (prm->mu_mode == FO_MU_LEARNED && !(prm->tr_tol >= 0.0)) return fail(ctx, FO_ERR_ARG, "tr_tol must be >= 0");
     if (prm->tile_n != 0 && prm->tile_n != 128 && prm->tile_n != 256)
@@ -1247,6 +1280,15 @@ fo_status density_batch(fo_ctx* ctx, int batch, const double* const* dH, const i
                 r.order = (int)std::lround(hr.order);
                 if (!hr.learned_ok) r.bisect_iters = hr.iters;
                 else r.bisect_iters = 0;
+            }
+            if (prm->mu_mode == FO_MU_ORDER) {
+                // the instance's own expansion: k - 1 baby steps, m_eff - 2 giant steps,
+                // m_eff - 1 Clenshaw steps (and the trace correction)
+                const int me = hr.m_eff > 0 ? hr.m_eff : p->sh.m;
+                r.n_gemm = (p->sh.k - 1) + (p->giants ? std::max(0, me - 2) : 0) + (me > 1 ? me - 1 : 0) +
+                           (p->fix ? 1 : 0);
+                r.order = hr.n_eff > 0 ? hr.n_eff : p->sh.n_terms;
+                r.m = me;
             }
             int status = hr.status;
             if (flag[0]) status = FO_ERR_DEVICE_TIMEOUT;

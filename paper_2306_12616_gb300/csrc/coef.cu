@@ -51,7 +51,8 @@ __global__ void k_dos_weights(const Inst* __restrict__ insts, int n_terms, int M
     const int64_t q = 2LL * j + 1, fourM = 4LL * M;
     int64_t r = 0;
     double s = 0.0;
-    for (int n = 1; n < n_terms; ++n) {
+    const int nt = eff_terms(in.res, n_terms);
+    for (int n = 1; n < nt; ++n) {
         r += q;
         if (r >= fourM) r -= fourM;
         s = fma(tau[n], ct[r], s);
@@ -187,7 +188,7 @@ __global__ void k_coeffs(const Inst* __restrict__ insts, const double* __restric
     const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (n >= km) return;
     double* c = in.c;
-    if (n >= n_terms) {
+    if (n >= eff_terms(in.res, n_terms)) {
         if (lane == 0) c[n] = 0.0;
         return;
     }
@@ -259,7 +260,8 @@ __global__ void k_poly_trace(const Inst* __restrict__ insts, int n_terms) {
     const Inst& in = insts[blockIdx.x];
     if (!in.res->active) return;
     double s = 0.0;
-    for (int n = threadIdx.x; n < n_terms; n += 32) s = fma(in.c[n], in.tau[n], s);
+    const int nt = eff_terms(in.res, n_terms);
+    for (int n = threadIdx.x; n < nt; n += 32) s = fma(in.c[n], in.tau[n], s);
     s = warp_sum(s);
     if (threadIdx.x == 0) in.res->trace_poly = s;
 }
@@ -389,8 +391,9 @@ __device__ __forceinline__ Split3 split_value(float v, int fp16, float pscale) {
 // a thread only reads what it copied) and multiplies them by the coefficients, staged as
 // duplicated pairs gsh[t][l] = (g_{t,l0+l}, g_{t,l0+l}) (zero beyond m): one 16-byte
 // broadcast load serves two R_l, each packed FMA two entries of the quad, and each R_l leaves
-// as one 16-byte store. The planes of R_{m-1} (the first operand of the giant steps) are
-// completed below the diagonal by k_mirror_planes.
+// as one 16-byte store. The planes of the instance's last R (R_{m-1}, or R_{m_eff-1} when a
+// learned order cut its expansion: the first operand of the Clenshaw steps) are written here
+// and completed below the diagonal by k_mirror_planes.
 template <int MAXM>
 __global__ void __launch_bounds__(256, 1) k_contract_f32(const Inst* __restrict__ insts, Work wct, int k, int m,
                                                           int l0, int n_tslots, int planes_last, int fp16,
@@ -409,6 +412,7 @@ __global__ void __launch_bounds__(256, 1) k_contract_f32(const Inst* __restrict_
     const int nt = k - 1;                                   // T_1 .. T_{k-1}
     float4* ring = reinterpret_cast<float4*>(fsh + 2 * k * MAXM);   // [stage][t][thread]
     const int64_t np = in.np, n = in.n;
+    const int lastl = (in.res->m_eff > 0 ? in.res->m_eff : m) - 1;   // R whose planes are written
     const int64_t q_all = ct_quads(np);
     const int64_t per = (int64_t)tpb * kCtSteps;
     const int64_t q0 = (int64_t)(blockIdx.x - wct.pre[i]) * per;
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(256, 1) k_contract_f32(const Inst* __restrict_
                 else v.w += g0;
             }
             *reinterpret_cast<float4*>(dst) = v;
-            if (l0 + l == m - 1 && planes_last > 0) {
+            if (l0 + l == lastl && planes_last > 0) {
                 const Split3 s0 = split_value(v.x, fp16, pscale), s1 = split_value(v.y, fp16, pscale);
                 const Split3 s2 = split_value(v.z, fp16, pscale), s3 = split_value(v.w, fp16, pscale);
                 // planes of R_l: 16-bit entries from float offset ps of the slot
@@ -514,11 +518,13 @@ __global__ void __launch_bounds__(256, 1) k_contract_f32(const Inst* __restrict_
 // and written transposed at (bj, bi); a diagonal block fills its own lower half. With ublk
 // only the diagonal 128-blocks are completed (a lower 128-block is then read as the
 // transpose of its upper counterpart).
-__global__ void __launch_bounds__(256) k_mirror_planes(const Inst* __restrict__ insts, Work ws, int slot,
+__global__ void __launch_bounds__(256) k_mirror_planes(const Inst* __restrict__ insts, Work ws, int slot0, int m,
                                                        int planes, int ublk, int* dbg) {
     __shared__ uint16_t tile[3][32][34];
     const int i = find_inst(ws.pre, 0, ws.count, blockIdx.x);
     if (!insts[i].res->active) return;
+    // the instance's last R: R_{m-1}, or R_{m_eff-1} for an expansion cut by a learned order
+    const int slot = slot0 + (insts[i].res->m_eff > 0 ? insts[i].res->m_eff : m) - 1;
     const int64_t np = insts[i].np;
     const int tn = (int)(np / 32);
     int bi = 0, b = blockIdx.x - ws.pre[i];
@@ -633,7 +639,7 @@ cudaError_t launch_contract(const Inst* in, Work we, Work wct, Work wsym, const 
             default: go(k_contract_f32<32>, 32, l0); break;
         }
     }
-    if (planes_last > 0) k_mirror_planes<<<wsym.total, 256, 0, s>>>(in, wsym, sh.n_tslots + sh.m - 1, planes_last,
+    if (planes_last > 0) k_mirror_planes<<<wsym.total, 256, 0, s>>>(in, wsym, sh.n_tslots, sh.m, planes_last,
                                                          sh.ublk, dbg);
     return cudaGetLastError();
 }

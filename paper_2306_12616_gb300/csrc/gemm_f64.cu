@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const __grid_constant__ StepLi
     const Step& st = steps.s[sidx];
     const int inst = find_inst(wt.pre, 0, wt.count, bt);
     const Inst& in = insts[inst];
-    if (!in.res->active) return;
+    if (!step_needed(in.res, st.need_m)) return;
     const int64_t np = in.np;
     const int n_real = (int)in.n;
     const int64_t sb = in.slot_bytes;

@@ -403,8 +403,9 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     }
     const Step& st = steps.s[sidx];
     const Inst& in = insts[inst];
-    if (!in.res->active) {
-        // an instance parked by the learned judge: its tiles count as done
+    if (!step_needed(in.res, st.need_m)) {
+        // an instance parked by the learned judge, or whose expansion does not need this
+        // step: its tiles count as done
         if constexpr (CHAIN) {
             if (threadIdx.x == 0) atomicAdd(steps.done + (inst - i0), 1);
         }
@@ -993,12 +994,13 @@ struct PTile {
     bool active;
 };
 __device__ __forceinline__ void persist_tile(int t, int tiles, int tile0, const int* __restrict__ pre, int i0,
-                                             int i1, const Inst* __restrict__ insts, int sym, PTile& d) {
+                                             int i1, const Inst* __restrict__ insts, int sym, const StepList& steps,
+                                             PTile& d) {
     d.sidx = t / tiles;
     const int gt = tile0 + t - d.sidx * tiles;
     d.inst = find_inst(pre, i0, i1, gt);
     const Inst& in = insts[d.inst];
-    d.active = in.res->active != 0;
+    d.active = step_needed(in.res, steps.s[d.sidx].need_m);
     const int np = (int)in.np;
     int I, J;
     tile_of(gt - __ldg(pre + d.inst), np / kBM, np / kBM, kBM, sym, I, J);
@@ -1258,7 +1260,7 @@ __global__ void __launch_bounds__(32 * (2 + DW + EW), 1)
                 constexpr bool U = decltype(ub_tag)::value;
                 for (int t = blockIdx.x; t < work; t += gridDim.x) {
                     PTile d;
-                    persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, d);
+                    persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, steps, d);
                     if (!d.active) continue;
                     const Step& st = steps.s[d.sidx];
                     const Inst& in = insts[d.inst];
@@ -1334,7 +1336,7 @@ __global__ void __launch_bounds__(32 * (2 + DW + EW), 1)
                 constexpr bool U = decltype(ub_tag)::value;
                 for (int t = blockIdx.x; t < work; t += gridDim.x) {
                     PTile d;
-                    persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, d);
+                    persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, steps, d);
                     if (!d.active) continue;
                     const uint32_t idesc0 = idesc_f16(d.tile_k, F16);
                     for (int kb = 0; kb < d.nk; ++kb, ++g, ++h) {
@@ -1390,7 +1392,7 @@ __global__ void __launch_bounds__(32 * (2 + DW + EW), 1)
         bool ok = true;
         for (int t = blockIdx.x; t < work && ok; t += gridDim.x) {
             PTile d;
-            persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, d);
+            persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, steps, d);
             if (!d.active) continue;
             float sum[NC];
 #pragma unroll
@@ -1439,7 +1441,7 @@ __global__ void __launch_bounds__(32 * (2 + DW + EW), 1)
         uint32_t nt = 0;
         for (int t = blockIdx.x; t < work; t += gridDim.x) {
             PTile d;
-            persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, d);
+            persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, steps, d);
             if (!d.active) continue;
             // the group decides together: after every warp's (bounded) wait, one thread samples
             // the abort flag (which any role may raise at any time) into s_go between two group

@@ -37,6 +37,8 @@ struct DevResult {
     int32_t active;       // 0: every kernel skips this instance
     int32_t evals;        // evaluations of P (learned mode)
     int32_t fixed;        // the trace correction was applied
+    int32_t m_eff;        // giant-step count of this instance's expansion (learned order); 0: the plan's m
+    int32_t n_eff;        // coefficients of this instance's expansion (learned order); 0: the plan's
     double mu_lo, mu_hi;  // final bracket of the mu search
     double mu0;           // learned proposal (learned mode)
     double mu_prev, tr_prev;  // previous evaluation (learned mode secant)
@@ -100,6 +102,8 @@ struct Step {
     int32_t fp16;
     int32_t lower_master;      // symmetric mode: also write the float32 master below the
                                // diagonal (the solver's slots keep it above the diagonal only)
+    int32_t need_m;            // instances whose expansion stops at m_eff <= need_m giant steps
+                               // skip this product (its output is zero or unused for them)
     int32_t fix64;             // with out64: P <- P + gamma (P - alpha A B^T) in float64, P the
                                // instance's float64 P (read and rewritten), gamma = res->gamma
     float alpha, beta, shift;  // float32 path; alpha includes the fp16 plane scales
@@ -145,6 +149,16 @@ struct Work {
     int count;        // instances
     int total;        // blocks
 };
+
+// Whether a product step is computed for an instance: it is active, and its expansion (cut at
+// m_eff giant steps by a learned order) needs the step's output.
+__device__ __forceinline__ bool step_needed(const DevResult* r, int need_m) {
+    return r->active && !(r->m_eff > 0 && r->m_eff <= need_m);
+}
+// Number of coefficients of an instance's expansion (the plan's unless a learned order cut it).
+__device__ __forceinline__ int eff_terms(const DevResult* r, int n_terms) {
+    return r->n_eff > 0 ? r->n_eff : n_terms;
+}
 
 // Largest j in [lo, hi) with pre[j] <= b (pre ascending, pre[lo] <= b < pre[hi]).
 __device__ __forceinline__ int find_inst(const int* __restrict__ pre, int lo, int hi, int b) {
@@ -292,6 +306,10 @@ constexpr int kMlpOut = 2;
 constexpr int kMlpNorm = 2 * kMlpIn + 2 * kMlpOut;
 constexpr float kMlpLossW0 = 1.0f;   // weight of the mu_x error
 constexpr float kMlpLossW1 = 0.1f;   // weight of the order error
+// The order target: the smallest L with sum_{j >= L} |c_j| <= kOrderEps. |T_j| <= 1 on the
+// scaled spectrum, so the expansion cut there is within kOrderEps of the full one in the
+// 2-norm (a quarter of the split forms' 1e-6 bar).
+constexpr double kOrderEps = 2.5e-7;
 struct MlpOffsets {
     int W1, b1, W2, b2, W3, b3, total;
 };
@@ -320,8 +338,10 @@ cudaError_t launch_features(const Inst* in, const InstIO* io, int batch, int k, 
                             cudaStream_t s);
 cudaError_t launch_targets(const Inst* in, int batch, int n_terms, float* tgt, cudaStream_t s);
 cudaError_t launch_assemble_low(const Inst* in, int batch, int k, cudaStream_t s);
+// The network's mu proposal (and, with use_order, the instance's expansion cut at the
+// proposed order times margin, rounded up to whole giant steps).
 cudaError_t launch_learned_mu(const Inst* in, int batch, const float* y, const float* norm, int n_terms,
-                              cudaStream_t s);
+                              int k, int m, int use_order, double margin, cudaStream_t s);
 cudaError_t launch_poly_width(const Inst* in, int batch, const Shape& sh, const double* ct, cudaStream_t s);
 cudaError_t launch_learned_check(const Inst* in, const InstIO* io, int batch, int round, int max_rounds,
                                  double tol, int is64, int* active_count, cudaStream_t s);

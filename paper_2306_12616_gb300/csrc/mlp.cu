@@ -153,21 +153,22 @@ __global__ void k_features(const Inst* __restrict__ insts, const InstIO* __restr
     feat[(int64_t)row * kMlpIn + c] = (float)v;
 }
 
-// Targets (mu_x, log2(L*) / log2(n_terms)) of every instance, from its mu, bounds,
-// coefficients c_j(mu) and moments tau_j (L*: the smallest L with every trace tail
-// |sum_{j>=L'} c_j tau_j| <= 1e-4 n for L' >= L). Row = caller index.
+// Targets (mu_x, log2(L*) / log2(n_terms)) of every instance, from its mu, bounds and
+// coefficients c_j(mu) (L*: the smallest L with sum_{j >= L} |c_j| <= kOrderEps). Row =
+// caller index.
 __global__ void k_targets(const Inst* __restrict__ insts, int batch, int n_terms, float* __restrict__ tgt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= batch) return;
     const Inst& in = insts[i];
     const DevResult* r = in.res;
     const double ea = r->bounds[0], eb = r->bounds[1];
-    const double n = (double)in.n;
+    // the order target: the smallest L with sum_{j >= L} |c_j| <= kOrderEps, so that the
+    // expansion cut at L terms is within kOrderEps of the full one in the 2-norm
     double tail = 0.0;
     int L = n_terms;
     for (int j = n_terms - 1; j >= 1; --j) {
-        tail += in.c[j] * in.tau[j];
-        if (fabs(tail) > 1e-4 * n) break;
+        tail += fabs(in.c[j]);
+        if (tail > kOrderEps) break;
         L = j;
     }
     const double lg = n_terms > 1 ? log2((double)n_terms) : 1.0;
@@ -189,8 +190,14 @@ __global__ void k_assemble_low(const Inst* __restrict__ insts, int batch, int k)
 }
 
 // mu0 = mid + half (m_x + s_x y0) clamped into the bounds, order = n_terms^(m_o + s_o y1).
+// The network's proposals: mu, and the expansion order L* (the number of terms whose
+// coefficient tail sum_{j >= L*} |c_j| is at most kOrderEps). With use_order the instance's expansion is cut at
+// n_eff = k m_eff coefficients, m_eff = ceil(margin L* / k) giant steps, clamped to [2, m]:
+// every coefficient from n_eff on is zero, and the products whose outputs that leaves zero
+// or unused are skipped (step_needed).
 __global__ void k_learned_mu(const Inst* __restrict__ insts, int batch, const float* __restrict__ y,
-                             const float* __restrict__ norm, int n_terms) {
+                             const float* __restrict__ norm, int n_terms, int k, int m, int use_order,
+                             double margin) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= batch) return;
     DevResult* r = insts[i].res;
@@ -203,10 +210,16 @@ __global__ void k_learned_mu(const Inst* __restrict__ insts, int batch, const fl
     mu = fmin(fmax(mu, ea), eb);
     r->mu = r->mu0 = mu;
     r->order = exp2(lo * log2((double)(n_terms > 1 ? n_terms : 2)));
+    if (use_order && m >= 2 && isfinite(r->order)) {
+        int me = (int)ceil(margin * fmax(r->order, 1.0) / (double)k);
+        me = me < 2 ? 2 : (me > m ? m : me);
+        r->m_eff = me;
+        r->n_eff = k * me < n_terms ? k * me : n_terms;
+    }
 }
 
 // The judge after evaluation `round` (0 = at the learned mu): accept when |tr P - N_e| <=
-// tol (tol <= 0: 1e-8 max(1, N_e) for float64, 2e-6 n for the split forms); otherwise, if
+// tol (tol <= 0: 1e-8 max(1, N_e) for float64, 1e-7 n for the split forms); otherwise, if
 // rounds remain, move mu by a Newton step on d tr P / d mu ~ tr(P (I - P)) / kT_p =
 // (tr P - ||P||_F^2) / kT_p (first round; kT_p the effective temperature of the truncated
 // expansion, k_poly_width, which is kT for an exact Fermi function) or a secant step
@@ -316,8 +329,8 @@ cudaError_t launch_assemble_low(const Inst* in, int batch, int k, cudaStream_t s
 }
 
 cudaError_t launch_learned_mu(const Inst* in, int batch, const float* y, const float* norm, int n_terms,
-                              cudaStream_t s) {
-    k_learned_mu<<<(batch + 127) / 128, 128, 0, s>>>(in, batch, y, norm, n_terms);
+                              int k, int m, int use_order, double margin, cudaStream_t s) {
+    k_learned_mu<<<(batch + 127) / 128, 128, 0, s>>>(in, batch, y, norm, n_terms, k, m, use_order, margin);
     return cudaGetLastError();
 }
 

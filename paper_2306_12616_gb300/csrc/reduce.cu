@@ -70,6 +70,7 @@ __global__ void k_set_io(const IoChunk p, InstIO* d_io, const Inst* insts) {
     r->kt_eff = 0.0;
     r->trace_raw = r->gamma = r->proj = 0.0;
     r->fixed = 0;
+    r->m_eff = r->n_eff = 0;
 }
 
 // ------------------------------------------------------------------ Gershgorin bounds

@@ -117,7 +117,7 @@ def test_learned_features_match_oracle(solver):
         assert np.allclose(feat[i], ref, atol=1e-6, rtol=1e-6), i   # float32 storage of float64 values
         orc = O.density_matrix(h, n / 2, kT, 64, route="eig", want_p=False)
         c = O.chebyshev_coeffs(kT, r["mu"], ea, eb, 64)
-        tref = M.targets(r["mu"], ea, eb, c, tau, n)
+        tref = M.targets(r["mu"], ea, eb, c)
         assert abs(tgt[i, 0] - tref[0]) <= 1e-6
         assert abs(tgt[i, 0] - (2 * orc.mu - ea - eb) / (eb - ea)) <= 1e-6
         assert abs(tgt[i, 1] - tref[1]) <= 1e-6

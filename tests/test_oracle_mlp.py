@@ -92,30 +92,49 @@ def test_features_of_a_diagonal_hamiltonian():
     assert (f[M.N_MOM + 2], f[M.N_MOM + 3]) == (-0.04, 0.06)
 
 
-def test_order_from_tail_brute_force():
+def test_order_from_coefficients_brute_force():
     rng = np.random.default_rng(4)
     for trial in range(50):
         nt = int(rng.integers(5, 40))
         c = rng.normal(size=nt) * np.exp(-0.3 * np.arange(nt))
-        tau = rng.uniform(-10, 10, nt)
-        n = 10
-        L = M.order_from_tail(c, tau, n, eps=1e-3)
+        L = M.order_from_coefficients(c, eps=1e-3)
 
         def ok(L0):
-            return all(abs(np.sum(c[j:] * tau[j:])) <= 1e-3 * n for j in range(max(L0, 1), nt))
+            return np.sum(np.abs(c[L0:])) <= 1e-3
 
-        assert ok(L)
-        assert L == 1 or not ok(L - 1) or L == nt
+        assert ok(L) and 1 <= L <= nt
         assert min(j for j in range(1, nt + 1) if ok(j)) == L
 
 
+def test_order_from_coefficients_geometric_closed_form():
+    # c_j = r^j: the tail from L is (r^L - r^nt) / (1 - r); the order is the smallest L >= 1
+    # with that at most eps
+    for r, nt, eps in ((0.5, 60, 1e-6), (0.9, 400, 2.5e-7), (0.97, 300, 1e-3)):
+        c = r ** np.arange(nt, dtype=np.float64)
+        L = M.order_from_coefficients(c, eps)
+        expect = next(j for j in range(1, nt + 1) if (r ** j - r ** nt) / (1 - r) <= eps * (1 + 1e-12))
+        assert L == expect
+
+
+def test_order_cut_bounds_the_change_of_p():
+    # the bound behind the target: the expansion cut at L* differs from the full one by at
+    # most sum_{j >= L*} |c_j| on every eigenvalue of X in [-1, 1]
+    rng = np.random.default_rng(9)
+    x = np.sort(rng.uniform(-1, 1, 200))
+    c = rng.normal(size=120) * np.exp(-0.08 * np.arange(120))
+    L = M.order_from_coefficients(c, eps=1e-4)
+    full = np.polynomial.chebyshev.chebval(x, c)
+    cut = np.polynomial.chebyshev.chebval(x, c[:L])
+    assert np.max(np.abs(full - cut)) <= np.sum(np.abs(c[L:])) <= 1e-4
+
+
 def test_targets_scale_mu_onto_the_chebyshev_axis():
-    c = np.array([0.5, 0.1, 0.0])
-    tau = np.array([4.0, 0.0, 0.0])
-    t = M.targets(1.0, -3.0, 7.0, c, tau, 4)
+    c = np.array([0.5, 0.1, 0.0, 0.0])
+    t = M.targets(1.0, -3.0, 7.0, c)
     assert t[0] == pytest.approx((2 * 1.0 - 4.0) / 10.0)
     mid, half = 2.0, 5.0
     assert mid + half * t[0] == pytest.approx(1.0)
+    assert t[1] == pytest.approx(0.5)    # c_1 = 0.1 > eps: L* = 2 terms; log2(2) / log2(4)
 
 
 def test_planted_backprop_mistake_is_caught(monkeypatch):
