@@ -798,6 +798,7 @@ def main():
                          "tile_store": results[n]["tile_store"]}
         if n in accuracy:
             per_n[str(n)].update(accuracy[n])
+        if n in fp64_ms:
             per_n[str(n)]["fp64_gpu_ms"] = fp64_ms[n]
     # the float64 path (one call per N, wall time around a synchronised call) against the
     # measured float64 GEMM rate: n_gemm symmetric products of n^2 (n + 1) flops each

@@ -629,10 +629,13 @@ fo_status run_chain(fo_ctx* ctx, Plan& p, const std::vector<Step>& steps, cudaSt
     return FO_OK;
 }
 
-// The product that writes the caller's float64 P (last Clenshaw or Horner step). In the split
-// forms its epilogue also leaves per-tile partials of tr P and ||P||_F^2, and, when the trace
-// correction follows, the planes of P in slot `pslot` (R_0's, read and then overwritten
-// entry by entry, like every Clenshaw step's R_l -> b_l) as the operands of P P.
+// The last Clenshaw or Horner step, which forms P. In the split forms its epilogue also leaves
+// partials of tr P and ||P||_F^2 per 128 x 128 block. Without the trace correction it writes
+// the caller's float64 P. With it, P goes to slot `pslot` instead (R_0's, read and then
+// overwritten entry by entry, like every Clenshaw step's R_l -> b_l): the float32 master on
+// both sides of the diagonal and the 16-bit planes, the operands of the correcting product
+// P P, whose epilogue writes the caller's P from that master (the float64 P of this step is
+// exactly the widening of its float32 values, so nothing is lost).
 void final_step_extras(const Plan& p, Step& st, int pslot) {
     if (p.sh.is64) return;
     st.part = p.part_tc;
@@ -640,6 +643,8 @@ void final_step_extras(const Plan& p, Step& st, int pslot) {
     if (p.fix) {
         st.out = pslot;
         st.planes = p.sh.planes;
+        st.lower_master = 1;
+        st.out64 = 0;
     }
 }
 
@@ -803,12 +808,14 @@ fo_status trace_stage(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int tmode)
 }
 
 // Trace correction of the split forms (after trace_stage with tmode 1 set gamma): the product
-// P P with the float64 epilogue P <- P + gamma (P - P P), the first-order shift of mu that
-// restores tr P = N_e, then the per-instance sum of the new trace and the removal of the
-// product's own float64 residual by the trace projection (k_tile_trace, mode 2).
+// P P whose epilogue writes the caller's float64 P = P + gamma (P - P P) (the first-order shift
+// of mu that restores tr P = N_e; the small term in float32, added in float64), then the
+// per-instance sum of the new trace and the removal of the product's own float64 residual by
+// the trace projection (k_tile_trace, mode 2).
 fo_status trace_fix(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     const int pslot = r_slot(p, 0);
-    Step st = make_step(p, pslot, pslot, -1, -1, -1, 1.0, 0.0, 0.0, false, false, false, true, ctx);
+    // A = B = P (planes), C = P's float32 master (beta 0: read by the correcting epilogue)
+    Step st = make_step(p, pslot, pslot, pslot, -1, -1, 1.0, 0.0, 0.0, false, false, false, true, ctx);
     st.fix64 = 1;
     st.part = p.part_tc;
     st.part_pre = p.wtc[1].dev.pre;

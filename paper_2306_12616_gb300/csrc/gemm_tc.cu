@@ -742,42 +742,35 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
     const double gam = fix ? insts[inst].res->gamma : 0.0;
     const int planes = st.planes;
     const int ew = warp - 2;  // 0..DW-1
-    // float64 result (the caller's P) of the pair (grow, gcol), (grow, gcol + 1) for the
-    // elements whose flag is set: the float32 value itself, or with fix the correction
-    // P + gamma (P - v) of the P already stored there (each element is read and rewritten by
-    // one thread; an element and its mirror hold the same bits, so both get the same result).
-    // Returns in (ta, fa) the written entries' contributions to the trace and to ||P||_F^2
-    // (those on or above the diagonal; strictly above counts twice).
     // Trace and Frobenius partials per (tile row, 128-column block): each (row, 64-column
     // piece) is reduced by a fixed shuffle tree over the lanes and the two pieces of a block
     // are added in column order, so the partials, and the sums over their rows, do not depend
     // on the tile width or on which warp handled the row (every tiling gives the same bits);
     // kept in the idle stage ring after the result tile
     double (*rowpart)[2][2] = reinterpret_cast<double (*)[2][2]>(smem + Cfg::kRowPartOff);
-    auto store64 = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool upper, double& ta,
-                       double& fa) {
-        ta = 0.0;
-        fa = 0.0;
-        if (grow >= n_real) return;
+    const float gam_f = (float)gam;
+    // the caller's float64 P at the pair (grow, gcol), (grow, gcol + 1), for the flagged entries
+    auto store64 = [&](int64_t grow, int64_t gcol, double x0, double x1, bool e0, bool e1) {
         double* dst = out64 + grow * ldo + gcol;
-        const bool e0 = w0 && gcol < n_real, e1 = w1 && gcol + 1 < n_real;
-        double x0 = (double)v0, x1 = (double)v1;
-        if (fix) {
-            if (e0) { const double p = dst[0]; x0 = fma(gam, p - x0, p); }
-            if (e1) { const double p = dst[1]; x1 = fma(gam, p - x1, p); }
-        }
         if (e0) dst[0] = x0;
         if (e1) dst[1] = x1;
-        if (upper) {
-            if (e0) {
-                if (gcol == grow) { ta += x0; fa = fma(x0, x0, fa); }
-                else fa = fma(2.0 * x0, x0, fa);
-            }
-            if (e1) {
-                if (gcol + 1 == grow) { ta += x1; fa = fma(x1, x1, fa); }
-                else fa = fma(2.0 * x1, x1, fa);
-            }
+    };
+    // contributions of the flagged entries (on or above the diagonal) to the trace, in float64,
+    // and to ||P||_F^2 (strictly above counts twice), from their float32 values y: that sum only
+    // sets gamma's denominator tr P - ||P||^2 and the reported ||P||^2, far above float32's
+    // resolution (float64 arithmetic is the scarce pipe of this GPU)
+    auto contrib = [&](int64_t grow, int64_t gcol, double x0, double x1, float y0, float y1, bool e0, bool e1,
+                       double& ta, float& fa) {
+        float f = 0.0f;
+        if (e0) {
+            if (gcol == grow) { ta += x0; f = fmaf(y0, y0, f); }
+            else f = fmaf(2.0f * y0, y0, f);
         }
+        if (e1) {
+            if (gcol + 1 == grow) { ta += x1; f = fmaf(y1, y1, f); }
+            else f = fmaf(2.0f * y1, y1, f);
+        }
+        fa = f;
     };
     // slot store (float32 master and 16-bit planes) of the same pair
     auto store_slot = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool master) {
@@ -867,25 +860,47 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             tile[r * LD + c] = v0;
             tile[r * LD + c + 1] = v1;
             const bool w0 = !sym || gcol >= grow, w1 = !sym || gcol + 1 >= grow;
-            double ta = 0.0, fa = 0.0;
-            if constexpr (F64) store64(grow, gcol, v0, v1, w0, w1, true, ta, fa);
+            double ta = 0.0;   // the diagonal entry, if this lane holds it
+            float fa = 0.0f;
+            if constexpr (F64) {
+                const bool e0 = w0 && grow < n_real && gcol < n_real, e1 = w1 && grow < n_real && gcol + 1 < n_real;
+                double x0 = (double)v0, x1 = (double)v1;
+                float y0 = v0, y1 = v1;
+                if (fix) {
+                    // P is the float32 master C written by the last Clenshaw step (the float64 P it
+                    // stands for is exactly its widening); the correction d = gamma (P - P P), ~1e-7
+                    // of P, in float32, added in float64; the mirror pass adds the same d
+                    const float d0 = gam_f * (cv[u].x - v0), d1 = gam_f * (cv[u].y - v1);
+                    x0 = (double)cv[u].x + (double)d0;
+                    x1 = (double)cv[u].y + (double)d1;
+                    y0 = cv[u].x + d0;
+                    y1 = cv[u].y + d1;
+                    tile[r * LD + c] = d0;
+                    tile[r * LD + c + 1] = d1;
+                }
+                if (out64) store64(grow, gcol, x0, x1, e0, e1);
+                if (st.part) contrib(grow, gcol, x0, x1, y0, y1, e0, e1, ta, fa);
+            }
             store_slot(grow, gcol, v0, v1, w0, w1, true);
             if (F64 && st.part) {
                 // this (row, piece)'s sums (the `continue` above is uniform across the warp:
                 // tile widths are multiples of 128); pieces 2b, 2b + 1 form the tile's
                 // 128-column block b, added in that order by the warp that owns the row
-                for (int o = 16; o > 0; o >>= 1) {
-                    ta += __shfl_xor_sync(0xffffffffu, ta, o);
-                    fa += __shfl_xor_sync(0xffffffffu, fa, o);
-                }
+                // ||P||^2: a float32 shuffle tree over the piece; the trace: the piece holds the
+                // row's diagonal entry at most once, fetched from its lane (float64 work is
+                // this GPU's scarcest: one shuffle instead of a float64 tree)
+                for (int o = 16; o > 0; o >>= 1) fa += __shfl_xor_sync(0xffffffffu, fa, o);
+                const int64_t dcol = grow - (gcol - 2 * lane);   // piece column of the diagonal
+                double tv = 0.0;
+                if (dcol >= 0 && dcol < 64) tv = __shfl_sync(0xffffffffu, ta, (int)(dcol >> 1));
                 if (lane == 0) {
                     double* rp = rowpart[r][h >> 1];
                     if (h & 1) {
-                        rp[0] += ta;
-                        rp[1] += fa;
+                        rp[0] += tv;
+                        rp[1] += (double)fa;
                     } else {
-                        rp[0] = ta;
-                        rp[1] = fa;
+                        rp[0] = tv;
+                        rp[1] = (double)fa;
                     }
                 }
             }
@@ -922,21 +937,30 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         // outside the tile's diagonal block nothing below the diagonal is written, except
         // into the caller's float64 P, which is returned whole
         const bool slot_rows = !(ub && !lower_master && grow >= (int64_t)m0 + kBM);
-        if (!slot_rows && !F64) break;
+        if (!slot_rows && !(F64 && out64)) break;
 #pragma unroll
         for (int h = 0; h < kBM / 64; ++h) {
             const int r = h * 64 + 2 * lane;
             const int64_t gcol = (int64_t)m0 + r;   // output column
             const float v0 = tile[r * LD + c], v1 = tile[(r + 1) * LD + c];
-            if constexpr (F64) {
-                double ta, fa;   // entries below the diagonal: counted twice by their mirrors above
-                store64(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, false, ta, fa);
+            if (F64 && out64) {
+                // entries below the diagonal (counted twice by their mirrors above)
+                const bool e0 = grow > gcol && grow < n_real && gcol < n_real;
+                const bool e1 = grow > gcol + 1 && grow < n_real && gcol + 1 < n_real;
+                if (fix) {
+                    // the lower float32 master of P (written by the last Clenshaw step) + the d of the
+                    // row pass: the bits of the mirrored entry
+                    const float2 pm = *reinterpret_cast<const float2*>(Cm + grow * ld + gcol);
+                    store64(grow, gcol, (double)pm.x + (double)v0, (double)pm.y + (double)v1, e0, e1);
+                } else {
+                    store64(grow, gcol, (double)v0, (double)v1, e0, e1);
+                }
             }
             if (slot_rows) store_slot(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, lower_master);
         }
     }
     };
-    if (out64) passes(std::true_type{});
+    if (out64 || st.part) passes(std::true_type{});
     else passes(std::false_type{});
     if constexpr (CHAIN) {
         // this tile's stores are complete: release them to the next step's tiles (generic
@@ -1037,30 +1061,25 @@ __device__ __forceinline__ void persist_epilogue(const Step& st, const Inst* __r
     const bool fix = out64 && st.fix64;
     const double gam = fix ? in.res->gamma : 0.0;
     const int planes = st.planes;
-    auto store64 = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool upper, double& ta,
-                       double& fa) {
-        ta = 0.0;
-        fa = 0.0;
-        if (grow >= n_real) return;
+    const float gam_f = (float)gam;
+    auto store64 = [&](int64_t grow, int64_t gcol, double x0, double x1, bool e0, bool e1) {
         double* dst = out64 + grow * ldo + gcol;
-        const bool e0 = w0 && gcol < n_real, e1 = w1 && gcol + 1 < n_real;
-        double x0 = (double)v0, x1 = (double)v1;
-        if (fix) {
-            if (e0) { const double p = dst[0]; x0 = fma(gam, p - x0, p); }
-            if (e1) { const double p = dst[1]; x1 = fma(gam, p - x1, p); }
-        }
         if (e0) dst[0] = x0;
         if (e1) dst[1] = x1;
-        if (upper) {
-            if (e0) {
-                if (gcol == grow) { ta += x0; fa = fma(x0, x0, fa); }
-                else fa = fma(2.0 * x0, x0, fa);
-            }
-            if (e1) {
-                if (gcol + 1 == grow) { ta += x1; fa = fma(x1, x1, fa); }
-                else fa = fma(2.0 * x1, x1, fa);
-            }
+    };
+    // trace in float64, ||P||_F^2 from the float32 values (as in k_tc_gemm)
+    auto contrib = [&](int64_t grow, int64_t gcol, double x0, double x1, float y0, float y1, bool e0, bool e1,
+                       double& ta, float& fa) {
+        float f = 0.0f;
+        if (e0) {
+            if (gcol == grow) { ta += x0; f = fmaf(y0, y0, f); }
+            else f = fmaf(2.0f * y0, y0, f);
         }
+        if (e1) {
+            if (gcol + 1 == grow) { ta += x1; f = fmaf(y1, y1, f); }
+            else f = fmaf(2.0f * y1, y1, f);
+        }
+        fa = f;
     };
     auto store_slot = [&](int64_t grow, int64_t gcol, float v0, float v1, bool w0, bool w1, bool master) {
         if (!(w0 || w1) || (!out_x && planes == 0)) return;
@@ -1131,23 +1150,42 @@ __device__ __forceinline__ void persist_epilogue(const Step& st, const Inst* __r
                 tile[r * LD + c] = v0;
                 tile[r * LD + c + 1] = v1;
                 const bool w0 = !sym || gcol >= grow, w1 = !sym || gcol + 1 >= grow;
-                double ta = 0.0, fa = 0.0;
-                if constexpr (F64) store64(grow, gcol, v0, v1, w0, w1, true, ta, fa);
+                double ta = 0.0;   // the diagonal entry, if this lane holds it
+                float fa = 0.0f;
+                if constexpr (F64) {
+                    const bool e0 = w0 && grow < n_real && gcol < n_real, e1 = w1 && grow < n_real && gcol + 1 < n_real;
+                    double x0 = (double)v0, x1 = (double)v1;
+                    float y0 = v0, y1 = v1;
+                    if (fix) {
+                        // P is the float32 master C written by the last Clenshaw step (the float64 P it
+                        // stands for is exactly its widening); the correction d = gamma (P - P P), ~1e-7
+                        // of P, in float32, added in float64; the mirror pass adds the same d
+                        const float d0 = gam_f * (cv[u].x - v0), d1 = gam_f * (cv[u].y - v1);
+                        x0 = (double)cv[u].x + (double)d0;
+                        x1 = (double)cv[u].y + (double)d1;
+                        y0 = cv[u].x + d0;
+                        y1 = cv[u].y + d1;
+                        tile[r * LD + c] = d0;
+                        tile[r * LD + c + 1] = d1;
+                    }
+                    if (out64) store64(grow, gcol, x0, x1, e0, e1);
+                    if (st.part) contrib(grow, gcol, x0, x1, y0, y1, e0, e1, ta, fa);
+                }
                 store_slot(grow, gcol, v0, v1, w0, w1, true);
                 if (F64 && st.part) {
                     // (row, 64-column piece) sums by a fixed shuffle tree; the two pieces of
                     // the row added in column order (the same bits as k_tc_gemm's partials)
-                    for (int o = 16; o > 0; o >>= 1) {
-                        ta += __shfl_xor_sync(0xffffffffu, ta, o);
-                        fa += __shfl_xor_sync(0xffffffffu, fa, o);
-                    }
+                    for (int o = 16; o > 0; o >>= 1) fa += __shfl_xor_sync(0xffffffffu, fa, o);
+                    const int64_t dcol = grow - (gcol - 2 * lane);
+                    double tv = 0.0;
+                    if (dcol >= 0 && dcol < 64) tv = __shfl_sync(0xffffffffu, ta, (int)(dcol >> 1));
                     if (lane == 0) {
                         if (h & 1) {
-                            rowpart[r][0] += ta;
-                            rowpart[r][1] += fa;
+                            rowpart[r][0] += tv;
+                            rowpart[r][1] += (double)fa;
                         } else {
-                            rowpart[r][0] = ta;
-                            rowpart[r][1] = fa;
+                            rowpart[r][0] = tv;
+                            rowpart[r][1] = (double)fa;
                         }
                     }
                 }
@@ -1171,22 +1209,28 @@ __device__ __forceinline__ void persist_epilogue(const Step& st, const Inst* __r
             const int c = ew * (TBN / EW) + cc;
             const int64_t grow = (int64_t)n0 + c;
             const bool slot_rows = !(ub && !lower_master && grow >= (int64_t)m0 + kBM);
-            if (!slot_rows && !F64) break;
+            if (!slot_rows && !(F64 && out64)) break;
 #pragma unroll
             for (int hh = 0; hh < kBM / 64; ++hh) {
                 const int r = hh * 64 + 2 * lane;
                 const int64_t gcol = (int64_t)m0 + r;
                 const float v0 = tile[r * LD + c], v1 = tile[(r + 1) * LD + c];
-                if constexpr (F64) {
-                    double ta, fa;
-                    store64(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, false, ta, fa);
+                if (F64 && out64) {
+                    const bool e0 = grow > gcol && grow < n_real && gcol < n_real;
+                    const bool e1 = grow > gcol + 1 && grow < n_real && gcol + 1 < n_real;
+                    if (fix) {
+                        const float2 pm = *reinterpret_cast<const float2*>(Cm + grow * ld + gcol);
+                        store64(grow, gcol, (double)pm.x + (double)v0, (double)pm.y + (double)v1, e0, e1);
+                    } else {
+                        store64(grow, gcol, (double)v0, (double)v1, e0, e1);
+                    }
                 }
                 if (slot_rows) store_slot(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, lower_master);
             }
         }
         // (the buffer goes back through res_empty, which counts every epilogue thread)
     };
-    if (out64) passes(std::true_type{});
+    if (out64 || st.part) passes(std::true_type{});
     else passes(std::false_type{});
 }
 
