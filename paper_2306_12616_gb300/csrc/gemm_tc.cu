@@ -73,51 +73,8 @@ namespace {
 constexpr int kBM = 128;            // tile rows (UMMA M)
 constexpr int kBK = 32;             // k elements per stage: 64 bytes of 16-bit data per row
 constexpr int kRowBytes = kBK * 2;  // = swizzle span of CU_TENSOR_MAP_SWIZZLE_64B
-constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: a legitimate wait is microseconds
-constexpr uint64_t kDrainNs = 200000000ull;   // 0.2 s for draining after an abort
 
 // ------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait. Returns false when the deadline passes or another role aborted.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
-                          volatile int* abort_flag) {
-    uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u) {
-            if (abort_flag && *abort_flag) return false;
-            const uint64_t t = gtimer();
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > limit_ns) return false;
-        }
-    }
-}
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
                                             int c1, int c2, int c3, int c4) {
     asm volatile(
@@ -263,31 +220,6 @@ struct TcCfg {
 // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0).
 __host__ __device__ constexpr int prod_a(int p) { return p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0); }
 __host__ __device__ constexpr int prod_b(int p) { return p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0); }
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Warp-uniform bounded wait: every lane observes the phase; the exit decision is shared.
-__device__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
-                               volatile int* abort_flag) {
-    const int lane = threadIdx.x & 31;
-    uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        const bool done = mbar_try_wait(bar, parity);
-        if (__all_sync(0xffffffffu, done)) return true;
-        if ((it & 255u) == 255u) {
-            int stop = 0;
-            if (lane == 0) {
-                if (abort_flag && *abort_flag) stop = 1;
-                const uint64_t t = gtimer();
-                if (t0 == 0) t0 = t;
-                else if (t - t0 > limit_ns) stop = 1;
-            }
-            if (__shfl_sync(0xffffffffu, stop, 0)) return false;
-        }
-    }
-}
 
 // Chain launches: bounded wait until *ctr >= need, with acquire semantics at GPU scope (the
 // CTAs that counted released their stores). Gives up, returning false, when another CTA

@@ -227,12 +227,16 @@ __device__ __forceinline__ void store_split(float v, float* x, uint16_t* p, int6
 
 // X = (2H - (emin+emax) I) / (emax - emin) into slot 0 (np x np, zero border), built from
 // the upper triangle of H only, so that X is exactly symmetric. One block per 32 x 32 tile
-// (bi, bj), bj >= bi, of one instance: the H tile is staged in shared memory and written
-// to X at (bi, bj) and, transposed, at (bj, bi). Output float64, or float32 + planes.
+// (bi, bj), bj >= bi, of one instance: the H tile is staged in shared memory, each of its
+// entries is scaled once (float64; off the diagonal as h * (2 / (emax - emin)), which equals
+// (2h) / (emax - emin) rounded once since both factors of 2 are exact) and the scaled tile is
+// written to X at (bi, bj) and, transposed, at (bj, bi). Output float64, or float32 + planes
+// (the float64 pipe of this GPU is narrow: one multiply and one conversion per entry).
 __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ insts,
                                                    const InstIO* __restrict__ io, Work ws,
                                                    const Shape sh, int* dbg) {
     __shared__ double tile[32][33];
+    __shared__ float tf[32][33];
     const int i = find_inst(ws.pre, 0, ws.count, blockIdx.x);
     const int64_t n = insts[i].n, np = insts[i].np, ld = io[i].ldh;
     const double* H = io[i].H;
@@ -242,11 +246,20 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
     while (b >= tn - bi) { b -= tn - bi; ++bi; }
     const int bj = bi + b;
     const double ea = res->bounds[0], eb = res->bounds[1];
-    const double inv = 1.0 / (eb - ea), csum = ea + eb;
+    const double inv = 1.0 / (eb - ea), inv2 = 2.0 * inv, csum = ea + eb;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int ry = ty; ry < 32; ry += 8) {
         const int64_t r = (int64_t)bi * 32 + ry, c = (int64_t)bj * 32 + tx;
         tile[ry][tx] = (r < n && c < n) ? H[r * ld + c] : 0.0;
+    }
+    // each thread scales the entries it loaded (the lower half of a diagonal tile is never
+    // read: it is written from the upper half)
+    for (int ry = ty; ry < 32; ry += 8) {
+        const int64_t r = (int64_t)bi * 32 + ry, c = (int64_t)bj * 32 + tx;
+        double v = 0.0;
+        if (r < n && c < n && (bi != bj || tx >= ry)) v = r == c ? (2.0 * tile[ry][tx] - csum) * inv : tile[ry][tx] * inv2;
+        if (sh.is64) tile[ry][tx] = v;
+        else tf[ry][tx] = (float)v;
     }
     __syncthreads();
     char* slot = insts[i].slots;
@@ -260,27 +273,24 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
         const bool lower = bi != bj && (!sh.ublk || bi * 32 / kPad == bj * 32 / kPad);
         for (int pass = 0; pass < (lower ? 2 : 1); ++pass) {
             int64_t r, c;
-            double h;
+            int tr, tc;   // entry of the scaled tile
             if (pass == 0) {
                 r = (int64_t)bi * 32 + ry;
                 c = (int64_t)bj * 32 + tx;
-                h = (bi == bj && tx < ry) ? tile[tx][ry] : tile[ry][tx];
+                const bool mir = bi == bj && tx < ry;
+                tr = mir ? tx : ry;
+                tc = mir ? ry : tx;
             } else {
                 r = (int64_t)bj * 32 + ry;
                 c = (int64_t)bi * 32 + tx;
-                h = tile[tx][ry];
-            }
-            double v = 0.0;
-            if (r < n && c < n) {
-                v = 2.0 * h;
-                if (r == c) v -= csum;
-                v *= inv;
+                tr = tx;
+                tc = ry;
             }
             const int64_t idx = r * np + c;
             if (!FO_CHK(dbg, r < np && c < np, 201, r, c)) continue;
-            if (sh.is64) X64[idx] = v;
+            if (sh.is64) X64[idx] = tile[tr][tc];
             // below the diagonal only the planes are kept (float32 masters: on and above it)
-            else store_split((float)v, r <= c ? X32 + idx : nullptr, P16 + idx, np * np, sh.planes, sh.fp16,
+            else store_split(tf[tr][tc], r <= c ? X32 + idx : nullptr, P16 + idx, np * np, sh.planes, sh.fp16,
                              sh.pscale_t);
         }
     }
@@ -335,7 +345,7 @@ __global__ void k_diag_sums(const Inst* __restrict__ insts, int is64) {
 // diagonal weigh the baby entries by 1 (the factor 2 of the strict upper triangle is applied
 // once at the end); the diagonal chunk of a row weighs them by 1, 1/2 or 0 right of, on or
 // left of the diagonal. Every lane sums at most kGChunks * kChunk / 32 products per pair in
-// T; lanes are combined by float64 shuffles and blocks by the partial sums (k_sum_partials).
+// T; lanes are combined by shuffles in T and blocks by the float64 partial sums (k_sum_partials).
 constexpr int kChunkBytes = 512;    // one chunk of one matrix: 128 float32 / 64 float64
 constexpr int kGChunks = 64;        // chunks per block
 constexpr int kCPS = 2;             // chunks per stage
@@ -560,11 +570,20 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
         const int tg = tile / nbq, tb = tile % nbq;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const float2 pr = unpack2(acc2[t][q]);
-            double v = sizeof(T) == 4 ? 2.0 * ((double)pr.x + (double)pr.y) : 2.0 * (double)acc[t][q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             const int g = TG * tg + q / TB, b = TB * tb + q % TB;
-            if (lane == 0 && g < ngiant && b < nbaby) partials[(int64_t)lb * npairs + g * nbaby + b] = v;
+            if constexpr (sizeof(T) == 4) {
+                // float32 tree over the lanes: the float64 pipe of this GPU retires about two
+                // lane operations per clock and SM, so a float64 tree per pair would cost more
+                // than the block's loads; one conversion per pair on lane 0
+                const float2 pr = unpack2(acc2[t][q]);
+                float v = pr.x + pr.y;
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && g < ngiant && b < nbaby) partials[(int64_t)lb * npairs + g * nbaby + b] = 2.0 * (double)v;
+            } else {
+                double v = 2.0 * (double)acc[t][q];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && g < ngiant && b < nbaby) partials[(int64_t)lb * npairs + g * nbaby + b] = v;
+            }
         }
     }
 }
