@@ -78,6 +78,9 @@ struct Plan {
     std::vector<Bucket> buckets;
     std::vector<Group> groups;
     std::vector<unsigned char> maps;   // 256 bytes per bucket: K-major and MN-major tensor maps
+    std::vector<GramBucket> gram_bk;   // float32 master geometry of the Frobenius-product kernel
+    std::vector<GramGroup> gram_grp;
+    GramGeom gram_geom{};
     HostWork wg, wsc, we, wr, wgr, wct, wtc[2], wf64;   // wtc[0]: 256-wide tiles, wtc[1]: 128-wide
     int tile_n = 0;
     int tile_ctas = 0;
@@ -513,6 +516,16 @@ fo_status place_plan(fo_ctx* ctx, Plan* p) {
                     return fail(ctx, FO_ERR_CUDA, "tensor map: " + err);
         }
     }
+    // geometry of the float32 masters for the Frobenius products' tensor maps
+    if (!sh.is64 && p->n_slots > 0) {
+        p->gram_bk.clear();
+        for (const Bucket& bk : p->buckets)
+            p->gram_bk.push_back(GramBucket{W + bk.off, bk.np, p->inst[bk.first].slot_bytes, bk.inst_bytes, bk.count});
+        p->gram_grp.clear();
+        for (const Group& g : p->groups) p->gram_grp.push_back(GramGroup{g.b0, g.nb, g.i0, g.i1});
+        p->gram_geom = GramGeom{p->gram_bk.data(), p->gram_grp.data(), (int)p->gram_grp.size(), p->n_slots,
+                                p->wgr.pre.data()};
+    }
     // the cosine table depends on M only (kept in the plan's own device tables)
     cudaError_t e = launch_cos_table(sh.M, p->ct, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -713,7 +726,8 @@ fo_status exact_moments(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     FO_CUDA(launch_diag_sums(p.d_inst, p.batch, sh.n_tslots, sh, s), "diag_sums");
     run->launches += 1;
     if (sh.m > 1 && sh.k > 1)
-        FO_CUDA(launch_gram(p.d_inst, p.batch, p.wgr.dev, sh.k - 1, sh.m - 1, 0, sh.k - 1, 0, sh.is64, s,
+        FO_CUDA(launch_gram(p.d_inst, p.batch, p.wgr.dev, sh.k - 1, sh.m - 1, 0, sh.k - 1, 0, sh.is64,
+                            sh.is64 ? nullptr : &p.gram_geom, ctx->flag, s,
                             &run->launches),
                 "gram");
     FO_CUDA(launch_assemble_moments(p.d_inst, p.batch, sh, s), "moments");
@@ -871,7 +885,8 @@ fo_status propose(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run, int use_order)
     int h = prof_begin(ctx, s, FO_STAGE_MOMENTS);
     int l0 = run->launches;
     FO_CUDA(launch_diag_sums(p.d_inst, B, sh.k, sh, s), "diag_sums");
-    FO_CUDA(launch_gram(p.d_inst, B, p.wgr.dev, sh.k - 1, 1, 0, sh.k, 0, sh.is64, s, &run->launches), "gram");
+    FO_CUDA(launch_gram(p.d_inst, B, p.wgr.dev, sh.k - 1, 1, 0, sh.k, 0, sh.is64,
+                        sh.is64 ? nullptr : &p.gram_geom, ctx->flag, s, &run->launches), "gram");
     FO_CUDA(launch_assemble_low(p.d_inst, B, sh.k, s), "low moments");
     run->launches += 2;
     prof_end(ctx, s, h, 0.0, run->launches - l0);

@@ -1579,6 +1579,23 @@ bool tc_make_map(void* map128, const void* planes0, int64_t np, int nplanes, int
     return true;
 }
 
+bool gram_make_map(void* map128, const GramBucket& b, int nslots, int box_slots, std::string* err) {
+    EncodeFn enc = get_encode(err);
+    if (!enc) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)b.np, (cuuint64_t)b.np, (cuuint64_t)nslots, (cuuint64_t)b.count};
+    cuuint64_t strides[3] = {(cuuint64_t)b.np * 4, (cuuint64_t)b.slot_bytes, (cuuint64_t)b.inst_bytes};
+    cuuint32_t box[4] = {128, 1, (cuuint32_t)box_slots, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap*>(map128), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                     const_cast<char*>(b.master0), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        if (err) *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
 cudaError_t tc_gemm(int prec, int tile_n, int ctas, int drain, const Step* steps, int nsteps, const Inst* in,
                     const InstIO* io, const int* pre, int i0, int i1, int tile0, int tiles, const void* maps, int b0,
                     int nb, int* err_flag, cudaStream_t s, std::string* err, int sym, int persist) {

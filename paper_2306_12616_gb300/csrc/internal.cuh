@@ -348,8 +348,31 @@ cudaError_t launch_scale(const Inst* in, const InstIO* io, Work ws, const Shape&
                          int* dbg);
 cudaError_t launch_diag_sums(const Inst* in, int batch, int count, const Shape& sh, cudaStream_t s);
 // gram[(g0 + g) * nbaby + b] = <slot giant0 + g, slot baby0 + b> for every instance.
+// Geometry of the float32 masters for the tensor maps of the Frobenius-product kernel: per
+// bucket of equally sized instances the master of slot 0 of its first instance, the strides
+// of slots and instances; per launch group (at most kMaxBuckets buckets) its instances.
+struct GramBucket {
+    const char* master0;
+    int64_t np, slot_bytes, inst_bytes;
+    int count;
+};
+struct GramGroup {
+    int b0, nb, i0, i1;   // buckets [b0, b0 + nb) hold instances [i0, i1)
+};
+struct GramGeom {
+    const GramBucket* bk;
+    const GramGroup* grp;
+    int ngroups;
+    int nslots;           // slots per instance
+    const int* pre_host;  // host copy of the Frobenius kernel's unit prefix (Work::pre)
+};
+// 4-D tensor map (column, row, slot, instance) over a bucket's float32 masters, box of 128
+// columns x 1 row x box_slots slots x 1 instance, no swizzle.
+bool gram_make_map(void* map128, const GramBucket& b, int nslots, int box_slots, std::string* err);
+// geom: the tensor-map geometry of float32 masters (null: the cp.async kernel, as for float64)
 cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0,
-                        int nbaby, int out_g0, int is64, cudaStream_t s, int* launches);
+                        int nbaby, int out_g0, int is64, const GramGeom* geom, int* err, cudaStream_t s,
+                        int* launches);
 // tau_0 .. tau_{n_terms-1} from the traces and the Frobenius products.
 cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, cudaStream_t s);
 cudaError_t launch_trace_frob(const Inst* in, const InstIO* io, Work wr, double* part, cudaStream_t s);

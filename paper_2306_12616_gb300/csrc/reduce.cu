@@ -4,6 +4,10 @@
 //
 // All reductions are deterministic: fixed per-thread order, warp shuffles, a fixed tree in
 // shared memory, and per-block partials summed in block order by a final kernel.
+#include <cstring>
+
+#include <cuda.h>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -74,6 +78,12 @@ __global__ void k_set_io(const IoChunk p, InstIO* d_io, const Inst* insts) {
 }
 
 // ------------------------------------------------------------------ Gershgorin bounds
+// Finite test on the bits (exponent field not all ones): integer work, where isfinite()
+// would take a slot of the narrow float64 pipe per entry.
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+}
+
 // One warp per row: r_i = sum_{j != i} |h_ij| (float64, lane-strided, shuffle tree),
 // lo_i = h_ii - r_i, hi_i = h_ii + r_i; per-block (min lo, max hi, any non-finite).
 __global__ void __launch_bounds__(32 * kGershRows) k_gershgorin_rows(const Inst* __restrict__ insts,
@@ -98,13 +108,13 @@ __global__ void __launch_bounds__(32 * kGershRows) k_gershgorin_rows(const Inst*
             for (int u = 0; u < 4; ++u) v[u] = __ldg(r + j + 32 * u);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                bad |= !isfinite(v[u]);
+                bad |= !finite_bits(v[u]);
                 if (j + 32 * u == row) d = v[u]; else s4[u] += fabs(v[u]);
             }
         }
         for (; j < n; j += 32) {
             const double v = __ldg(r + j);
-            bad |= !isfinite(v);
+            bad |= !finite_bits(v);
             if (j == row) d = v; else s4[0] += fabs(v);
         }
         double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
@@ -588,6 +598,279 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     }
 }
 
+// Frobenius products of float32 masters, the same unit partials as k_gram<float>: one
+// partial per (instance, kGChunks upper chunks, pair), written as 2 x the unit's sum with
+// the diagonal entry weighed 1/2. Persistent blocks (one per SM) take the units of one
+// group of tensor-map buckets round-robin. One thread of warp ncons loads each chunk (128
+// consecutive entries of one matrix row) of a stage with two TMA copies, a box of 128
+// columns x 1 row x ngiant slots from the giant matrices and one of nbaby slots from the
+// baby matrices (4-D tensor maps over (column, row, slot, instance) of the float32
+// masters): two copies per chunk instead of one per matrix, since the copy engine's cost
+// per copy, not the bytes, bounded a ring fed by per-matrix bulk copies. The ring is S
+// stages of CPS chunks, laid out (stage, chunk, staged row, entry) with padding rows zero;
+// the copy thread publishes each chunk's diagonal position before it arms the stage's
+// `full` mbarrier, and the consumer warps release a stage through `empty`. Consumer warp w
+// owns the (giant, baby) tile w / H of TG x TB pairs and every H-th 32-entry group of each
+// stage: lane l multiplies entry l of the group in the TG giant rows with the same entry of
+// the TB baby rows, two giant rows per packed FMA (the baby value in both halves), so one
+// staged word feeds TB / 2 or TG packed FMAs. At the end of a unit a warp's sums are
+// reduced over its lanes by halving exchanges (each lane keeps half of what it holds, five
+// times: about 124 shuffles instead of 5 per sum), the H warps of a tile are added through
+// shared memory and the tile's first warp writes the partials. Every wait is bounded; a
+// wait that gives up sets the block's abort flag and the device error flag, the consumers
+// keep to the control flow without computing (so that every named barrier is reached), and
+// the copy thread waits, bounded, for the copies it issued before the block exits.
+constexpr int kRMaxStages = 6;                     // ring depth at most
+constexpr int kRSmemBudget = 200 * 1024;           // ring bytes at most
+constexpr int kRMaxCPS = 8;                        // chunks per stage at most
+constexpr int kRMaxCons = 8;                       // consumer warps
+constexpr int kRThreads = 32 * (kRMaxCons + 1);
+constexpr int kRMaxRows = 64;                      // staged rows (padded groups)
+constexpr int kRChunk = kChunkBytes / 4;           // float32 entries per chunk
+
+struct GramMaps {
+    CUtensorMap g[kMaxBuckets];   // boxes of 128 columns x 1 row x ngiant slots
+    CUtensorMap b[kMaxBuckets];   // boxes of 128 columns x 1 row x nbaby slots
+};
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// (row, chunk of the row) of upper chunk c of an np x np matrix cut into kc-entry chunks
+__device__ __forceinline__ void upper_chunk_pos(int64_t c, int64_t np, int kc, int& row, int& cc) {
+    const int64_t cpr = np / kc;
+    int64_t b = 0, cum = 0;
+    while (cum + (int64_t)kc * (cpr - b) <= c) {
+        cum += (int64_t)kc * (cpr - b);
+        ++b;
+    }
+    const int64_t off = c - cum, per = cpr - b;
+    row = (int)((int64_t)kc * b + off / per);
+    cc = (int)(b + off % per);
+}
+
+// One halving exchange: lanes with `BIT` set keep v[HS..2HS), the others v[0..HS), each
+// adding its partner's copy of the half it keeps (lane ^ BIT); the kept half moves to v[0..HS).
+template <int HS, int BIT>
+__device__ __forceinline__ void halve_lanes(float (&v)[128], int lane) {
+    const bool up = (lane & BIT) != 0;
+#pragma unroll
+    for (int q = 0; q < HS; ++q) {
+        const float send = up ? v[q] : v[q + HS];
+        const float keep = up ? v[q + HS] : v[q];
+        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, BIT);
+    }
+}
+
+template <int TG, int TB>
+__global__ void __launch_bounds__(kRThreads, 1)
+    k_gram_ring(const __grid_constant__ GramMaps maps, const Inst* __restrict__ insts, Work wgr, int u0, int u1,
+                int b0, int giant0, int ngiant, int baby0, int nbaby, int H, int S, int CPS, int* err) {
+    static_assert(TG % 2 == 0 && TG * TB <= 128, "tile");
+    constexpr int NP = TG * TB;
+    constexpr int RS = kRChunk;                         // row stride of the ring (floats)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ngq = (ngiant + TG - 1) / TG, nbq = (nbaby + TB - 1) / TB;
+    const int R = TG * ngq + TB * nbq;                  // staged rows; padding rows stay zero
+    const int ncons = ngq * nbq * H;
+    const int chunk_floats = R * RS;
+    const int stage_floats = CPS * chunk_floats;
+    // the ring starts on a 1024-byte boundary (every TMA destination is then 512-byte aligned)
+    unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    float* ring = reinterpret_cast<float*>(sm);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)S * stage_floats * 4);
+    uint64_t* empty = full + kRMaxStages;
+    float* red = reinterpret_cast<float*>(empty + kRMaxStages);   // [ncons][32 lanes][4]
+    // per stage and chunk: (row, first column) when the chunk holds its row's diagonal entry
+    // (the row's first upper chunk), else row -1
+    __shared__ int2 s_diag[kRMaxStages][kRMaxCPS];
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bro0 = TG * ngq;                          // first baby row of a chunk
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], ncons);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int q = threadIdx.x; q < S * stage_floats; q += blockDim.x) {
+        const int j = (q / RS) % R;
+        if ((j >= ngiant && j < bro0) || j >= bro0 + nbaby) ring[q] = 0.0f;
+    }
+    __syncthreads();
+
+    const int nreal = ngiant + nbaby;
+    volatile int* va = &s_abort;
+    // warp-uniform view of the abort flag (lane 0 reads it)
+    auto aborted = [&]() -> bool {
+        int a = 0;
+        if (lane == 0) a = *va;
+        return __shfl_sync(0xffffffffu, a, 0) != 0;
+    };
+    // ring position: slot and the parity of its current use
+    int slot = 0;
+    uint32_t phase = 0;
+    if (warp == ncons) {
+        // ---------------------------------------------------------------- copy thread
+        if (lane != 0) return;
+        int64_t issued = 0;                 // stages whose copies were issued
+        bool stop = false;
+        for (int u = u0 + blockIdx.x; u < u1 && !stop; u += gridDim.x) {
+            const int i = find_inst(wgr.pre, 0, wgr.count, u);
+            const Inst& in = insts[i];
+            if (!in.res->active) continue;
+            const int64_t np = in.np, nchunks = upper_chunks(np, kRChunk);
+            const int cpr = (int)(np / kRChunk);
+            const int64_t c0 = (int64_t)(u - wgr.pre[i]) * kGChunks;
+            const int nch = (int)((c0 + kGChunks < nchunks ? c0 + kGChunks : nchunks) - c0);
+            const CUtensorMap* mg = &maps.g[in.bucket - b0];
+            const CUtensorMap* mb = &maps.b[in.bucket - b0];
+            int row, cc;
+            upper_chunk_pos(c0, np, kRChunk, row, cc);
+            for (int st = 0; st * CPS < nch; ++st) {
+                if (issued >= S && !mbar_wait(&empty[slot], phase ^ 1u, kWaitNs, va)) {
+                    *va = 1;
+                    atomicExch(err, 1);
+                }
+                if (*va) {
+                    stop = true;
+                    break;
+                }
+                const int nc = nch - st * CPS < CPS ? nch - st * CPS : CPS;
+                mbar_expect_tx(&full[slot], (uint32_t)(nc * nreal * kChunkBytes));
+                float* dst = ring + (size_t)slot * stage_floats;
+                for (int q = 0; q < nc; ++q, dst += chunk_floats) {
+                    s_diag[slot][q] = make_int2(cc == row / kRChunk ? row : -1, cc * kRChunk);
+                    tma_load_4d(dst, mg, &full[slot], cc * kRChunk, row, giant0, in.in_bucket);
+                    tma_load_4d(dst + bro0 * RS, mb, &full[slot], cc * kRChunk, row, baby0, in.in_bucket);
+                    if (++cc == cpr) cc = ++row / kRChunk;
+                }
+                ++issued;
+                if (++slot == S) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+        // an aborted block waits for the copies it issued before it exits
+        if (*va) {
+            for (int64_t g = issued > S ? issued - S : 0; g < issued; ++g)
+                mbar_wait(&full[g % S], (uint32_t)(g / S) & 1u, kDrainNs, nullptr);
+        }
+        return;
+    }
+    if (warp > ncons) return;
+
+    // -------------------------------------------------------------------- consumers
+    const int tile = warp / H, hh = warp % H;
+    const int gro = TG * (tile / nbq), bro = bro0 + TB * (tile % nbq);
+    f32x2 acc[TG / 2][TB];
+#pragma unroll
+    for (int a = 0; a < TG / 2; ++a)
+#pragma unroll
+        for (int b = 0; b < TB; ++b) acc[a][b] = 0ull;
+    for (int u = u0 + blockIdx.x; u < u1; u += gridDim.x) {
+        const int i = find_inst(wgr.pre, 0, wgr.count, u);
+        const Inst& in = insts[i];
+        if (!in.res->active) continue;
+        const int64_t nchunks = upper_chunks(in.np, kRChunk);
+        const int lb = u - wgr.pre[i];
+        const int64_t c0 = (int64_t)lb * kGChunks;
+        const int nch = (int)((c0 + kGChunks < nchunks ? c0 + kGChunks : nchunks) - c0);
+        for (int st = 0; st * CPS < nch; ++st) {
+            const bool ok = !aborted() && mbar_wait_warp(&full[slot], phase, kWaitNs, va);
+            if (!ok && lane == 0 && !*va) {
+                *va = 1;
+                atomicExch(err, 1);
+            }
+            const int nc = nch - st * CPS < CPS ? nch - st * CPS : CPS;
+            if (ok) {
+                const int sbase = slot * stage_floats;
+                const int gi = sbase + gro * RS + lane, bi = sbase + bro * RS + lane;
+                for (int q = hh; q < nc * (kRChunk / 32); q += H) {
+                    const int off = (q >> 2) * chunk_floats + (q & 3) * 32;   // chunk q / 4, group q % 4
+                    float gv[TG], bv[TB];
+#pragma unroll
+                    for (int a = 0; a < TG; ++a) gv[a] = ring[gi + a * RS + off];
+#pragma unroll
+                    for (int b = 0; b < TB; ++b) bv[b] = ring[bi + b * RS + off];
+                    const int2 dg = s_diag[slot][q >> 2];
+                    if (dg.x >= 0) {
+                        // left of the diagonal the words are stale: select, never multiply
+                        const int col = dg.y + (q & 3) * 32 + lane;
+                        const float wb = col > dg.x ? 1.0f : 0.5f;
+#pragma unroll
+                        for (int b = 0; b < TB; ++b) bv[b] = col >= dg.x ? wb * bv[b] : 0.0f;
+#pragma unroll
+                        for (int a = 0; a < TG; ++a) gv[a] = col >= dg.x ? gv[a] : 0.0f;
+                    }
+#pragma unroll
+                    for (int b = 0; b < TB; ++b) {
+                        const f32x2 bb = pack2(bv[b], bv[b]);
+#pragma unroll
+                        for (int a = 0; a < TG / 2; ++a) ffma2(acc[a][b], pack2(gv[2 * a], gv[2 * a + 1]), bb);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (++slot == S) {
+                slot = 0;
+                phase ^= 1u;
+            }
+        }
+
+        // unit end: halving exchanges over the lanes; lane l keeps entries base(l) + 0..3
+        float v[128];
+#pragma unroll
+        for (int q = 0; q < 128; ++q) {
+            if (q < NP) {
+                const float2 pr = unpack2(acc[(q / TB) / 2][q % TB]);
+                v[q] = ((q / TB) & 1) ? pr.y : pr.x;
+            } else {
+                v[q] = 0.0f;
+            }
+        }
+        halve_lanes<64, 16>(v, lane);
+        halve_lanes<32, 8>(v, lane);
+        halve_lanes<16, 4>(v, lane);
+        halve_lanes<8, 2>(v, lane);
+        halve_lanes<4, 1>(v, lane);
+        const int base = ((lane >> 4) & 1) * 64 + ((lane >> 3) & 1) * 32 + ((lane >> 2) & 1) * 16 +
+                         ((lane >> 1) & 1) * 8 + (lane & 1) * 4;
+        if (H > 1) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) red[(warp * 32 + lane) * 4 + j] = v[j];
+            asm volatile("bar.sync 1, %0;" ::"r"(ncons * 32) : "memory");
+        }
+        if (hh == 0) {
+            const int npairs = ngiant * nbaby;
+            double* partials = in.gpart + (int64_t)lb * npairs;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float sum = v[j];
+                for (int w = 1; w < H; ++w) sum += red[((warp + w) * 32 + lane) * 4 + j];
+                const int q = base + j;
+                const int ga = gro + q / TB, b = (bro - bro0) + q % TB;
+                if (q < NP && ga < ngiant && b < nbaby) partials[ga * nbaby + b] = (double)(2.0f * sum);
+            }
+        }
+        if (H > 1) asm volatile("bar.sync 1, %0;" ::"r"(ncons * 32) : "memory");
+#pragma unroll
+        for (int a = 0; a < TG / 2; ++a)
+#pragma unroll
+            for (int b = 0; b < TB; ++b) acc[a][b] = 0ull;
+    }
+}
+
 // gram[out0 + pq] = sum over the instance's blocks of partial pq, in a fixed order; one
 // block per (pair, instance), threads strided over the partials.
 __global__ void k_sum_partials(const Inst* __restrict__ insts, int npairs, int out0) {
@@ -895,10 +1178,117 @@ int gram_shape(int ngiant, int nbaby) {
     return best;
 }
 
+// Register tiles of the float32 ring kernel (TG giant x TB baby rows per warp).
+constexpr int kRingShapes[][2] = {{10, 10}, {8, 10}, {8, 9}, {10, 8}, {8, 8}, {6, 10}, {4, 10}, {2, 10}};
+constexpr int kNumRingShapes = (int)(sizeof(kRingShapes) / sizeof(kRingShapes[0]));
+
+// Giant row groups one ring launch takes for a tile shape: the tiles fit the consumer warps
+// and the staged rows fit the ring; 0 when the babies alone do not fit.
+int ring_groups_per_launch(int tg, int tb, int ngiant, int nbaby) {
+    const int ngq = (ngiant + tg - 1) / tg, nbq = (nbaby + tb - 1) / tb;
+    int g = kRMaxCons / nbq;
+    if (g > (kRMaxRows - tb * nbq) / tg) g = (kRMaxRows - tb * nbq) / tg;
+    if (g > ngq) g = ngq;
+    return g < 1 ? 0 : g;
+}
+
+// Tile shape of the ring kernel for ngiant x nbaby pairs: the fewest launches (each launch
+// reads every baby matrix once more), then the fewest multiply slots (padding rows cost
+// FMAs and shared reads), then the fewest staged rows. -1 when none fits.
+int gram_ring_shape(int ngiant, int nbaby) {
+    int best = -1;
+    long bl = 0, bs = 0, br = 0;
+    for (int i = 0; i < kNumRingShapes; ++i) {
+        const int tg = kRingShapes[i][0], tb = kRingShapes[i][1];
+        const int gp = ring_groups_per_launch(tg, tb, ngiant, nbaby);
+        if (gp == 0) continue;
+        const int ngq = (ngiant + tg - 1) / tg, nbq = (nbaby + tb - 1) / tb;
+        const long l = (ngq + gp - 1) / gp, slots = (long)ngq * nbq * tg * tb, rows = (long)tg * ngq + tb * nbq;
+        if (best < 0 || l < bl || (l == bl && (slots < bs || (slots == bs && rows < br)))) {
+            best = i;
+            bl = l;
+            bs = slots;
+            br = rows;
+        }
+    }
+    return best;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <int TG, int TB>
+cudaError_t launch_gram_ring(const Inst* in, int batch, Work wgr, const GramGeom& geom, int giant0, int ngiant,
+                             int baby0, int nbaby, int out_g0, int* err, cudaStream_t s, int* launches) {
+    const int gmax = TG * ring_groups_per_launch(TG, TB, ngiant, nbaby);
+    if (gmax <= 0) return cudaErrorInvalidValue;
+    const int nbq = (nbaby + TB - 1) / TB;
+    for (int g = 0; g < ngiant; g += gmax) {
+        const int ng = ngiant - g < gmax ? ngiant - g : gmax;
+        const int ngq = (ng + TG - 1) / TG, tiles = ngq * nbq;
+        const int H = tiles == 1 ? 8 : (tiles == 2 ? 4 : (tiles <= 4 ? 2 : 1));
+        const int ncons = tiles * H;
+        const int rows = TG * ngq + TB * nbq;
+        // chunks per stage: as many as leave a ring of two stages in the budget
+        int CPS = kRMaxCPS;
+        while (CPS > 1 && (int)(kRSmemBudget / ((size_t)rows * CPS * kChunkBytes)) < 2) --CPS;
+        const size_t stage_bytes = (size_t)rows * CPS * kChunkBytes;
+        int S = (int)(kRSmemBudget / stage_bytes);
+        if (S > kRMaxStages) S = kRMaxStages;
+        if (S < 2) return cudaErrorInvalidValue;
+        const size_t smem = 1024 + (size_t)S * stage_bytes + 2 * kRMaxStages * sizeof(uint64_t) +
+                            (size_t)ncons * 32 * 4 * sizeof(float);
+        cudaFuncSetAttribute(k_gram_ring<TG, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        for (int q = 0; q < geom.ngroups; ++q) {
+            const GramGroup& gr = geom.grp[q];
+            GramMaps maps;
+            std::memset(&maps, 0, sizeof(maps));
+            for (int b = 0; b < gr.nb; ++b) {
+                const GramBucket& bk = geom.bk[gr.b0 + b];
+                if (!gram_make_map(&maps.g[b], bk, geom.nslots, ng, nullptr) ||
+                    !gram_make_map(&maps.b[b], bk, geom.nslots, nbaby, nullptr))
+                    return cudaErrorInvalidValue;
+            }
+            const int u0 = geom.pre_host[gr.i0], u1 = geom.pre_host[gr.i1];
+            if (u1 <= u0) continue;
+            const int grid = u1 - u0 < sm_count() ? u1 - u0 : sm_count();
+            k_gram_ring<TG, TB><<<grid, 32 * (ncons + 1), smem, s>>>(maps, in, wgr, u0, u1, gr.b0, giant0 + g, ng,
+                                                                     baby0, nbaby, H, S, CPS, err);
+            if (launches) *launches += 1;
+        }
+        const int npairs = ng * nbaby;
+        k_sum_partials<<<dim3(npairs, batch), 128, 0, s>>>(in, npairs, (out_g0 + g) * nbaby);
+        if (launches) *launches += 1;
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngiant, int baby0, int nbaby,
-                        int out_g0, int is64, cudaStream_t s, int* launches) {
+                        int out_g0, int is64, const GramGeom* geom, int* err, cudaStream_t s, int* launches) {
     if (ngiant <= 0 || nbaby <= 0) return cudaSuccess;
     if (nbaby > 32) return cudaErrorInvalidValue;
+    if (!is64 && geom) {
+        switch (gram_ring_shape(ngiant, nbaby)) {
+            case 0: return launch_gram_ring<10, 10>(in, batch, wgr, *geom, giant0, ngiant, baby0, nbaby, out_g0, err, s, launches);
+            case 1: return launch_gram_ring<8, 10>(in, batch, wgr, *geom, giant0, ngiant, baby0, nbaby, out_g0, err, s, launches);
+            case 2: return launch_gram_ring<8, 9>(in, batch, wgr, *geom, giant0, ngiant, baby0, nbaby, out_g0, err, s, launches);
+            case 3: return launch_gram_ring<10, 8>(in, batch, wgr, *geom, giant0, ngiant, baby0, nbaby, out_g0, err, s, launches);
+            case 4: return launch_gram_ring<8, 8>(in, batch, wgr, *geom, giant0, ngiant, baby0, nbaby, out_g0, err, s, launches);
+            case 5: return launch_gram_ring<6, 10>(in, batch, wgr, *geom, giant0, ngiant, baby0, nbaby, out_g0, err, s, launches);
+            case 6: return launch_gram_ring<4, 10>(in, batch, wgr, *geom, giant0, ngiant, baby0, nbaby, out_g0, err, s, launches);
+            case 7: return launch_gram_ring<2, 10>(in, batch, wgr, *geom, giant0, ngiant, baby0, nbaby, out_g0, err, s, launches);
+            default: break;   // no shape fits: the cp.async kernel below
+        }
+    }
     switch (gram_shape(ngiant, nbaby)) {
         case 1: return launch_gram_shape<5, 5, 1>(in, batch, wgr, giant0, ngiant, baby0, nbaby, out_g0, is64, s, launches);
         case 2: return launch_gram_shape<4, 5, 1>(in, batch, wgr, giant0, ngiant, baby0, nbaby, out_g0, is64, s, launches);
