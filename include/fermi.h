@@ -326,12 +326,27 @@ fo_status fo_density_matrix_host(fo_ctx *ctx, const double *hH, int64_t n, int64
  * batch, copies every P back to hP[b] (hP[b][n[b] x n[b], ldp[b]]), then synchronises.
  * Rows of one instance that are contiguous (ld[b] == n[b]) move as one linear copy; pinned
  * host memory makes the copies asynchronous. Arguments as in fo_density_matrix_batched.
+ *
+ * The copies run on two streams of the context (host to device, device to host) into one of
+ * two device staging slots used in turn; the solve runs on `stream` after its inputs have
+ * arrived, and the copy back waits for the solve. With FO_FLAG_NO_RESULT_SYNC the call
+ * returns once everything is enqueued (res is left untouched): consecutive calls then
+ * overlap the input copy of one call and the output copy of the previous one with a solve.
+ * The caller keeps hH[b] unchanged and reads hP[b] only after fo_host_wait; a call reuses
+ * a staging slot after the copies of the call two before it have finished.
  */
 fo_status fo_density_matrix_batched_host(fo_ctx *ctx, int32_t batch, const double *const *hH,
                                          const int64_t *n, const int64_t *ld, const double *n_e,
                                          const double *kT, const fo_params *params,
                                          double *const *hP, const int64_t *ldp, fo_result *res,
                                          void *stream);
+
+/*
+ * Waits until every host-buffer call of the context has finished, its results copied to the
+ * host buffers. Returns FO_OK, FO_ERR_DEVICE_TIMEOUT when a kernel of the last call gave up
+ * a bounded wait (each call clears the device flag when it starts), or FO_ERR_CUDA.
+ */
+fo_status fo_host_wait(fo_ctx *ctx);
 
 /*
  * Chebyshev moments tau_j = tr T_j(X), j < n_moments, of the scaled Hamiltonian on the

@@ -21,7 +21,8 @@ __all__ = [
     "FoParams", "FoResult", "FermiError", "lib", "library_path", "EXPORTED_SYMBOLS",
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_chebyshev_coeffs", "fo_density_matrix", "fo_density_matrix_host",
-    "fo_density_matrix_batched", "fo_density_matrix_batched_host", "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
+    "fo_density_matrix_batched", "fo_density_matrix_batched_host", "fo_host_wait", "fo_moments",
+    "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "FoProfile",
     "fo_spectral_bounds_noalloc", "FO_NOALLOC_MAX_N", "fo_learned_features", "fo_mlp_init",
     "fo_mlp_set_params", "fo_mlp_get_params", "fo_mlp_forward", "fo_mlp_gradients", "fo_mlp_train",
     "fo_mlp_save", "fo_mlp_load", "FO_MLP_INPUTS", "FO_MLP_OUTPUTS", "FO_MLP_PARAMS", "FO_MLP_NORM",
@@ -48,8 +49,8 @@ MU_MODES = {"fixed": FO_MU_FIXED, "bisect": FO_MU_BISECT, "learned": FO_MU_LEARN
 EXPORTED_SYMBOLS = (
     "fo_create", "fo_destroy", "fo_last_error", "fo_status_string", "fo_version",
     "fo_spectral_bounds", "fo_spectral_bounds_noalloc", "fo_chebyshev_coeffs", "fo_density_matrix",
-    "fo_density_matrix_host", "fo_density_matrix_batched", "fo_density_matrix_batched_host", "fo_moments",
-    "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "fo_learned_features", "fo_mlp_init",
+    "fo_density_matrix_host", "fo_density_matrix_batched", "fo_density_matrix_batched_host", "fo_host_wait",
+    "fo_moments", "fo_recurrence_product", "fo_profile_enable", "fo_profile_read", "fo_learned_features", "fo_mlp_init",
     "fo_mlp_set_params", "fo_mlp_get_params", "fo_mlp_forward", "fo_mlp_gradients", "fo_mlp_train",
     "fo_mlp_save", "fo_mlp_load",
 )
@@ -148,6 +149,7 @@ def lib() -> ctypes.CDLL:
             "fo_density_matrix_batched_host": (ctypes.c_int, [_c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                                               _c_ptr, ctypes.POINTER(FoParams), _c_ptr,
                                                               _c_ptr, _c_ptr, _c_ptr]),
+            "fo_host_wait": (ctypes.c_int, [_c_ptr]),
             "fo_learned_features": (ctypes.c_int, [_c_ptr, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                                    ctypes.POINTER(FoParams), _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
             "fo_mlp_init": (ctypes.c_int, [_c_ptr, ctypes.c_uint64]),
@@ -240,6 +242,10 @@ def fo_density_matrix_batched_host(ctx, batch, h_h_ptrs, n, ld, n_e, kT, params:
                                    ldp, results, stream=0) -> int:
     return lib().fo_density_matrix_batched_host(ctx, batch, h_h_ptrs, n, ld, n_e, kT, ctypes.byref(params),
                                                 h_p_ptrs, ldp, results, stream)
+
+
+def fo_host_wait(ctx) -> int:
+    return lib().fo_host_wait(ctx)
 
 
 def fo_learned_features(ctx, batch, d_h_ptrs, n, ld, n_e, kT, params: FoParams, d_feat, d_target,
@@ -402,7 +408,9 @@ class Solver:
         return ps, ([r.as_dict() for r in res] if res is not None else None)
 
     def density_matrix_batched_host(self, hs, n_e, params: FoParams, outs, kT=None, stream=None):
-        """hs, outs: CPU float64 tensors (pinned for asynchronous copies). Returns result dicts."""
+        """hs, outs: CPU float64 tensors (pinned for asynchronous copies). Returns result dicts;
+        with FO_FLAG_NO_RESULT_SYNC in params the call only enqueues its copies and solve (the
+        dicts are then not filled): keep hs unchanged and read outs after host_wait()."""
         B = len(hs)
         ptr, i64, dbl = ctypes.c_void_p * B, ctypes.c_int64 * B, ctypes.c_double * B
         res = (FoResult * B)()
@@ -412,6 +420,10 @@ class Solver:
             dbl(*[float(x) for x in kT]) if kT is not None else None, params,
             ptr(*[o.data_ptr() for o in outs]), i64(*[o.stride(0) for o in outs]), res, _stream_handle(stream)))
         return [r.as_dict() for r in res]
+
+    def host_wait(self):
+        """Waits for every host-buffer call of this solver (fo_host_wait)."""
+        self._check(fo_host_wait(self.ctx))
 
     # ------------------------------------------------------------ learned mu
     def learned_features(self, hs, n_e, params: FoParams, kT=None, stream=None):

@@ -133,8 +133,16 @@ struct fo_ctx {
     void* ws = nullptr;        // device workspace shared by the plans
     size_t ws_bytes = 0;
     uint64_t ws_gen = 1;       // bumped when the workspace moves (cached plans go stale)
-    void* stage = nullptr;     // device staging for the host-buffer entry point
-    size_t stage_bytes = 0;
+    // host-buffer entry point: two device staging slots used in turn, copy streams
+    struct HostSlot {
+        void* buf = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t in = nullptr, done = nullptr, out = nullptr;   // inputs copied, solved, outputs copied
+        bool used = false;
+    };
+    HostSlot hslot[2];
+    int hnext = 0;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
     int* flag = nullptr;       // [0] tensor-core wait timeout, [1..3] self-check record
     std::vector<std::unique_ptr<Plan>> plans;   // most recently used last
     DevResult* hres = nullptr; // pinned readback buffer
@@ -1542,7 +1550,13 @@ fo_status fo_destroy(fo_ctx* ctx) {
         ctx->plans.clear();
         for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
         if (ctx->ws) cudaFree(ctx->ws);
-        if (ctx->stage) cudaFree(ctx->stage);
+        for (auto& hs : ctx->hslot) {
+            if (hs.buf) cudaFree(hs.buf);
+            for (cudaEvent_t e : {hs.in, hs.done, hs.out})
+                if (e) cudaEventDestroy(e);
+        }
+        if (ctx->h2d) cudaStreamDestroy(ctx->h2d);
+        if (ctx->d2h) cudaStreamDestroy(ctx->d2h);
         if (ctx->flag) cudaFree(ctx->flag);
         if (ctx->hres) cudaFreeHost(ctx->hres);
         if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -1635,6 +1649,16 @@ fo_status fo_density_matrix_batched_host(fo_ctx* ctx, int32_t batch, const doubl
             return fail(ctx, FO_ERR_ARG, "bad instance arguments");
     DeviceGuard g(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool async = (params->flags & FO_FLAG_NO_RESULT_SYNC) != 0;
+    if (!ctx->h2d) {
+        FO_CUDA(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking), "copy stream");
+        FO_CUDA(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking), "copy stream");
+        for (auto& hs : ctx->hslot)
+            for (cudaEvent_t* e : {&hs.in, &hs.done, &hs.out})
+                FO_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "copy event");
+    }
+    fo_ctx::HostSlot& hs = ctx->hslot[ctx->hnext];
+    ctx->hnext ^= 1;
     // device staging: H and P of every instance, densely packed
     std::vector<size_t> off(batch);
     size_t total = 0;
@@ -1642,50 +1666,72 @@ fo_status fo_density_matrix_batched_host(fo_ctx* ctx, int32_t batch, const doubl
         off[b] = total;
         total += 2 * align256((size_t)n[b] * n[b] * 8);
     }
-    if (ctx->stage_bytes < total) {
-        if (ctx->stage) {
-            cudaDeviceSynchronize();
-            cudaFree(ctx->stage);
-            ctx->stage = nullptr;
-            ctx->stage_bytes = 0;
+    if (hs.bytes < total) {
+        if (hs.buf) {
+            FO_CUDA(cudaEventSynchronize(hs.out), "staging slot");
+            cudaFree(hs.buf);
+            hs.buf = nullptr;
+            hs.bytes = 0;
         }
-        if (cudaMalloc(&ctx->stage, total) != cudaSuccess) {
+        if (cudaMalloc(&hs.buf, total) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, FO_ERR_NOMEM, "staging allocation failed");
         }
-        ctx->stage_bytes = total;
+        hs.bytes = total;
+        hs.used = false;
     }
+    // the slot's previous outputs have left (and its previous solve has finished) before its
+    // inputs are overwritten
+    if (hs.used) FO_CUDA(cudaStreamWaitEvent(ctx->h2d, hs.out, 0), "slot wait");
     std::vector<const double*> dH(batch);
     std::vector<double*> dP(batch);
     std::vector<int64_t> ldn(n, n + batch);
-    char* base = reinterpret_cast<char*>(ctx->stage);
+    char* base = reinterpret_cast<char*>(hs.buf);
     for (int b = 0; b < batch; ++b) {
         double* h = reinterpret_cast<double*>(base + off[b]);
         dH[b] = h;
         dP[b] = reinterpret_cast<double*>(base + off[b] + align256((size_t)n[b] * n[b] * 8));
         const int64_t l = ld ? ld[b] : n[b];
         if (l == n[b])   // contiguous rows: one linear copy
-            FO_CUDA(cudaMemcpyAsync(h, hH[b], (size_t)n[b] * n[b] * 8, cudaMemcpyHostToDevice, st), "H2D");
+            FO_CUDA(cudaMemcpyAsync(h, hH[b], (size_t)n[b] * n[b] * 8, cudaMemcpyHostToDevice, ctx->h2d), "H2D");
         else
-            FO_CUDA(cudaMemcpy2DAsync(h, n[b] * 8, hH[b], l * 8, n[b] * 8, n[b], cudaMemcpyHostToDevice, st),
+            FO_CUDA(cudaMemcpy2DAsync(h, n[b] * 8, hH[b], l * 8, n[b] * 8, n[b], cudaMemcpyHostToDevice, ctx->h2d),
                     "H2D");
     }
+    FO_CUDA(cudaEventRecord(hs.in, ctx->h2d), "copy event");
+    FO_CUDA(cudaStreamWaitEvent(st, hs.in, 0), "inputs wait");
     fo_params prm = *params;
-    prm.flags &= ~FO_FLAG_NO_RESULT_SYNC;
+    if (!async) prm.flags &= ~FO_FLAG_NO_RESULT_SYNC;
     std::vector<fo_result> local(batch);
     fo_status s = density_batch(ctx, batch, dH.data(), n, ldn.data(), n_e, kT, &prm, dP.data(), ldn.data(),
                                 res ? res : local.data(), st);
     if (s != FO_OK && s != FO_ERR_NOT_CONVERGED) return s;
+    FO_CUDA(cudaEventRecord(hs.done, st), "solve event");
+    FO_CUDA(cudaStreamWaitEvent(ctx->d2h, hs.done, 0), "solve wait");
     for (int b = 0; b < batch; ++b) {
         const int64_t l = ldp ? ldp[b] : n[b];
         if (l == n[b])
-            FO_CUDA(cudaMemcpyAsync(hP[b], dP[b], (size_t)n[b] * n[b] * 8, cudaMemcpyDeviceToHost, st), "D2H");
+            FO_CUDA(cudaMemcpyAsync(hP[b], dP[b], (size_t)n[b] * n[b] * 8, cudaMemcpyDeviceToHost, ctx->d2h), "D2H");
         else
-            FO_CUDA(cudaMemcpy2DAsync(hP[b], l * 8, dP[b], n[b] * 8, n[b] * 8, n[b], cudaMemcpyDeviceToHost, st),
+            FO_CUDA(cudaMemcpy2DAsync(hP[b], l * 8, dP[b], n[b] * 8, n[b] * 8, n[b], cudaMemcpyDeviceToHost,
+                                      ctx->d2h),
                     "D2H");
     }
-    FO_CUDA(cudaStreamSynchronize(st), "sync");
+    FO_CUDA(cudaEventRecord(hs.out, ctx->d2h), "copy event");
+    hs.used = true;
+    if (!async) FO_CUDA(cudaEventSynchronize(hs.out), "sync");
     return s;
+}
+
+fo_status fo_host_wait(fo_ctx* ctx) {
+    if (!ctx) return FO_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    for (auto& hs : ctx->hslot)
+        if (hs.used) FO_CUDA(cudaEventSynchronize(hs.out), "host wait");
+    int flag = 0;
+    FO_CUDA(cudaMemcpy(&flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost), "flag readback");
+    if (flag) return fail(ctx, FO_ERR_DEVICE_TIMEOUT, "a kernel gave up a bounded wait");
+    return FO_OK;
 }
 
 fo_status fo_density_matrix_host(fo_ctx* ctx, const double* hH, int64_t n, int64_t ld, double n_e,

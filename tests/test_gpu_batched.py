@@ -16,7 +16,7 @@ import torch
 
 import oracle as O
 import synth
-from paper_2306_12616_gb300 import FO_FLAG_GRAPH
+from paper_2306_12616_gb300 import FO_FLAG_GRAPH, FO_FLAG_NO_RESULT_SYNC, FoParams
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -171,3 +171,28 @@ def test_batched_host_buffers_equal_device_buffers(solver):
     rh = solver.density_matrix_batched_host(hin, [n / 2 for n in ns], prm, outs, kT=kts)
     for a, b, x, y in zip(pd, outs, rd, rh):
         assert torch.equal(a.cpu(), b) and x["mu"] == y["mu"]
+
+
+def test_pipelined_host_calls_equal_synchronous_calls(solver):
+    """Host-buffer calls enqueued back to back (FO_FLAG_NO_RESULT_SYNC: the copies of
+    neighbouring calls overlap the solves, on two staging slots used in turn) give the same
+    bits as synchronous calls; four calls cycle both slots twice, with different inputs."""
+    prm = solver.params(300, 0.1, precision="bf16x3", mu_mode="bisect")
+    prm_async = FoParams.from_buffer_copy(prm)
+    prm_async.flags |= FO_FLAG_NO_RESULT_SYNC
+    calls = []
+    for seed in (11, 12, 13, 14):
+        ns, kts, hs = batch(3, seed, 64, 400)
+        hin = [torch.from_numpy(h).pin_memory() for h in hs]
+        ref = [torch.empty((n, n), dtype=torch.float64).pin_memory() for n in ns]
+        solver.density_matrix_batched_host(hin, [n / 2 for n in ns], prm, ref, kT=kts)
+        calls.append((ns, kts, hin, ref))
+    outs = []
+    for ns, kts, hin, _ in calls:
+        out = [torch.full((n, n), float("nan"), dtype=torch.float64).pin_memory() for n in ns]
+        solver.density_matrix_batched_host(hin, [n / 2 for n in ns], prm_async, out, kT=kts)
+        outs.append(out)
+    solver.host_wait()
+    for (_, _, _, ref), out in zip(calls, outs):
+        for a, b in zip(ref, out):
+            assert torch.equal(a, b)
