@@ -65,6 +65,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "fpbits.h"
 #include "internal.cuh"
 
 namespace fo {
@@ -796,15 +797,15 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             float fa = 0.0f;
             if constexpr (F64) {
                 const bool e0 = w0 && grow < n_real && gcol < n_real, e1 = w1 && grow < n_real && gcol + 1 < n_real;
-                double x0 = (double)v0, x1 = (double)v1;
+                double x0 = widen_f32(v0), x1 = widen_f32(v1);
                 float y0 = v0, y1 = v1;
                 if (fix) {
                     // P is the float32 master C written by the last Clenshaw step (the float64 P it
                     // stands for is exactly its widening); the correction d = gamma (P - P P), ~1e-7
                     // of P, in float32, added in float64; the mirror pass adds the same d
                     const float d0 = gam_f * (cv[u].x - v0), d1 = gam_f * (cv[u].y - v1);
-                    x0 = (double)cv[u].x + (double)d0;
-                    x1 = (double)cv[u].y + (double)d1;
+                    x0 = widen_f32(cv[u].x) + widen_f32(d0);
+                    x1 = widen_f32(cv[u].y) + widen_f32(d1);
                     y0 = cv[u].x + d0;
                     y1 = cv[u].y + d1;
                     tile[r * LD + c] = d0;
@@ -883,9 +884,9 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
                     // the lower float32 master of P (written by the last Clenshaw step) + the d of the
                     // row pass: the bits of the mirrored entry
                     const float2 pm = *reinterpret_cast<const float2*>(Cm + grow * ld + gcol);
-                    store64(grow, gcol, (double)pm.x + (double)v0, (double)pm.y + (double)v1, e0, e1);
+                    store64(grow, gcol, widen_f32(pm.x) + widen_f32(v0), widen_f32(pm.y) + widen_f32(v1), e0, e1);
                 } else {
-                    store64(grow, gcol, (double)v0, (double)v1, e0, e1);
+                    store64(grow, gcol, widen_f32(v0), widen_f32(v1), e0, e1);
                 }
             }
             if (slot_rows) store_slot(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, lower_master);
@@ -1086,15 +1087,15 @@ __device__ __forceinline__ void persist_epilogue(const Step& st, const Inst* __r
                 float fa = 0.0f;
                 if constexpr (F64) {
                     const bool e0 = w0 && grow < n_real && gcol < n_real, e1 = w1 && grow < n_real && gcol + 1 < n_real;
-                    double x0 = (double)v0, x1 = (double)v1;
+                    double x0 = widen_f32(v0), x1 = widen_f32(v1);
                     float y0 = v0, y1 = v1;
                     if (fix) {
                         // P is the float32 master C written by the last Clenshaw step (the float64 P it
                         // stands for is exactly its widening); the correction d = gamma (P - P P), ~1e-7
                         // of P, in float32, added in float64; the mirror pass adds the same d
                         const float d0 = gam_f * (cv[u].x - v0), d1 = gam_f * (cv[u].y - v1);
-                        x0 = (double)cv[u].x + (double)d0;
-                        x1 = (double)cv[u].y + (double)d1;
+                        x0 = widen_f32(cv[u].x) + widen_f32(d0);
+                        x1 = widen_f32(cv[u].y) + widen_f32(d1);
                         y0 = cv[u].x + d0;
                         y1 = cv[u].y + d1;
                         tile[r * LD + c] = d0;
@@ -1152,9 +1153,9 @@ __device__ __forceinline__ void persist_epilogue(const Step& st, const Inst* __r
                     const bool e1 = grow > gcol + 1 && grow < n_real && gcol + 1 < n_real;
                     if (fix) {
                         const float2 pm = *reinterpret_cast<const float2*>(Cm + grow * ld + gcol);
-                        store64(grow, gcol, (double)pm.x + (double)v0, (double)pm.y + (double)v1, e0, e1);
+                        store64(grow, gcol, widen_f32(pm.x) + widen_f32(v0), widen_f32(pm.y) + widen_f32(v1), e0, e1);
                     } else {
-                        store64(grow, gcol, (double)v0, (double)v1, e0, e1);
+                        store64(grow, gcol, widen_f32(v0), widen_f32(v1), e0, e1);
                     }
                 }
                 if (slot_rows) store_slot(grow, gcol, v0, v1, grow > gcol, grow > gcol + 1, lower_master);
