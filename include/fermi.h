@@ -274,7 +274,9 @@ fo_status fo_chebyshev_coeffs(fo_ctx *ctx, double kT, double mu, double emin, do
  * the float32 masters of the split forms leave tr P off n_e by their rounding (~1e-8 n). With
  * gamma = (n_e - tr P)/(tr P - ||P||_F^2) the call applies P <- P + gamma (P - P^2), the
  * first-order shift of mu by gamma kT for the Fermi function (df/dmu = f(1-f)/kT), as one
- * more symmetric product P P with a float64 epilogue, and then adds r/n to the diagonal,
+ * more symmetric product P P with a float64 epilogue (for FO_PREC_BF16X3 in BF16x1: its
+ * ~4e-3 relative error reaches P only through gamma, ~1e-6, so P moves by ~1e-8 at most;
+ * FP16X2 keeps FP16x2), and then adds r/n to the diagonal,
  * r = n_e - tr P the float64 residual that this product's own rounding leaves (the
  * Frobenius-nearest matrix with trace n_e; skipped when |r| > 1e-4 max(1, n_e)). It is a
  * correction of rounding, not a search for mu: it is applied only when it moves P by at most

@@ -576,7 +576,10 @@ Step make_step(const Plan& p, int a, int b, int c, int d, int out, double alpha,
 
 // Independent products of the whole batch (one stage), at most kMaxSteps per launch.
 fo_status run_products(fo_ctx* ctx, Plan& p, const Step* steps, int nsteps, cudaStream_t s, const char* tag,
-                       int index, Run* run) {
+                       int index, Run* run, int prec = -1) {
+    if (prec < 0) prec = p.key.prec;
+    // flops of these products: the plan's, scaled to this precision's split products
+    const double flops = p.sh.is64 ? p.flops_product : p.flops_product / split_count(p.key.prec) * split_count(prec);
     for (int q0 = 0; q0 < nsteps; q0 += kMaxSteps) {
         const int nq = std::min(kMaxSteps, nsteps - q0);
         const int h = prof_begin(ctx, s, FO_STAGE_PRODUCTS);
@@ -589,7 +592,7 @@ fo_status run_products(fo_ctx* ctx, Plan& p, const Step* steps, int nsteps, cuda
             for (const Group& g : p.groups) {
                 std::string err;
                 const int tile0 = w.pre[g.i0];
-                cudaError_t e = tc_gemm(p.key.prec, p.tile_n, p.tile_ctas, p.tile_drain, steps + q0, nq, p.d_inst, p.d_io,
+                cudaError_t e = tc_gemm(prec, p.tile_n, p.tile_ctas, p.tile_drain, steps + q0, nq, p.d_inst, p.d_io,
                                         w.dev.pre, g.i0, g.i1, tile0, w.pre[g.i1] - tile0,
                                         p.maps.data() + 256 * (size_t)g.b0, g.b0, g.nb, ctx->flag, s, &err,
                                         p.key.sym ? (p.sh.ublk ? 2 : 1) : 0, p.tile_persist);
@@ -602,7 +605,7 @@ fo_status run_products(fo_ctx* ctx, Plan& p, const Step* steps, int nsteps, cuda
                 ++launches;
             }
         }
-        prof_end(ctx, s, h, p.flops_product * nq, launches);
+        prof_end(ctx, s, h, flops * nq, launches);
         run->launches += launches;
         run->n_gemm += nq;
     }
@@ -610,9 +613,16 @@ fo_status run_products(fo_ctx* ctx, Plan& p, const Step* steps, int nsteps, cuda
 }
 
 fo_status run_product(fo_ctx* ctx, Plan& p, const Step& st, cudaStream_t s, const char* tag, int index,
-                      Run* run) {
-    return run_products(ctx, p, &st, 1, s, tag, index, run);
+                      Run* run, int prec = -1) {
+    return run_products(ctx, p, &st, 1, s, tag, index, run, prec);
 }
+
+// Precision of the trace correction's product P P. Its error enters P only through
+// gamma (P - P P) with |gamma| ~ 1e-6 (the correction runs only where it is rounding-sized),
+// so BF16x1's ~4e-3 relative error of P P moves P by ~1e-8 at most, far below the 1e-6 bar;
+// the plans in BF16x3 form it with one split product instead of six (plane 0 of P). FP16x2
+// plans keep their own precision (their planes are scaled float16).
+int fix_precision(const Plan& p) { return p.key.prec == FO_PREC_BF16X3 ? FO_PREC_BF16X1 : p.key.prec; }
 
 // A chain of dependent products (step q reads what step q - 1 wrote) of the whole batch: one
 // launch per group of instances and per kMaxChain steps when the plan runs chains
@@ -662,8 +672,10 @@ void final_step_extras(const Plan& p, Step& st, int pslot) {
     st.part = p.part_tc;
     st.part_pre = p.wtc[1].dev.pre;
     if (p.fix) {
+        // P's float32 master on both sides of the diagonal, and the planes the correcting
+        // product reads
         st.out = pslot;
-        st.planes = p.sh.planes;
+        st.planes = fix_precision(p) == FO_PREC_BF16X1 ? 1 : p.sh.planes;
         st.lower_master = 1;
         st.out64 = 0;
     }
@@ -841,7 +853,7 @@ fo_status trace_fix(fo_ctx* ctx, Plan& p, cudaStream_t s, Run* run) {
     st.fix64 = 1;
     st.part = p.part_tc;
     st.part_pre = p.wtc[1].dev.pre;
-    FO_TRY(run_product(ctx, p, st, s, "trace fix", 0, run));
+    FO_TRY(run_product(ctx, p, st, s, "trace fix", 0, run, fix_precision(p)));
     return trace_stage(ctx, p, s, run, 2);
 }
 

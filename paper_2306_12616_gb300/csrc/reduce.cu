@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "fpbits.h"
 #include "internal.cuh"
 
 namespace fo {
@@ -241,7 +242,8 @@ __device__ __forceinline__ void store_split(float v, float* x, uint16_t* p, int6
 // entries is scaled once (float64; off the diagonal as h * (2 / (emax - emin)), which equals
 // (2h) / (emax - emin) rounded once since both factors of 2 are exact) and the scaled tile is
 // written to X at (bi, bj) and, transposed, at (bj, bi). Output float64, or float32 + planes
-// (the float64 pipe of this GPU is narrow: one multiply and one conversion per entry).
+// (the float64 pipe of this GPU is narrow: one multiply per entry; the rounding to float32 is
+// done with integer operations).
 __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ insts,
                                                    const InstIO* __restrict__ io, Work ws,
                                                    const Shape sh, int* dbg) {
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
         double v = 0.0;
         if (r < n && c < n && (bi != bj || tx >= ry)) v = r == c ? (2.0 * tile[ry][tx] - csum) * inv : tile[ry][tx] * inv2;
         if (sh.is64) tile[ry][tx] = v;
-        else tf[ry][tx] = (float)v;
+        else tf[ry][tx] = narrow_f64(v);   // the float32 rounding, in integer operations
     }
     __syncthreads();
     char* slot = insts[i].slots;

@@ -71,8 +71,10 @@ def test_bf16x3_tight_binding_bisection(solver, n):
 def test_trace_correction_is_the_stated_update(solver):
     """The corrected P against the uncorrected one (FO_FLAG_NO_TRACE_FIX, same kernels up to
     the last product): P_fix = P_raw + gamma (P_raw - P_raw^2) + d I with the reported gamma
-    and d (P_raw^2 in float64 here; the GPU forms it in BF16x3), and the change is of the
-    size of the split form's rounding."""
+    and d (P_raw^2 in float64 here; the GPU forms it in BF16x1: each product of two
+    bf16-rounded entries is within about 2^-7 relative of the exact one, and ||P||_2 <= 1
+    bounds sum_k |P_ik||P_kj| by 1, so every entry of P^2 is within ~2^-7 and the difference
+    within 1e-2 |gamma|), and the change is of the size of the split form's rounding."""
     import paper_2306_12616_gb300 as fo
     n = 1000
     h = to_dev(synth.tight_binding(n, 2000 + n))
@@ -87,7 +89,7 @@ def test_trace_correction_is_the_stated_update(solver):
     assert r["trace_gamma"] != 0.0 and abs(r["trace"] - n / 2) <= 1e-8
     p, q = p.cpu().numpy(), q.cpu().numpy()
     upd = q + r["trace_gamma"] * (q - q @ q) + r["trace_proj"] * np.eye(n)
-    assert np.max(np.abs(p - upd)) <= 1e-6 * abs(r["trace_gamma"]) + 1e-15
+    assert np.max(np.abs(p - upd)) <= 1e-2 * abs(r["trace_gamma"]) + 1e-15
     assert np.linalg.norm(p - q) / math.sqrt(n) <= 3e-7   # below the split form's own error
 
 
@@ -158,7 +160,9 @@ def test_profiler_counts_products(solver):
     solver.profile_enable(False)
     assert prof["products"]["launches"] == res["n_gemm"]
     assert prof["call"]["launches"] == res["n_launches"]
-    assert prof["products"]["flops"] == pytest.approx(res["n_gemm"] * 6 * n * n * (n + 1))
+    # the expansion's products in BF16x3 (6 split products each), the trace correction's in
+    # BF16x1 (1)
+    assert prof["products"]["flops"] == pytest.approx(((res["n_gemm"] - 1) * 6 + 1) * n * n * (n + 1))
     assert 0 < prof["products"]["ms"] <= prof["call"]["ms"]
 
 
