@@ -90,9 +90,9 @@ __device__ void trace_at(double mu, const double* __restrict__ w, const double* 
 
 // Root of F(mu) = sum_n c_n(mu) tau_n - N_e, one block per instance. Bracket [emin, emax],
 // widened by 10 kT (at most 8 times per side). Inside the bracket a Newton step on the
-// exact derivative of the node sum is taken when it stays in the bracket and the bracket
-// has halved within the last two evaluations, a halving otherwise; the bracket shrinks with
-// the sign of F at every evaluated point. The first
+// exact derivative of the node sum is taken when it stays in the bracket and is at most
+// half the step before the last one, a halving otherwise; the bracket shrinks with the sign
+// of F at every evaluated point. The first
 // point is the midpoint, or res->mu0 when start_mu0 is set and mu0 lies inside the
 // bracket (the learned proposal). Stop when |F| <= 1e-12 max(1, N_e) (mu = that point) or
 // the bracket is narrower than 1e-15 (emax - emin) (mu = midpoint), at most max_iter
@@ -135,10 +135,11 @@ __global__ void __launch_bounds__(512) k_bisect(const Inst* __restrict__ insts,
         bool done = false;
         double x = 0.5 * (lo + hi);
         if (start_mu0 && res->mu0 > lo && res->mu0 < hi) x = res->mu0;
-        // bracket widths after the previous two evaluations: a Newton step is taken only while
-        // the bracket halves at least every two evaluations (near the root the rounding of F
-        // can keep Newton steps on one side, moving one end by tiny amounts)
-        double w1 = INFINITY, w2 = INFINITY;
+        // the last two steps: a Newton step is taken only when it is at most half the step
+        // before the last one (near the root the rounding of F can make Newton steps stall on
+        // one side, each moving one end of the bracket by a tiny amount; quadratic convergence
+        // passes this test)
+        double dx = hi - lo, dxold = dx;
         for (int it = 1; it <= max_iter; ++it) {
             double f, df;
             trace_at(x, w, ct, M, mid, half, inv2kT, sh, &f, &df);
@@ -147,11 +148,11 @@ __global__ void __launch_bounds__(512) k_bisect(const Inst* __restrict__ insts,
             if (fabs(f) <= tol_f) { mu = x; done = true; break; }
             if (f < 0.0) lo = x; else hi = x;
             if (hi - lo <= tol_w) { mu = 0.5 * (lo + hi); done = true; break; }
-            const bool stalled = hi - lo > 0.5 * w2;
-            w2 = w1;
-            w1 = hi - lo;
             const double cand = (df > 0.0) ? x - f / df : lo;
-            x = (!stalled && cand > lo && cand < hi) ? cand : 0.5 * (lo + hi);
+            const double xn = (cand > lo && cand < hi && fabs(cand - x) <= 0.5 * fabs(dxold)) ? cand : 0.5 * (lo + hi);
+            dxold = dx;
+            dx = xn - x;
+            x = xn;
         }
         if (!done) {
             mu = 0.5 * (lo + hi);
