@@ -110,21 +110,22 @@ __global__ void __launch_bounds__(512) k_bisect(const Inst* __restrict__ insts,
     const double ea = res->bounds[0], eb = res->bounds[1];
     const double mid = 0.5 * (eb + ea), half = 0.5 * (eb - ea), inv2kT = 0.5 / kT;
     double lo = ea, hi = eb, t;
+    // F at the bracket ends, from the widening loops (evaluated again only where a loop ended
+    // by widening past its last evaluation)
+    double flo = 1.0, fhi = -1.0;
+    bool have_lo = false, have_hi = false;
     for (int q = 0; q < 8; ++q) {
         trace_at(lo, w, ct, M, mid, half, inv2kT, sh, &t, nullptr);
-        if (t - n_e <= 0.0) break;
+        if (t - n_e <= 0.0) { flo = t - n_e; have_lo = true; break; }
         lo -= 10.0 * kT;
     }
     for (int q = 0; q < 8; ++q) {
         trace_at(hi, w, ct, M, mid, half, inv2kT, sh, &t, nullptr);
-        if (t - n_e >= 0.0) break;
+        if (t - n_e >= 0.0) { fhi = t - n_e; have_hi = true; break; }
         hi += 10.0 * kT;
     }
-    double flo, fhi;
-    trace_at(lo, w, ct, M, mid, half, inv2kT, sh, &flo, nullptr);
-    trace_at(hi, w, ct, M, mid, half, inv2kT, sh, &fhi, nullptr);
-    flo -= n_e;
-    fhi -= n_e;
+    if (!have_lo) { trace_at(lo, w, ct, M, mid, half, inv2kT, sh, &flo, nullptr); flo -= n_e; }
+    if (!have_hi) { trace_at(hi, w, ct, M, mid, half, inv2kT, sh, &fhi, nullptr); fhi -= n_e; }
     int status = FO_OK, iters = 0;
     double mu = 0.5 * (lo + hi);
     if (flo > 0.0 || fhi < 0.0) {
@@ -203,10 +204,17 @@ __global__ void k_coeffs(const Inst* __restrict__ insts, const double* __restric
     }
     const double* f = in.f;
     const int64_t fourM = 4LL * M;
+    // cos(n theta_j) = ct[n (2j + 1) mod 4M], the index advanced by 64 n per lane step; nodes
+    // where f is exactly 0 (more than 40 kT above mu) add nothing and are skipped (the same
+    // sum, fewer float64 operations)
+    const int64_t step = (64LL * n) % fourM;
+    int64_t r = ((int64_t)n * (2LL * lane + 1)) % fourM;
     double s = 0.0;
     for (int j = lane; j < M; j += 32) {
-        const int64_t r = ((int64_t)n * (2LL * j + 1)) % fourM;
-        s = fma(f[j], ct[r], s);
+        const double fj = f[j];
+        if (fj != 0.0) s = fma(fj, ct[r], s);
+        r += step;
+        if (r >= fourM) r -= fourM;
     }
     s = warp_sum(s);
     if (lane == 0) c[n] = (n == 0 ? 1.0 : 2.0) * s / (double)M;
@@ -578,7 +586,10 @@ cudaError_t launch_dos_weights(const Inst* in, int batch, const Shape& sh, const
 
 cudaError_t launch_bisect(const Inst* in, const InstIO* io, int batch, const Shape& sh, const double* ct,
                           int max_iter, int start_mu0, cudaStream_t s) {
-    k_bisect<<<batch, 512, 0, s>>>(in, io, ct, sh.M, max_iter, start_mu0);
+    // four warps per instance: the node sums are few float64 operations per thread, the
+    // float64 shuffle trees and the block reduction are per warp (this GPU's float64 pipe is
+    // narrow), so fewer warps finish an evaluation sooner
+    k_bisect<<<batch, 128, 0, s>>>(in, io, ct, sh.M, max_iter, start_mu0);
     return cudaGetLastError();
 }
 
