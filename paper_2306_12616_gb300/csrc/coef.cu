@@ -204,17 +204,10 @@ __global__ void k_coeffs(const Inst* __restrict__ insts, const double* __restric
     }
     const double* f = in.f;
     const int64_t fourM = 4LL * M;
-    // cos(n theta_j) = ct[n (2j + 1) mod 4M], the index advanced by 64 n per lane step; nodes
-    // where f is exactly 0 (more than 40 kT above mu) add nothing and are skipped (the same
-    // sum, fewer float64 operations)
-    const int64_t step = (64LL * n) % fourM;
-    int64_t r = ((int64_t)n * (2LL * lane + 1)) % fourM;
     double s = 0.0;
     for (int j = lane; j < M; j += 32) {
-        const double fj = f[j];
-        if (fj != 0.0) s = fma(fj, ct[r], s);
-        r += step;
-        if (r >= fourM) r -= fourM;
+        const int64_t r = ((int64_t)n * (2LL * j + 1)) % fourM;
+        s = fma(f[j], ct[r], s);
     }
     s = warp_sum(s);
     if (lane == 0) c[n] = (n == 0 ? 1.0 : 2.0) * s / (double)M;
