@@ -182,10 +182,14 @@ __global__ void k_fermi_nodes(const Inst* __restrict__ insts, const InstIO* __re
     const Inst& in = insts[blockIdx.y];
     const DevResult* res = in.res;
     if (!res->active) return;
+    // 1 / (2 kT) once per block (a float64 division per node would dominate this kernel)
+    __shared__ double s_inv2kT;
+    if (threadIdx.x == 0) s_inv2kT = 0.5 / io[blockIdx.y].kT;
+    __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     const double ea = res->bounds[0], eb = res->bounds[1];
-    in.f[j] = fermi(0.5 * (eb + ea) + 0.5 * (eb - ea) * ct[2 * j + 1], res->mu, 0.5 / io[blockIdx.y].kT);
+    in.f[j] = fermi(0.5 * (eb + ea) + 0.5 * (eb - ea) * ct[2 * j + 1], res->mu, s_inv2kT);
 }
 
 // c_n = (2 - delta_{n0}) / M sum_j f_j cos(n theta_j) for n < n_terms, 0 for n_terms <= n < km.

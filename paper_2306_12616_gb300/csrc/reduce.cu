@@ -257,13 +257,22 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
     int bi = 0, b = blockIdx.x - ws.pre[i];
     while (b >= tn - bi) { b -= tn - bi; ++bi; }
     const int bj = bi + b;
-    const double ea = res->bounds[0], eb = res->bounds[1];
-    const double inv = 1.0 / (eb - ea), inv2 = 2.0 * inv, csum = ea + eb;
+    // the scale factors once per block: a float64 division per thread would cost more than
+    // the block's multiplies on this GPU's narrow float64 pipe
+    __shared__ double s_par[3];
+    if (threadIdx.x == 0) {
+        const double ea = res->bounds[0], eb = res->bounds[1];
+        s_par[0] = 1.0 / (eb - ea);
+        s_par[1] = 2.0 * s_par[0];
+        s_par[2] = ea + eb;
+    }
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int ry = ty; ry < 32; ry += 8) {
         const int64_t r = (int64_t)bi * 32 + ry, c = (int64_t)bj * 32 + tx;
         tile[ry][tx] = (r < n && c < n) ? H[r * ld + c] : 0.0;
     }
+    __syncthreads();
+    const double inv = s_par[0], inv2 = s_par[1], csum = s_par[2];
     // each thread scales the entries it loaded (the lower half of a diagonal tile is never
     // read: it is written from the upper half)
     for (int ry = ty; ry < 32; ry += 8) {
