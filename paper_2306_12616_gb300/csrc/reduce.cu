@@ -278,7 +278,12 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
     for (int ry = ty; ry < 32; ry += 8) {
         const int64_t r = (int64_t)bi * 32 + ry, c = (int64_t)bj * 32 + tx;
         double v = 0.0;
-        if (r < n && c < n && (bi != bj || tx >= ry)) v = r == c ? (2.0 * tile[ry][tx] - csum) * inv : tile[ry][tx] * inv2;
+        if (r < n && c < n && (bi != bj || tx >= ry)) {
+            v = tile[ry][tx] * inv2;
+            // the diagonal only in diagonal tiles (a block-uniform test, so that the other
+            // tiles carry no float64 work for it)
+            if (bi == bj && r == c) v = (2.0 * tile[ry][tx] - csum) * inv;
+        }
         if (sh.is64) tile[ry][tx] = v;
         else tf[ry][tx] = narrow_f64(v);   // the float32 rounding, in integer operations
     }
