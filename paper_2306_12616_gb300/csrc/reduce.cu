@@ -85,6 +85,11 @@ __device__ __forceinline__ bool finite_bits(double v) {
     return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
 }
 
+// |v| by clearing the sign bit (integer work; the float64 pipe then only adds).
+__device__ __forceinline__ double abs_bits(double v) {
+    return __longlong_as_double(__double_as_longlong(v) & 0x7fffffffffffffffll);
+}
+
 // One warp per row: r_i = sum_{j != i} |h_ij| (float64, lane-strided, shuffle tree),
 // lo_i = h_ii - r_i, hi_i = h_ii + r_i; per-block (min lo, max hi, any non-finite).
 __global__ void __launch_bounds__(32 * kGershRows) k_gershgorin_rows(const Inst* __restrict__ insts,
@@ -110,13 +115,13 @@ __global__ void __launch_bounds__(32 * kGershRows) k_gershgorin_rows(const Inst*
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 bad |= !finite_bits(v[u]);
-                if (j + 32 * u == row) d = v[u]; else s4[u] += fabs(v[u]);
+                if (j + 32 * u == row) d = v[u]; else s4[u] += abs_bits(v[u]);
             }
         }
         for (; j < n; j += 32) {
             const double v = __ldg(r + j);
             bad |= !finite_bits(v);
-            if (j == row) d = v; else s4[0] += fabs(v);
+            if (j == row) d = v; else s4[0] += abs_bits(v);
         }
         double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         s = warp_sum(s);
