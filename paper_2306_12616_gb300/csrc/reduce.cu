@@ -981,8 +981,9 @@ __global__ void k_trace_frob_final(const Inst* __restrict__ insts, Work we, cons
 }
 
 // Trace of P from the partials of its float64-output product, one per 128 x 128 block on and
-// above the diagonal; one warp per instance, lane l sums blocks l, l + 32, ... in order, then a
-// fixed shuffle tree (the same bits for every tile configuration of the product).
+// above the diagonal; one block of 256 threads per instance, thread t sums blocks t, t + 256,
+// ... in order, then a fixed shuffle and shared-memory tree (the same bits for every tile
+// configuration of the product).
 //  mode 0: tr P and ||P||_F^2 of the result (no correction).
 //  mode 1: before the trace correction. The split products leave tr P off N_e by their
 //    rounding (float32 masters: ~1e-8 N). The correction is the first-order shift of mu
@@ -998,22 +999,23 @@ __global__ void k_trace_frob_final(const Inst* __restrict__ insts, Work we, cons
 //    ones) for the correcting product.
 //  mode 2: after the correcting product, whose own split-product rounding leaves a float64
 //    residual r = N_e - tr P (|gamma| times the rounding of tr P^2). The matrix nearest to P
-//    in the Frobenius norm with trace N_e is P + (r / n) I: the warp adds r / n to the n
+//    in the Frobenius norm with trace N_e is P + (r / n) I: the block adds r / n to the n
 //    diagonal entries when the correction was applied and |r| <= 1e-4 max(1, N_e) (a larger
 //    residual is left in place for the caller to see) and sums the new diagonal for the
 //    reported trace.
 __global__ void k_tile_trace(const Inst* __restrict__ insts, const InstIO* __restrict__ io, const int* pre,
                              const double* part, int mode) {
+    __shared__ double sh[33];
     const int i = blockIdx.x;
     DevResult* r = insts[i].res;
     if (mode == 1 ? r->status != FO_OK : !r->active) return;
     double tr = 0.0, fr = 0.0;
-    for (int b = pre[i] + (int)threadIdx.x; b < pre[i + 1]; b += 32) {
+    for (int b = pre[i] + (int)threadIdx.x; b < pre[i + 1]; b += blockDim.x) {
         tr += part[2 * (int64_t)b];
         fr += part[2 * (int64_t)b + 1];
     }
-    tr = warp_sum(tr);
-    fr = warp_sum(fr);
+    tr = block_sum(tr, sh);
+    fr = block_sum(fr, sh);
     if (mode == 0) {
         if (threadIdx.x == 0) {
             r->trace = tr;
@@ -1048,12 +1050,12 @@ __global__ void k_tile_trace(const Inst* __restrict__ insts, const InstIO* __res
     double d = 0.0;
     if (r->fixed && fabs(res) <= 1e-4 * fmax(1.0, n_e) && isfinite(res)) d = res / (double)n;
     double t2 = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += 32) {
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
         const double v = P[j * ldp + j] + d;
         if (d != 0.0) P[j * ldp + j] = v;
         t2 += v;
     }
-    t2 = warp_sum(t2);
+    t2 = block_sum(t2, sh);
     if (threadIdx.x == 0) {
         // ||P + d I||^2 = ||P||^2 + 2 d tr P + n d^2
         r->frob2 = fr + 2.0 * d * tr + (double)n * d * d;
@@ -1325,7 +1327,9 @@ cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, 
 
 cudaError_t launch_tile_trace(const Inst* in, const InstIO* io, int batch, const int* pre, const double* part,
                               int mode, cudaStream_t s) {
-    k_tile_trace<<<batch, 32, 0, s>>>(in, io, pre, part, mode);
+    // 256 threads per instance: the partials and the diagonal of P (one sector per entry) are
+    // read by enough threads to keep the loads in flight
+    k_tile_trace<<<batch, 256, 0, s>>>(in, io, pre, part, mode);
     return cudaGetLastError();
 }
 
