@@ -908,21 +908,25 @@ __global__ void k_sum_partials(const Inst* __restrict__ insts, int npairs, int o
 // tau[0..n_terms) from baby traces diag[0..k) (T_1..T_k), giant traces diag[k + l - 2]
 // (T_{lk}, l = 2..m-1) and gram[(l-1)*(k-1) + (i-1)] = <T_{lk}, T_i> (l = 1..m-1,
 // i = 1..k-1) through tau_{lk+i} = 2 <T_{lk}, T_i> - tau_{lk-i} (Eq. identity).
+// Within one l the k - 1 moments are independent (tau_{lk-i} belongs to the range of l - 1):
+// threads take i, the block steps through l (a serial loop of dependent global loads took
+// tens of microseconds).
 __global__ void k_assemble_moments(const Inst* __restrict__ insts, int k, int m, int n_terms) {
-    if (threadIdx.x != 0) return;
     const Inst& in = insts[blockIdx.x];
     if (!in.res->active) return;
     const double* diag = in.diag;
     const double* gram = in.gram;
     double* tau = in.tau;
-    tau[0] = (double)in.n;
-    for (int i = 1; i <= k && i < n_terms; ++i) tau[i] = diag[i - 1];
+    if (threadIdx.x == 0) tau[0] = (double)in.n;
+    for (int i = 1 + (int)threadIdx.x; i <= k && i < n_terms; i += blockDim.x) tau[i] = diag[i - 1];
+    __syncthreads();
     for (int l = 1; l < m; ++l) {
         const int base = l * k;
         if (base >= n_terms) break;
-        if (l >= 2) tau[base] = diag[k + l - 2];
-        for (int i = 1; i < k && base + i < n_terms; ++i)
+        if (l >= 2 && threadIdx.x == 0) tau[base] = diag[k + l - 2];
+        for (int i = 1 + (int)threadIdx.x; i < k && base + i < n_terms; i += blockDim.x)
             tau[base + i] = 2.0 * gram[(l - 1) * (k - 1) + (i - 1)] - tau[base - i];
+        __syncthreads();
     }
 }
 
@@ -1321,7 +1325,7 @@ cudaError_t launch_gram(const Inst* in, int batch, Work wgr, int giant0, int ngi
 }
 
 cudaError_t launch_assemble_moments(const Inst* in, int batch, const Shape& sh, cudaStream_t s) {
-    k_assemble_moments<<<batch, 32, 0, s>>>(in, sh.k, sh.m, sh.n_terms);
+    k_assemble_moments<<<batch, 64, 0, s>>>(in, sh.k, sh.m, sh.n_terms);
     return cudaGetLastError();
 }
 
