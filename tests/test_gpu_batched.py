@@ -68,6 +68,22 @@ def test_batch_equals_single_calls(solver):
         assert torch.max(torch.abs(p1 - p)).item() <= 1e-9
 
 
+def test_more_buckets_than_one_launch_group(solver):
+    """18 distinct padded sizes (n_pad = 128 .. 2304): more buckets than one grouped launch
+    carries tensor maps for (16), so the products and the Frobenius products run one launch per
+    group of buckets; each instance against its single call, and the trace bar."""
+    ns = [100 + 128 * i for i in range(18)]
+    hs = [synth.tight_binding(n, 900 + n) for n in ns]
+    hd = [to_dev(h) for h in hs]
+    prm = solver.params(300, 0.1, precision="bf16x3", mu_mode="bisect")
+    ps, res = solver.density_matrix_batched(hd, [n / 2 for n in ns], prm)
+    for h, n, p, r in zip(hd, ns, ps, res):
+        assert r["status"] == 0 and abs(r["trace"] - n / 2) <= 1e-8
+        p1, r1 = solver.density_matrix(h, n / 2, prm)
+        assert abs(r1["mu"] - r["mu"]) <= 1e-9 * (r["emax"] - r["emin"])
+        assert torch.max(torch.abs(p1 - p)).item() <= 1e-9
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "fp16x2", "bf16x1"])
 def test_tile_configs_bit_identical(solver, prec):
     """Every tile configuration and plane storage the autotuner may pick gives the same bits."""
