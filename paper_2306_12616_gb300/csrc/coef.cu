@@ -397,49 +397,55 @@ __device__ __forceinline__ Split3 split_value(float v, int fp16, float pscale) {
 // R_l for l0 <= l < min(l0 + MAXM, m) (MAXM = m rounded up to a multiple of 4, at most 32;
 // m > 32 takes several launches), on and above the diagonal only (the float32 masters of the
 // T_i are maintained there; R_l is symmetric). The upper triangle is walked as 16-byte quads
-// (row r from column 4 floor(r / 4) to the end; ct_quads), one quad per thread and step,
-// consecutive threads on consecutive quads; quad q of the flattened order lies in the row
-// group b = floor(r / 4) with C(b) <= q < C(b + 1), C(b) = b np - 2 b (b - 1), found by a
-// square root and corrected exactly. Each thread stages the quads of T_1..T_{k-1} it will
-// use into its own slots of an S-stage shared-memory ring by cp.async (no block barrier:
-// a thread only reads what it copied) and multiplies them by the coefficients, staged as
-// duplicated pairs gsh[t][l] = (g_{t,l0+l}, g_{t,l0+l}) (zero beyond m): one 16-byte
-// broadcast load serves two R_l, each packed FMA two entries of the quad, and each R_l leaves
-// as one 16-byte store. The planes of the instance's last R (R_{m-1}, or R_{m_eff-1} when a
+// (row r from column 4 floor(r / 4) to the end; ct_quads), one quad per pair of adjacent
+// threads and step, consecutive pairs on consecutive quads; quad q of the flattened order lies
+// in the row group b = floor(r / 4) with C(b) <= q < C(b + 1), C(b) = b np - 2 b (b - 1),
+// found by a square root and corrected exactly. The two threads of a pair stage alternate
+// quads of T_1..T_{k-1} into the pair's slots of an S-stage shared-memory ring by cp.async
+// (a warp barrier, not a block barrier, publishes them to the partner) and each forms half
+// of the R_l from all k - 1 quads with the coefficients, staged as duplicated pairs
+// gsh[t][l] = (g_{t,l0+l}, g_{t,l0+l}) (zero beyond m): one 16-byte broadcast load serves two
+// R_l, each packed FMA two entries of the quad, and each R_l leaves as one 16-byte store.
+// Two threads per quad halve the accumulators per thread and double the warps per SM that
+// keep copies in flight. The planes of the instance's last R (R_{m-1}, or R_{m_eff-1} when a
 // learned order cut its expansion: the first operand of the Clenshaw steps) are written here
 // and completed below the diagonal by k_mirror_planes.
 template <int MAXM>
-__global__ void __launch_bounds__(256, 1) k_contract_f32(const Inst* __restrict__ insts, Work wct, int k, int m,
+__global__ void __launch_bounds__(512, 1) k_contract_f32(const Inst* __restrict__ insts, Work wct, int k, int m,
                                                           int l0, int n_tslots, int planes_last, int fp16,
                                                           float pscale, int S, int* dbg) {
+    static_assert(MAXM % 4 == 0, "l pairs per half");
+    constexpr int HM = MAXM / 2;                           // R_l per thread
     extern __shared__ __align__(16) float fsh[];
     const int i = find_inst(wct.pre, 0, wct.count, blockIdx.x);
     const Inst& in = insts[i];
     if (!in.res->active) return;
-    const int tpb = blockDim.x, tid = threadIdx.x;
-    for (int q = tid; q < k * MAXM; q += tpb) {
+    const int tid = threadIdx.x;
+    const int npr = blockDim.x >> 1;                       // thread pairs: one quad per pair
+    const int pr = tid >> 1, h = tid & 1;                  // pair, and which half of the R_l
+    for (int q = tid; q < k * MAXM; q += blockDim.x) {
         const int t = q / MAXM, l = l0 + q - t * MAXM;
         const float g = l < m ? (float)in.g[l * k + t] : 0.0f;
         fsh[2 * q] = g;
         fsh[2 * q + 1] = g;
     }
     const int nt = k - 1;                                   // T_1 .. T_{k-1}
-    float4* ring = reinterpret_cast<float4*>(fsh + 2 * k * MAXM);   // [stage][t][thread]
+    float4* ring = reinterpret_cast<float4*>(fsh + 2 * k * MAXM);   // [stage][t][pair]
     const int64_t np = in.np, n = in.n;
     const int lastl = (in.res->m_eff > 0 ? in.res->m_eff : m) - 1;   // R whose planes are written
     const int64_t q_all = ct_quads(np);
-    const int64_t per = (int64_t)tpb * kCtSteps;
+    const int64_t per = (int64_t)npr * kCtSteps;
     const int64_t q0 = (int64_t)(blockIdx.x - wct.pre[i]) * per;
     const int64_t q1 = q0 + per < q_all ? q0 + per : q_all;
-    const int nsteps = (int)((q1 - q0 + tpb - 1) / tpb);
+    const int nsteps = (int)((q1 - q0 + npr - 1) / npr);
     const int64_t tstride = in.slot_bytes / 4;
     const int64_t ps = np * np;
     const float* tbase = reinterpret_cast<const float*>(in.slots);
     float* rbase = reinterpret_cast<float*>(in.slots + n_tslots * in.slot_bytes);
     const int64_t G = np / 4;                               // row groups
-    // (row, column) of this thread's quad of step j, or row -1 past the block's range
+    // (row, column) of this pair's quad of step j, or row -1 past the block's range
     auto locate = [&](int j, int64_t& r, int64_t& c) {
-        const int64_t q = q0 + (int64_t)j * tpb + tid;
+        const int64_t q = q0 + (int64_t)j * npr + pr;
         r = -1;
         c = 0;
         if (q >= q1) return;
@@ -455,74 +461,78 @@ __global__ void __launch_bounds__(256, 1) k_contract_f32(const Inst* __restrict_
         r = 4 * b + off / len;
         c = 4 * b + 4 * (off % len);
     };
+    // the pair's quads of T_1..T_{k-1}: each thread copies every other one
     auto issue = [&](int j) {
         int64_t r, c;
         locate(j, r, c);
-        if (r >= 0 && nt > 0) {
-            float4* dst = ring + (int64_t)(j % S) * nt * tpb + tid;
-            const float* src = tbase + r * np + c;   // slot t holds T_{t+1}
+        if (r >= 0 && nt > h) {
+            float4* dst = ring + (int64_t)(j % S) * nt * npr + (int64_t)h * npr + pr;
+            const float* src = tbase + r * np + c + (int64_t)h * tstride;   // slot t holds T_{t+1}
 #pragma unroll 1
-            for (int t = 0; t < nt; ++t, dst += tpb, src += tstride) cp_async16(dst, src);
+            for (int t = h; t < nt; t += 2, dst += 2 * npr, src += 2 * tstride) cp_async16(dst, src);
         }
         cp_async_commit();
     };
     for (int j = 0; j < S - 1; ++j) issue(j);
     __syncthreads();   // the coefficient table
-    const ulonglong2* gtab = reinterpret_cast<const ulonglong2*>(fsh);   // [t][l / 2]
+    const ulonglong2* gtab = reinterpret_cast<const ulonglong2*>(fsh) + h * (HM / 2);   // [t][l / 2], this half
     for (int j = 0; j < nsteps; ++j) {
         issue(j + S - 1);
         cp_async_wait_dyn(S - 1);   // this thread's copies of step j have landed
+        __syncwarp();               // and its partner's: both halves of the pair's quads are visible
         int64_t r, c;
         locate(j, r, c);
-        if (r < 0) continue;
-        const float4* seg = ring + (int64_t)(j % S) * nt * tpb + tid;
-        f32x2 acc[MAXM][2];   // R_{l0+l} at entries (0, 1) and (2, 3) of the quad
-#pragma unroll
-        for (int l = 0; l < MAXM; ++l) acc[l][0] = acc[l][1] = 0ull;
-#pragma unroll 2
-        for (int t = 0; t < nt; ++t) {
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(seg + (int64_t)t * tpb);
-            const ulonglong2* gt = gtab + (t + 1) * (MAXM / 2);
-#pragma unroll
-            for (int l2 = 0; l2 < MAXM / 2; ++l2) {
-                const ulonglong2 g = gt[l2];   // (g_l, g_l), (g_{l+1}, g_{l+1})
-                ffma2(acc[2 * l2][0], v.x, g.x);
-                ffma2(acc[2 * l2][1], v.y, g.x);
-                ffma2(acc[2 * l2 + 1][0], v.x, g.y);
-                ffma2(acc[2 * l2 + 1][1], v.y, g.y);
-            }
-        }
         const int64_t idx = r * np + c;
-        if (!FO_CHK(dbg, idx >= 0 && idx + 3 < ps && (idx & 3) == 0, 302, (int)r, idx)) continue;
-        const int dg = (r < n && c == (r & ~int64_t(3))) ? (int)(r & 3) : -1;   // diagonal entry
-        float* dst = rbase + (int64_t)l0 * tstride + idx;
+        if (r >= 0 && FO_CHK(dbg, idx >= 0 && idx + 3 < ps && (idx & 3) == 0, 302, (int)r, idx)) {
+            const float4* seg = ring + (int64_t)(j % S) * nt * npr + pr;
+            f32x2 acc[HM][2];   // R_{l0 + h HM + l} at entries (0, 1) and (2, 3) of the quad
 #pragma unroll
-        for (int l = 0; l < MAXM; ++l, dst += tstride) {
-            if (l0 + l >= m) break;
-            float2 a = unpack2(acc[l][0]), b = unpack2(acc[l][1]);
-            float4 v = make_float4(a.x, a.y, b.x, b.y);
-            if (dg >= 0) {   // g_{0,l}: the t = 0 row (T_0 = I)
-                const float g0 = fsh[2 * l];
-                if (dg == 0) v.x += g0;
-                else if (dg == 1) v.y += g0;
-                else if (dg == 2) v.z += g0;
-                else v.w += g0;
+            for (int l = 0; l < HM; ++l) acc[l][0] = acc[l][1] = 0ull;
+#pragma unroll 2
+            for (int t = 0; t < nt; ++t) {
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(seg + (int64_t)t * npr);
+                const ulonglong2* gt = gtab + (t + 1) * (MAXM / 2);
+#pragma unroll
+                for (int l2 = 0; l2 < HM / 2; ++l2) {
+                    const ulonglong2 g = gt[l2];   // (g_l, g_l), (g_{l+1}, g_{l+1})
+                    ffma2(acc[2 * l2][0], v.x, g.x);
+                    ffma2(acc[2 * l2][1], v.y, g.x);
+                    ffma2(acc[2 * l2 + 1][0], v.x, g.y);
+                    ffma2(acc[2 * l2 + 1][1], v.y, g.y);
+                }
             }
-            *reinterpret_cast<float4*>(dst) = v;
-            if (l0 + l == lastl && planes_last > 0) {
-                const Split3 s0 = split_value(v.x, fp16, pscale), s1 = split_value(v.y, fp16, pscale);
-                const Split3 s2 = split_value(v.z, fp16, pscale), s3 = split_value(v.w, fp16, pscale);
-                // planes of R_l: 16-bit entries from float offset ps of the slot
-                uint16_t* pl = reinterpret_cast<uint16_t*>(dst - idx + ps) + idx;
+            const int dg = (r < n && c == (r & ~int64_t(3))) ? (int)(r & 3) : -1;   // diagonal entry
+            float* dst = rbase + (int64_t)(l0 + h * HM) * tstride + idx;
 #pragma unroll
-                for (int p = 0; p < 3; ++p) {
-                    if (p >= planes_last) break;
-                    const uint2 w = make_uint2((uint32_t)s0.p[p] | ((uint32_t)s1.p[p] << 16),
-                                               (uint32_t)s2.p[p] | ((uint32_t)s3.p[p] << 16));
-                    *reinterpret_cast<uint2*>(pl + p * ps) = w;
+            for (int l = 0; l < HM; ++l, dst += tstride) {
+                const int L = l0 + h * HM + l;
+                if (L >= m) break;
+                float2 a = unpack2(acc[l][0]), b = unpack2(acc[l][1]);
+                float4 v = make_float4(a.x, a.y, b.x, b.y);
+                if (dg >= 0) {   // g_{0,l}: the t = 0 row (T_0 = I)
+                    const float g0 = fsh[2 * (h * HM + l)];
+                    if (dg == 0) v.x += g0;
+                    else if (dg == 1) v.y += g0;
+                    else if (dg == 2) v.z += g0;
+                    else v.w += g0;
+                }
+                *reinterpret_cast<float4*>(dst) = v;
+                if (L == lastl && planes_last > 0) {
+                    const Split3 s0 = split_value(v.x, fp16, pscale), s1 = split_value(v.y, fp16, pscale);
+                    const Split3 s2 = split_value(v.z, fp16, pscale), s3 = split_value(v.w, fp16, pscale);
+                    // planes of R_l: 16-bit entries from float offset ps of the slot
+                    uint16_t* pl = reinterpret_cast<uint16_t*>(dst - idx + ps) + idx;
+#pragma unroll
+                    for (int p = 0; p < 3; ++p) {
+                        if (p >= planes_last) break;
+                        const uint2 w = make_uint2((uint32_t)s0.p[p] | ((uint32_t)s1.p[p] << 16),
+                                                   (uint32_t)s2.p[p] | ((uint32_t)s3.p[p] << 16));
+                        *reinterpret_cast<uint2*>(pl + p * ps) = w;
+                    }
                 }
             }
         }
+        __syncwarp();   // both threads are done with the pair's ring slot before it is refilled
     }
     cp_async_wait<0>();
 }
@@ -640,8 +650,8 @@ cudaError_t launch_contract(const Inst* in, Work we, Work wct, Work wsym, const 
     auto go = [&](auto kern, int maxm, int l0) {
         const size_t smem = (size_t)2 * sh.k * maxm * sizeof(float) + S * stage_bytes;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<wct.total, tpb, smem, s>>>(in, wct, sh.k, sh.m, l0, sh.n_tslots, planes_last, sh.fp16, sh.pscale_r,
-                                          S, dbg);
+        kern<<<wct.total, 2 * tpb, smem, s>>>(in, wct, sh.k, sh.m, l0, sh.n_tslots, planes_last, sh.fp16,
+                                              sh.pscale_r, S, dbg);
     };
     for (int l0 = 0; l0 < sh.m; l0 += 32) {
         const int mm = sh.m - l0 < 32 ? sh.m - l0 : 32;   // R_l of this launch

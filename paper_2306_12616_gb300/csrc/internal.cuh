@@ -290,11 +290,12 @@ __host__ __device__ inline int ew_blocks(int64_t np) {
     return (int)((np + r - 1) / r);
 }
 // Contraction of the float32 forms: the upper triangle is walked as 16-byte quads (row r
-// holds the quads from column 4 floor(r / 4) to np - 4), ct_threads(k) per block, one quad
-// per thread and step, kCtSteps steps per block.
+// holds the quads from column 4 floor(r / 4) to np - 4), ct_threads(k) thread pairs per block,
+// one quad per pair and step (each thread of the pair stages half of the k - 1 quads and forms
+// half of the R_l), kCtSteps steps per block.
 constexpr int kCtSteps = 16;
 __host__ __device__ inline int ct_threads(int k) {
-    // two stages of the k - 1 staged quads of every thread within ~200 KB of shared memory
+    // two stages of the k - 1 staged quads of every pair within ~200 KB of shared memory
     int t = 256;
     while (t > 64 && 2 * (int64_t)t * (k - 1) * 16 > 200 * 1024) t /= 2;
     return t;
