@@ -401,7 +401,7 @@ __device__ __forceinline__ Split3 split_value(float v, int fp16, float pscale) {
 // threads and step, consecutive pairs on consecutive quads; quad q of the flattened order lies
 // in the row group b = floor(r / 4) with C(b) <= q < C(b + 1), C(b) = b np - 2 b (b - 1),
 // found by a square root and corrected exactly. The two threads of a pair stage alternate
-// quads of T_1..T_{k-1} into the pair's slots of an S-stage shared-memory ring by cp.async
+// quads of T_1..T_{k-1} into the pair's slots of a two-stage shared-memory ring by cp.async
 // (a warp barrier, not a block barrier, publishes them to the partner) and each forms half
 // of the R_l from all k - 1 quads with the coefficients, staged as duplicated pairs
 // gsh[t][l] = (g_{t,l0+l}, g_{t,l0+l}) (zero beyond m): one 16-byte broadcast load serves two
@@ -411,9 +411,9 @@ __device__ __forceinline__ Split3 split_value(float v, int fp16, float pscale) {
 // learned order cut its expansion: the first operand of the Clenshaw steps) are written here
 // and completed below the diagonal by k_mirror_planes.
 template <int MAXM>
-__global__ void __launch_bounds__(512, 1) k_contract_f32(const Inst* __restrict__ insts, Work wct, int k, int m,
+__global__ void __launch_bounds__(128, 4) k_contract_f32(const Inst* __restrict__ insts, Work wct, int k, int m,
                                                           int l0, int n_tslots, int planes_last, int fp16,
-                                                          float pscale, int S, int* dbg) {
+                                                          float pscale, int* dbg) {
     static_assert(MAXM % 4 == 0, "l pairs per half");
     constexpr int HM = MAXM / 2;                           // R_l per thread
     extern __shared__ __align__(16) float fsh[];
@@ -442,63 +442,70 @@ __global__ void __launch_bounds__(512, 1) k_contract_f32(const Inst* __restrict_
     const int64_t ps = np * np;
     const float* tbase = reinterpret_cast<const float*>(in.slots);
     float* rbase = reinterpret_cast<float*>(in.slots + n_tslots * in.slot_bytes);
-    const int64_t G = np / 4;                               // row groups
-    // (row, column) of this pair's quad of step j, or row -1 past the block's range
-    auto locate = [&](int j, int64_t& r, int64_t& c) {
-        const int64_t q = q0 + (int64_t)j * npr + pr;
+    // (row, column) of this pair's quad of step j, or row -1 past the block's range. 32-bit
+    // integers (n_pad <= 65536: q < n_pad (n_pad + 4) / 8 < 2^31, b n_pad < 2^30), so the
+    // division is a short 32-bit one
+    const int npi = (int)np, G = npi / 4;                   // row groups
+    auto locate = [&](int j, int& r, int& c) {
+        const int64_t q64 = q0 + (int64_t)j * npr + pr;
         r = -1;
         c = 0;
-        if (q >= q1) return;
-        const float d = (float)(np + 2) * (float)(np + 2) - 8.0f * (float)q;
-        int64_t b = (int64_t)(((float)(np + 2) - sqrtf(d > 0.0f ? d : 0.0f)) * 0.25f);
+        if (q64 >= q1) return;
+        const int q = (int)q64;
+        const float e = (float)(npi + 2);
+        const float d = e * e - 8.0f * (float)q;
+        int b = (int)((e - sqrtf(d > 0.0f ? d : 0.0f)) * 0.25f);
         if (b < 0) b = 0;
         if (b > G - 1) b = G - 1;
-        auto C = [&](int64_t x) { return x * np - 2 * x * (x - 1); };
+        auto C = [&](int x) { return x * npi - 2 * x * (x - 1); };
         while (b > 0 && C(b) > q) --b;
         while (b + 1 < G && C(b + 1) <= q) ++b;
-        const int64_t len = G - b;                          // quads per row of the group
-        const int64_t off = q - C(b);
-        r = 4 * b + off / len;
-        c = 4 * b + 4 * (off % len);
+        const int len = G - b;                              // quads per row of the group
+        const int off = q - C(b);
+        const int dr = off / len;
+        r = 4 * b + dr;
+        c = 4 * b + 4 * (off - dr * len);
     };
-    // the pair's quads of T_1..T_{k-1}: each thread copies every other one
-    auto issue = [&](int j) {
-        int64_t r, c;
-        locate(j, r, c);
+    // the pair's quads of T_1..T_{k-1} at (r, c) into stage st: each thread copies every other one
+    auto issue = [&](int st, int r, int c) {
         if (r >= 0 && nt > h) {
-            float4* dst = ring + (int64_t)(j % S) * nt * npr + (int64_t)h * npr + pr;
-            const float* src = tbase + r * np + c + (int64_t)h * tstride;   // slot t holds T_{t+1}
+            float4* dst = ring + (int64_t)st * nt * npr + (int64_t)h * npr + pr;
+            const float* src = tbase + (int64_t)r * np + c + (int64_t)h * tstride;   // slot t holds T_{t+1}
 #pragma unroll 1
             for (int t = h; t < nt; t += 2, dst += 2 * npr, src += 2 * tstride) cp_async16(dst, src);
         }
         cp_async_commit();
     };
-    for (int j = 0; j < S - 1; ++j) issue(j);
+    int r, c;   // the quad of the current step, located when its copies were issued
+    locate(0, r, c);
+    issue(0, r, c);
     __syncthreads();   // the coefficient table
-    const ulonglong2* gtab = reinterpret_cast<const ulonglong2*>(fsh) + h * (HM / 2);   // [t][l / 2], this half
+    const float4* gtab = reinterpret_cast<const float4*>(fsh) + h * (HM / 2);   // [t][l / 2], this half
     for (int j = 0; j < nsteps; ++j) {
-        issue(j + S - 1);
-        cp_async_wait_dyn(S - 1);   // this thread's copies of step j have landed
-        __syncwarp();               // and its partner's: both halves of the pair's quads are visible
-        int64_t r, c;
-        locate(j, r, c);
-        const int64_t idx = r * np + c;
-        if (r >= 0 && FO_CHK(dbg, idx >= 0 && idx + 3 < ps && (idx & 3) == 0, 302, (int)r, idx)) {
-            const float4* seg = ring + (int64_t)(j % S) * nt * npr + pr;
-            f32x2 acc[HM][2];   // R_{l0 + h HM + l} at entries (0, 1) and (2, 3) of the quad
+        int rn, cn;
+        locate(j + 1, rn, cn);
+        issue((j + 1) & 1, rn, cn);
+        cp_async_wait<1>();   // this thread's copies of step j have landed
+        __syncwarp();         // and its partner's: both halves of the pair's quads are visible
+        const int64_t idx = (int64_t)r * np + c;
+        if (r >= 0 && FO_CHK(dbg, idx >= 0 && idx + 3 < ps && (idx & 3) == 0, 302, r, idx)) {
+            const float4* vp = ring + (int64_t)(j & 1) * nt * npr + pr;   // T_1's quad of this pair
+            const float4* gp = gtab + MAXM / 2;                             // row t = 1
+            float2 acc[HM][2];   // R_{l0 + h HM + l} at entries (0, 1) and (2, 3) of the quad
 #pragma unroll
-            for (int l = 0; l < HM; ++l) acc[l][0] = acc[l][1] = 0ull;
+            for (int l = 0; l < HM; ++l) acc[l][0] = acc[l][1] = make_float2(0.0f, 0.0f);
 #pragma unroll 2
-            for (int t = 0; t < nt; ++t) {
-                const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(seg + (int64_t)t * npr);
-                const ulonglong2* gt = gtab + (t + 1) * (MAXM / 2);
+            for (int t = 0; t < nt; ++t, vp += npr, gp += MAXM / 2) {
+                const float4 v = *vp;
+                const float2 v01 = make_float2(v.x, v.y), v23 = make_float2(v.z, v.w);
 #pragma unroll
                 for (int l2 = 0; l2 < HM / 2; ++l2) {
-                    const ulonglong2 g = gt[l2];   // (g_l, g_l), (g_{l+1}, g_{l+1})
-                    ffma2(acc[2 * l2][0], v.x, g.x);
-                    ffma2(acc[2 * l2][1], v.y, g.x);
-                    ffma2(acc[2 * l2 + 1][0], v.x, g.y);
-                    ffma2(acc[2 * l2 + 1][1], v.y, g.y);
+                    const float4 g = gp[l2];   // (g_l, g_l, g_{l+1}, g_{l+1})
+                    const float2 ga = make_float2(g.x, g.y), gb = make_float2(g.z, g.w);
+                    acc[2 * l2][0] = __ffma2_rn(v01, ga, acc[2 * l2][0]);
+                    acc[2 * l2][1] = __ffma2_rn(v23, ga, acc[2 * l2][1]);
+                    acc[2 * l2 + 1][0] = __ffma2_rn(v01, gb, acc[2 * l2 + 1][0]);
+                    acc[2 * l2 + 1][1] = __ffma2_rn(v23, gb, acc[2 * l2 + 1][1]);
                 }
             }
             const int dg = (r < n && c == (r & ~int64_t(3))) ? (int)(r & 3) : -1;   // diagonal entry
@@ -507,8 +514,7 @@ __global__ void __launch_bounds__(512, 1) k_contract_f32(const Inst* __restrict_
             for (int l = 0; l < HM; ++l, dst += tstride) {
                 const int L = l0 + h * HM + l;
                 if (L >= m) break;
-                float2 a = unpack2(acc[l][0]), b = unpack2(acc[l][1]);
-                float4 v = make_float4(a.x, a.y, b.x, b.y);
+                float4 v = make_float4(acc[l][0].x, acc[l][0].y, acc[l][1].x, acc[l][1].y);
                 if (dg >= 0) {   // g_{0,l}: the t = 0 row (T_0 = I)
                     const float g0 = fsh[2 * (h * HM + l)];
                     if (dg == 0) v.x += g0;
@@ -533,6 +539,8 @@ __global__ void __launch_bounds__(512, 1) k_contract_f32(const Inst* __restrict_
             }
         }
         __syncwarp();   // both threads are done with the pair's ring slot before it is refilled
+        r = rn;
+        c = cn;
     }
     cp_async_wait<0>();
 }
@@ -642,16 +650,14 @@ cudaError_t launch_contract(const Inst* in, Work we, Work wct, Work wsym, const 
         return cudaGetLastError();
     }
     const int planes_last = sh.m > 1 ? sh.planes : 0;
-    // ring depth: as many stages (2 to 4) of every thread's k - 1 quads as fit ~200 KB
+    // two ring stages of every pair's k - 1 quads
     const int tpb = ct_threads(sh.k);
     const size_t stage_bytes = (size_t)(sh.k - 1) * tpb * 16;
-    int S = 4;
-    while (S > 2 && stage_bytes * S > 200 * 1024) --S;
     auto go = [&](auto kern, int maxm, int l0) {
-        const size_t smem = (size_t)2 * sh.k * maxm * sizeof(float) + S * stage_bytes;
+        const size_t smem = (size_t)2 * sh.k * maxm * sizeof(float) + 2 * stage_bytes;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<wct.total, 2 * tpb, smem, s>>>(in, wct, sh.k, sh.m, l0, sh.n_tslots, planes_last, sh.fp16,
-                                              sh.pscale_r, S, dbg);
+                                              sh.pscale_r, dbg);
     };
     for (int l0 = 0; l0 < sh.m; l0 += 32) {
         const int mm = sh.m - l0 < 32 ? sh.m - l0 : 32;   // R_l of this launch

@@ -180,13 +180,6 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-// cp.async.wait_group for a run-time count (0 to 3)
-__device__ __forceinline__ void cp_async_wait_dyn(int n) {
-    if (n <= 0) cp_async_wait<0>();
-    else if (n == 1) cp_async_wait<1>();
-    else if (n == 2) cp_async_wait<2>();
-    else cp_async_wait<3>();
-}
 
 // ------------------------------------------------- mbarriers and bounded waits
 // Every wait on the device is bounded: a legitimate wait is microseconds; on expiry the
@@ -294,11 +287,11 @@ __host__ __device__ inline int ew_blocks(int64_t np) {
 // one quad per pair and step (each thread of the pair stages half of the k - 1 quads and forms
 // half of the R_l), kCtSteps steps per block.
 constexpr int kCtSteps = 16;
-__host__ __device__ inline int ct_threads(int k) {
-    // two stages of the k - 1 staged quads of every pair within ~200 KB of shared memory
-    int t = 256;
-    while (t > 64 && 2 * (int64_t)t * (k - 1) * 16 > 200 * 1024) t /= 2;
-    return t;
+__host__ __device__ inline int ct_threads(int) {
+    // 64 pairs: the two ring stages take 2 (k - 1) 1 KB (39 KB at k = 20, 126 KB at the largest
+    // k = 64), so that up to four blocks share an SM (128 registers per thread); small blocks
+    // measured faster than 128 or 256 pairs, and deeper rings than two stages slower
+    return 64;
 }
 __host__ __device__ inline int64_t ct_quads(int64_t np) { return np * (np + 4) / 8; }
 __host__ __device__ inline int ct_blocks(int64_t np, int k) {

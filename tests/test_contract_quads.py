@@ -59,3 +59,15 @@ def test_group_boundaries_large(npad):
             assert r // 4 == b and steps <= 4
     # the last quad is the last row's only one
     assert locate(quads(npad) - 1, npad)[:2] == (npad - 1, npad - 4)
+
+
+def test_indices_fit_32_bits_at_the_largest_size():
+    """The kernel locates quads in 32-bit integers: at the largest n_pad (65536, the library's
+    size limit) the quad index, C(b) and b n_pad stay below 2^31."""
+    npad = 65536
+    g = npad // 4
+    assert quads(npad) < 2 ** 31
+    b = np.arange(g, dtype=np.int64)
+    assert int((b * npad).max()) < 2 ** 31
+    assert int((b * npad - 2 * b * (b - 1)).max()) < 2 ** 31
+    assert int((2 * b * (b - 1)).max()) < 2 ** 31
