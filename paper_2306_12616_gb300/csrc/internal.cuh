@@ -254,24 +254,10 @@ __device__ inline bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint64_t l
 }
 
 
-// Two float32 values in one 64-bit register (low lane = x) and d = a * b + c on both lanes
-// at once (fma.rn.f32x2, sm_100 and later): the same round-to-nearest result per lane as
-// fmaf, at half the instruction count. Operands stay packed across a loop (loaded from
-// shared memory as 64-bit pairs), so packing is paid once, not per FMA.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pack2(float x, float y) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-    return r;
-}
-__device__ __forceinline__ float2 unpack2(f32x2 v) {
-    float2 o;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(v));
-    return o;
-}
-__device__ __forceinline__ void ffma2(f32x2& acc, f32x2 a, f32x2 b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
+// Packed float32 FMA: __ffma2_rn (sm_100 and later) forms a * b + c on both halves of a float2
+// at once, the same round-to-nearest result per half as fmaf at half the instruction count.
+// The builtin keeps the operands in register pairs the compiler allocates itself (inline
+// PTX on 64-bit integers cost a register move per FMA).
 
 // Elementwise row blocks: a block covers ew_rows(np) rows (about 8192 entries).
 __host__ __device__ inline int ew_rows(int64_t np) {

@@ -493,13 +493,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
     };
 
     T acc[TPW][NP];        // float64 sums
-    f32x2 acc2[TPW][NP];   // float32 sums of the even / odd entries
+    float2 acc2[TPW][NP];   // float32 sums of the even / odd entries
 #pragma unroll
     for (int t = 0; t < TPW; ++t)
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             acc[t][q] = T(0);
-            acc2[t][q] = 0ull;
+            acc2[t][q] = make_float2(0.0f, 0.0f);
         }
 
     // shared-memory offsets of this warp's tiles (-1: none)
@@ -569,14 +569,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
                         }
                     }
                     if constexpr (sizeof(T) == 4) {
-                        const ulonglong2* gp = reinterpret_cast<const ulonglong2*>(&gv[0][0]);
-                        const ulonglong2* bp = reinterpret_cast<const ulonglong2*>(&bv[0][0]);
 #pragma unroll
                         for (int a = 0; a < TG; ++a)
 #pragma unroll
                             for (int b = 0; b < TB; ++b) {
-                                ffma2(acc2[t][TB * a + b], gp[a].x, bp[b].x);
-                                ffma2(acc2[t][TB * a + b], gp[a].y, bp[b].y);
+                                float2& s2 = acc2[t][TB * a + b];
+                                s2 = __ffma2_rn(make_float2(gv[a][0], gv[a][1]), make_float2(bv[b][0], bv[b][1]), s2);
+                                s2 = __ffma2_rn(make_float2(gv[a][2], gv[a][3]), make_float2(bv[b][2], bv[b][3]), s2);
                             }
                     } else {
 #pragma unroll
@@ -606,7 +605,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const Inst* __restrict
                 // float32 tree over the lanes: the float64 pipe of this GPU retires about two
                 // lane operations per clock and SM, so a float64 tree per pair would cost more
                 // than the block's loads; one conversion per pair on lane 0
-                const float2 pr = unpack2(acc2[t][q]);
+                const float2 pr = acc2[t][q];
                 float v = pr.x + pr.y;
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0 && g < ngiant && b < nbaby) partials[(int64_t)lb * npairs + g * nbaby + b] = 2.0 * (double)v;
@@ -793,11 +792,11 @@ __global__ void __launch_bounds__(kRThreads, 1)
     // -------------------------------------------------------------------- consumers
     const int tile = warp / H, hh = warp % H;
     const int gro = TG * (tile / nbq), bro = bro0 + TB * (tile % nbq);
-    f32x2 acc[TG / 2][TB];
+    float2 acc[TG / 2][TB];
 #pragma unroll
     for (int a = 0; a < TG / 2; ++a)
 #pragma unroll
-        for (int b = 0; b < TB; ++b) acc[a][b] = 0ull;
+        for (int b = 0; b < TB; ++b) acc[a][b] = make_float2(0.0f, 0.0f);
     for (int u = u0 + blockIdx.x; u < u1; u += gridDim.x) {
         const int i = find_inst(wgr.pre, 0, wgr.count, u);
         const Inst& in = insts[i];
@@ -835,9 +834,10 @@ __global__ void __launch_bounds__(kRThreads, 1)
                     }
 #pragma unroll
                     for (int b = 0; b < TB; ++b) {
-                        const f32x2 bb = pack2(bv[b], bv[b]);
+                        const float2 bb = make_float2(bv[b], bv[b]);
 #pragma unroll
-                        for (int a = 0; a < TG / 2; ++a) ffma2(acc[a][b], pack2(gv[2 * a], gv[2 * a + 1]), bb);
+                        for (int a = 0; a < TG / 2; ++a)
+                            acc[a][b] = __ffma2_rn(make_float2(gv[2 * a], gv[2 * a + 1]), bb, acc[a][b]);
                     }
                 }
             }
@@ -854,7 +854,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
 #pragma unroll
         for (int q = 0; q < 128; ++q) {
             if (q < NP) {
-                const float2 pr = unpack2(acc[(q / TB) / 2][q % TB]);
+                const float2 pr = acc[(q / TB) / 2][q % TB];
                 v[q] = ((q / TB) & 1) ? pr.y : pr.x;
             } else {
                 v[q] = 0.0f;
@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
 #pragma unroll
         for (int a = 0; a < TG / 2; ++a)
 #pragma unroll
-            for (int b = 0; b < TB; ++b) acc[a][b] = 0ull;
+            for (int b = 0; b < TB; ++b) acc[a][b] = make_float2(0.0f, 0.0f);
     }
 }
 
