@@ -180,6 +180,23 @@ def test_more_than_32_giant_coefficients(solver):
     assert err <= 1e-6, err
 
 
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-6), ("fp64", 1e-10)])
+def test_largest_expansion_k_m_64(solver, prec, tol):
+    """4096 terms, the largest expansion: k = m = 64, so the contraction stages 63 masters per
+    quad (its largest shared-memory ring) and covers R_0..R_63 in two launches, and the
+    Clenshaw chain has 64 steps."""
+    n = 200
+    h = synth.tight_binding(n, 31)
+    prm = solver.params(4096, 0.01, precision=prec, mu_mode="fixed", mu=-6.0)
+    p, res = solver.density_matrix(to_dev(h), 0.0, prm)
+    assert (res["k"], res["m"]) == (64, 64) and res["status"] == 0
+    c = O.chebyshev_coeffs(0.01, -6.0, res["emin"], res["emax"], 4096)
+    ref = O.poly_eig(h, c, res["emin"], res["emax"])
+    err = np.linalg.norm(p.cpu().numpy() - ref) / math.sqrt(n)
+    print(f"{prec} k = m = 64: ||dP||/sqrt(N) = {err:.2e}")
+    assert err <= tol, err
+
+
 def test_cached_plans_survive_other_plans(solver):
     """Plans are cached per context and share its workspace: a plan reused after another
     plan's call (which overwrote the workspace without growing it) gives the same bits."""
