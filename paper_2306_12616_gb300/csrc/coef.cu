@@ -552,31 +552,37 @@ __global__ void __launch_bounds__(128, 4) k_contract_f32(const Inst* __restrict_
 // transpose of its upper counterpart).
 __global__ void __launch_bounds__(256) k_mirror_planes(const Inst* __restrict__ insts, Work ws, int slot0, int m,
                                                        int planes, int ublk, int* dbg) {
-    __shared__ uint16_t tile[3][32][34];
+    __shared__ uint16_t tile[3][32][33];
     const int i = find_inst(ws.pre, 0, ws.count, blockIdx.x);
     if (!insts[i].res->active) return;
     // the instance's last R: R_{m-1}, or R_{m_eff-1} for an expansion cut by a learned order
     const int slot = slot0 + (insts[i].res->m_eff > 0 ? insts[i].res->m_eff : m) - 1;
     const int64_t np = insts[i].np;
     const int tn = (int)(np / 32);
-    int bi = 0, b = blockIdx.x - ws.pre[i];
-    while (b >= tn - bi) { b -= tn - bi; ++bi; }
-    const int bj = bi + b;
+    int bi, bj;
+    upper_tile(blockIdx.x - ws.pre[i], tn, bi, bj);
     if (ublk && bi * 32 / kPad != bj * 32 / kPad) return;
     const int64_t ps = np * np;
-    uint16_t* P16 = reinterpret_cast<uint16_t*>(insts[i].slots + insts[i].slot_bytes * slot + 4 * ps);
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    // 32-bit words of 16-bit entries (row offsets and tile columns are even)
+    uint32_t* P32 = reinterpret_cast<uint32_t*>(insts[i].slots + insts[i].slot_bytes * slot + 4 * ps);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // word of a tile row, row
     for (int pl = 0; pl < planes; ++pl)
-        for (int ry = ty; ry < 32; ry += 8)
-            tile[pl][ry][tx] = P16[pl * ps + ((int64_t)bi * 32 + ry) * np + (int64_t)bj * 32 + tx];
+        for (int ry = ty; ry < 32; ry += 16) {
+            const uint32_t w = P32[(pl * ps + ((int64_t)bi * 32 + ry) * np + (int64_t)bj * 32) / 2 + tx];
+            tile[pl][ry][2 * tx] = (uint16_t)(w & 0xffffu);
+            tile[pl][ry][2 * tx + 1] = (uint16_t)(w >> 16);
+        }
     __syncthreads();
     for (int pl = 0; pl < planes; ++pl)
-        for (int ry = ty; ry < 32; ry += 8) {
-            // output (bj*32 + ry, bi*32 + tx) = input (bi*32 + tx, bj*32 + ry), below the diagonal
-            const int64_t r = (int64_t)bj * 32 + ry, c = (int64_t)bi * 32 + tx;
+        for (int ry = ty; ry < 32; ry += 16) {
+            // output (bj*32 + ry, bi*32 + 2 tx + e) = input (bi*32 + 2 tx + e, bj*32 + ry), e = 0, 1.
+            // Written where the first entry is below the diagonal; the second is then below it
+            // or on it, and the diagonal entry is its own transpose (the same value rewritten)
+            const int64_t r = (int64_t)bj * 32 + ry, c = (int64_t)bi * 32 + 2 * tx;
             if (r <= c) continue;
-            if (!FO_CHK(dbg, r < np && c < np, 303, r, c)) continue;
-            P16[pl * ps + r * np + c] = tile[pl][tx][ry];
+            if (!FO_CHK(dbg, r < np && c + 1 < np, 303, r, c)) continue;
+            const uint32_t w = (uint32_t)tile[pl][2 * tx][ry] | ((uint32_t)tile[pl][2 * tx + 1][ry] << 16);
+            P32[(pl * ps + r * np + c) / 2] = w;
         }
 }
 

@@ -39,9 +39,8 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const __grid_constant__ StepLi
     const int64_t ldo = io[inst].ldp;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int t = (int)(np / BM);
-    int I = 0, b = bt - wt.pre[inst];
-    while (b >= t - I) { b -= t - I; ++I; }
-    const int J = I + b;
+    int I, J;
+    upper_tile(bt - wt.pre[inst], t, I, J);
     const int64_t m0 = (int64_t)I * BM, n0 = (int64_t)J * BN;
     double acc[4][4];
 #pragma unroll

@@ -170,6 +170,23 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ pre, int lo, in
     return lo;
 }
 
+// Tile (bi, bj), bj >= bi, that is the b-th of the upper triangle of a tn x tn tile grid in
+// row-major order: row bi holds tn - bi tiles, so the rows before it hold
+// P(bi) = bi tn - bi (bi - 1) / 2. bi is the root of P(x) = b, estimated by a float32 square
+// root and corrected exactly (a loop over the rows would cost O(tn) per block).
+__device__ __forceinline__ void upper_tile(int b, int tn, int& bi, int& bj) {
+    const float e = 2.0f * (float)tn + 1.0f;
+    const float d = e * e - 8.0f * (float)b;
+    int r = (int)((e - sqrtf(d > 0.0f ? d : 0.0f)) * 0.5f);
+    if (r < 0) r = 0;
+    if (r > tn - 1) r = tn - 1;
+    auto P = [&](int x) { return x * tn - x * (x - 1) / 2; };
+    while (r > 0 && P(r) > b) --r;
+    while (r + 1 < tn && P(r + 1) <= b) ++r;
+    bi = r;
+    bj = r + (b - P(r));
+}
+
 // Asynchronous 16-byte global -> shared copies (cp.async, L2 only) and their group waits.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(

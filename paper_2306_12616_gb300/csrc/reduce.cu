@@ -259,9 +259,8 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
     const double* H = io[i].H;
     const DevResult* res = insts[i].res;
     const int tn = (int)(np / 32);
-    int bi = 0, b = blockIdx.x - ws.pre[i];
-    while (b >= tn - bi) { b -= tn - bi; ++bi; }
-    const int bj = bi + b;
+    int bi, bj;
+    upper_tile(blockIdx.x - ws.pre[i], tn, bi, bj);
     // the scale factors once per block: a float64 division per thread would cost more than
     // the block's multiplies on this GPU's narrow float64 pipe
     __shared__ double s_par[3];
