@@ -410,9 +410,9 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         return smem + s * Cfg::kStageBytes + PA * kBoxBytes + p * Cfg::kBBoxes * kBoxBytes;
     };
 
-    float sum[NC];  // a drain thread's accumulated columns of its tile row
+    float2 sum[NC / 2];  // a drain thread's accumulated columns of its tile row, in pairs
 #pragma unroll
-    for (int j = 0; j < NC; ++j) sum[j] = 0.0f;
+    for (int j = 0; j < NC / 2; ++j) sum[j] = make_float2(0.0f, 0.0f);
     bool ok = true;
 
     if (warp == 0) {
@@ -599,7 +599,9 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
                     uint32_t r[32];
                     tmem_ld32(t_row + buf * TBN + cb * 32, r);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) sum[cb * 32 + j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 16; ++j)
+                        sum[cb * 16 + j] = __fadd2_rn(
+                            sum[cb * 16 + j], make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])));
                 }
             } else {
                 // half the registers per thread: 16-column loads
@@ -609,7 +611,9 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
                     uint32_t r[16];
                     tmem_ld16(t_row + buf * TBN + cb * 16, r);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) sum[cb * 16 + j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 8; ++j)
+                        sum[cb * 8 + j] = __fadd2_rn(
+                            sum[cb * 8 + j], make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])));
                 }
             }
             fence_before();
@@ -646,7 +650,10 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         const int q = warp & 3, grp = (warp - 2) >> 2;
         const int rl = q * 32 + lane;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) tile[rl * LD + grp * NC + c] = st.alpha * sum[c];
+        for (int c = 0; c < NC / 2; ++c) {
+            tile[rl * LD + grp * NC + 2 * c] = st.alpha * sum[c].x;
+            tile[rl * LD + grp * NC + 2 * c + 1] = st.alpha * sum[c].y;
+        }
     }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * DW) : "memory");
     if constexpr (CHAIN) {
@@ -1371,9 +1378,9 @@ __global__ void __launch_bounds__(32 * (2 + DW + EW), 1)
             PTile d;
             persist_tile(t, tiles, tile0, pre, i0, i1, insts, sym, steps, d);
             if (!d.active) continue;
-            float sum[NC];
+            float2 sum[NC / 2];   // accumulated columns, in pairs
 #pragma unroll
-            for (int j = 0; j < NC; ++j) sum[j] = 0.0f;
+            for (int j = 0; j < NC / 2; ++j) sum[j] = make_float2(0.0f, 0.0f);
             // columns the MMAs write (the others keep the border's zero)
             const int wcols = d.tile_k - grp * NC < 0 ? 0 : (d.tile_k - grp * NC > NC ? NC : d.tile_k - grp * NC);
             for (int kb = 0; kb < d.nk; ++kb, ++h) {
@@ -1390,7 +1397,9 @@ __global__ void __launch_bounds__(32 * (2 + DW + EW), 1)
                     uint32_t r[16];
                     tmem_ld16(t_row + buf * TBN + cb * 16, r);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) sum[cb * 16 + j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 8; ++j)
+                        sum[cb * 8 + j] = __fadd2_rn(
+                            sum[cb * 8 + j], make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])));
                 }
                 fence_before();
                 mbar_arrive(&seg_empty[buf]);
@@ -1404,7 +1413,10 @@ __global__ void __launch_bounds__(32 * (2 + DW + EW), 1)
             const float alpha = steps.s[d.sidx].alpha;
             const int rl = q * 32 + lane;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) tile[rl * LD + grp * NC + c] = alpha * sum[c];
+            for (int c = 0; c < NC / 2; ++c) {
+                tile[rl * LD + grp * NC + 2 * c] = alpha * sum[c].x;
+                tile[rl * LD + grp * NC + 2 * c + 1] = alpha * sum[c].y;
+            }
             mbar_arrive(res_full);
             ++nt;
         }
