@@ -219,10 +219,12 @@ const char *fo_version(void);
 
 /*
  * Spectral bounds (Sec. "Chebyshev expansions": e_a, e_b enclose the spectrum).
- * Gershgorin discs: emin = min_i (h_ii - sum_{j!=i} |h_ij|), emax = max_i (h_ii + sum ...),
- * reduced in float64 with warp shuffles. A degenerate interval (width <= 1e-12 max(1,|e|))
- * becomes centre -+ 1. Writes d_bounds[0] = emin, d_bounds[1] = emax (device, 2 doubles)
- * and d_bounds[2] = 0.0 if H is finite, 1.0 otherwise (3 doubles). Asynchronous; n >= 1, ld >= n.
+ * Gershgorin discs: emin = min_i (h_ii - sum_{j!=i} |h_ij|), emax = max_i (h_ii + sum ...);
+ * each row sum is formed exactly (128-bit integer fixed point) and rounded to float64 once,
+ * so the bounds do not depend on the order of the terms. A degenerate interval
+ * (width <= 1e-12 max(1,|e|)) becomes centre -+ 1. Writes d_bounds[0] = emin,
+ * d_bounds[1] = emax (device, 2 doubles) and d_bounds[2] = 0.0 if H is finite, 1.0
+ * otherwise (3 doubles). Asynchronous; n >= 1, ld >= n.
  */
 fo_status fo_spectral_bounds(fo_ctx *ctx, const double *dH, int64_t n, int64_t ld,
                              double *d_bounds, void *stream);
@@ -231,8 +233,8 @@ fo_status fo_spectral_bounds(fo_ctx *ctx, const double *dH, int64_t n, int64_t l
  * Spectral bounds for callers that cannot allocate device memory when they need them (for
  * example code running inside a memory pool it does not own, or an embedding that forbids
  * cudaMalloc after start-up). The paper has no counterpart: this is a service entry point.
- * It computes the same bounds as fo_spectral_bounds up to float64 rounding (the row sums
- * are added in a different order), with the same outputs in d_bounds[0..2], but needs no
+ * It computes the same bounds as fo_spectral_bounds, bit for bit (both sum each row exactly
+ * and round the sum once), with the same outputs in d_bounds[0..2], but needs no
  * context and allocates nothing: its per-block partial results live in a fixed
  * 128 KiB array in device memory that is part of the library image, resident on every GPU
  * that loads the library until the process exits.

@@ -12,6 +12,7 @@
 // must be serialised by the caller.
 #include <cuda_runtime.h>
 
+#include "exactsum.h"
 #include "internal.cuh"
 
 namespace fo {
@@ -33,7 +34,9 @@ __device__ __forceinline__ double wsum(double v) {
     return v;
 }
 
-// Block b handles rows [8b, 8b + 8): warp w sums |h_ij|, j != i, of row 8b + w in float64.
+// Block b handles rows [8b, 8b + 8): warp w sums |h_ij|, j != i, of row 8b + w exactly (the
+// 128-bit fixed-point sums of csrc/exactsum.h, rounded to float64 once), so that the bounds
+// are the same bits as those of the context entry point, whatever the order of the terms.
 __global__ void __launch_bounds__(32 * kRowsPerBlock) k_bounds_rows_static(const double* __restrict__ H,
                                                                            int64_t n, int64_t ld,
                                                                            Partial* part) {
@@ -42,14 +45,24 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock) k_bounds_rows_static(const
     double lo = INFINITY, hi = -INFINITY;
     int bad = 0;
     if (row < n) {
-        const double* r = H + row * ld;
-        double s = 0.0, d = 0.0;
+        const unsigned long long* r = reinterpret_cast<const unsigned long long*>(H + row * ld);
+        XAcc acc{0, 0, 0};
+        double d = 0.0;
         for (int64_t j = lane; j < n; j += 32) {
-            const double v = r[j];
-            bad |= !isfinite(v);
-            if (j == row) d = v; else s += fabs(v);
+            const uint64_t v = r[j];
+            const bool fin = ((v >> 52) & 0x7ff) != 0x7ff;
+            bad |= !fin;
+            if (j == row) d = __longlong_as_double((long long)v);
+            else if (fin) xacc_add_abs(acc, v);
         }
-        s = wsum(s);
+        for (int o = 16; o > 0; o >>= 1) {
+            XAcc other;
+            other.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+            other.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+            other.e = __shfl_xor_sync(0xffffffffu, acc.e, o);
+            xacc_merge(acc, other);
+        }
+        const double s = xacc_to_double(acc);
         d = wsum(d);
         lo = d - s;
         hi = d + s;

@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "exactsum.h"
 #include "fpbits.h"
 #include "internal.cuh"
 
@@ -79,19 +80,10 @@ __global__ void k_set_io(const IoChunk p, InstIO* d_io, const Inst* insts) {
 }
 
 // ------------------------------------------------------------------ Gershgorin bounds
-// Finite test on the bits (exponent field not all ones): integer work, where isfinite()
-// would take a slot of the narrow float64 pipe per entry.
-__device__ __forceinline__ bool finite_bits(double v) {
-    return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
-}
-
-// |v| by clearing the sign bit (integer work; the float64 pipe then only adds).
-__device__ __forceinline__ double abs_bits(double v) {
-    return __longlong_as_double(__double_as_longlong(v) & 0x7fffffffffffffffll);
-}
-
-// One warp per row: r_i = sum_{j != i} |h_ij| (float64, lane-strided, shuffle tree),
-// lo_i = h_ii - r_i, hi_i = h_ii + r_i; per-block (min lo, max hi, any non-finite).
+// One warp per row: r_i = sum_{j != i} |h_ij| summed exactly (lane-strided 128-bit
+// fixed-point sums merged by a butterfly, rounded to float64 once: csrc/exactsum.h; the
+// float64 adds it replaces bound the kernel on this GPU's narrow float64 pipe), lo_i = h_ii -
+// r_i, hi_i = h_ii + r_i; per-block (min lo, max hi, any non-finite).
 __global__ void __launch_bounds__(32 * kGershRows) k_gershgorin_rows(const Inst* __restrict__ insts,
                                                                      const InstIO* __restrict__ io,
                                                                      Work wg, double* part) {
@@ -104,27 +96,38 @@ __global__ void __launch_bounds__(32 * kGershRows) k_gershgorin_rows(const Inst*
     double lo = INFINITY, hi = -INFINITY;
     int bad = 0;
     if (row < n) {
-        const double* r = H + row * ld;
-        double s4[4] = {0.0, 0.0, 0.0, 0.0}, d = 0.0;
-        // four independent sums, so that four loads per lane are in flight
+        const unsigned long long* r = reinterpret_cast<const unsigned long long*>(H + row * ld);
+        XAcc acc{0, 0, 0};
+        double d = 0.0;
+        // four loads per lane in flight
         int64_t j = lane;
         for (; j + 96 < n; j += 128) {
-            double v[4];
+            uint64_t v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) v[u] = __ldg(r + j + 32 * u);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                bad |= !finite_bits(v[u]);
-                if (j + 32 * u == row) d = v[u]; else s4[u] += abs_bits(v[u]);
+                const bool fin = ((v[u] >> 52) & 0x7ff) != 0x7ff;
+                bad |= !fin;
+                if (j + 32 * u == row) d = __longlong_as_double((long long)v[u]);
+                else if (fin) xacc_add_abs(acc, v[u]);
             }
         }
         for (; j < n; j += 32) {
-            const double v = __ldg(r + j);
-            bad |= !finite_bits(v);
-            if (j == row) d = v; else s4[0] += abs_bits(v);
+            const uint64_t v = __ldg(r + j);
+            const bool fin = ((v >> 52) & 0x7ff) != 0x7ff;
+            bad |= !fin;
+            if (j == row) d = __longlong_as_double((long long)v);
+            else if (fin) xacc_add_abs(acc, v);
         }
-        double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-        s = warp_sum(s);
+        for (int o = 16; o > 0; o >>= 1) {
+            XAcc other;
+            other.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+            other.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+            other.e = __shfl_xor_sync(0xffffffffu, acc.e, o);
+            xacc_merge(acc, other);
+        }
+        const double s = xacc_to_double(acc);
         d = warp_sum(d);
         lo = d - s;
         hi = d + s;

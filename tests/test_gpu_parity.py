@@ -43,6 +43,24 @@ def test_bounds_match_oracle(solver, n):
     assert b[2] == 0.0
 
 
+@pytest.mark.parametrize("n,kind", [(1, "rand"), (33, "rand"), (1000, "rand"), (776, "tb"), (2048, "tb")])
+def test_bounds_are_correctly_rounded_row_sums(solver, n, kind):
+    """The Gershgorin radii are the row sums of |h_ij| rounded once (exact integer sums on the
+    device): the bounds equal, bit for bit, min/max of h_ii -/+ math.fsum(|h_ij|, j != i) with
+    the float64 subtraction and addition, for any order of the terms."""
+    h = synth.random_symmetric(n, 300 + n) if kind == "rand" else synth.tight_binding(n, 300 + n)
+    if kind == "rand":
+        h[0, -1] = h[-1, 0] = 1e-200   # a far smaller entry and a large one in the same rows
+        h[0, 0] = 3e5
+    b = solver.spectral_bounds(to_dev(h)).cpu().numpy()
+    r = np.array([math.fsum(np.abs(np.delete(h[i], i))) for i in range(n)])
+    d = np.diag(h)
+    lo, hi = np.min(d - r), np.max(d + r)
+    if n == 1:
+        lo, hi = d[0] - 1.0, d[0] + 1.0   # a single entry: the degenerate interval is widened
+    assert b[0] == lo and b[1] == hi and b[2] == 0.0
+
+
 def test_bounds_flag_nonfinite(solver):
     h = synth.random_symmetric(40, 1)
     h[3, 7] = np.nan

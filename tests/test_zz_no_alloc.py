@@ -31,7 +31,8 @@ def test_noalloc_matches_context_entry_point_twice(solver):
         d = torch.from_numpy(h).to(DEV)
         ref = solver.spectral_bounds(d).cpu().numpy()
         got = noalloc_bounds(d)
-        np.testing.assert_allclose(got[:2], ref[:2], rtol=1e-13, atol=0)
+        # both sum each row exactly and round once: the same bits
+        assert got[0] == ref[0] and got[1] == ref[1]
         assert got[2] == ref[2] == 0.0
 
 
