@@ -96,4 +96,75 @@ FO_HD inline float narrow_f64(double x) {
     return f;
 }
 
+// float32 of the exact product a * b of two finite float64 numbers (round to nearest, ties to
+// even; one rounding, where RN32(RN64(a b)) rounds twice), with integer operations only: the
+// 53-bit significands multiply into a 106-bit integer, whose leading 24 bits with the guard
+// and sticky bits below give the float32 significand; a subnormal float32 result keeps
+// fewer bits, an overflow gives infinity. The scaling of H multiplies every upper entry by
+// 2 / (e_b - e_a) and stores it as float32: a float64 multiply per entry ran on the narrow
+// float64 pipe.
+FO_HD inline uint64_t fo_mulhi64(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+FO_HD inline int fo_clz64(uint64_t a) {
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)a);
+#else
+    return a ? __builtin_clzll(a) : 64;
+#endif
+}
+FO_HD inline float mul_rn_f32(double a, double b) {
+    uint64_t ua, ub;
+    memcpy(&ua, &a, 8);
+    memcpy(&ub, &b, 8);
+    const uint32_t sign = (uint32_t)((ua ^ ub) >> 32) & 0x80000000u;
+    int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
+    uint64_t ma = ua & 0x000fffffffffffffull, mb = ub & 0x000fffffffffffffull;
+    uint32_t r = 0;
+    if ((ea | ma) != 0 && (eb | mb) != 0) {
+        if (ea == 0) ea = 1;
+        else ma |= 1ull << 52;
+        if (eb == 0) eb = 1;
+        else mb |= 1ull << 52;
+        const uint64_t lo = ma * mb, hi = fo_mulhi64(ma, mb);   // the product, < 2^106
+        const int p = hi ? 127 - fo_clz64(hi) : 63 - fo_clz64(lo);
+        // product = (hi:lo) 2^(ea + eb - 2150); float32 biased exponent when normal:
+        int E = p + ea + eb - 2150 + 127;
+        int sh = p - 23;   // right shift that leaves 24 significant bits
+        if (E <= 0) {      // subnormal: fewer bits
+            sh += 1 - E;
+            E = 0;
+        }
+        uint64_t m = 0, guard = 0, sticky = 0;
+        if (sh <= 0) {
+            m = lo << (-sh);
+        } else if (sh < 64) {
+            m = (lo >> sh) | (hi << (64 - sh));
+            guard = (lo >> (sh - 1)) & 1u;
+            sticky = lo & ((1ull << (sh - 1)) - 1);
+        } else if (sh == 64) {
+            m = hi;
+            guard = lo >> 63;
+            sticky = lo << 1;
+        } else if (sh < 128) {
+            const int s2 = sh - 64;
+            m = hi >> s2;
+            guard = (hi >> (s2 - 1)) & 1u;
+            sticky = (hi & ((1ull << (s2 - 1)) - 1)) | lo;
+        }   // sh >= 128: below half the smallest subnormal (the product is < 2^106)
+        if (guard && (sticky != 0 || (m & 1u))) ++m;
+        // a carry out of the significand moves into the exponent field by itself
+        const uint64_t bits = E == 0 ? m : ((uint64_t)(E - 1) << 23) + m;
+        r = bits >= 0x7f800000ull ? 0x7f800000u : (uint32_t)bits;
+    }
+    r |= sign;
+    float f;
+    memcpy(&f, &r, 4);
+    return f;
+}
+
 }  // namespace fo

@@ -281,18 +281,23 @@ __global__ void __launch_bounds__(256) k_scale_sym(const Inst* __restrict__ inst
     __syncthreads();
     const double inv = s_par[0], inv2 = s_par[1], csum = s_par[2];
     // each thread scales the entries it loaded (the lower half of a diagonal tile is never
-    // read: it is written from the upper half)
+    // read: it is written from the upper half); the diagonal's formula only in diagonal tiles
+    // (a block-uniform test, so that the other tiles carry no float64 work for it)
     for (int ry = ty; ry < 32; ry += 8) {
         const int64_t r = (int64_t)bi * 32 + ry, c = (int64_t)bj * 32 + tx;
-        double v = 0.0;
-        if (r < n && c < n && (bi != bj || tx >= ry)) {
-            v = tile[ry][tx] * inv2;
-            // the diagonal only in diagonal tiles (a block-uniform test, so that the other
-            // tiles carry no float64 work for it)
-            if (bi == bj && r == c) v = (2.0 * tile[ry][tx] - csum) * inv;
+        const bool in = r < n && c < n && (bi != bj || tx >= ry);
+        const bool dg = bi == bj && r == c;
+        if (sh.is64) {
+            double v = 0.0;
+            if (in) v = dg ? (2.0 * tile[ry][tx] - csum) * inv : tile[ry][tx] * inv2;
+            tile[ry][tx] = v;
+        } else {
+            // float32 of the exact product in integer operations (the float64 multiply was
+            // this kernel's bound on the narrow float64 pipe)
+            float f = 0.0f;
+            if (in) f = dg ? narrow_f64((2.0 * tile[ry][tx] - csum) * inv) : mul_rn_f32(tile[ry][tx], inv2);
+            tf[ry][tx] = f;
         }
-        if (sh.is64) tile[ry][tx] = v;
-        else tf[ry][tx] = narrow_f64(v);   // the float32 rounding, in integer operations
     }
     __syncthreads();
     char* slot = insts[i].slots;
