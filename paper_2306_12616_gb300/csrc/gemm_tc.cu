@@ -181,11 +181,6 @@ __host__ __device__ constexpr uint32_t idesc_f16(int tile_n, bool fp16) {
            ((uint32_t)(tile_n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
-__device__ __forceinline__ uint16_t bits_bf16(float v) {
-    __nv_bfloat16 h = __float2bfloat16_rn(v);
-    return *reinterpret_cast<uint16_t*>(&h);
-}
-
 constexpr int kBoxBytes = kBM * kRowBytes;   // one 128-row TMA box of one plane: 8 KB
 
 struct TcMaps {
@@ -240,23 +235,30 @@ __device__ bool wait_count(const int* ctr, int need, const int* err_flag) {
     }
 }
 
-__device__ __forceinline__ void split3(float x, bool f16, float pscale, uint16_t& p0, uint16_t& p1,
-                                       uint16_t& p2) {
+// The 16-bit planes of two neighbouring entries, as the 32-bit words the stores write (low
+// half: x0's plane, high half: x1's). BF16x3: p0 = bf16(x), p1 = bf16(x - p0), p2 =
+// bf16(x - p0 - p1), each rounded to nearest; FP16x2: the entry scaled by pscale, p0 =
+// fp16(x), p1 = fp16(x - p0). One packed conversion serves both entries of a plane.
+__device__ __forceinline__ void split3x2(float x0, float x1, bool f16, float pscale, uint32_t& w0, uint32_t& w1,
+                                         uint32_t& w2) {
+    auto bits2 = [](auto v) {
+        uint32_t u;
+        memcpy(&u, &v, 4);
+        return u;
+    };
     if (!f16) {
-        const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
-        const float r1 = x - __bfloat162float(b0);
-        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-        const float r2 = r1 - __bfloat162float(b1);
-        p0 = *reinterpret_cast<const uint16_t*>(&b0);
-        p1 = *reinterpret_cast<const uint16_t*>(&b1);
-        p2 = bits_bf16(r2);
+        w0 = bits2(__floats2bfloat162_rn(x0, x1));
+        const float r0 = x0 - __uint_as_float(w0 << 16), r1 = x1 - __uint_as_float(w0 & 0xffff0000u);
+        w1 = bits2(__floats2bfloat162_rn(r0, r1));
+        const float s0 = r0 - __uint_as_float(w1 << 16), s1 = r1 - __uint_as_float(w1 & 0xffff0000u);
+        w2 = bits2(__floats2bfloat162_rn(s0, s1));
     } else {
-        const float xs = x * pscale;
-        const __half f0 = __float2half_rn(xs);
-        const __half f1 = __float2half_rn(xs - __half2float(f0));
-        p0 = *reinterpret_cast<const uint16_t*>(&f0);
-        p1 = *reinterpret_cast<const uint16_t*>(&f1);
-        p2 = 0;
+        const float y0 = x0 * pscale, y1 = x1 * pscale;
+        const __half2 f = __floats2half2_rn(y0, y1);
+        const float2 b = __half22float2(f);
+        w0 = bits2(f);
+        w1 = bits2(__floats2half2_rn(y0 - b.x, y1 - b.y));
+        w2 = 0;
     }
 }
 
@@ -717,19 +719,15 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
         if (!(w0 || w1) || (!out_x && planes == 0)) return;
         const int64_t o = grow * ld + gcol;
         if (!FO_CHK(st.dbg, o >= 0 && o + 2 <= ld * ld, 111, grow, gcol)) return;
-        uint16_t a0 = 0, a1 = 0, a2 = 0, b0v = 0, b1v = 0, b2v = 0;
-        if (planes > 0) {
-            split3(v0, F16, st.plane_scale, a0, a1, a2);
-            split3(v1, F16, st.plane_scale, b0v, b1v, b2v);
-        }
+        uint32_t q0 = 0, q1 = 0, q2 = 0;   // the planes of the pair, one 32-bit word each
+        if (planes > 0) split3x2(v0, v1, F16, st.plane_scale, q0, q1, q2);
         if (w0 && w1) {
             if (out_x && master) *reinterpret_cast<float2*>(out_x + o) = make_float2(v0, v1);
             if (planes > 0) {
                 uint16_t* pl = out_p + o;
-                *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0v << 16);
-                if (planes > 1) *reinterpret_cast<uint32_t*>(pl + pstride) = (uint32_t)a1 | ((uint32_t)b1v << 16);
-                if (planes > 2)
-                    *reinterpret_cast<uint32_t*>(pl + 2 * pstride) = (uint32_t)a2 | ((uint32_t)b2v << 16);
+                *reinterpret_cast<uint32_t*>(pl) = q0;
+                if (planes > 1) *reinterpret_cast<uint32_t*>(pl + pstride) = q1;
+                if (planes > 2) *reinterpret_cast<uint32_t*>(pl + 2 * pstride) = q2;
             }
         } else {
             const int e = w0 ? 0 : 1;
@@ -737,9 +735,10 @@ __global__ void __launch_bounds__(32 * (2 + DW), MINB)
             if (out_x && master) out_x[o + e] = v;
             if (planes > 0) {
                 uint16_t* pl = out_p + o + e;
-                pl[0] = w0 ? a0 : b0v;
-                if (planes > 1) pl[pstride] = w0 ? a1 : b1v;
-                if (planes > 2) pl[2 * pstride] = w0 ? a2 : b2v;
+                const int sh = w0 ? 0 : 16;
+                pl[0] = (uint16_t)(q0 >> sh);
+                if (planes > 1) pl[pstride] = (uint16_t)(q1 >> sh);
+                if (planes > 2) pl[2 * pstride] = (uint16_t)(q2 >> sh);
             }
         }
     };
@@ -1025,19 +1024,15 @@ __device__ __forceinline__ void persist_epilogue(const Step& st, const Inst* __r
         if (!(w0 || w1) || (!out_x && planes == 0)) return;
         const int64_t o = grow * ld + gcol;
         if (!FO_CHK(st.dbg, o >= 0 && o + 2 <= ld * ld, 111, grow, gcol)) return;
-        uint16_t a0 = 0, a1 = 0, a2 = 0, b0v = 0, b1v = 0, b2v = 0;
-        if (planes > 0) {
-            split3(v0, F16, st.plane_scale, a0, a1, a2);
-            split3(v1, F16, st.plane_scale, b0v, b1v, b2v);
-        }
+        uint32_t q0 = 0, q1 = 0, q2 = 0;   // the planes of the pair, one 32-bit word each
+        if (planes > 0) split3x2(v0, v1, F16, st.plane_scale, q0, q1, q2);
         if (w0 && w1) {
             if (out_x && master) *reinterpret_cast<float2*>(out_x + o) = make_float2(v0, v1);
             if (planes > 0) {
                 uint16_t* pl = out_p + o;
-                *reinterpret_cast<uint32_t*>(pl) = (uint32_t)a0 | ((uint32_t)b0v << 16);
-                if (planes > 1) *reinterpret_cast<uint32_t*>(pl + pstride) = (uint32_t)a1 | ((uint32_t)b1v << 16);
-                if (planes > 2)
-                    *reinterpret_cast<uint32_t*>(pl + 2 * pstride) = (uint32_t)a2 | ((uint32_t)b2v << 16);
+                *reinterpret_cast<uint32_t*>(pl) = q0;
+                if (planes > 1) *reinterpret_cast<uint32_t*>(pl + pstride) = q1;
+                if (planes > 2) *reinterpret_cast<uint32_t*>(pl + 2 * pstride) = q2;
             }
         } else {
             const int e = w0 ? 0 : 1;
@@ -1045,9 +1040,10 @@ __device__ __forceinline__ void persist_epilogue(const Step& st, const Inst* __r
             if (out_x && master) out_x[o + e] = v;
             if (planes > 0) {
                 uint16_t* pl = out_p + o + e;
-                pl[0] = w0 ? a0 : b0v;
-                if (planes > 1) pl[pstride] = w0 ? a1 : b1v;
-                if (planes > 2) pl[2 * pstride] = w0 ? a2 : b2v;
+                const int sh = w0 ? 0 : 16;
+                pl[0] = (uint16_t)(q0 >> sh);
+                if (planes > 1) pl[pstride] = (uint16_t)(q1 >> sh);
+                if (planes > 2) pl[2 * pstride] = (uint16_t)(q2 >> sh);
             }
         }
     };
