@@ -1,14 +1,15 @@
-// float32 <-> float64 conversions with integer operations only.
+// float32 <-> float64 conversions, and the float32 of a float64 product, with integer
+// operations only.
 //
 // The conversion instructions run on the float64 pipe, which on this GPU retires about two
 // lane operations per clock and SM; the epilogues that write the float64 density matrix
-// widen every entry, and the scaling narrows every entry of H, so they build the bit patterns
-// with integer operations instead. Widening
+// widen every entry, and the scaling multiplies every entry of H and rounds it to float32, so
+// they build the bit patterns with integer operations instead. Widening
 // (IEEE 754 binary32 -> binary64 is exact: the exponent is rebiased by 1023 - 127, the 23
 // fraction bits move to the top of the 52; a subnormal float32 becomes a normal float64).
-// NaN keeps its payload and quiet bit. Host-compilable, so that a host test can compare both
+// NaN keeps its payload and quiet bit. Host-compilable, so that a host test can compare them
 // with the C++ conversions (every float32 bit pattern; random and rounding-boundary float64
-// patterns).
+// patterns) and the product with an fma-based reference.
 #pragma once
 
 #include <stdint.h>
